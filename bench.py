@@ -1,0 +1,519 @@
+#!/usr/bin/env python
+"""Benchmark of the event-to-flow path: flow frames/s at 1280x720.
+
+Workload: the 1280x720 synthetic stream (201 windows of 10 ms, 150k-400k
+events each, 12 rigid objects with their own affine motion, 3 % noise,
+seed 1 + rank), i.e. 200 flow frames per step.  One step = one pass of the
+whole path (edge image, denoise, exact EDT, surface, pyramid, inverse
+search, densification, variational refinement) over every window of the
+stream, with all events resident in HBM before the timed region (715 MB
+of events per step, larger than the 129 MB L2).
+
+Prints one JSON line (rank 0).  `value` is the plain path (one
+ebof_process_window call per window); `batched` is the same stream through
+ebof_process_windows; `e2e` goes through ebof_process_window_host with the
+events in pinned host memory and the flow read back every window;
+`roofline` covers the dominant stage; `cpu_baseline` is the FP64 oracle on
+a bounded sample of the same stream, on this host's cores.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "flow frames/s at 1280x720 (batched vs plain), p99 latency, EPE vs FP64 oracle"
+UNIT = "frames/s"
+W_, H_ = 1280, 720
+N_WINDOWS = 201
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--windows", type=int, default=N_WINDOWS)
+    ap.add_argument("--batch", type=int, default=40, help="windows per batched call")
+    ap.add_argument("--cpu-frames", type=int, default=0,
+                    help="oracle sample size (default: one frame per worker)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- oracle leg
+def _oracle_frame(args):
+    """FP64 oracle for one frame pair (previous window, current window)."""
+    import oracle
+    (w0, w1, prm) = args
+    s0 = oracle.surface_from_events(W_, H_, *w0, connectivity=prm["connectivity"],
+                                    n_d=prm["n_d"], n_f=prm["n_f"], alpha=prm["alpha"])
+    s1 = oracle.surface_from_events(W_, H_, *w1, connectivity=prm["connectivity"],
+                                    n_d=prm["n_d"], n_f=prm["n_f"], alpha=prm["alpha"])
+    U = oracle.flow(255.0 * s0["S"], 255.0 * s1["S"], levels=prm["levels"],
+                    patch=prm["patch"], stride=prm["stride"], gn_iters=prm["gn_iters"],
+                    var_outer=prm["var_outer"], var_sor=prm["var_sor"],
+                    var_delta=prm["var_delta"], var_gamma=prm["var_gamma"],
+                    var_alpha=prm["var_alpha"], sor_omega=prm["sor_omega"])
+    return U.astype(np.float32)
+
+
+def _params_dict(p):
+    return {k: getattr(p, k) for k, _ in type(p)._fields_}
+
+
+def _window_tuple(stream, k):
+    x, y, t, _, tb, te = stream.window(k)
+    return (np.ascontiguousarray(x), np.ascontiguousarray(y), np.ascontiguousarray(t), tb, te)
+
+
+def oracle_sample(stream, prm, frames, workers):
+    """Time the oracle on `frames` frame pairs spread over `workers` processes."""
+    import oracle
+    oracle.build()
+    tasks = [(_window_tuple(stream, k), _window_tuple(stream, k + 1), prm)
+             for k in range(frames)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_noop, range(workers))  # start the workers outside the timed region
+        t0 = time.perf_counter()
+        flows = pool.map(_oracle_frame, tasks, chunksize=1)
+        dt = time.perf_counter() - t0
+    return flows, dt
+
+
+def _oracle_noop(_):
+    import oracle  # noqa: F401
+    return 0
+
+
+def cpu_workers():
+    n = os.cpu_count() or 1
+    return max(1, min(n, 16))
+
+
+def run_reference(args, rank):
+    """The reference arm: the FP64 oracle, as it stands, on this host's cores."""
+    if rank != 0:
+        return
+    import ctypes  # noqa: F401
+    from paper_2112_10591_gb300 import synth
+    stream = synth.workload_1280x720(seed=1, n_windows=3)
+    prm = _reference_params()
+    workers = cpu_workers()
+    frames_per_step = workers
+    times = []
+    for i in range(args.warmup + args.steps):
+        k = [j % 2 for j in range(frames_per_step)]
+        tasks = [(_window_tuple(stream, kk), _window_tuple(stream, kk + 1), prm) for kk in k]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers) as pool:
+            pool.map(_oracle_noop, range(workers))
+            t0 = time.perf_counter()
+            pool.map(_oracle_frame, tasks, chunksize=1)
+            dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = frames_per_step * len(times) / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "1280x720 stream, frame pairs of 150k-400k-event windows",
+                   "frames_per_step": frames_per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": "%d frame pairs of the 1280x720 stream per step, one per "
+                                   "process" % frames_per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def _reference_params():
+    # the library's defaults for a 1280x720 sensor, written out (no library load)
+    return dict(connectivity=8, n_d=1, n_f=9, alpha=1.08, levels=5, patch=12, stride=4,
+                gn_iters=12, var_outer=5, var_sor=5, var_delta=5.0, var_gamma=10.0,
+                var_alpha=20.0, sor_omega=1.6)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline
+def algorithmic_bytes(stage, geo_levels, n_events, P, frames):
+    """Algorithmic bytes of one stage over `frames` windows: each stage's
+    inputs read once and outputs written once (formulas in the design doc)."""
+    Pl = [w * h for (w, h, npx, npy) in geo_levels]
+    npl = [npx * npy for (w, h, npx, npy) in geo_levels]
+    L = len(geo_levels)
+    outer, sor = 5, 5
+    per = {
+        "scatter": 13 * n_events / frames,
+        "denoise_fill": 4 * P,
+        "edt_cols": 5 * P,
+        "edt_rows_surface": 8 * P,
+        "pyramid": sum(12 * Pl[l] for l in range(L)) + sum(20 * Pl[l] for l in range(1, L)),
+        "patch_search": sum(16 * Pl[l] + 16 * npl[l] for l in range(L)),
+        "densify": sum(16 * Pl[l] + 8 * npl[l] for l in range(L)),
+        "var_warp": outer * sum(16 * p for p in Pl),
+        "var_coeff": outer * sum(56 * p for p in Pl),
+        "var_sor": outer * 2 * sor * sum(34 * p for p in Pl),
+        "var_add": outer * sum(24 * p for p in Pl),
+        "flow_out": 16 * P,
+    }
+    return per.get(stage, 0.0) * frames
+
+
+def geo_levels(p):
+    out = []
+    for l in range(p.levels):
+        w, h = p.width >> l, p.height >> l
+        if w < p.patch or h < p.patch:
+            break
+        npx = (w - p.patch + p.stride - 1) // p.stride + 1
+        npy = (h - p.patch + p.stride - 1) // p.stride + 1
+        out.append((w, h, npx, npy))
+    return out
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2112_10591_gb300 as eb
+    from paper_2112_10591_gb300 import synth
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    stream = synth.workload_1280x720(seed=1 + rank, n_windows=args.windows)
+    nwin = stream.n_windows
+    frames_per_step = nwin - 1
+    W, H = stream.width, stream.height
+    P = W * H
+
+    # oracle sample (rank 0, N = 1 only) before any GPU work: spawn-safe
+    cpu = None
+    oracle_flows = None
+    prm = eb.ebof_default_params(W, H)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        workers = cpu_workers()
+        nfr = args.cpu_frames or workers
+        oracle_flows, dt = oracle_sample(stream, _params_dict(prm), nfr, workers)
+        cpu = {"value": nfr / dt, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": "%d frame pairs (windows 0..%d) of the 1280x720 stream, one per "
+                         "process, FP64, %.1f s wall" % (nfr, nfr, dt)}
+
+    eb.load()
+    xs = torch.from_numpy(stream.x).to(dev)
+    ys = torch.from_numpy(stream.y).to(dev)
+    ts = torch.from_numpy(stream.t).to(dev)
+    ps = torch.from_numpy(stream.p).to(dev)
+    off = [int(v) for v in stream.offsets]
+    tb = [int(v) for v in stream.t_begin]
+    flows = torch.empty((nwin, 2, H, W), dtype=torch.float32, device=dev)
+    st, s = eb.ebof_stream_create(prm, local)
+    eb.check(st, "ebof_stream_create")
+    cs = torch.cuda.current_stream(dev)
+    handle = cs.cuda_stream
+    lib = eb.load()
+
+    def step_plain(ev_a=None, ev_b=None):
+        eb.check(lib.ebof_stream_reset(s.handle), "reset")
+        for k in range(nwin):
+            a, b = off[k], off[k + 1]
+            if ev_a is not None:
+                ev_a[k].record(cs)
+            r = lib.ebof_process_window(
+                s.handle, xs.data_ptr() + 2 * a, ys.data_ptr() + 2 * a, ts.data_ptr() + 8 * a,
+                ps.data_ptr() + a, b - a, tb[k], tb[k] + stream.dt, flows[k].data_ptr(),
+                None, None, None, handle)
+            if r < 0:
+                raise eb.EbofError(r, "process_window")
+            if ev_b is not None:
+                ev_b[k].record(cs)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step_plain()
+    barrier()
+    evs_a = [torch.cuda.Event(enable_timing=True) for _ in range(nwin)]
+    evs_b = [torch.cuda.Event(enable_timing=True) for _ in range(nwin)]
+    lat = []
+    clk = ClockSampler(local)
+    clk.start()
+    launches0 = eb.ebof_kernel_launches()
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    t_start.record(cs)
+    for i in range(args.steps):
+        step_plain(evs_a, evs_b)
+        if i + 1 < args.steps:  # keep the per-window events of this step
+            torch.cuda.synchronize(dev)
+            lat += [evs_a[k].elapsed_time(evs_b[k]) for k in range(1, nwin)]
+    t_end.record(cs)
+    barrier()
+    wall = time.perf_counter() - w0
+    lat += [evs_a[k].elapsed_time(evs_b[k]) for k in range(1, nwin)]
+    launches = eb.ebof_kernel_launches() - launches0
+    clocks = clk.stop()
+    ms = t_start.elapsed_time(t_end)
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms = float(tmax.item())
+    value = frames_per_step * args.steps * world / (ms / 1000.0)
+
+    # stage profile over the same steps (events bracket each stage's launches)
+    eb.check(eb.ebof_stream_set_profiling(s, True))
+    for _ in range(max(1, min(args.steps, 2))):
+        step_plain()
+    torch.cuda.synchronize(dev)
+    pst, prof = eb.ebof_stream_get_profile(s)
+    eb.check(pst)
+    eb.ebof_stream_set_profiling(s, False)
+    prof_frames = (nwin) * max(1, min(args.steps, 2))
+    total_ms = sum(v[0] for v in prof.values()) or 1.0
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    dom_ms, dom_launches = prof[dom]
+    gl = geo_levels(prm)
+    n_events = int(off[-1]) * max(1, min(args.steps, 2))
+    alg = algorithmic_bytes(dom, gl, n_events, P, prof_frames)
+    # the first window of each step has no previous surface: no flow stages
+    flow_stages = ("patch_search", "densify", "var_warp", "var_coeff", "var_sor", "var_add",
+                   "flow_out")
+    if dom in flow_stages:
+        alg = alg * (nwin - 1) / nwin
+    per_launch_bytes = alg / max(dom_launches, 1)
+    per_launch_s = dom_ms / 1000.0 / max(dom_launches, 1)
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    peak, peak_kind = load_peaks()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_kind,
+                "bytes_per_launch": per_launch_bytes, "us_per_launch": per_launch_s * 1e6,
+                "stage_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items()}}
+
+    # batched path: the same stream through ebof_process_windows
+    batched = None
+    B = max(1, min(args.batch, nwin - 1))
+    if B > 1:
+        pb = eb.ebof_default_params(W, H)
+        pb.max_batch = B
+        stb, sb = eb.ebof_stream_create(pb, local)
+        if stb >= 0:
+            def step_batched():
+                eb.check(lib.ebof_stream_reset(sb.handle), "reset")
+                k = 0
+                while k < nwin:
+                    n = min(B, nwin - k)
+                    a, b = off[k], off[k + n]
+                    r = lib.ebof_process_windows(
+                        sb.handle, n, xs.data_ptr() + 2 * a, ys.data_ptr() + 2 * a,
+                        ts.data_ptr() + 8 * a, ps.data_ptr() + a, b - a, tb[k], stream.dt,
+                        flows[k].data_ptr(), None, None, None, handle)
+                    if r < 0:
+                        raise eb.EbofError(r, "process_windows")
+                    k += n
+            for _ in range(args.warmup):
+                step_batched()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(cs)
+            for _ in range(args.steps):
+                step_batched()
+            e1.record(cs)
+            barrier()
+            bms = e0.elapsed_time(e1)
+            tb_ = torch.tensor([bms], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(tb_, op=dist.ReduceOp.MAX)
+            bms = float(tb_.item())
+            batched = {"value": frames_per_step * args.steps * world / (bms / 1000.0),
+                       "unit": UNIT, "windows_per_call": B,
+                       "ms_per_step": bms / args.steps}
+            sb.close()
+        else:
+            batched = {"unavailable": eb.ebof_status_string(stb)}
+
+    # EPE of the GPU flow against the oracle sample (same windows)
+    epe = None
+    if oracle_flows is not None:
+        step_plain()
+        torch.cuda.synchronize(dev)
+        es = []
+        for k, U in enumerate(oracle_flows):
+            g = flows[k + 1].cpu().numpy()
+            es.append(np.hypot(g[0] - U[0], g[1] - U[1]))
+        e = np.stack(es)
+        epe = {"mean_px": float(e.mean()), "p99_px": float(np.percentile(e, 99)),
+               "frames": len(es)}
+
+    # end-to-end through the host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(stream.x).pin_memory().numpy()
+        hy = torch.from_numpy(stream.y).pin_memory().numpy()
+        ht = torch.from_numpy(stream.t).pin_memory().numpy()
+        hflow = torch.empty((2, H, W), dtype=torch.float32).pin_memory().numpy()
+
+        def step_host():
+            eb.check(lib.ebof_stream_reset(s.handle), "reset")
+            for k in range(nwin):
+                a, b = off[k], off[k + 1]
+                r = lib.ebof_process_window_host(
+                    s.handle, hx.ctypes.data + 2 * a, hy.ctypes.data + 2 * a,
+                    ht.ctypes.data + 8 * a, b - a, tb[k], tb[k] + stream.dt, hflow.ctypes.data,
+                    handle)
+                if r < 0:
+                    raise eb.EbofError(r, "process_window_host")
+
+        for _ in range(min(args.warmup, 1)):
+            step_host()
+        barrier()
+        h0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        barrier()
+        hs = time.perf_counter() - h0
+        th = torch.tensor([hs], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(th, op=dist.ReduceOp.MAX)
+        hs = float(th.item())
+        e2e = {"value": frames_per_step * args.steps * world / hs, "unit": UNIT,
+               "h2d_bytes_per_step": int(off[-1]) * 12,
+               "d2h_bytes_per_step": nwin * 2 * P * 4}
+
+    if rank == 0:
+        lat = np.asarray(lat)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1280x720 single stream, %d windows of 10 ms (%d flow "
+                                   "frames), 150k-400k events/window, 12 affine objects, "
+                                   "3%% noise, seed 1+rank" % (nwin, frames_per_step),
+                       "path": "plain: one ebof_process_window call per window",
+                       "levels": prm.levels, "patch": prm.patch, "stride": prm.stride,
+                       "gn_iters": prm.gn_iters, "var": "%dx%d" % (prm.var_outer, prm.var_sor),
+                       "l2": "inputs larger than L2: %.0f MB of events per step"
+                             % (int(off[-1]) * 13 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "p50_latency_ms": float(np.percentile(lat, 50)),
+            "p99_latency_ms": float(np.percentile(lat, 99)),
+            "mpx_per_s": value * P / 1e6,
+            "wall_s": wall,
+            "batched": batched,
+            "epe_vs_oracle": epe,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * ebof.h -- C ABI of the GB300 event-based optical flow library (libebof.so).
+ *
+ * The library computes the event-to-flow path of Brebion, Moreau and
+ * Davoine, "Real-Time Optical Flow for Vehicular Perception with Low- and
+ * High-Resolution Event Cameras": the events (x, y, t, p) of a time window
+ * go in (§III-A), a dense optical-flow field from the previous window to
+ * this one comes out (§III-D).  Between the two, on one GPU:
+ *   - the binary edge image of the window (§III-A),
+ *   - denoising and filling (Alg. 1, Alg. 2 of §III-B),
+ *   - the exact Euclidean distance transform, as int32 squared distances,
+ *     and the inverse exponential distance surface d_exp (Eq. 1, §III-C),
+ *   - a Dense Inverse Search flow block on 255 * d_exp (§III-D leaves the
+ *     frame-based method open): image pyramid, per-patch inverse-
+ *     compositional Gauss-Newton, patch densification, variational
+ *     refinement,
+ *   - per-stream device state holding the previous window's pyramid.
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are DEVICE pointers on the stream's device; h_* are
+ *     host pointers.  The caller owns all of them; they must stay valid until
+ *     the work enqueued on `cuda_stream` has completed.
+ *   - Images are dense row-major [height][width]; flow is planar
+ *     [2][height][width] (u = x component first, then v), in pixels per
+ *     window, mapping the previous window to the current one.
+ *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     Calls only enqueue work; none synchronises the host except
+ *     ebof_stream_sync and the *_host variants.
+ *   - Argument errors are reported synchronously and enqueue nothing.
+ *     Errors found on the device (a failed bounds check) are latched in the
+ *     stream and reported by ebof_stream_sync.
+ *   - Events outside the window or outside the image are not errors: they
+ *     are dropped and counted.
+ *   - One ebof_stream must not be used from two host threads at once
+ *     (detected: EBOF_ERR_BUSY).  Distinct streams are independent.
+ */
+#ifndef EBOF_H
+#define EBOF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EBOF_OK = 0,
+    EBOF_NO_PREVIOUS = 1,          /* first window: surface built, flow zero-filled */
+    EBOF_ERR_INVALID_ARG = -1,
+    EBOF_ERR_OOM = -2,
+    EBOF_ERR_CUDA = -3,
+    EBOF_ERR_TIMEOUT = -4,
+    EBOF_ERR_DEVICE_BOUNDS = -5,   /* a kernel's own bounds check fired */
+    EBOF_ERR_UNSUPPORTED = -6,     /* parameter outside what the kernels support */
+    EBOF_ERR_BUSY = -7             /* stream used from two host threads */
+} ebof_status;
+
+/* Method parameters.  Fill with ebof_default_params, then override. */
+typedef struct {
+    uint32_t struct_size;   /* = sizeof(ebof_params); checked for ABI evolution */
+    int32_t width, height;  /* 1 .. 16384 each */
+    int32_t connectivity;   /* 4: the 4 direct neighbours of Alg. 1/2; 8: 3x3 ring */
+    int32_t n_d;            /* Alg. 1 threshold; 0 disables denoising */
+    int32_t n_f;            /* Alg. 2 threshold; > connectivity disables filling */
+    float alpha;            /* Eq. 1 spreading parameter (1.08 = d_sat 6 px, Eq. 3) */
+    int32_t levels;         /* pyramid levels (capped so each level holds a patch) */
+    int32_t patch;          /* patch side ps, 4 .. 16 */
+    int32_t stride;         /* patch grid stride, >= 1 */
+    int32_t gn_iters;       /* Gauss-Newton iterations per patch, >= 0 */
+    int32_t var_outer;      /* variational fixed-point iterations, >= 0 */
+    int32_t var_sor;        /* red-black SOR sweeps per fixed-point iteration, >= 0 */
+    float var_delta;        /* data term weight */
+    float var_gamma;        /* gradient-constancy weight */
+    float var_alpha;        /* smoothness weight */
+    float sor_omega;        /* SOR relaxation, 0 < omega < 2 */
+    int32_t max_batch;      /* most windows one ebof_process_windows call may take */
+} ebof_params;
+
+/* Counts of one processed window. */
+typedef struct {
+    int64_t events;         /* events passed for this window (batched: whole call) */
+    int64_t in_window;      /* events with t_begin <= t < t_end */
+    int64_t dropped_time;   /* events outside [t_begin, t_end) (batched: whole call) */
+    int64_t dropped_oob;    /* in-window events with x >= width or y >= height */
+    int64_t edge_px;        /* edge pixels after denoising and filling */
+    int32_t levels_used;    /* pyramid levels the flow used; 0 = no flow */
+    int32_t has_flow;       /* 1 if a previous window existed */
+} ebof_window_stats;
+
+typedef struct ebof_stream ebof_stream;
+
+/* Defaults for a width x height sensor: connectivity 8, n_d 1, filling off,
+ * alpha 1.08 (§IV-A), 3 levels of 8x8 patches below 640 px width and 5 levels
+ * of 12x12 patches from 640 px, stride 4, 12 Gauss-Newton iterations, 5 x 5
+ * variational iterations (delta 5, gamma 10, alpha 20, omega 1.6),
+ * max_batch 1. */
+void ebof_default_params(ebof_params *p, int32_t width, int32_t height);
+
+/* Eq. 2 with eps = 1/255 (Eq. 3): alpha = d_sat / ln(255). */
+float ebof_alpha_from_dsat(float d_sat);
+
+/* Allocates all device state of one camera stream on `device` (about
+ * 200 bytes per pixel per batch slot).  Returns EBOF_ERR_OOM if the device
+ * memory is not available, EBOF_ERR_UNSUPPORTED for parameters the kernels
+ * do not support.  *out is NULL on failure. */
+ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **out);
+
+/* Frees the stream after waiting for its work.  NULL is accepted. */
+ebof_status ebof_stream_destroy(ebof_stream *s);
+
+/* Forgets the previous window: the next call returns EBOF_NO_PREVIOUS.
+ * Waits for work already enqueued on the stream. */
+ebof_status ebof_stream_reset(ebof_stream *s);
+
+/* One window (§III-A..§III-D).  d_x, d_y, d_t: n_events events (SoA);
+ * d_p (polarity) may be NULL and is never read (§III-A ignores polarity).
+ * Window = [t_begin, t_end), microseconds.  d_flow [2][H][W] is required.
+ * Optional outputs (NULL to skip): d_edge [H][W] the denoised and filled
+ * edge image (the paper's mask for restricting the flow, §III-D), d_edt
+ * [H][W] squared distances (INT32_MAX when the window has no edge pixel),
+ * d_surface [H][W] d_exp of Eq. 1.  Returns EBOF_NO_PREVIOUS (flow zero)
+ * for the first window after create/reset, else EBOF_OK. */
+ebof_status ebof_process_window(ebof_stream *s, const uint16_t *d_x, const uint16_t *d_y,
+                                const int64_t *d_t, const int8_t *d_p, int64_t n_events,
+                                int64_t t_begin, int64_t t_end, float *d_flow,
+                                uint8_t *d_edge, int32_t *d_edt, float *d_surface,
+                                void *cuda_stream);
+
+/* n_windows consecutive windows of one stream in one call (1 <= n_windows
+ * <= max_batch): window k is [t_begin + k*dt, t_begin + (k+1)*dt); every
+ * event goes to the window its timestamp falls in.  Outputs are stacked per
+ * window: d_flow [n][2][H][W], optional d_edge/d_edt/d_surface [n][H][W].
+ * Flow k maps window k-1 to window k (window -1 = the stream's previous
+ * window).  Same result as n_windows ebof_process_window calls. */
+ebof_status ebof_process_windows(ebof_stream *s, int32_t n_windows, const uint16_t *d_x,
+                                 const uint16_t *d_y, const int64_t *d_t, const int8_t *d_p,
+                                 int64_t n_events, int64_t t_begin, int64_t dt,
+                                 float *d_flow, uint8_t *d_edge, int32_t *d_edt,
+                                 float *d_surface, void *cuda_stream);
+
+/* Flow block only (§III-D) on a caller-given surface d_surface [H][W] with
+ * values d_exp in [0, 1] (the flow runs on 255 * d_surface); it becomes the
+ * stream's previous window.  Same return values as ebof_process_window. */
+ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *d_flow,
+                                 void *cuda_stream);
+
+/* ebof_process_window with HOST buffers: copies the events to the device,
+ * runs the window and copies the flow back into h_flow [2][H][W], all on
+ * `cuda_stream`, then synchronises it.  Pinned host memory makes the copies
+ * asynchronous to the host; pageable memory works but is slower. */
+ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const uint16_t *h_y,
+                                     const int64_t *h_t, int64_t n_events, int64_t t_begin,
+                                     int64_t t_end, float *h_flow, void *cuda_stream);
+
+/* Waits for the stream's work, then reports the first device-side error
+ * (if any) and copies the counts of the last call's windows into out[0..
+ * n_out-1] (n_out may be 0 and out NULL).  The latched error is cleared. */
+ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_out);
+
+/* Exact squared EDT and Eq. 1 surface of a caller-given binary edge image
+ * d_edge [H][W] (non-zero = edge pixel): the separable passes of §III-C.
+ * d_scratch: caller-owned device buffer of at least width*height int32
+ * (column distances).  d_edt [H][W] required; d_surface [H][W] optional.
+ * No per-stream state is used. */
+ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32_t *d_scratch,
+                     int32_t *d_edt, float *d_surface, float alpha, void *cuda_stream);
+
+/* ---- tracing: per-stage CUDA-event timing (§IV Table VII reports per-block
+ * times; these are the GPU equivalents).  Timing brackets each stage's
+ * launches with cudaEvents on the caller's stream; it is off by default. */
+typedef enum {
+    EBOF_STAGE_SCATTER = 0,      /* edge image (§III-A) */
+    EBOF_STAGE_DENOISE_FILL,     /* Alg. 1 + Alg. 2 */
+    EBOF_STAGE_EDT_COLS,         /* EDT column pass */
+    EBOF_STAGE_EDT_ROWS_SURFACE, /* EDT row pass + Eq. 1 */
+    EBOF_STAGE_PYRAMID,          /* downsampling + gradients */
+    EBOF_STAGE_PATCH_SEARCH,     /* inverse search */
+    EBOF_STAGE_DENSIFY,          /* densification */
+    EBOF_STAGE_VAR_WARP,         /* variational: warp */
+    EBOF_STAGE_VAR_COEFF,        /* variational: linearised system */
+    EBOF_STAGE_VAR_SOR,          /* variational: SOR sweeps */
+    EBOF_STAGE_VAR_ADD,          /* variational: U += dU */
+    EBOF_STAGE_FLOW_OUT,         /* flow to the caller's layout */
+    EBOF_STAGE_COUNT
+} ebof_stage;
+
+/* Enables (1) or disables (0) stage timing and clears the accumulators. */
+ebof_status ebof_stream_set_profiling(ebof_stream *s, int32_t enable);
+
+/* Waits for the recorded stages, then writes the accumulated milliseconds
+ * and kernel launch counts per stage into ms[0..n-1] and launches[0..n-1]
+ * (either may be NULL; n <= EBOF_STAGE_COUNT). */
+ebof_status ebof_stream_get_profile(ebof_stream *s, double *ms, int64_t *launches, int32_t n);
+
+/* Name of a stage ("scatter", "patch_search", ...). */
+const char *ebof_stage_name(int32_t stage);
+
+/* Kernels this library has launched in the process so far (all streams). */
+uint64_t ebof_kernel_launches(void);
+
+/* Static text for a status code. */
+const char *ebof_status_string(ebof_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EBOF_H */

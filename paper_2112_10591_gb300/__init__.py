@@ -1,0 +1,16 @@
+"""GB300-native event-based optical flow (Brebion, Moreau, Davoine).
+
+The compute lives in libebof.so (CUDA, sm_103a); ``binding`` exposes its C
+ABI (include/ebof.h) under the same names.  ``synth`` draws the seeded
+synthetic event streams used by the tests and the benchmark.
+"""
+from .binding import (  # noqa: F401
+    EBOF_ERR_BUSY, EBOF_ERR_CUDA, EBOF_ERR_DEVICE_BOUNDS, EBOF_ERR_INVALID_ARG,
+    EBOF_ERR_OOM, EBOF_ERR_TIMEOUT, EBOF_ERR_UNSUPPORTED, EBOF_NO_PREVIOUS, EBOF_OK,
+    EbofError, Stream, check, ebof_alpha_from_dsat, ebof_default_params, ebof_edt,
+    ebof_params, ebof_process_surface, ebof_process_window, ebof_process_window_host,
+    ebof_process_windows, ebof_status_string, ebof_stream_create, ebof_stream_destroy,
+    ebof_stream_reset, ebof_stream_sync, ebof_window_stats, library_path, load,
+    EBOF_STAGE_COUNT, ebof_kernel_launches, ebof_stage_name, ebof_stream_get_profile,
+    ebof_stream_set_profiling,
+)

@@ -1,0 +1,308 @@
+"""Thin Python binding of libebof.so (include/ebof.h), by ctypes.
+
+The functions carry the C names and only marshal arguments: torch tensors
+become device pointers, the current torch CUDA stream becomes the
+``cuda_stream`` argument, and status codes come back as ints (negative =
+error).  Every step of the path runs in the library's CUDA kernels; if the
+library is missing, ``load()`` raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+EBOF_OK = 0
+EBOF_NO_PREVIOUS = 1
+EBOF_ERR_INVALID_ARG = -1
+EBOF_ERR_OOM = -2
+EBOF_ERR_CUDA = -3
+EBOF_ERR_TIMEOUT = -4
+EBOF_ERR_DEVICE_BOUNDS = -5
+EBOF_ERR_UNSUPPORTED = -6
+EBOF_ERR_BUSY = -7
+
+
+class ebof_params(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("connectivity", ctypes.c_int32),
+        ("n_d", ctypes.c_int32), ("n_f", ctypes.c_int32),
+        ("alpha", ctypes.c_float),
+        ("levels", ctypes.c_int32), ("patch", ctypes.c_int32),
+        ("stride", ctypes.c_int32), ("gn_iters", ctypes.c_int32),
+        ("var_outer", ctypes.c_int32), ("var_sor", ctypes.c_int32),
+        ("var_delta", ctypes.c_float), ("var_gamma", ctypes.c_float),
+        ("var_alpha", ctypes.c_float), ("sor_omega", ctypes.c_float),
+        ("max_batch", ctypes.c_int32),
+    ]
+
+
+class ebof_window_stats(ctypes.Structure):
+    _fields_ = [
+        ("events", ctypes.c_int64), ("in_window", ctypes.c_int64),
+        ("dropped_time", ctypes.c_int64), ("dropped_oob", ctypes.c_int64),
+        ("edge_px", ctypes.c_int64), ("levels_used", ctypes.c_int32),
+        ("has_flow", ctypes.c_int32),
+    ]
+
+
+class EbofError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__("%s: %s (%d)" % (what or "ebof", ebof_status_string(status), status))
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libebof.so; build it first if it is missing and a toolkit exists."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or not _build.up_to_date():
+                if not build_if_missing:
+                    raise ImportError("libebof.so is not built (%s)" % path)
+                _build.build()
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def _declare(L):
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    P = ctypes.POINTER
+    L.ebof_default_params.argtypes = [P(ebof_params), i32, i32]
+    L.ebof_default_params.restype = None
+    L.ebof_alpha_from_dsat.argtypes = [f32]
+    L.ebof_alpha_from_dsat.restype = f32
+    L.ebof_stream_create.argtypes = [P(ebof_params), ctypes.c_int, P(vp)]
+    L.ebof_stream_destroy.argtypes = [vp]
+    L.ebof_stream_reset.argtypes = [vp]
+    L.ebof_process_window.argtypes = [vp, vp, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
+    L.ebof_process_windows.argtypes = [vp, i32, vp, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
+    L.ebof_process_surface.argtypes = [vp, vp, vp, vp]
+    L.ebof_process_window_host.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, vp]
+    L.ebof_stream_sync.argtypes = [vp, P(ebof_window_stats), i32]
+    L.ebof_edt.argtypes = [vp, i32, i32, vp, vp, vp, f32, vp]
+    L.ebof_stream_set_profiling.argtypes = [vp, i32]
+    L.ebof_stream_get_profile.argtypes = [vp, P(ctypes.c_double), P(i64), i32]
+    L.ebof_stage_name.argtypes = [i32]
+    L.ebof_stage_name.restype = ctypes.c_char_p
+    L.ebof_kernel_launches.argtypes = []
+    L.ebof_kernel_launches.restype = ctypes.c_uint64
+    L.ebof_status_string.argtypes = [ctypes.c_int]
+    L.ebof_status_string.restype = ctypes.c_char_p
+    for name in ("ebof_stream_create", "ebof_stream_destroy", "ebof_stream_reset",
+                 "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
+                 "ebof_process_window_host", "ebof_stream_sync", "ebof_edt",
+                 "ebof_stream_set_profiling", "ebof_stream_get_profile"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+# ---------------------------------------------------------------- marshalling
+def _ptr(t, dtype=None, numel=None, name="tensor", device=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if device is not None and t.device.index != device:
+        raise ValueError("%s is on cuda:%d, the stream is on cuda:%d" % (name, t.device.index, device))
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s needs at least %d elements, has %d" % (name, numel, t.numel()))
+    return t.data_ptr()
+
+
+def _hptr(a, dtype, numel=None, name="array"):
+    """Host pointer of a contiguous numpy array or CPU tensor."""
+    import numpy as np
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                raise ValueError("%s must be in host memory" % name)
+            a = a.numpy()
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError("%s must be a C-contiguous %s array" % (name, np.dtype(dtype)))
+    if numel is not None and a.size < numel:
+        raise ValueError("%s needs at least %d elements" % (name, numel))
+    return a.ctypes.data
+
+
+def _stream_handle(cuda_stream):
+    if cuda_stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(cuda_stream, int):
+        return cuda_stream
+    return cuda_stream.cuda_stream
+
+
+# ---------------------------------------------------------------- C names
+def ebof_default_params(width: int, height: int) -> ebof_params:
+    p = ebof_params()
+    load().ebof_default_params(ctypes.byref(p), int(width), int(height))
+    return p
+
+
+def ebof_alpha_from_dsat(d_sat: float) -> float:
+    return float(load().ebof_alpha_from_dsat(float(d_sat)))
+
+
+def ebof_status_string(status: int) -> str:
+    return load().ebof_status_string(int(status)).decode()
+
+
+class Stream:
+    """Owner of an ``ebof_stream*`` handle (destroyed on close / GC)."""
+
+    def __init__(self, handle: int, params: ebof_params, device: int):
+        self.handle = handle
+        self.params = params
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().ebof_stream_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ebof_stream_create(params: ebof_params, device: int = 0):
+    """Returns (status, Stream or None)."""
+    h = ctypes.c_void_p()
+    st = load().ebof_stream_create(ctypes.byref(params), int(device), ctypes.byref(h))
+    if st < 0:
+        return st, None
+    p = ebof_params()
+    ctypes.memmove(ctypes.byref(p), ctypes.byref(params), ctypes.sizeof(p))
+    return st, Stream(h.value, p, int(device))
+
+
+def ebof_stream_destroy(stream: Stream) -> int:
+    stream.close()
+    return EBOF_OK
+
+
+def ebof_stream_reset(stream: Stream) -> int:
+    return load().ebof_stream_reset(stream.handle)
+
+
+def ebof_process_window(stream: Stream, x, y, t, p, t_begin: int, t_end: int, flow,
+                        edge=None, edt=None, surface=None, cuda_stream=None) -> int:
+    import torch
+    W, H, dev = stream.params.width, stream.params.height, stream.device
+    n = 0 if x is None else x.numel()
+    return load().ebof_process_window(
+        stream.handle, _ptr(x, torch.uint16, n, "x", dev), _ptr(y, torch.uint16, n, "y", dev),
+        _ptr(t, torch.int64, n, "t", dev), _ptr(p, torch.int8, n, "p", dev), n, int(t_begin),
+        int(t_end), _ptr(flow, torch.float32, 2 * W * H, "flow", dev),
+        _ptr(edge, torch.uint8, W * H, "edge", dev), _ptr(edt, torch.int32, W * H, "edt", dev),
+        _ptr(surface, torch.float32, W * H, "surface", dev), _stream_handle(cuda_stream))
+
+
+def ebof_process_windows(stream: Stream, n_windows: int, x, y, t, p, t_begin: int, dt: int,
+                         flow, edge=None, edt=None, surface=None, cuda_stream=None) -> int:
+    import torch
+    W, H, dev = stream.params.width, stream.params.height, stream.device
+    n = 0 if x is None else x.numel()
+    k = int(n_windows)
+    return load().ebof_process_windows(
+        stream.handle, k, _ptr(x, torch.uint16, n, "x", dev), _ptr(y, torch.uint16, n, "y", dev),
+        _ptr(t, torch.int64, n, "t", dev), _ptr(p, torch.int8, n, "p", dev), n, int(t_begin),
+        int(dt), _ptr(flow, torch.float32, k * 2 * W * H, "flow", dev),
+        _ptr(edge, torch.uint8, k * W * H, "edge", dev),
+        _ptr(edt, torch.int32, k * W * H, "edt", dev),
+        _ptr(surface, torch.float32, k * W * H, "surface", dev), _stream_handle(cuda_stream))
+
+
+def ebof_process_surface(stream: Stream, surface, flow, cuda_stream=None) -> int:
+    import torch
+    W, H, dev = stream.params.width, stream.params.height, stream.device
+    return load().ebof_process_surface(
+        stream.handle, _ptr(surface, torch.float32, W * H, "surface", dev),
+        _ptr(flow, torch.float32, 2 * W * H, "flow", dev), _stream_handle(cuda_stream))
+
+
+def ebof_process_window_host(stream: Stream, x, y, t, t_begin: int, t_end: int, flow,
+                             cuda_stream=None) -> int:
+    import numpy as np
+    W, H = stream.params.width, stream.params.height
+    n = len(x)
+    return load().ebof_process_window_host(
+        stream.handle, _hptr(x, np.uint16, n, "x"), _hptr(y, np.uint16, n, "y"),
+        _hptr(t, np.int64, n, "t"), n, int(t_begin), int(t_end),
+        _hptr(flow, np.float32, 2 * W * H, "flow"), _stream_handle(cuda_stream))
+
+
+def ebof_stream_sync(stream: Stream, n_out: int = 1):
+    """Returns (status, [ebof_window_stats] * n_out)."""
+    arr = (ebof_window_stats * max(1, n_out))()
+    st = load().ebof_stream_sync(stream.handle, arr, int(n_out))
+    return st, [arr[i] for i in range(n_out)]
+
+
+def ebof_edt(edge, width: int, height: int, scratch, edt, surface=None, alpha: float = 1.08,
+             cuda_stream=None) -> int:
+    import torch
+    n = int(width) * int(height)
+    return load().ebof_edt(_ptr(edge, torch.uint8, n, "edge"), int(width), int(height),
+                           _ptr(scratch, torch.int32, n, "scratch"),
+                           _ptr(edt, torch.int32, n, "edt"),
+                           _ptr(surface, torch.float32, n, "surface"), float(alpha),
+                           _stream_handle(cuda_stream))
+
+
+EBOF_STAGE_COUNT = 12
+
+
+def ebof_stream_set_profiling(stream: Stream, enable: bool) -> int:
+    return load().ebof_stream_set_profiling(stream.handle, 1 if enable else 0)
+
+
+def ebof_stream_get_profile(stream: Stream):
+    """Returns (status, {stage name: (ms, launches)})."""
+    ms = (ctypes.c_double * EBOF_STAGE_COUNT)()
+    ln = (ctypes.c_int64 * EBOF_STAGE_COUNT)()
+    st = load().ebof_stream_get_profile(stream.handle, ms, ln, EBOF_STAGE_COUNT)
+    return st, {ebof_stage_name(i): (ms[i], ln[i]) for i in range(EBOF_STAGE_COUNT)}
+
+
+def ebof_stage_name(stage: int) -> str:
+    return load().ebof_stage_name(int(stage)).decode()
+
+
+def ebof_kernel_launches() -> int:
+    return int(load().ebof_kernel_launches())
+
+
+def check(status: int, what: str = "") -> int:
+    """Raise EbofError for a negative status; return it otherwise."""
+    if status < 0:
+        raise EbofError(status, what)
+    return status

@@ -1,0 +1,588 @@
+// capi.cu -- the C ABI of include/ebof.h: per-stream device state, argument
+// checks, stage sequencing and error reporting.  All compute is in the
+// kernels of k_front.cu and k_flow.cu; this file only allocates, validates
+// and enqueues.
+#include "ebof.h"
+#include "ebof_internal.cuh"
+#include "profiler.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+using namespace ebof;
+
+namespace ebof {
+
+Geometry make_geometry(int width, int height, int levels, int ps, int stride)
+{
+    Geometry g;
+    std::memset(&g, 0, sizeof(g));
+    g.width = width;
+    g.height = height;
+    int L = 0;
+    while (L < levels && L < kMaxLevels && (width >> L) >= ps && (height >> L) >= ps) ++L;
+    g.levels = L;
+    const int nalloc = std::max(L, 1);  // level 0 always exists (the surface)
+    size_t off = 0;
+    g.max_patches = 0;
+    for (int l = 0; l < nalloc; ++l) {
+        Level &lv = g.lv[l];
+        lv.w = width >> l;
+        lv.h = height >> l;
+        lv.pitch = round_up(lv.w, 32);
+        lv.plane = (size_t)lv.pitch * lv.h;
+        lv.npx = lv.w >= ps ? (lv.w - ps + stride - 1) / stride + 1 : 0;
+        lv.npy = lv.h >= ps ? (lv.h - ps + stride - 1) / stride + 1 : 0;
+        g.max_patches = std::max(g.max_patches, lv.npx * lv.npy);
+        g.pyr_off[l] = off;
+        off += 3 * lv.plane;
+    }
+    g.pyr_floats = off;
+    return g;
+}
+
+}  // namespace ebof
+
+struct ebof_stream {
+    ebof_params p;
+    int device;
+    Geometry geo;
+    int pitch0;
+    size_t e_fs, g_fs, pyr_fs, up_fs, u_fs, work_fs;
+    uint8_t *E = nullptr, *Ed = nullptr, *Edf = nullptr;
+    int32_t *g = nullptr;
+    float *pyr = nullptr;
+    int nslots = 0, head = 0;
+    bool has_prev = false;
+    float *up = nullptr, *Ua = nullptr, *Ub = nullptr, *work = nullptr;
+    DevStats *dstats = nullptr;
+    unsigned long long *d_dropped_time = nullptr;
+    int *d_err = nullptr;
+    float *flow_stage = nullptr;  // device flow for the host-buffer call
+    void *ev_stage = nullptr;     // device events for the host-buffer call
+    size_t ev_stage_bytes = 0;
+    // bookkeeping of the last call
+    int last_n = 0;
+    int64_t last_events = 0;
+    bool last_had_prev = false;
+    cudaEvent_t done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool have_last = false;
+    std::atomic<int> busy{0};
+    Profiler prof;
+};
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_attr_done[kMaxDevices];
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+        if (ok && dev >= 0 && dev < kMaxDevices && !g_attr_done[dev].exchange(1)) {
+            init_front_attributes();
+            init_flow_attributes();
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct ProfScope {
+    explicit ProfScope(Profiler *p) { tl_prof = p; }
+    ~ProfScope() { tl_prof = nullptr; }
+};
+
+struct BusyGuard {
+    std::atomic<int> *flag;
+    bool ok;
+    explicit BusyGuard(std::atomic<int> &f) : flag(&f)
+    {
+        int expect = 0;
+        ok = f.compare_exchange_strong(expect, 1);
+    }
+    ~BusyGuard()
+    {
+        if (ok) flag->store(0);
+    }
+};
+
+bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
+
+ebof_status check_params(const ebof_params *p)
+{
+    if (!p || p->struct_size != sizeof(ebof_params)) return EBOF_ERR_INVALID_ARG;
+    if (p->width < 1 || p->height < 1 || p->width > kMaxDim || p->height > kMaxDim)
+        return EBOF_ERR_INVALID_ARG;
+    if (p->connectivity != 4 && p->connectivity != 8) return EBOF_ERR_INVALID_ARG;
+    if (p->n_d < 0 || p->n_f < 0) return EBOF_ERR_INVALID_ARG;
+    if (!(std::isfinite(p->alpha) && p->alpha > 0.0f)) return EBOF_ERR_INVALID_ARG;
+    if (p->levels < 1 || p->levels > kMaxLevels) return EBOF_ERR_INVALID_ARG;
+    if (p->stride < 1 || p->gn_iters < 0 || p->gn_iters > 10000) return EBOF_ERR_INVALID_ARG;
+    if (p->var_outer < 0 || p->var_outer > 1000 || p->var_sor < 0 || p->var_sor > 1000)
+        return EBOF_ERR_INVALID_ARG;
+    if (!finite_nonneg(p->var_delta) || !finite_nonneg(p->var_gamma) ||
+        !finite_nonneg(p->var_alpha))
+        return EBOF_ERR_INVALID_ARG;
+    if (!(p->sor_omega > 0.0f && p->sor_omega < 2.0f)) return EBOF_ERR_INVALID_ARG;
+    if (p->max_batch < 1 || p->max_batch > 4096) return EBOF_ERR_INVALID_ARG;
+    if (p->patch < 4 || p->patch > kMaxPatch) return EBOF_ERR_UNSUPPORTED;
+    return EBOF_OK;
+}
+
+template <class T>
+cudaError_t dmalloc(T **ptr, size_t bytes)
+{
+    return cudaMalloc((void **)ptr, std::max<size_t>(bytes, 256));
+}
+
+void free_all(ebof_stream *s)
+{
+    cudaFree(s->E); cudaFree(s->Ed); cudaFree(s->Edf); cudaFree(s->g); cudaFree(s->pyr);
+    cudaFree(s->up); cudaFree(s->Ua); cudaFree(s->Ub); cudaFree(s->work);
+    cudaFree(s->dstats); cudaFree(s->d_dropped_time); cudaFree(s->d_err);
+    cudaFree(s->flow_stage); cudaFree(s->ev_stage);
+    if (s->done) cudaEventDestroy(s->done);
+}
+
+FlowParams flow_params(const ebof_params &p)
+{
+    FlowParams fp;
+    fp.ps = p.patch;
+    fp.stride = p.stride;
+    fp.gn_iters = p.gn_iters;
+    fp.var_outer = p.var_outer;
+    fp.var_sor = p.var_sor;
+    fp.delta = p.var_delta;
+    fp.gamma = p.var_gamma;
+    fp.alpha_s = p.var_alpha;
+    fp.omega = p.sor_omega;
+    return fp;
+}
+
+// The whole path for n consecutive windows (or one caller-given surface).
+ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const int64_t *t,
+                int64_t nev, int64_t t_begin, int64_t dt, const float *surface_in,
+                float *d_flow, uint8_t *d_edge, int32_t *d_edt, float *d_surface,
+                cudaStream_t st)
+{
+    const ebof_params &p = s->p;
+    const Geometry &geo = s->geo;
+    const int W = p.width, H = p.height;
+    ProfScope prof_scope(&s->prof);
+    cudaGetLastError();  // start from a clean error state
+    if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
+
+    if (n > 1 && s->head + n >= s->nslots) {
+        if (s->has_prev && s->head != 0)
+            cudaMemcpyAsync(s->pyr, s->pyr + (size_t)s->head * s->pyr_fs,
+                            s->pyr_fs * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        s->head = 0;
+    }
+    const int cur_first = n == 1 ? (s->head + 1) % s->nslots : s->head + 1;
+    cudaMemsetAsync(s->dstats, 0, sizeof(DevStats) * n, st);
+    cudaMemsetAsync(s->d_dropped_time, 0, sizeof(unsigned long long), st);
+    float *I0cur = s->pyr + (size_t)cur_first * s->pyr_fs;
+
+    if (surface_in) {
+        launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, st);
+    } else {
+        cudaMemsetAsync(s->E, 0, s->e_fs * n, st);
+        launch_scatter(x, y, t, nev, t_begin, dt, n, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
+                       s->d_dropped_time, st);
+        launch_denoise_fill(s->E, s->Ed, s->Edf, W, H, s->pitch0, s->e_fs, n, p.connectivity,
+                            p.n_d, p.n_f, d_edge, s->dstats, st);
+        launch_edt_columns(s->Edf, s->pitch0, s->e_fs, W, H, s->g, s->pitch0, s->g_fs, n, st);
+        launch_edt_rows_surface(s->g, s->pitch0, s->g_fs, W, H, p.alpha, d_edt, d_surface,
+                                I0cur, s->pitch0, s->pyr_fs, n, st);
+    }
+
+    // A5: pyramid and gradients of the current window(s)
+    const int nlev = std::max(geo.levels, 1);
+    for (int l = 0; l < nlev; ++l) {
+        const Level &lv = geo.lv[l];
+        float *I = I0cur + geo.pyr_off[l];
+        if (l > 0) {
+            const Level &lp = geo.lv[l - 1];
+            launch_downsample(I0cur + geo.pyr_off[l - 1], lp.w, lp.h, lp.pitch, I, lv.w, lv.h,
+                              lv.pitch, s->pyr_fs, n, st);
+        }
+        launch_gradients(I, I + lv.plane, I + 2 * lv.plane, lv.w, lv.h, lv.pitch, s->pyr_fs, n,
+                         st);
+    }
+
+    // A6-A9: flow for every window that has a previous one
+    const bool had_prev = s->has_prev;
+    const int ff = had_prev ? 0 : 1;
+    const int nf = n - ff;
+    const size_t flow_frame = (size_t)2 * W * H;
+    if (geo.levels > 0 && nf > 0) {
+        const int prev_first = n == 1 ? s->head : s->head + ff;
+        const int curf_first = n == 1 ? cur_first : s->head + 1 + ff;
+        const FlowParams fp = flow_params(p);
+        float *Ucur = nullptr, *Uc = nullptr;
+        const Level *lvc = nullptr;
+        for (int l = geo.levels - 1; l >= 0; --l) {
+            const Level &lv = geo.lv[l];
+            const float *I0 = s->pyr + (size_t)prev_first * s->pyr_fs + geo.pyr_off[l];
+            const float *I1 = s->pyr + (size_t)curf_first * s->pyr_fs + geo.pyr_off[l];
+            Ucur = (Uc == s->Ua) ? s->Ub : s->Ua;
+            launch_patch_search(I0, I0 + lv.plane, I0 + 2 * lv.plane, I1, lv, s->pyr_fs, Uc, lvc,
+                                s->u_fs, s->up, s->up_fs, nf, fp, s->d_err, st);
+            launch_densify(I0, I1, lv, s->pyr_fs, s->up, s->up_fs, Ucur, s->u_fs, nf, fp, st);
+            launch_variational(I0, I0 + lv.plane, I0 + 2 * lv.plane, I1, lv, s->pyr_fs, Ucur,
+                               s->u_fs, s->work, s->work_fs, nf, fp, st);
+            Uc = Ucur;
+            lvc = &lv;
+        }
+        launch_flow_out(Ucur, W, H, s->pitch0, s->u_fs, d_flow + (size_t)ff * flow_frame, nf,
+                        st);
+    }
+    if (geo.levels == 0)
+        cudaMemsetAsync(d_flow, 0, sizeof(float) * flow_frame * n, st);
+    else if (ff == 1)
+        cudaMemsetAsync(d_flow, 0, sizeof(float) * flow_frame, st);
+
+    s->head = n == 1 ? cur_first : s->head + n;
+    s->has_prev = true;
+    s->last_n = n;
+    s->last_events = nev;
+    s->last_had_prev = had_prev;
+    cudaEventRecord(s->done, st);
+    s->last_stream = st;
+    s->have_last = true;
+    if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
+    return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
+}
+
+bool events_ok(const void *x, const void *y, const void *t, int64_t n)
+{
+    return n >= 0 && (n == 0 || (x && y && t));
+}
+
+}  // namespace
+
+extern "C" {
+
+void ebof_default_params(ebof_params *p, int32_t width, int32_t height)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(ebof_params);
+    p->width = width;
+    p->height = height;
+    p->connectivity = 8;
+    p->n_d = 1;
+    p->n_f = 9;
+    p->alpha = 1.08f;
+    const bool hr = width >= 640;
+    p->levels = hr ? 5 : 3;
+    p->patch = hr ? 12 : 8;
+    p->stride = 4;
+    p->gn_iters = 12;
+    p->var_outer = 5;
+    p->var_sor = 5;
+    p->var_delta = 5.0f;
+    p->var_gamma = 10.0f;
+    p->var_alpha = 20.0f;
+    p->sor_omega = 1.6f;
+    p->max_batch = 1;
+}
+
+float ebof_alpha_from_dsat(float d_sat) { return d_sat / std::log(255.0f); }
+
+ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **out)
+{
+    if (!out) return EBOF_ERR_INVALID_ARG;
+    *out = nullptr;
+    const ebof_status ps = check_params(p);
+    if (ps != EBOF_OK) return ps;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return device < 0 ? EBOF_ERR_INVALID_ARG : EBOF_ERR_CUDA;
+    DeviceGuard dg(device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    ebof_stream *s = new (std::nothrow) ebof_stream();
+    if (!s) return EBOF_ERR_OOM;
+    s->p = *p;
+    s->device = device;
+    s->geo = make_geometry(p->width, p->height, p->levels, p->patch, p->stride);
+    const Geometry &geo = s->geo;
+    const int B = p->max_batch;
+    s->pitch0 = geo.lv[0].pitch;
+    const size_t plane0 = geo.lv[0].plane;
+    s->e_fs = plane0;
+    s->g_fs = plane0;
+    s->pyr_fs = geo.pyr_floats;
+    s->up_fs = (size_t)2 * std::max(geo.max_patches, 1);
+    s->u_fs = 2 * plane0;
+    s->work_fs = 9 * plane0;
+    s->nslots = B + 1;
+    bool ok = true;
+    ok &= dmalloc(&s->E, s->e_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->Ed, s->e_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->Edf, s->e_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->g, sizeof(int32_t) * s->g_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->pyr, sizeof(float) * s->pyr_fs * s->nslots) == cudaSuccess;
+    ok &= dmalloc(&s->up, sizeof(float) * s->up_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->Ua, sizeof(float) * s->u_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->Ub, sizeof(float) * s->u_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->work, sizeof(float) * s->work_fs * B) == cudaSuccess;
+    ok &= dmalloc(&s->dstats, sizeof(DevStats) * B) == cudaSuccess;
+    ok &= dmalloc(&s->d_dropped_time, sizeof(unsigned long long)) == cudaSuccess;
+    ok &= dmalloc(&s->d_err, sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&s->flow_stage, sizeof(float) * 2 * (size_t)p->width * p->height) == cudaSuccess;
+    ok &= cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(s);
+        delete s;
+        return EBOF_ERR_OOM;
+    }
+    cudaMemset(s->d_err, 0, sizeof(int));
+    cudaMemset(s->dstats, 0, sizeof(DevStats) * B);
+    cudaMemset(s->d_dropped_time, 0, sizeof(unsigned long long));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_all(s);
+        delete s;
+        return EBOF_ERR_CUDA;
+    }
+    *out = s;
+    return EBOF_OK;
+}
+
+ebof_status ebof_stream_destroy(ebof_stream *s)
+{
+    if (!s) return EBOF_OK;
+    DeviceGuard dg(s->device);
+    if (s->have_last) cudaEventSynchronize(s->done);
+    free_all(s);
+    delete s;
+    return EBOF_OK;
+}
+
+ebof_status ebof_stream_reset(ebof_stream *s)
+{
+    if (!s) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (s->have_last && cudaEventSynchronize(s->done) != cudaSuccess) return EBOF_ERR_CUDA;
+    s->has_prev = false;
+    s->head = 0;
+    return EBOF_OK;
+}
+
+ebof_status ebof_process_window(ebof_stream *s, const uint16_t *d_x, const uint16_t *d_y,
+                                const int64_t *d_t, const int8_t *d_p, int64_t n_events,
+                                int64_t t_begin, int64_t t_end, float *d_flow, uint8_t *d_edge,
+                                int32_t *d_edt, float *d_surface, void *cuda_stream)
+{
+    (void)d_p;  // polarity is not used (§III-A)
+    if (!s || !d_flow || !events_ok(d_x, d_y, d_t, n_events) || t_end < t_begin)
+        return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    return run(s, 1, d_x, d_y, d_t, n_events, t_begin, t_end - t_begin, nullptr, d_flow, d_edge,
+               d_edt, d_surface, (cudaStream_t)cuda_stream);
+}
+
+ebof_status ebof_process_windows(ebof_stream *s, int32_t n_windows, const uint16_t *d_x,
+                                 const uint16_t *d_y, const int64_t *d_t, const int8_t *d_p,
+                                 int64_t n_events, int64_t t_begin, int64_t dt, float *d_flow,
+                                 uint8_t *d_edge, int32_t *d_edt, float *d_surface,
+                                 void *cuda_stream)
+{
+    (void)d_p;
+    if (!s || !d_flow || !events_ok(d_x, d_y, d_t, n_events) || dt < 0) return EBOF_ERR_INVALID_ARG;
+    if (n_windows < 1 || n_windows > s->p.max_batch) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    return run(s, n_windows, d_x, d_y, d_t, n_events, t_begin, dt, nullptr, d_flow, d_edge,
+               d_edt, d_surface, (cudaStream_t)cuda_stream);
+}
+
+ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *d_flow,
+                                 void *cuda_stream)
+{
+    if (!s || !d_surface || !d_flow) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    return run(s, 1, nullptr, nullptr, nullptr, 0, 0, 0, d_surface, d_flow, nullptr, nullptr,
+               nullptr, (cudaStream_t)cuda_stream);
+}
+
+ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const uint16_t *h_y,
+                                     const int64_t *h_t, int64_t n_events, int64_t t_begin,
+                                     int64_t t_end, float *h_flow, void *cuda_stream)
+{
+    if (!s || !h_flow || !events_ok(h_x, h_y, h_t, n_events) || t_end < t_begin)
+        return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t n = (size_t)n_events;
+    const size_t bx = ((2 * n + 255) / 256) * 256;
+    const size_t need = 2 * bx + 8 * n;
+    if (need > s->ev_stage_bytes) {
+        if (s->have_last) cudaEventSynchronize(s->done);
+        cudaFree(s->ev_stage);
+        s->ev_stage = nullptr;
+        s->ev_stage_bytes = 0;
+        if (cudaMalloc(&s->ev_stage, std::max<size_t>(need, 1 << 20)) != cudaSuccess) {
+            cudaGetLastError();
+            return EBOF_ERR_OOM;
+        }
+        s->ev_stage_bytes = std::max<size_t>(need, 1 << 20);
+    }
+    char *base = (char *)s->ev_stage;
+    uint16_t *dx = (uint16_t *)base;
+    uint16_t *dy = (uint16_t *)(base + bx);
+    int64_t *dt = (int64_t *)(base + 2 * bx);
+    if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
+    if (n) {
+        cudaMemcpyAsync(dx, h_x, 2 * n, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(dy, h_y, 2 * n, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(dt, h_t, 8 * n, cudaMemcpyHostToDevice, st);
+    }
+    ebof_status r = run(s, 1, dx, dy, dt, n_events, t_begin, t_end - t_begin, nullptr,
+                        s->flow_stage, nullptr, nullptr, nullptr, st);
+    if (r < 0) return r;
+    cudaMemcpyAsync(h_flow, s->flow_stage, sizeof(float) * 2 * (size_t)s->p.width * s->p.height,
+                    cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return EBOF_ERR_CUDA;
+    return r;
+}
+
+ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_out)
+{
+    if (!s || n_out < 0 || (n_out > 0 && !out)) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    if (s->have_last && cudaEventSynchronize(s->done) != cudaSuccess) return EBOF_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return EBOF_ERR_CUDA;
+    const int n = std::min<int>(n_out, s->last_n);
+    if (n > 0) {
+        DevStats hs[64];
+        unsigned long long dropped_time = 0;
+        cudaMemcpy(&dropped_time, s->d_dropped_time, sizeof(dropped_time),
+                   cudaMemcpyDeviceToHost);
+        for (int k0 = 0; k0 < n; k0 += 64) {
+            const int m = std::min(64, n - k0);
+            if (cudaMemcpy(hs, s->dstats + k0, sizeof(DevStats) * m, cudaMemcpyDeviceToHost) !=
+                cudaSuccess)
+                return EBOF_ERR_CUDA;
+            for (int k = 0; k < m; ++k) {
+                ebof_window_stats &o = out[k0 + k];
+                o.events = s->last_events;
+                o.in_window = (int64_t)hs[k].in_window;
+                o.dropped_time = (int64_t)dropped_time;
+                o.dropped_oob = (int64_t)hs[k].dropped_oob;
+                o.edge_px = (int64_t)hs[k].edge_px;
+                const bool hf = (k0 + k) > 0 || s->last_had_prev;
+                o.has_flow = hf ? 1 : 0;
+                o.levels_used = hf ? s->geo.levels : 0;
+            }
+        }
+    }
+    if (err) {
+        cudaMemset(s->d_err, 0, sizeof(int));
+        return EBOF_ERR_DEVICE_BOUNDS;
+    }
+    return EBOF_OK;
+}
+
+ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32_t *d_scratch,
+                     int32_t *d_edt, float *d_surface, float alpha, void *cuda_stream)
+{
+    if (!d_edge || !d_scratch || !d_edt || width < 1 || height < 1 || width > kMaxDim ||
+        height > kMaxDim || !(std::isfinite(alpha) && alpha > 0.0f))
+        return EBOF_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EBOF_ERR_CUDA;
+    DeviceGuard dg(dev);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaGetLastError();
+    const size_t plane = (size_t)width * height;
+    launch_edt_columns(d_edge, width, plane, width, height, d_scratch, width, plane, 1, st);
+    launch_edt_rows_surface(d_scratch, width, plane, width, height, alpha, d_edt, d_surface,
+                            nullptr, width, plane, 1, st);
+    return cudaGetLastError() == cudaSuccess ? EBOF_OK : EBOF_ERR_CUDA;
+}
+
+ebof_status ebof_stream_set_profiling(ebof_stream *s, int32_t enable)
+{
+    if (!s) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    s->prof.reset();
+    s->prof.on = enable != 0;
+    if (s->prof.on) {
+        // create the events up front so that timed regions never create any
+        while (s->prof.pool.size() < 65536) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) break;
+            s->prof.pool.push_back(e);
+        }
+    }
+    return EBOF_OK;
+}
+
+ebof_status ebof_stream_get_profile(ebof_stream *s, double *ms, int64_t *launches, int32_t n)
+{
+    if (!s || n < 0 || n > EBOF_STAGE_COUNT) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    s->prof.flush();
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = s->prof.ms[i];
+        if (launches) launches[i] = s->prof.launches[i];
+    }
+    return EBOF_OK;
+}
+
+const char *ebof_stage_name(int32_t stage) { return stage_name(stage); }
+
+uint64_t ebof_kernel_launches(void) { return g_launches.load(); }
+
+const char *ebof_status_string(ebof_status st)
+{
+    switch (st) {
+    case EBOF_OK: return "ok";
+    case EBOF_NO_PREVIOUS: return "first window: no previous surface, flow zero";
+    case EBOF_ERR_INVALID_ARG: return "invalid argument";
+    case EBOF_ERR_OOM: return "out of device memory";
+    case EBOF_ERR_CUDA: return "CUDA error";
+    case EBOF_ERR_TIMEOUT: return "device wait timed out";
+    case EBOF_ERR_DEVICE_BOUNDS: return "device bounds check failed";
+    case EBOF_ERR_UNSUPPORTED: return "unsupported parameter";
+    case EBOF_ERR_BUSY: return "stream in use by another thread";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

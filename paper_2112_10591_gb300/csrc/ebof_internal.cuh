@@ -1,0 +1,116 @@
+// ebof_internal.cuh -- internal declarations shared by the CUDA translation
+// units of libebof.so.  Nothing here is part of the C ABI (include/ebof.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ebof {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMaxDim = 16384;
+constexpr int kMaxPatch = 16;
+constexpr int32_t kInfD = 2147483647;  // squared distance with no edge pixel
+
+// Device error bits, latched in StreamState::d_err.
+constexpr int kErrBounds = 1;
+
+__host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Geometry of one pyramid level.  Internal images are row-major with a row
+// pitch rounded up to 32 elements (128-byte rows for 4-byte types).
+struct Level {
+    int w, h, pitch;
+    size_t plane;      // pitch * h elements
+    int npx, npy;      // patch grid (reading F2); 0 if no patch fits
+};
+
+// Geometry of a whole frame: the level chain plus the level-0 pitches.
+struct Geometry {
+    int width, height;
+    int levels;        // levels used by the flow (capped, reading F1)
+    Level lv[kMaxLevels];
+    size_t pyr_floats; // floats of one pyramid slot (I, Ix, Iy at every level)
+    size_t pyr_off[kMaxLevels];  // offset of level l in a slot (I; Ix, Iy follow)
+    int max_patches;   // largest npx * npy over the levels
+};
+
+Geometry make_geometry(int width, int height, int levels, int ps, int stride);
+
+// Per-window event counters kept on the device (one per batch slot).
+struct DevStats {
+    unsigned long long in_window;
+    unsigned long long dropped_oob;
+    unsigned long long edge_px;
+    unsigned long long pad;
+};
+
+// Kernel parameter bundles ---------------------------------------------------
+
+struct FlowParams {
+    int ps, stride, gn_iters;
+    int var_outer, var_sor;
+    float delta, gamma, alpha_s, omega;
+};
+
+// Launchers (each enqueues on `st`; frames = batch size). ---------------------
+
+// A1: clear edge images, scatter events of n_windows consecutive windows.
+void launch_scatter(const uint16_t *x, const uint16_t *y, const int64_t *t, int64_t n,
+                    int64_t t_begin, int64_t dt, int n_windows, int W, int H, int pitch,
+                    uint8_t *E, size_t frame_stride, DevStats *stats,
+                    unsigned long long *dropped_time, cudaStream_t st);
+
+// A2: Alg. 1 then Alg. 2; writes E_df (pitched) and optional dense export.
+void launch_denoise_fill(const uint8_t *E, uint8_t *Ed, uint8_t *Edf, int W, int H, int pitch,
+                         size_t frame_stride, int frames, int conn, int n_d, int n_f,
+                         uint8_t *export_dense, DevStats *stats, cudaStream_t st);
+
+// A3: per-column distance to the nearest edge pixel (G_INF = W + H if none).
+void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stride, int W,
+                        int H, int32_t *g, int g_pitch, size_t g_frame_stride, int frames,
+                        cudaStream_t st);
+
+// A4: per-row lower envelope -> D, fused Eq. 1 surface and 255 * surface.
+void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
+                             float alpha, int32_t *D_dense, float *S_dense, float *I0,
+                             int i_pitch, size_t i_frame_stride, int frames, cudaStream_t st);
+
+// Per-device kernel attributes (opt-in shared memory); call with the device current.
+void init_front_attributes();
+void init_flow_attributes();
+
+// Surface given by the caller -> 255 * d_exp into the level-0 image.
+void launch_surface_to_intensity(const float *S, int W, int H, float *I0, int pitch,
+                                 cudaStream_t st);
+
+// A5: gradients of level l, and downsample l -> l+1 (then its gradients).
+void launch_gradients(const float *I, float *Ix, float *Iy, int w, int h, int pitch,
+                      size_t frame_stride, int frames, cudaStream_t st);
+void launch_downsample(const float *I, int w, int h, int pitch, float *out, int wc, int hc,
+                       int pitch_c, size_t frame_stride, int frames, cudaStream_t st);
+
+// A6: patch inverse search at one level.
+void launch_patch_search(const float *I0, const float *I0x, const float *I0y, const float *I1,
+                         const Level &lv, size_t pyr_frame_stride, const float *Uc,
+                         const Level *lvc, size_t uc_frame_stride, float *up,
+                         size_t up_frame_stride, int frames, const FlowParams &fp,
+                         int *err, cudaStream_t st);
+
+// A7: densification.
+void launch_densify(const float *I0, const float *I1, const Level &lv, size_t pyr_frame_stride,
+                    const float *up, size_t up_frame_stride, float *U, size_t u_frame_stride,
+                    int frames, const FlowParams &fp, cudaStream_t st);
+
+// A8: variational refinement of U in place.
+void launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
+                        const Level &lv, size_t pyr_frame_stride, float *U,
+                        size_t u_frame_stride, float *work, size_t work_frame_stride,
+                        int frames, const FlowParams &fp, cudaStream_t st);
+
+// A9: level-0 flow to the caller's dense planar layout.
+void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,
+                     float *flow, int frames, cudaStream_t st);
+
+}  // namespace ebof

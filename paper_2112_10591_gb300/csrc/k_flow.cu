@@ -1,0 +1,474 @@
+// k_flow.cu -- the frame-based flow block (§III-D) as Dense Inverse Search.
+//
+// §III-D leaves the frame-based method open; this block is Dense Inverse
+// Search (Kroeger et al., ECCV 2016) on the 8-bit intensity I = 255 * d_exp
+// of Eq. 1:
+//   pyramid     2x2 box means, central-difference gradients (replicated border)
+//   search      per-patch inverse-compositional Gauss-Newton on mean-
+//               normalised patches, determinant guard, reset rule
+//   densify     weights 1 / max(1, |I1(x + u_i) - I0(x)|)
+//   variational normalised data + gradient-constancy + smoothness terms,
+//               lagged robust weights, red-black SOR
+// All arithmetic is FP32; the readings of the open points are those of the
+// FP64 oracle this library is tested against.
+#include "ebof_internal.cuh"
+#include "profiler.cuh"
+
+namespace ebof {
+
+namespace {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// Bilinear sample with the position clamped to [0, w-1] x [0, h-1].
+__device__ __forceinline__ float bilinear(const float *__restrict__ I, int w, int h, int pitch,
+                                          float x, float y)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
+    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
+    const float xf = floorf(x), yf = floorf(y);
+    const int x0 = (int)xf, y0 = (int)yf;
+    const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+    const float fx = x - xf, fy = y - yf;
+    const float a = I[(size_t)y0 * pitch + x0], b = I[(size_t)y0 * pitch + x1];
+    const float c = I[(size_t)y1 * pitch + x0], d = I[(size_t)y1 * pitch + x1];
+    return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
+}
+
+// ---------------------------------------------------------------- A5
+__global__ void gradients_kernel(const float *__restrict__ I, float *__restrict__ Ix,
+                                 float *__restrict__ Iy, int w, int h, int pitch, size_t fs)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const size_t fo = (size_t)blockIdx.z * fs;
+    const float *im = I + fo;
+    const int xp = min(x + 1, w - 1), xm = max(x - 1, 0);
+    const int yp = min(y + 1, h - 1), ym = max(y - 1, 0);
+    const size_t p = (size_t)y * pitch + x;
+    Ix[fo + p] = 0.5f * (im[(size_t)y * pitch + xp] - im[(size_t)y * pitch + xm]);
+    Iy[fo + p] = 0.5f * (im[(size_t)yp * pitch + x] - im[(size_t)ym * pitch + x]);
+}
+
+__global__ void downsample_kernel(const float *__restrict__ I, int pitch, float *__restrict__ out,
+                                  int wc, int hc, int pitch_c, size_t fs)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= wc || y >= hc) return;
+    const float *im = I + (size_t)blockIdx.z * fs;
+    const size_t r0 = (size_t)(2 * y) * pitch + 2 * x, r1 = r0 + pitch;
+    out[(size_t)blockIdx.z * fs + (size_t)y * pitch_c + x] =
+        0.25f * (im[r0] + im[r0 + 1] + im[r1] + im[r1 + 1]);
+}
+
+// ---------------------------------------------------------------- A6
+// Group of G lanes per patch (G = 8 for ps <= 8, else 16); lane c < ps owns
+// patch column c and keeps its template, gradients and warped samples in
+// registers.  Patch sums are reduced over the group with xor shuffles, so a
+// warp serves 32 / G patches.  Every lane of a warp runs the same number of
+// iterations (guarded patches iterate on a dummy determinant and are
+// discarded), so the shuffles never diverge.
+template <int G>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int PS, int G>
+__global__ void __launch_bounds__(128)
+patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
+                    const float *__restrict__ I0yb, const float *__restrict__ I1b, int w, int h,
+                    int pitch, size_t pfs, int npx, int npy, const float *__restrict__ Ucb, int wc,
+                    int hc, int pitch_c, size_t plane_c, size_t ucfs, float *__restrict__ upb,
+                    size_t upfs, int stride, int iters, int *err)
+{
+    const int f = blockIdx.y;
+    const int c = threadIdx.x % G;
+    const int np = npx * npy;
+    const int pid_raw = blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+    const bool real = pid_raw < np;
+    const int pid = real ? pid_raw : np - 1;
+    const int i = pid % npx, j = pid / npx;
+    const int x0 = min(i * stride, w - PS), y0 = min(j * stride, h - PS);
+    const bool active = c < PS;
+    const float *I0 = I0b + (size_t)f * pfs, *I0x = I0xb + (size_t)f * pfs;
+    const float *I0y = I0yb + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
+    if (x0 < 0 || y0 < 0) {  // cannot happen when the level holds a patch
+        if (real && c == 0) atomicOr(err, kErrBounds);
+    }
+
+    // F3: start value from the next coarser level
+    float u0 = 0.0f, v0 = 0.0f;
+    if (Ucb) {
+        const int cx = clampi((2 * x0 + PS) / 4, 0, wc - 1);
+        const int cy = clampi((2 * y0 + PS) / 4, 0, hc - 1);
+        const float *Uc = Ucb + (size_t)f * ucfs;
+        u0 = 2.0f * Uc[(size_t)cy * pitch_c + cx];
+        v0 = 2.0f * Uc[plane_c + (size_t)cy * pitch_c + cx];
+    }
+
+    // F4: template, mean-normalised gradients, Hessian
+    float T[PS], GX[PS], GY[PS];
+    float sT = 0.0f, sgx = 0.0f, sgy = 0.0f;
+    const int xc = active ? x0 + c : x0;
+#pragma unroll
+    for (int r = 0; r < PS; ++r) {
+        const size_t p = (size_t)(y0 + r) * pitch + xc;
+        T[r] = active ? I0[p] : 0.0f;
+        GX[r] = active ? I0x[p] : 0.0f;
+        GY[r] = active ? I0y[p] : 0.0f;
+        sT += T[r]; sgx += GX[r]; sgy += GY[r];
+    }
+    constexpr float inv_n = 1.0f / (PS * PS);
+    sT = group_sum<G>(sT); sgx = group_sum<G>(sgx); sgy = group_sum<G>(sgy);
+    const float mT = sT * inv_n, mgx = sgx * inv_n, mgy = sgy * inv_n;
+    float h11 = 0.0f, h12 = 0.0f, h22 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < PS; ++r) {
+        if (active) { GX[r] -= mgx; GY[r] -= mgy; }
+        h11 += GX[r] * GX[r]; h12 += GX[r] * GY[r]; h22 += GY[r] * GY[r];
+    }
+    h11 = group_sum<G>(h11); h12 = group_sum<G>(h12); h22 = group_sum<G>(h22);
+    const float det = h11 * h22 - h12 * h12;
+    const bool guard = !(det > 1e-6f * (float)(PS * PS) * (float)(PS * PS));
+    const float inv_det = guard ? 0.0f : 1.0f / det;
+
+    float u = u0, v = v0;
+    for (int it = 0; it < iters; ++it) {
+        float Wv[PS];
+        float sw = 0.0f;
+        const float xs = (float)xc + u;
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+            Wv[r] = active ? bilinear(I1, w, h, pitch, xs, (float)(y0 + r) + v) : 0.0f;
+            sw += Wv[r];
+        }
+        const float mw = group_sum<G>(sw) * inv_n;
+        float b1 = 0.0f, b2 = 0.0f;
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+            const float res = active ? (Wv[r] - mw) - (T[r] - mT) : 0.0f;
+            b1 += GX[r] * res; b2 += GY[r] * res;
+        }
+        b1 = group_sum<G>(b1); b2 = group_sum<G>(b2);
+        u -= (h22 * b1 - h12 * b2) * inv_det;
+        v -= (h11 * b2 - h12 * b1) * inv_det;
+    }
+    if (guard || !(hypotf(u - u0, v - v0) <= (float)PS)) { u = u0; v = v0; }
+    if (real && c == 0) {
+        float *up = upb + (size_t)f * upfs;
+        up[pid] = u;
+        up[(size_t)np + pid] = v;
+    }
+}
+
+// ---------------------------------------------------------------- A7
+__device__ __forceinline__ void cover_range(int x, int n, int ps, int stride, int cnt, int &lo,
+                                            int &hi, bool &last)
+{
+    // regular patches k < cnt - 1 have origin k * stride; the last one is
+    // flush with the border at n - ps
+    const int t = x - ps + 1;
+    lo = t <= 0 ? 0 : (t + stride - 1) / stride;
+    hi = min(cnt - 2, x / stride);
+    last = x >= n - ps;
+}
+
+__global__ void densify_kernel(const float *__restrict__ I0b, const float *__restrict__ I1b,
+                               int w, int h, int pitch, size_t pfs, const float *__restrict__ upb,
+                               size_t upfs, int npx, int npy, float *__restrict__ Ub, size_t ufs,
+                               size_t plane, int ps, int stride)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const int f = blockIdx.z;
+    const float *I0 = I0b + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
+    const float *up = upb + (size_t)f * upfs;
+    const int np = npx * npy;
+    int ilo, ihi, jlo, jhi;
+    bool ilast, jlast;
+    cover_range(x, w, ps, stride, npx, ilo, ihi, ilast);
+    cover_range(y, h, ps, stride, npy, jlo, jhi, jlast);
+    const float i0 = I0[(size_t)y * pitch + x];
+    float nu = 0.0f, nv = 0.0f, den = 0.0f;
+    for (int jj = jlo; jj <= jhi + 1; ++jj) {
+        int j = jj;
+        if (jj == jhi + 1) { if (!jlast) break; j = npy - 1; }
+        for (int ii = ilo; ii <= ihi + 1; ++ii) {
+            int i = ii;
+            if (ii == ihi + 1) { if (!ilast) break; i = npx - 1; }
+            const int id = j * npx + i;
+            const float u = up[id], v = up[(size_t)np + id];
+            const float r = bilinear(I1, w, h, pitch, (float)x + u, (float)y + v) - i0;
+            const float lam = 1.0f / fmaxf(1.0f, fabsf(r));
+            nu += lam * u; nv += lam * v; den += lam;
+        }
+    }
+    float *U = Ub + (size_t)f * ufs;
+    const size_t p = (size_t)y * pitch + x;
+    U[p] = den > 0.0f ? nu / den : 0.0f;
+    U[plane + p] = den > 0.0f ? nv / den : 0.0f;
+}
+
+// ---------------------------------------------------------------- A8
+// Work planes (each lv.plane floats) of one frame.
+enum { kW1 = 0, kA11, kA12, kA22, kB1, kB2, kAS, kDU, kDV, kWorkPlanes };
+
+__global__ void warp_kernel(const float *__restrict__ I1b, int w, int h, int pitch, size_t pfs,
+                            const float *__restrict__ Ub, size_t ufs, size_t plane,
+                            float *__restrict__ workb, size_t wfs)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const int f = blockIdx.z;
+    const float *U = Ub + (size_t)f * ufs;
+    const size_t p = (size_t)y * pitch + x;
+    workb[(size_t)f * wfs + kW1 * plane + p] =
+        bilinear(I1b + (size_t)f * pfs, w, h, pitch, (float)x + U[p], (float)y + U[plane + p]);
+}
+
+__device__ __forceinline__ float psi_prime(float s2) { return 0.5f * rsqrtf(s2 + 1e-6f); }
+
+__global__ void coeff_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
+                             const float *__restrict__ I0yb, int w, int h, int pitch, size_t pfs,
+                             const float *__restrict__ Ub, size_t ufs, size_t plane,
+                             float *__restrict__ workb, size_t wfs, float delta, float gamma,
+                             float alpha_s)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const int f = blockIdx.z;
+    float *wk = workb + (size_t)f * wfs;
+    const float *W1 = wk + kW1 * plane;
+    const float *U = Ub + (size_t)f * ufs;
+    auto at = [&](int xx, int yy) { return W1[(size_t)yy * pitch + xx]; };
+    auto dx = [&](int xx, int yy) {
+        return 0.5f * (at(min(xx + 1, w - 1), yy) - at(max(xx - 1, 0), yy));
+    };
+    auto dy = [&](int xx, int yy) {
+        return 0.5f * (at(xx, min(yy + 1, h - 1)) - at(xx, max(yy - 1, 0)));
+    };
+    const int xp = min(x + 1, w - 1), xm = max(x - 1, 0);
+    const int yp = min(y + 1, h - 1), ym = max(y - 1, 0);
+    const size_t p = (size_t)y * pitch + x;
+    const float Ix = dx(x, y), Iy = dy(x, y);
+    const float Ixx = 0.5f * (dx(xp, y) - dx(xm, y));
+    const float Ixy = 0.5f * (dx(x, yp) - dx(x, ym));
+    const float Iyy = 0.5f * (dy(x, yp) - dy(x, ym));
+    const size_t fo = (size_t)f * pfs;
+    const float Iz = at(x, y) - I0b[fo + p];
+    const float Ixz = Ix - I0xb[fo + p];
+    const float Iyz = Iy - I0yb[fo + p];
+    const float nd = 1.0f / (Ix * Ix + Iy * Iy + 0.01f);
+    const float ng = 1.0f / (Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + 0.01f);
+    float ad = delta * nd * psi_prime(nd * Iz * Iz);
+    float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
+    const float u = U[p], v = U[plane + p];
+    const float wx = (float)x + u, wy = (float)y + v;
+    if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) { ad = 0.0f; ag = 0.0f; }
+    const float ux = x + 1 < w ? U[p + 1] - u : 0.0f;
+    const float uy = y + 1 < h ? U[p + pitch] - u : 0.0f;
+    const float vx = x + 1 < w ? U[plane + p + 1] - v : 0.0f;
+    const float vy = y + 1 < h ? U[plane + p + pitch] - v : 0.0f;
+    wk[kA11 * plane + p] = ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy);
+    wk[kA12 * plane + p] = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
+    wk[kA22 * plane + p] = ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy);
+    wk[kB1 * plane + p] = -ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
+    wk[kB2 * plane + p] = -ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
+    wk[kAS * plane + p] = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
+    wk[kDU * plane + p] = 0.0f;
+    wk[kDV * plane + p] = 0.0f;
+}
+
+// One red-black half sweep: pixels with (x + y) & 1 == colour.
+__global__ void sor_kernel(int w, int h, int pitch, const float *__restrict__ Ub, size_t ufs,
+                           size_t plane, float *__restrict__ workb, size_t wfs, int colour,
+                           float omega)
+{
+    const int xh = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = 2 * xh + ((y + colour) & 1);
+    if (x >= w || y >= h) return;
+    const int f = blockIdx.z;
+    float *wk = workb + (size_t)f * wfs;
+    const float *U = Ub + (size_t)f * ufs;
+    const float *as = wk + kAS * plane;
+    float *du = wk + kDU * plane, *dv = wk + kDV * plane;
+    const size_t p = (size_t)y * pitch + x;
+    const float asp = as[p], up = U[p], vp = U[plane + p];
+    float sw = 0.0f, su = 0.0f, sv = 0.0f;
+    auto nb = [&](size_t q) {
+        const float wn = 0.5f * (asp + as[q]);
+        sw += wn;
+        su += wn * (U[q] + du[q] - up);
+        sv += wn * (U[plane + q] + dv[q] - vp);
+    };
+    if (x > 0) nb(p - 1);
+    if (x + 1 < w) nb(p + 1);
+    if (y > 0) nb(p - pitch);
+    if (y + 1 < h) nb(p + pitch);
+    const float a11 = wk[kA11 * plane + p] + sw, a12 = wk[kA12 * plane + p];
+    const float a22 = wk[kA22 * plane + p] + sw;
+    const float r1 = su + wk[kB1 * plane + p], r2 = sv + wk[kB2 * plane + p];
+    float d1 = du[p], d2 = dv[p];
+    if (a11 > 0.0f) d1 = (1.0f - omega) * d1 + omega * (r1 - a12 * d2) / a11;
+    if (a22 > 0.0f) d2 = (1.0f - omega) * d2 + omega * (r2 - a12 * d1) / a22;
+    du[p] = d1;
+    dv[p] = d2;
+}
+
+__global__ void add_kernel(int w, int h, int pitch, float *__restrict__ Ub, size_t ufs,
+                           size_t plane, const float *__restrict__ workb, size_t wfs)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const int f = blockIdx.z;
+    float *U = Ub + (size_t)f * ufs;
+    const float *wk = workb + (size_t)f * wfs;
+    const size_t p = (size_t)y * pitch + x;
+    U[p] += wk[kDU * plane + p];
+    U[plane + p] += wk[kDV * plane + p];
+}
+
+__global__ void flow_out_kernel(const float *__restrict__ Ub, int W, int H, int pitch,
+                                size_t ufs, size_t plane, float *__restrict__ flow)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    const int f = blockIdx.z;
+    const float *U = Ub + (size_t)f * ufs;
+    const size_t o = (size_t)f * 2 * W * H + (size_t)y * W + x;
+    flow[o] = U[(size_t)y * pitch + x];
+    flow[o + (size_t)W * H] = U[plane + (size_t)y * pitch + x];
+}
+
+template <int PS>
+void search_ps(const float *I0, const float *I0x, const float *I0y, const float *I1,
+               const Level &lv, size_t pfs, const float *Uc, const Level *lvc, size_t ucfs,
+               float *up, size_t upfs, int frames, const FlowParams &fp, int *err, cudaStream_t st)
+{
+    constexpr int G = PS <= 8 ? 8 : 16;
+    const int np = lv.npx * lv.npy;
+    const int per_block = 128 / G;
+    dim3 grd((np + per_block - 1) / per_block, frames);
+    patch_search_kernel<PS, G><<<grd, 128, 0, st>>>(
+        I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pfs, lv.npx, lv.npy, Uc, lvc ? lvc->w : 0,
+        lvc ? lvc->h : 0, lvc ? lvc->pitch : 0, lvc ? lvc->plane : 0, ucfs, up, upfs, fp.stride,
+        fp.gn_iters, err);
+}
+
+dim3 grid2d(int w, int h, int frames, dim3 blk)
+{
+    return dim3((w + blk.x - 1) / blk.x, (h + blk.y - 1) / blk.y, frames);
+}
+
+}  // namespace
+
+void init_flow_attributes() {}
+
+void launch_gradients(const float *I, float *Ix, float *Iy, int w, int h, int pitch,
+                      size_t frame_stride, int frames, cudaStream_t st)
+{
+    StageScope sc(kStPyramid, 1, st);
+    dim3 blk(32, 8);
+    gradients_kernel<<<grid2d(w, h, frames, blk), blk, 0, st>>>(I, Ix, Iy, w, h, pitch,
+                                                                frame_stride);
+}
+
+void launch_downsample(const float *I, int w, int h, int pitch, float *out, int wc, int hc,
+                       int pitch_c, size_t frame_stride, int frames, cudaStream_t st)
+{
+    (void)w; (void)h;
+    StageScope sc(kStPyramid, 1, st);
+    dim3 blk(32, 8);
+    downsample_kernel<<<grid2d(wc, hc, frames, blk), blk, 0, st>>>(I, pitch, out, wc, hc,
+                                                                   pitch_c, frame_stride);
+}
+
+void launch_patch_search(const float *I0, const float *I0x, const float *I0y, const float *I1,
+                         const Level &lv, size_t pyr_frame_stride, const float *Uc,
+                         const Level *lvc, size_t uc_frame_stride, float *up,
+                         size_t up_frame_stride, int frames, const FlowParams &fp, int *err,
+                         cudaStream_t st)
+{
+    if (lv.npx * lv.npy <= 0) return;
+    StageScope sc(kStSearch, 1, st);
+#define EBOF_PS(N)                                                                              \
+    case N:                                                                                     \
+        search_ps<N>(I0, I0x, I0y, I1, lv, pyr_frame_stride, Uc, lvc, uc_frame_stride, up,      \
+                     up_frame_stride, frames, fp, err, st);                                     \
+        break;
+    switch (fp.ps) {
+        EBOF_PS(4) EBOF_PS(5) EBOF_PS(6) EBOF_PS(7) EBOF_PS(8) EBOF_PS(9) EBOF_PS(10)
+        EBOF_PS(11) EBOF_PS(12) EBOF_PS(13) EBOF_PS(14) EBOF_PS(15) EBOF_PS(16)
+        default: break;
+    }
+#undef EBOF_PS
+}
+
+void launch_densify(const float *I0, const float *I1, const Level &lv, size_t pyr_frame_stride,
+                    const float *up, size_t up_frame_stride, float *U, size_t u_frame_stride,
+                    int frames, const FlowParams &fp, cudaStream_t st)
+{
+    StageScope sc(kStDensify, 1, st);
+    dim3 blk(32, 8);
+    densify_kernel<<<grid2d(lv.w, lv.h, frames, blk), blk, 0, st>>>(
+        I0, I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, up, up_frame_stride, lv.npx, lv.npy, U,
+        u_frame_stride, lv.plane, fp.ps, fp.stride);
+}
+
+void launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
+                        const Level &lv, size_t pyr_frame_stride, float *U,
+                        size_t u_frame_stride, float *work, size_t work_frame_stride,
+                        int frames, const FlowParams &fp, cudaStream_t st)
+{
+    dim3 blk(32, 8);
+    const dim3 grd = grid2d(lv.w, lv.h, frames, blk);
+    const dim3 grd_half = grid2d((lv.w + 1) / 2, lv.h, frames, blk);
+    for (int k = 0; k < fp.var_outer; ++k) {
+        {
+            StageScope sc(kStVarWarp, 1, st);
+            warp_kernel<<<grd, blk, 0, st>>>(I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, U,
+                                             u_frame_stride, lv.plane, work, work_frame_stride);
+        }
+        {
+            StageScope sc(kStVarCoeff, 1, st);
+            coeff_kernel<<<grd, blk, 0, st>>>(I0, I0x, I0y, lv.w, lv.h, lv.pitch,
+                                              pyr_frame_stride, U, u_frame_stride, lv.plane, work,
+                                              work_frame_stride, fp.delta, fp.gamma, fp.alpha_s);
+        }
+        if (fp.var_sor > 0) {
+            StageScope sc(kStVarSor, 2 * fp.var_sor, st);
+            for (int s = 0; s < fp.var_sor; ++s)
+                for (int colour = 0; colour < 2; ++colour)
+                    sor_kernel<<<grd_half, blk, 0, st>>>(lv.w, lv.h, lv.pitch, U, u_frame_stride,
+                                                         lv.plane, work, work_frame_stride,
+                                                         colour, fp.omega);
+        }
+        {
+            StageScope sc(kStVarAdd, 1, st);
+            add_kernel<<<grd, blk, 0, st>>>(lv.w, lv.h, lv.pitch, U, u_frame_stride, lv.plane,
+                                            work, work_frame_stride);
+        }
+    }
+}
+
+void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,
+                     float *flow, int frames, cudaStream_t st)
+{
+    StageScope sc(kStFlowOut, 1, st);
+    dim3 grd((W + 255) / 256, H, frames);
+    flow_out_kernel<<<grd, 256, 0, st>>>(U, W, H, pitch, u_frame_stride,
+                                         (size_t)pitch * H, flow);
+}
+
+}  // namespace ebof
