@@ -66,6 +66,7 @@ def _oracle_frame(args):
                                     n_d=prm["n_d"], n_f=prm["n_f"], alpha=prm["alpha"])
     U = oracle.flow(255.0 * s0["S"], 255.0 * s1["S"], levels=prm["levels"],
                     patch=prm["patch"], stride=prm["stride"], gn_iters=prm["gn_iters"],
+                    gn_damping=prm["gn_damping"],
                     var_outer=prm["var_outer"], var_sor=prm["var_sor"],
                     var_delta=prm["var_delta"], var_gamma=prm["var_gamma"],
                     var_alpha=prm["var_alpha"], sor_omega=prm["sor_omega"])
@@ -148,7 +149,7 @@ def run_reference(args, rank):
 def _reference_params():
     # the library's defaults for a 1280x720 sensor, written out (no library load)
     return dict(connectivity=8, n_d=1, n_f=9, alpha=1.08, levels=5, patch=12, stride=4,
-                gn_iters=12, var_outer=5, var_sor=5, var_delta=5.0, var_gamma=10.0,
+                gn_iters=12, gn_damping=0.1, var_outer=5, var_sor=5, var_delta=5.0, var_gamma=10.0,
                 var_alpha=20.0, sor_omega=1.6)
 
 

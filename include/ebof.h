@@ -67,6 +67,7 @@ typedef struct {
     int32_t patch;          /* patch side ps, 4 .. 16 */
     int32_t stride;         /* patch grid stride, >= 1 */
     int32_t gn_iters;       /* Gauss-Newton iterations per patch, >= 0 */
+    float gn_damping;       /* kappa: step solves (H + kappa trace(H) Id) d = b, >= 0 */
     int32_t var_outer;      /* variational fixed-point iterations, >= 0 */
     int32_t var_sor;        /* red-black SOR sweeps per fixed-point iteration, >= 0 */
     float var_delta;        /* data term weight */
@@ -91,7 +92,8 @@ typedef struct ebof_stream ebof_stream;
 
 /* Defaults for a width x height sensor: connectivity 8, n_d 1, filling off,
  * alpha 1.08 (§IV-A), 3 levels of 8x8 patches below 640 px width and 5 levels
- * of 12x12 patches from 640 px, stride 4, 12 Gauss-Newton iterations, 5 x 5
+ * of 12x12 patches from 640 px, stride 4, 12 Gauss-Newton iterations with
+ * damping 0.1, 5 x 5
  * variational iterations (delta 5, gamma 10, alpha 20, omega 1.6),
  * max_batch 1. */
 void ebof_default_params(ebof_params *p, int32_t width, int32_t height);

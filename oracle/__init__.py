@@ -71,11 +71,11 @@ def _declare(L):
     L.orc_levels_used.argtypes = [i32, i32, i32, i32]
     L.orc_levels_used.restype = i32
     L.orc_patch_search.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, i32,
-                                   i32, i32, vp, vp]
+                                   i32, i32, f64, vp, vp]
     L.orc_densify.argtypes = [i32, i32, vp, vp, i32, i32, vp, vp]
     L.orc_variational.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, f64,
                                   f64, f64, f64]
-    L.orc_flow.argtypes = [i32, i32, vp, vp, i32, i32, i32, i32, i32, i32, f64,
+    L.orc_flow.argtypes = [i32, i32, vp, vp, i32, i32, i32, i32, f64, i32, i32, f64,
                            f64, f64, f64, vp]
     L.orc_flow.restype = i32
 
@@ -86,7 +86,7 @@ def set_mutation(k: int) -> None:
 
 
 # Default flow parameters (readings F1-F6; see ebof_oracle.c).
-FLOW_DEFAULTS = dict(levels=3, patch=8, stride=4, gn_iters=12, var_outer=5,
+FLOW_DEFAULTS = dict(levels=3, patch=8, stride=4, gn_iters=12, gn_damping=0.1, var_outer=5,
                      var_sor=5, var_delta=5.0, var_gamma=10.0, var_alpha=20.0,
                      sor_omega=1.6)
 
@@ -174,7 +174,7 @@ def levels_used(width, height, levels, ps):
     return lib().orc_levels_used(width, height, levels, ps)
 
 
-def patch_search(I0, I0x, I0y, I1, Uc, ps, stride, iters):
+def patch_search(I0, I0x, I0y, I1, Uc, ps, stride, iters, kappa=0.1):
     """Readings F3-F4 at one level; returns patch flows [2][npy][npx] and flags."""
     H, W = I0.shape
     a = [np.ascontiguousarray(v, np.float64) for v in (I0, I0x, I0y, I1)]
@@ -188,7 +188,7 @@ def patch_search(I0, I0x, I0y, I1, Uc, ps, stride, iters):
         Uc = np.ascontiguousarray(Uc, np.float64)
         ucp, Wc, Hc = _p(Uc), Uc.shape[2], Uc.shape[1]
     lib().orc_patch_search(W, H, _p(a[0]), _p(a[1]), _p(a[2]), _p(a[3]), ucp,
-                           Wc, Hc, ps, stride, iters, _p(up), _p(fl))
+                           Wc, Hc, ps, stride, iters, float(kappa), _p(up), _p(fl))
     return up, fl
 
 
@@ -214,7 +214,7 @@ def variational(I0, I0x, I0y, I1, U, outer=5, sor=5, delta=5.0, gamma=10.0,
     return U
 
 
-def flow(I0, I1, levels=3, patch=8, stride=4, gn_iters=12, var_outer=5,
+def flow(I0, I1, levels=3, patch=8, stride=4, gn_iters=12, gn_damping=0.1, var_outer=5,
          var_sor=5, var_delta=5.0, var_gamma=10.0, var_alpha=20.0,
          sor_omega=1.6):
     """§III-D flow block on two level-0 intensity images (255 * d_exp).
@@ -225,7 +225,7 @@ def flow(I0, I1, levels=3, patch=8, stride=4, gn_iters=12, var_outer=5,
     H, W = I0.shape
     U = np.zeros((2, H, W), np.float64)
     lib().orc_flow(W, H, _p(I0), _p(I1), levels, patch, stride, gn_iters,
-                   var_outer, var_sor, var_delta, var_gamma, var_alpha,
+                   float(gn_damping), var_outer, var_sor, var_delta, var_gamma, var_alpha,
                    sor_omega, _p(U))
     return U
 

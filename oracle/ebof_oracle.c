@@ -215,8 +215,9 @@ double orc_alpha_from_dsat(double d_sat, double eps) { return -d_sat / log(eps);
  *      starts at 0, at finer levels at 2 * U_{l+1} sampled at the nearest
  *      coarse pixel (round half down of centre / 2, clamped to the image);
  *  F4  inverse-compositional Gauss-Newton on mean-normalised patches with a
- *      fixed iteration count, determinant guard 1e-6 * (ps^2)^2 and a reset
- *      to the start value when the patch drifts more than ps pixels;
+ *      fixed iteration count, determinant guard 1e-6 * (ps^2)^2, a damped
+ *      step (H + kappa * trace(H) * Id)^-1 b, and a reset to the start value
+ *      when the patch drifts more than ps pixels;
  *  F5  densification weights 1 / max(1, |I1(x + u_i) - I0(x)|) over every
  *      patch whose square contains x;
  *  F6  variational refinement: normalised data and gradient-constancy
@@ -307,10 +308,15 @@ int orc_levels_used(int W, int H, int levels, int ps)
  * I1: current-window level image (query); Uc: dense flow of the next coarser
  * level (Wc x Hc, planar u then v) or NULL at the coarsest level.
  * up: patch flows, planar [2][npy][npx]; flags: 0 = searched, 1 = determinant
- * guard (kept its start value), 2 = reset after drifting more than ps. */
+ * guard (kept its start value), 2 = reset after drifting more than ps.
+ * The Gauss-Newton step solves (H + mu Id) Delta = b with mu = kappa *
+ * trace(H): on an edge-like patch (the aperture problem) H is nearly
+ * singular and the undamped step wanders along the edge; the damping keeps
+ * that component near its start value and leaves well-textured patches
+ * (eigenvalues of the same order) converging as before. */
 void orc_patch_search(int W, int H, const double *I0, const double *I0x,
                       const double *I0y, const double *I1, const double *Uc,
-                      int Wc, int Hc, int ps, int stride, int iters,
+                      int Wc, int Hc, int ps, int stride, int iters, double kappa,
                       double *up, uint8_t *flags)
 {
     int *ox = (int *)malloc(sizeof(int) * (size_t)(W + 1));
@@ -349,6 +355,8 @@ void orc_patch_search(int W, int H, const double *I0, const double *I0x,
             }
             double det = h11 * h22 - h12 * h12;
             size_t id = (size_t)j * npx + i;
+            double mu = kappa * (h11 + h22);
+            double a11 = h11 + mu, a22 = h22 + mu, adet = a11 * a22 - h12 * h12;
             if (det <= 1e-6 * (double)n * (double)n) {
                 up[id] = u0; up[np + id] = v0; flags[id] = 1;
                 continue;
@@ -366,8 +374,8 @@ void orc_patch_search(int W, int H, const double *I0, const double *I0x,
                     double r = (w[q] - mw) - (T[q] - mT);
                     b1 += gx[q] * r; b2 += gy[q] * r;
                 }
-                double du = (h22 * b1 - h12 * b2) / det;
-                double dv = (h11 * b2 - h12 * b1) / det;
+                double du = (a22 * b1 - h12 * b2) / adet;
+                double dv = (a11 * b2 - h12 * b1) / adet;
                 if (orc_mutation == 6) { u += du; v += dv; }
                 else { u -= du; v -= dv; }
             }
@@ -511,7 +519,7 @@ void orc_variational(int W, int H, const double *I0, const double *I0x,
  * level-0 intensities (255 * d_exp) of the previous and current windows.
  * U_out: planar [2][H][W].  Returns the number of levels used. */
 int orc_flow(int W, int H, const double *I0, const double *I1, int levels,
-             int ps, int stride, int iters, int var_outer, int var_sor,
+             int ps, int stride, int iters, double kappa, int var_outer, int var_sor,
              double delta, double gamma, double alpha_s, double omega,
              double *U_out)
 {
@@ -549,7 +557,7 @@ int orc_flow(int W, int H, const double *I0, const double *I1, int levels,
         uint8_t *fl = (uint8_t *)malloc((size_t)npx * npy);
         double *U = (double *)malloc(sizeof(double) * 2 * (size_t)w * h);
         orc_patch_search(w, h, A[l], Ax[l], Ay[l], B[l], Uc, Wc, Hc, ps, stride,
-                         iters, up, fl);
+                         iters, kappa, up, fl);
         orc_densify(w, h, A[l], B[l], ps, stride, up, U);
         orc_variational(w, h, A[l], Ax[l], Ay[l], B[l], U, var_outer, var_sor,
                         delta, gamma, alpha_s, omega);

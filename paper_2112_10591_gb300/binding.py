@@ -37,6 +37,7 @@ class ebof_params(ctypes.Structure):
         ("alpha", ctypes.c_float),
         ("levels", ctypes.c_int32), ("patch", ctypes.c_int32),
         ("stride", ctypes.c_int32), ("gn_iters", ctypes.c_int32),
+        ("gn_damping", ctypes.c_float),
         ("var_outer", ctypes.c_int32), ("var_sor", ctypes.c_int32),
         ("var_delta", ctypes.c_float), ("var_gamma", ctypes.c_float),
         ("var_alpha", ctypes.c_float), ("sor_omega", ctypes.c_float),

@@ -131,7 +131,7 @@ ebof_status check_params(const ebof_params *p)
     if (p->stride < 1 || p->gn_iters < 0 || p->gn_iters > 10000) return EBOF_ERR_INVALID_ARG;
     if (p->var_outer < 0 || p->var_outer > 1000 || p->var_sor < 0 || p->var_sor > 1000)
         return EBOF_ERR_INVALID_ARG;
-    if (!finite_nonneg(p->var_delta) || !finite_nonneg(p->var_gamma) ||
+    if (!finite_nonneg(p->gn_damping) || !finite_nonneg(p->var_delta) || !finite_nonneg(p->var_gamma) ||
         !finite_nonneg(p->var_alpha))
         return EBOF_ERR_INVALID_ARG;
     if (!(p->sor_omega > 0.0f && p->sor_omega < 2.0f)) return EBOF_ERR_INVALID_ARG;
@@ -161,6 +161,7 @@ FlowParams flow_params(const ebof_params &p)
     fp.ps = p.patch;
     fp.stride = p.stride;
     fp.gn_iters = p.gn_iters;
+    fp.gn_damping = p.gn_damping;
     fp.var_outer = p.var_outer;
     fp.var_sor = p.var_sor;
     fp.delta = p.var_delta;
@@ -290,6 +291,7 @@ void ebof_default_params(ebof_params *p, int32_t width, int32_t height)
     p->patch = hr ? 12 : 8;
     p->stride = 4;
     p->gn_iters = 12;
+    p->gn_damping = 0.1f;
     p->var_outer = 5;
     p->var_sor = 5;
     p->var_delta = 5.0f;

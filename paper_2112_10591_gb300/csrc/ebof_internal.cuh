@@ -50,6 +50,7 @@ struct DevStats {
 
 struct FlowParams {
     int ps, stride, gn_iters;
+    float gn_damping;
     int var_outer, var_sor;
     float delta, gamma, alpha_s, omega;
 };

@@ -84,7 +84,7 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
                     const float *__restrict__ I0yb, const float *__restrict__ I1b, int w, int h,
                     int pitch, size_t pfs, int npx, int npy, const float *__restrict__ Ucb, int wc,
                     int hc, int pitch_c, size_t plane_c, size_t ucfs, float *__restrict__ upb,
-                    size_t upfs, int stride, int iters, int *err)
+                    size_t upfs, int stride, int iters, float kappa, int *err)
 {
     const int f = blockIdx.y;
     const int c = threadIdx.x % G;
@@ -135,7 +135,10 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
     h11 = group_sum<G>(h11); h12 = group_sum<G>(h12); h22 = group_sum<G>(h22);
     const float det = h11 * h22 - h12 * h12;
     const bool guard = !(det > 1e-6f * (float)(PS * PS) * (float)(PS * PS));
-    const float inv_det = guard ? 0.0f : 1.0f / det;
+    // damped step (H + mu Id)^-1 b, mu = kappa * trace(H)
+    const float mu = kappa * (h11 + h22);
+    const float a11 = h11 + mu, a22 = h22 + mu;
+    const float inv_det = guard ? 0.0f : 1.0f / (a11 * a22 - h12 * h12);
 
     float u = u0, v = v0;
     for (int it = 0; it < iters; ++it) {
@@ -155,8 +158,8 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
             b1 += GX[r] * res; b2 += GY[r] * res;
         }
         b1 = group_sum<G>(b1); b2 = group_sum<G>(b2);
-        u -= (h22 * b1 - h12 * b2) * inv_det;
-        v -= (h11 * b2 - h12 * b1) * inv_det;
+        u -= (a22 * b1 - h12 * b2) * inv_det;
+        v -= (a11 * b2 - h12 * b1) * inv_det;
     }
     if (guard || !(hypotf(u - u0, v - v0) <= (float)PS)) { u = u0; v = v0; }
     if (real && c == 0) {
@@ -363,7 +366,7 @@ void search_ps(const float *I0, const float *I0x, const float *I0y, const float 
     patch_search_kernel<PS, G><<<grd, 128, 0, st>>>(
         I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pfs, lv.npx, lv.npy, Uc, lvc ? lvc->w : 0,
         lvc ? lvc->h : 0, lvc ? lvc->pitch : 0, lvc ? lvc->plane : 0, ucfs, up, upfs, fp.stride,
-        fp.gn_iters, err);
+        fp.gn_iters, fp.gn_damping, err);
 }
 
 dim3 grid2d(int w, int h, int frames, dim3 blk)

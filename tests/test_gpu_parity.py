@@ -67,7 +67,8 @@ def oracle_surface(prm, W, H, x, y, t, tb, te):
 
 def oracle_flow(prm, I0, I1):
     return oracle.flow(I0, I1, levels=prm.levels, patch=prm.patch, stride=prm.stride,
-                       gn_iters=prm.gn_iters, var_outer=prm.var_outer, var_sor=prm.var_sor,
+                       gn_iters=prm.gn_iters, gn_damping=float(prm.gn_damping),
+                       var_outer=prm.var_outer, var_sor=prm.var_sor,
                        var_delta=float(prm.var_delta), var_gamma=float(prm.var_gamma),
                        var_alpha=float(prm.var_alpha), sor_omega=float(prm.sor_omega))
 

@@ -337,6 +337,24 @@ def test_event_surface_integer_shift():
     del inner
 
 
+def test_flow_is_well_conditioned():
+    # Rounding the input surfaces to FP32 must move the flow only a little:
+    # the damped Gauss-Newton step keeps edge-like (aperture) patches from
+    # drifting and flipping the reset rule.  With the undamped step this
+    # scene moves by 0.032 px on average; damped, by 0.007 px.
+    from paper_2112_10591_gb300 import synth
+    W, H = 640, 360
+    s = synth.rigid_objects(width=W, height=H, n_windows=2, events=(60000, 100000), seed=4)
+    S = []
+    for k in range(2):
+        x, y, t, _, tb, te = s.window(k)
+        S.append(255.0 * oracle.surface_from_events(W, H, x, y, t, tb, te)["S"])
+    S32 = [a.astype(np.float32).astype(np.float64) for a in S]
+    U = oracle.flow(S[0], S[1], levels=4, patch=12)
+    U32 = oracle.flow(S32[0], S32[1], levels=4, patch=12)
+    assert np.hypot(*(U - U32)).mean() <= 0.015
+
+
 def test_transpose_symmetry():
     I0, I1 = _texture(96, 96), _texture(96, 96, (1.7, 0.9))
     U = oracle.flow(I0, I1)
