@@ -167,6 +167,28 @@ ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_o
 ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32_t *d_scratch,
                      int32_t *d_edt, float *d_surface, float alpha, void *cuda_stream);
 
+/* ebof_edt without caller scratch, for callers that cannot allocate device
+ * memory: code that must not call cudaMalloc once running (a real-time loop
+ * where an allocation may synchronise the device and has no latency bound),
+ * code inside a host framework that owns all device memory through its own
+ * allocator, or code running while a stream is being captured, where
+ * cudaMalloc is not allowed.  The paper has no counterpart; this is a
+ * deployment variant of the separable EDT entry point above.
+ * Same inputs, outputs and result as ebof_edt, but the column distances are
+ * kept in a static device array of 2^21 int32 (8 MiB) that every device
+ * which loads the library holds until the process exits, so width*height
+ * must not exceed 2^21 (EBOF_ERR_INVALID_ARG otherwise).  The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, and each call
+ * overwrites every entry it reads, so nothing carries over from the previous
+ * call; calls that overlap on the GPU (on different streams, or from
+ * different threads without ordering) race on the array and give wrong
+ * results. */
+ebof_status ebof_edt_static(const uint8_t *d_edge, int32_t width, int32_t height,
+                            int32_t *d_edt, float *d_surface, float alpha, void *cuda_stream);
+
 /* ---- tracing: per-stage CUDA-event timing (§IV Table VII reports per-block
  * times; these are the GPU equivalents).  Timing brackets each stage's
  * launches with cudaEvents on the caller's stream; it is off by default. */

@@ -96,6 +96,7 @@ def _declare(L):
     L.ebof_process_window_host.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, vp]
     L.ebof_stream_sync.argtypes = [vp, P(ebof_window_stats), i32]
     L.ebof_edt.argtypes = [vp, i32, i32, vp, vp, vp, f32, vp]
+    L.ebof_edt_static.argtypes = [vp, i32, i32, vp, vp, f32, vp]
     L.ebof_stream_set_profiling.argtypes = [vp, i32]
     L.ebof_stream_get_profile.argtypes = [vp, P(ctypes.c_double), P(i64), i32]
     L.ebof_stage_name.argtypes = [i32]
@@ -107,7 +108,7 @@ def _declare(L):
     for name in ("ebof_stream_create", "ebof_stream_destroy", "ebof_stream_reset",
                  "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
                  "ebof_process_window_host", "ebof_stream_sync", "ebof_edt",
-                 "ebof_stream_set_profiling", "ebof_stream_get_profile"):
+                 "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -277,6 +278,18 @@ def ebof_edt(edge, width: int, height: int, scratch, edt, surface=None, alpha: f
                            _ptr(edt, torch.int32, n, "edt"),
                            _ptr(surface, torch.float32, n, "surface"), float(alpha),
                            _stream_handle(cuda_stream))
+
+
+def ebof_edt_static(edge, width: int, height: int, edt, surface=None, alpha: float = 1.08,
+                    cuda_stream=None) -> int:
+    """ebof_edt with the library's static scratch: for callers that cannot
+    allocate device memory (width * height <= 2**21)."""
+    import torch
+    n = int(width) * int(height)
+    return load().ebof_edt_static(_ptr(edge, torch.uint8, n, "edge"), int(width), int(height),
+                                  _ptr(edt, torch.int32, n, "edt"),
+                                  _ptr(surface, torch.float32, n, "surface"), float(alpha),
+                                  _stream_handle(cuda_stream))
 
 
 EBOF_STAGE_COUNT = 12
