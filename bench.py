@@ -427,9 +427,19 @@ def main():
             if world > 1:
                 dist.all_reduce(tb_, op=dist.ReduceOp.MAX)
             bms = float(tb_.item())
+            eb.check(eb.ebof_stream_set_profiling(sb, True))
+            step_batched()
+            torch.cuda.synchronize(dev)
+            _, bprof = eb.ebof_stream_get_profile(sb)
+            eb.ebof_stream_set_profiling(sb, False)
+            btot = sum(v[0] for v in bprof.values()) or 1.0
             batched = {"value": frames_per_step * args.steps * world / (bms / 1000.0),
                        "unit": UNIT, "windows_per_call": B,
-                       "ms_per_step": bms / args.steps}
+                       "ms_per_step": bms / args.steps,
+                       "stage_ms_per_frame": {k: round(v[0] / frames_per_step, 4)
+                                              for k, v in bprof.items() if v[1]},
+                       "stage_share": {k: round(v[0] / btot, 4) for k, v in bprof.items()
+                                       if v[1]}}
             sb.close()
         else:
             batched = {"unavailable": eb.ebof_status_string(stb)}

@@ -241,8 +241,10 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
             launch_patch_search(I0, I0 + lv.plane, I0 + 2 * lv.plane, I1, lv, s->pyr_fs, Uc, lvc,
                                 s->u_fs, s->up, s->up_fs, nf, fp, s->d_err, st);
             launch_densify(I0, I1, lv, s->pyr_fs, s->up, s->up_fs, Ucur, s->u_fs, nf, fp, st);
-            launch_variational(I0, I0 + lv.plane, I0 + 2 * lv.plane, I1, lv, s->pyr_fs, Ucur,
-                               s->u_fs, s->work, s->work_fs, nf, fp, st);
+            // the coarser flow is consumed by the search: its buffer is free
+            float *Utmp = (Ucur == s->Ua) ? s->Ub : s->Ua;
+            Ucur = launch_variational(I0, I0 + lv.plane, I0 + 2 * lv.plane, I1, lv, s->pyr_fs,
+                                      Ucur, Utmp, s->u_fs, s->work, s->work_fs, nf, fp, st);
             Uc = Ucur;
             lvc = &lv;
         }

@@ -1,0 +1,30 @@
+// dev_common.cuh -- small device helpers shared by the flow kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ebof {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// Bilinear sample with the position clamped to [0, w-1] x [0, h-1].
+__device__ __forceinline__ float bilinear(const float *__restrict__ I, int w, int h, int pitch,
+                                          float x, float y)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
+    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
+    const float xf = floorf(x), yf = floorf(y);
+    const int x0 = (int)xf, y0 = (int)yf;
+    const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+    const float fx = x - xf, fy = y - yf;
+    const float a = I[(size_t)y0 * pitch + x0], b = I[(size_t)y0 * pitch + x1];
+    const float c = I[(size_t)y1 * pitch + x0], d = I[(size_t)y1 * pitch + x1];
+    return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
+}
+
+// Robust penaliser derivative Psi'(s^2) = 1 / (2 sqrt(s^2 + eps^2)), eps = 1e-3.
+__device__ __forceinline__ float psi_prime(float s2) { return 0.5f * rsqrtf(s2 + 1e-6f); }
+
+constexpr float kZeta2 = 0.01f;  // zeta^2 of the constraint normalisation
+
+}  // namespace ebof

@@ -104,11 +104,18 @@ void launch_densify(const float *I0, const float *I1, const Level &lv, size_t py
                     const float *up, size_t up_frame_stride, float *U, size_t u_frame_stride,
                     int frames, const FlowParams &fp, cudaStream_t st);
 
-// A8: variational refinement of U in place.
-void launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
-                        const Level &lv, size_t pyr_frame_stride, float *U,
-                        size_t u_frame_stride, float *work, size_t work_frame_stride,
-                        int frames, const FlowParams &fp, cudaStream_t st);
+// A8: variational refinement of U.  Returns the buffer holding the result:
+// U itself, or Utmp (same shape as U) when the fused kernel ping-pongs.
+float *launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
+                          const Level &lv, size_t pyr_frame_stride, float *U, float *Utmp,
+                          size_t u_frame_stride, float *work, size_t work_frame_stride,
+                          int frames, const FlowParams &fp, cudaStream_t st);
+bool var_fused_supported(int var_sor);
+void init_var_attributes();
+float *launch_variational_fused(const float *I0, const float *I0x, const float *I0y,
+                                const float *I1, const Level &lv, size_t pyr_frame_stride,
+                                float *U, float *Utmp, size_t u_frame_stride, int frames,
+                                const FlowParams &fp, cudaStream_t st);
 
 // A9: level-0 flow to the caller's dense planar layout.
 void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,

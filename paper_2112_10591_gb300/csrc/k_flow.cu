@@ -13,27 +13,11 @@
 // FP64 oracle this library is tested against.
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
+#include "dev_common.cuh"
 
 namespace ebof {
 
 namespace {
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-// Bilinear sample with the position clamped to [0, w-1] x [0, h-1].
-__device__ __forceinline__ float bilinear(const float *__restrict__ I, int w, int h, int pitch,
-                                          float x, float y)
-{
-    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
-    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
-    const float xf = floorf(x), yf = floorf(y);
-    const int x0 = (int)xf, y0 = (int)yf;
-    const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
-    const float fx = x - xf, fy = y - yf;
-    const float a = I[(size_t)y0 * pitch + x0], b = I[(size_t)y0 * pitch + x1];
-    const float c = I[(size_t)y1 * pitch + x0], d = I[(size_t)y1 * pitch + x1];
-    return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
-}
 
 // ---------------------------------------------------------------- A5
 __global__ void gradients_kernel(const float *__restrict__ I, float *__restrict__ Ix,
@@ -113,7 +97,7 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
 
     // F4: template, mean-normalised gradients, Hessian
     float T[PS], GX[PS], GY[PS];
-    float sT = 0.0f, sgx = 0.0f, sgy = 0.0f;
+    float sgx = 0.0f, sgy = 0.0f;
     const int xc = active ? x0 + c : x0;
 #pragma unroll
     for (int r = 0; r < PS; ++r) {
@@ -121,11 +105,11 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
         T[r] = active ? I0[p] : 0.0f;
         GX[r] = active ? I0x[p] : 0.0f;
         GY[r] = active ? I0y[p] : 0.0f;
-        sT += T[r]; sgx += GX[r]; sgy += GY[r];
+        sgx += GX[r]; sgy += GY[r];
     }
     constexpr float inv_n = 1.0f / (PS * PS);
-    sT = group_sum<G>(sT); sgx = group_sum<G>(sgx); sgy = group_sum<G>(sgy);
-    const float mT = sT * inv_n, mgx = sgx * inv_n, mgy = sgy * inv_n;
+    sgx = group_sum<G>(sgx); sgy = group_sum<G>(sgy);
+    const float mgx = sgx * inv_n, mgy = sgy * inv_n;
     float h11 = 0.0f, h12 = 0.0f, h22 = 0.0f;
 #pragma unroll
     for (int r = 0; r < PS; ++r) {
@@ -138,23 +122,54 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
     // damped step (H + mu Id)^-1 b, mu = kappa * trace(H)
     const float mu = kappa * (h11 + h22);
     const float a11 = h11 + mu, a22 = h22 + mu;
-    const float inv_det = guard ? 0.0f : 1.0f / (a11 * a22 - h12 * h12);
+    const float inv_det = guard ? 0.0f : __fdividef(1.0f, a11 * a22 - h12 * h12);
+
 
     float u = u0, v = v0;
+    const float lim = (float)(w + h);
     for (int it = 0; it < iters; ++it) {
+        // The displacement is the same for the whole patch: when every
+        // sample of the patch and its right/lower neighbour lies inside the
+        // image, the clamped bilinear sample reduces to fixed weights on a
+        // fixed (PS+1) x (PS+1) window, and each row's horizontal lerp serves
+        // two output rows.
+        const float uc = fminf(fmaxf(u, -lim), lim), vc = fminf(fmaxf(v, -lim), lim);
+        const float fu = floorf(uc), fv = floorf(vc);
+        const int sx0 = x0 + (int)fu, sy0 = y0 + (int)fv;
+        const float ax = uc - fu, ay = vc - fv;
+        const bool fast = sx0 >= 0 && sy0 >= 0 && sx0 + PS <= w - 1 && sy0 + PS <= h - 1 &&
+                          uc == u && vc == v;
         float Wv[PS];
-        float sw = 0.0f;
-        const float xs = (float)xc + u;
+        if (fast) {
+            if (active) {
+                const float *pp = I1 + (size_t)sy0 * pitch + sx0 + c;
+                float a = pp[0], b = pp[1];
+                float hp = a + ax * (b - a);
 #pragma unroll
-        for (int r = 0; r < PS; ++r) {
-            Wv[r] = active ? bilinear(I1, w, h, pitch, xs, (float)(y0 + r) + v) : 0.0f;
-            sw += Wv[r];
+                for (int r = 0; r < PS; ++r) {
+                    const float *q = pp + (size_t)(r + 1) * pitch;
+                    const float c2 = q[0], d2 = q[1];
+                    const float hn = c2 + ax * (d2 - c2);
+                    Wv[r] = hp + ay * (hn - hp);
+                    hp = hn;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < PS; ++r) Wv[r] = 0.0f;
+            }
+        } else {
+            const float xs = (float)xc + u;
+#pragma unroll
+            for (int r = 0; r < PS; ++r)
+                Wv[r] = active ? bilinear(I1, w, h, pitch, xs, (float)(y0 + r) + v) : 0.0f;
         }
-        const float mw = group_sum<G>(sw) * inv_n;
+        // b = sum g ((w - mean w) - (T - mean T)); the mean-normalised
+        // gradients sum to zero, so both means drop out of b: b = sum g (w - T)
+        // (exactly zero when the warped patch equals the template)
         float b1 = 0.0f, b2 = 0.0f;
 #pragma unroll
         for (int r = 0; r < PS; ++r) {
-            const float res = active ? (Wv[r] - mw) - (T[r] - mT) : 0.0f;
+            const float res = Wv[r] - T[r];
             b1 += GX[r] * res; b2 += GY[r] * res;
         }
         b1 = group_sum<G>(b1); b2 = group_sum<G>(b2);
@@ -236,8 +251,6 @@ __global__ void warp_kernel(const float *__restrict__ I1b, int w, int h, int pit
         bilinear(I1b + (size_t)f * pfs, w, h, pitch, (float)x + U[p], (float)y + U[plane + p]);
 }
 
-__device__ __forceinline__ float psi_prime(float s2) { return 0.5f * rsqrtf(s2 + 1e-6f); }
-
 __global__ void coeff_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
                              const float *__restrict__ I0yb, int w, int h, int pitch, size_t pfs,
                              const float *__restrict__ Ub, size_t ufs, size_t plane,
@@ -269,8 +282,8 @@ __global__ void coeff_kernel(const float *__restrict__ I0b, const float *__restr
     const float Iz = at(x, y) - I0b[fo + p];
     const float Ixz = Ix - I0xb[fo + p];
     const float Iyz = Iy - I0yb[fo + p];
-    const float nd = 1.0f / (Ix * Ix + Iy * Iy + 0.01f);
-    const float ng = 1.0f / (Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + 0.01f);
+    const float nd = 1.0f / (Ix * Ix + Iy * Iy + kZeta2);
+    const float ng = 1.0f / (Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
     float ad = delta * nd * psi_prime(nd * Iz * Iz);
     float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
     const float u = U[p], v = U[plane + p];
@@ -376,7 +389,7 @@ dim3 grid2d(int w, int h, int frames, dim3 blk)
 
 }  // namespace
 
-void init_flow_attributes() {}
+void init_flow_attributes() { init_var_attributes(); }
 
 void launch_gradients(const float *I, float *Ix, float *Iy, int w, int h, int pitch,
                       size_t frame_stride, int frames, cudaStream_t st)
@@ -429,11 +442,16 @@ void launch_densify(const float *I0, const float *I1, const Level &lv, size_t py
         u_frame_stride, lv.plane, fp.ps, fp.stride);
 }
 
-void launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
-                        const Level &lv, size_t pyr_frame_stride, float *U,
-                        size_t u_frame_stride, float *work, size_t work_frame_stride,
-                        int frames, const FlowParams &fp, cudaStream_t st)
+float *launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
+                          const Level &lv, size_t pyr_frame_stride, float *U, float *Utmp,
+                          size_t u_frame_stride, float *work, size_t work_frame_stride,
+                          int frames, const FlowParams &fp, cudaStream_t st)
 {
+    if (fp.var_outer <= 0) return U;
+    if (var_fused_supported(fp.var_sor))
+        return launch_variational_fused(I0, I0x, I0y, I1, lv, pyr_frame_stride, U, Utmp,
+                                        u_frame_stride, frames, fp, st);
+    // many sweeps: one launch per step, state in global memory
     dim3 blk(32, 8);
     const dim3 grd = grid2d(lv.w, lv.h, frames, blk);
     const dim3 grd_half = grid2d((lv.w + 1) / 2, lv.h, frames, blk);
@@ -463,6 +481,7 @@ void launch_variational(const float *I0, const float *I0x, const float *I0y, con
                                             work, work_frame_stride);
         }
     }
+    return U;
 }
 
 void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,

@@ -114,47 +114,101 @@ __global__ void fill_kernel(const uint8_t *__restrict__ Ed, uint8_t *__restrict_
 }
 
 // ---------------------------------------------------------------- A3
-// One thread per (column, frame): distance to the nearest edge pixel above
-// (forward sweep) and below (backward sweep).  Columns without any edge
-// pixel get G_INF = W + H, larger than any distance in the image.
-__global__ void edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W,
-                                int H, int32_t *__restrict__ g, int gpitch, size_t gfs)
+// Column pass: g(x, y) = distance to the nearest edge pixel in column x, or
+// G_INF = W + H for a column without any (larger than any in-image
+// distance).  A block covers 32 columns; thread (c, k) owns column c's
+// chunk k of CH rows (CH a multiple of 32, at most 512).  It packs its
+// chunk into bit masks, publishes the first and last edge row of the chunk,
+// and after one barrier finds, for each row, the nearest edge pixel above
+// (highest set bit at or above the row, else the previous chunks) and below
+// (lowest set bit at or below, else the next chunks) with bit scans.  Row
+// writes of a warp are 32 consecutive int32.
+constexpr int kColMaxWords = 16;   // CH <= 512 rows
+constexpr int kColMaxChunks = 32;  // chunks per column
+
+__global__ void __launch_bounds__(1024)
+edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, int H,
+                int32_t *__restrict__ g, int gpitch, size_t gfs, int CH)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= W) return;
-    const uint8_t *e = E + (size_t)blockIdx.y * efs + x;
-    int32_t *gc = g + (size_t)blockIdx.y * gfs + x;
-    const int ginf = W + H;
-    int last = -1;
-    for (int y = 0; y < H; ++y) {
-        if (e[(size_t)y * epitch]) last = y;
-        gc[(size_t)y * gpitch] = last < 0 ? ginf : y - last;
-    }
-    last = -1;
-    for (int y = H - 1; y >= 0; --y) {
-        if (e[(size_t)y * epitch]) last = y;
-        if (last >= 0) {
-            const int d = last - y;
-            int32_t *q = gc + (size_t)y * gpitch;
-            if (d < *q) *q = d;
+    __shared__ int s_first[kColMaxChunks][32], s_last[kColMaxChunks][32];
+    const int c = threadIdx.x, k = threadIdx.y, nch = blockDim.y;
+    const int x = blockIdx.x * 32 + c;
+    const bool colok = x < W;
+    const uint8_t *e = E + (size_t)blockIdx.y * efs;
+    const int y0 = k * CH, y1 = min(H, y0 + CH);
+    const int nw = (CH + 31) / 32;
+    unsigned mask[kColMaxWords];
+    int first = -1, last = -1;
+#pragma unroll
+    for (int wi = 0; wi < kColMaxWords; ++wi) {
+        unsigned m = 0;
+        if (wi < nw && colok) {
+            for (int b = 0; b < 32; ++b) {
+                const int y = y0 + wi * 32 + b;
+                if (y < y1 && e[(size_t)y * epitch + x]) m |= 1u << b;
+            }
         }
+        mask[wi] = m;
+        if (m) {
+            if (first < 0) first = y0 + wi * 32 + __ffs(m) - 1;
+            last = y0 + wi * 32 + 31 - __clz(m);
+        }
+    }
+    s_first[k][c] = first;
+    s_last[k][c] = last;
+    __syncthreads();
+    if (!colok || y0 >= H) return;
+    int above = -1, below = -1;
+    for (int j = k - 1; j >= 0; --j)
+        if (s_last[j][c] >= 0) { above = s_last[j][c]; break; }
+    for (int j = k + 1; j < nch; ++j)
+        if (s_first[j][c] >= 0) { below = s_first[j][c]; break; }
+    const int ginf = W + H;
+    int32_t *gc = g + (size_t)blockIdx.y * gfs + x;
+    int run_above = above;  // nearest edge row before word wi
+#pragma unroll
+    for (int wi = 0; wi < kColMaxWords; ++wi) {
+        if (wi >= nw) break;
+        int next_first = below;  // nearest edge row after word wi
+#pragma unroll
+        for (int wj = kColMaxWords - 1; wj > wi; --wj)
+            if (wj < nw && mask[wj]) next_first = y0 + wj * 32 + __ffs(mask[wj]) - 1;
+        const unsigned m = mask[wi];
+        for (int b = 0; b < 32; ++b) {
+            const int y = y0 + wi * 32 + b;
+            if (y >= y1) break;
+            const unsigned up = m & (0xffffffffu >> (31 - b));  // bits 0..b
+            const unsigned dn = m & (0xffffffffu << b);         // bits b..31
+            const int a = up ? y0 + wi * 32 + 31 - __clz(up) : run_above;
+            const int bl = dn ? y0 + wi * 32 + __ffs(dn) - 1 : next_first;
+            int d = ginf;
+            if (a >= 0) d = y - a;
+            if (bl >= 0 && bl - y < d) d = bl - y;
+            gc[(size_t)y * gpitch] = d;
+        }
+        if (m) run_above = y0 + wi * 32 + 31 - __clz(m);
     }
 }
 
 // ---------------------------------------------------------------- A4
-// Row pass, one warp per row.  The row's column distances h(x') = g(x', y)^2
-// are staged in shared memory.  Each lane owns a band of ceil(W / 32)
-// consecutive columns and builds the lower envelope of the parabolas
-// f_x'(x) = (x - x')^2 + h(x') of its band's columns (the stack construction
-// of the separable exact EDT, with exact integer breakpoint comparisons).
-// D(x) is the minimum over all bands' envelopes: the lane's own envelope is
-// walked in step with x; the other bands are visited nearest first, skipped
-// once (distance to the band)^2 reaches the best value so far, and each is
-// evaluated at x by binary search over its breakpoints.  The result is the
-// exact minimum, hence bit-identical to any other exact EDT.  The epilogue
-// applies Eq. 1 and the 8-bit scale, and writes through shared memory so
-// that global stores are coalesced.
-constexpr int kRowWarpsMax = 4;  // rows per block
+// Row pass: D(x) = min over columns x' of (x - x')^2 + h(x'), h(x') =
+// g(x', y)^2 -- the lower envelope of the row's parabolas, evaluated at every
+// pixel.  WPR warps serve one row; the row is cut into NB = 32 * WPR bands of
+// B = ceil(W / NB) columns, one band per lane.
+//  1. The row's h is staged in shared memory (-1: column without edge pixels).
+//  2. Each lane builds the lower envelope of its band's parabolas (the stack
+//     construction of the separable exact EDT; breakpoints compared exactly
+//     in 64-bit integers).
+//  3. Each lane walks its band's pixels left to right.  For every band within
+//     kRowNear bands it keeps a pointer into that band's envelope and moves it
+//     forward while the next parabola is not higher at x; since the owner of x
+//     within one envelope never moves left as x grows, the walk costs O(1) per
+//     pixel on average.  Farther bands are visited (nearest first, binary
+//     search for the owner) only while their distance^2 is below the best
+//     value so far.
+//  4. Eq. 1 and the 8-bit scale, with coalesced stores.
+// Every step is an exact integer minimum, so D is bit-identical to any exact EDT.
+constexpr int kRowNear = 2;
 
 // With sites a < b < c on an envelope, is b hidden once c arrives?
 // Breakpoint s(p, q) = ((h_q + q^2) - (h_p + p^2)) / (2 (q - p)) for p < q;
@@ -167,91 +221,129 @@ __device__ __forceinline__ bool hidden(int a, int b, int c, const int32_t *h)
     return (fc - fb) * (long long)(b - a) <= (fb - fa) * (long long)(c - b);
 }
 
-__device__ __forceinline__ long long para(int x, int site, const int32_t *h)
+// (x - site)^2 + h(site) < 2^29 for images up to 16384 px a side.
+__device__ __forceinline__ int para(int x, int site, const int32_t *h)
 {
-    const long long d = (long long)(x - site);
-    return d * d + (long long)h[site];
+    const int d = x - site;
+    return d * d + h[site];
 }
 
+__host__ __device__ __forceinline__ size_t rows_smem_words(int W, int wpr)
+{
+    return 3 * (size_t)W + 32 * (size_t)wpr + 1;
+}
+
+template <int WPR>
 __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs,
                                         int W, int H, int rows_per_block, float alpha,
                                         int32_t *__restrict__ D_dense,
                                         float *__restrict__ S_dense, float *__restrict__ I0,
                                         int ipitch, size_t ifs)
 {
+    constexpr int NB = 32 * WPR;
     extern __shared__ int32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int y = blockIdx.x * rows_per_block + warp;
+    const int rib = warp / WPR, sub = warp % WPR;
+    const int y = blockIdx.x * rows_per_block + rib;
     const int f = blockIdx.y;
-    int32_t *h = smem + (size_t)warp * (3 * (size_t)W + 32);  // g^2, or -1: empty column
-    int32_t *stk = h + W;                                       // envelope sites per band
-    int32_t *res = stk + W;                                     // D per pixel of the row
-    int32_t *cnts = res + W;                                    // envelope size per band
-    if (y >= H) return;  // the whole warp leaves together
-    const int32_t *grow = g + (size_t)f * gfs + (size_t)y * gpitch;
+    const bool valid = y < H;
+    int32_t *h = smem + (size_t)rib * rows_smem_words(W, WPR);
+    int32_t *stk = h + W;       // envelope sites, per band
+    int32_t *res = stk + W;     // D per pixel of the row
+    int32_t *cnts = res + W;    // envelope size per band
+    int32_t *anyf = cnts + NB;  // row has an edge pixel
+    const int tr = sub * 32 + lane;  // thread index within the row
     const int ginf = W + H;
-    int any = 0;
-    for (int x = lane; x < W; x += 32) {
-        const int gv = grow[x];
-        h[x] = gv >= ginf ? -1 : gv * gv;
-        any |= gv < ginf ? 1 : 0;
+    if (tr == 0) *anyf = 0;
+    __syncthreads();
+    if (valid) {
+        const int32_t *grow = g + (size_t)f * gfs + (size_t)y * gpitch;
+        int any = 0;
+        for (int x = tr; x < W; x += NB) {
+            const int gv = grow[x];
+            h[x] = gv >= ginf ? -1 : gv * gv;
+            any |= gv < ginf ? 1 : 0;
+        }
+        if (any) *anyf = 1;  // benign race: every writer stores 1
     }
-    any = __any_sync(0xffffffffu, any);
-    __syncwarp();
+    __syncthreads();
+    const bool any = valid && *anyf;
 
-    const int B = (W + 31) / 32;
-    const int a = min(W, lane * B), b = min(W, a + B);  // this lane's band [a, b)
+    const int B = (W + NB - 1) / NB;
+    const int bi = tr;  // this lane's band
+    const int a = min(W, bi * B), b = min(W, a + B);
     int cnt = 0;
-    for (int q = a; q < b; ++q) {
-        if (h[q] < 0) continue;
-        while (cnt >= 2 && hidden(stk[a + cnt - 2], stk[a + cnt - 1], q, h)) --cnt;
-        stk[a + cnt++] = q;
+    if (any) {
+        for (int q = a; q < b; ++q) {
+            if (h[q] < 0) continue;
+            while (cnt >= 2 && hidden(stk[a + cnt - 2], stk[a + cnt - 1], q, h)) --cnt;
+            stk[a + cnt++] = q;
+        }
     }
-    cnts[lane] = cnt;
-    __syncwarp();
+    if (valid) cnts[bi] = cnt;
+    __syncthreads();
 
-    int k = 0;
-    for (int x = a; x < b; ++x) {
-        long long best = 0x7fffffffffffffffLL;
-        if (any) {
-            if (cnt > 0) {
-                while (k + 1 < cnt && para(x, stk[a + k + 1], h) <= para(x, stk[a + k], h)) ++k;
-                best = para(x, stk[a + k], h);
+    if (any) {
+        int ptr[2 * kRowNear + 1];
+#pragma unroll
+        for (int k = 0; k <= 2 * kRowNear; ++k) ptr[k] = 0;
+        for (int x = a; x < b; ++x) {
+            int best = 0x7fffffff;
+#pragma unroll
+            for (int k = 0; k <= 2 * kRowNear; ++k) {
+                const int M = bi + k - kRowNear;
+                if (M < 0 || M >= NB) continue;
+                const int ma = min(W, M * B), mb = min(W, ma + B);
+                const int cM = cnts[M];
+                if (cM == 0) continue;
+                const int gap = M < bi ? x - (mb - 1) : (M > bi ? ma - x : 0);
+                if (M != bi && gap * gap >= best) continue;
+                const int32_t *sl = stk + ma;
+                int pk = ptr[k];
+                int cur = para(x, sl[pk], h);
+                while (pk + 1 < cM) {
+                    const int nxt = para(x, sl[pk + 1], h);
+                    if (nxt > cur) break;
+                    cur = nxt;
+                    ++pk;
+                }
+                ptr[k] = pk;
+                best = min(best, cur);
             }
-            for (int dist = 1; dist < 32; ++dist) {
+            for (int dist = kRowNear + 1; dist < NB; ++dist) {
                 bool progress = false;
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
-                    const int L = side ? lane + dist : lane - dist;
-                    if (L < 0 || L >= 32) continue;
-                    const int la = min(W, L * B), lb = min(W, la + B);
-                    if (la >= lb) continue;
-                    const long long gap = side ? (long long)(la - x) : (long long)(x - (lb - 1));
+                    const int M = side ? bi + dist : bi - dist;
+                    if (M < 0 || M >= NB) continue;
+                    const int ma = min(W, M * B), mb = min(W, ma + B);
+                    if (ma >= mb) continue;
+                    const long long gap = side ? (long long)(ma - x) : (long long)(x - (mb - 1));
                     if (gap * gap >= best) continue;
                     progress = true;
-                    const int cL = cnts[L];
-                    if (cL == 0) continue;
-                    const int32_t *s = stk + la;
-                    int lo = 0, hi = cL - 1;
+                    const int cM = cnts[M];
+                    if (cM == 0) continue;
+                    const int32_t *sl = stk + ma;
+                    int lo = 0, hi = cM - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
-                        if (para(x, s[mid + 1], h) <= para(x, s[mid], h)) lo = mid + 1;
+                        if (para(x, sl[mid + 1], h) <= para(x, sl[mid], h)) lo = mid + 1;
                         else hi = mid;
                     }
-                    const long long v = para(x, s[lo], h);
-                    if (v < best) best = v;
+                    best = min(best, para(x, sl[lo], h));
                 }
                 if (!progress) break;
             }
+            res[x] = best;
         }
-        res[x] = any ? (int32_t)best : kInfD;
     }
-    __syncwarp();
+    __syncthreads();
 
+    if (!valid) return;
     float *irow = I0 ? I0 + (size_t)f * ifs + (size_t)y * ipitch : nullptr;
     const size_t dbase = (size_t)f * W * H + (size_t)y * W;
-    for (int x = lane; x < W; x += 32) {
-        const int32_t D = res[x];
+    for (int x = tr; x < W; x += NB) {
+        const int32_t D = any ? res[x] : kInfD;
         float S = 1.0f;
         if (D != kInfD) S = 1.0f - expf(-sqrtf((float)D) / alpha);
         if (irow) irow[x] = 255.0f * S;
@@ -308,16 +400,23 @@ void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stri
                         cudaStream_t st)
 {
     StageScope sc(kStEdtCols, 1, st);
-    dim3 grd((W + 127) / 128, frames);
-    edt_cols_kernel<<<grd, 128, 0, st>>>(E, edge_pitch, edge_frame_stride, W, H, g, g_pitch,
-                                         g_frame_stride);
+    // chunks of CH rows, CH a multiple of 32: at most 32 chunks of at most 512 rows
+    int nch = (H + 31) / 32;
+    if (nch > kColMaxChunks) nch = kColMaxChunks;
+    int CH = ((H + nch - 1) / nch + 31) / 32 * 32;
+    nch = (H + CH - 1) / CH;
+    dim3 blk(32, nch), grd((W + 31) / 32, frames);
+    edt_cols_kernel<<<grd, blk, 0, st>>>(E, edge_pitch, edge_frame_stride, W, H, g, g_pitch,
+                                         g_frame_stride, CH);
 }
 
-size_t edt_rows_smem(int W, int rows) { return (size_t)rows * (3 * (size_t)W + 32) * 4; }
+int edt_rows_wpr(int W) { return W >= 640 ? 2 : 1; }
+
+size_t edt_rows_smem(int W, int rows) { return (size_t)rows * rows_smem_words(W, edt_rows_wpr(W)) * 4; }
 
 int edt_rows_per_block(int W)
 {
-    int rows = kRowWarpsMax;
+    int rows = edt_rows_wpr(W) == 2 ? 2 : 4;
     while (rows > 1 && edt_rows_smem(W, rows) > 200 * 1024) --rows;
     return rows;
 }
@@ -327,17 +426,25 @@ void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_strid
                              int i_pitch, size_t i_frame_stride, int frames, cudaStream_t st)
 {
     const int rows = edt_rows_per_block(W);
+    const int wpr = edt_rows_wpr(W);
     const size_t smem = edt_rows_smem(W, rows);
     StageScope sc(kStEdtRows, 1, st);
     dim3 grd((H + rows - 1) / rows, frames);
-    edt_rows_surface_kernel<<<grd, 32 * rows, smem, st>>>(g, g_pitch, g_frame_stride, W, H, rows,
-                                                          alpha, D_dense, S_dense, I0, i_pitch,
-                                                          i_frame_stride);
+    if (wpr == 2)
+        edt_rows_surface_kernel<2><<<grd, 32 * 2 * rows, smem, st>>>(
+            g, g_pitch, g_frame_stride, W, H, rows, alpha, D_dense, S_dense, I0, i_pitch,
+            i_frame_stride);
+    else
+        edt_rows_surface_kernel<1><<<grd, 32 * rows, smem, st>>>(
+            g, g_pitch, g_frame_stride, W, H, rows, alpha, D_dense, S_dense, I0, i_pitch,
+            i_frame_stride);
 }
 
 void init_front_attributes()
 {
-    cudaFuncSetAttribute(edt_rows_surface_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(edt_rows_surface_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         210 * 1024);
+    cudaFuncSetAttribute(edt_rows_surface_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          210 * 1024);
 }
 
