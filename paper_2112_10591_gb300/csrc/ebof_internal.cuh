@@ -114,8 +114,9 @@ bool var_fused_supported(int var_sor);
 void init_var_attributes();
 float *launch_variational_fused(const float *I0, const float *I0x, const float *I0y,
                                 const float *I1, const Level &lv, size_t pyr_frame_stride,
-                                float *U, float *Utmp, size_t u_frame_stride, int frames,
-                                const FlowParams &fp, cudaStream_t st);
+                                float *U, float *Utmp, size_t u_frame_stride, float *coef,
+                                size_t coef_frame_stride, int frames, const FlowParams &fp,
+                                cudaStream_t st);
 
 // A9: level-0 flow to the caller's dense planar layout.
 void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,

@@ -450,7 +450,7 @@ float *launch_variational(const float *I0, const float *I0x, const float *I0y, c
     if (fp.var_outer <= 0) return U;
     if (var_fused_supported(fp.var_sor))
         return launch_variational_fused(I0, I0x, I0y, I1, lv, pyr_frame_stride, U, Utmp,
-                                        u_frame_stride, frames, fp, st);
+                                        u_frame_stride, work, work_frame_stride, frames, fp, st);
     // many sweeps: one launch per step, state in global memory
     dim3 blk(32, 8);
     const dim3 grd = grid2d(lv.w, lv.h, frames, blk);

@@ -1,23 +1,23 @@
-// k_var.cu -- variational refinement (reading F6), one fused kernel per
+// k_var.cu -- variational refinement (reading F6): two kernels per
 // fixed-point iteration.
 //
-// One block owns a 64x64 region of the level image and refines the flow of
-// its (64 - 2R)^2 interior, R = 2 * sweeps - 1.  The block
-//   1. stages U and the warped image I1(x + U) for the region + 2 px,
-//   2. builds derivatives of the warped image and smoothness weights for the
-//      region + 1 px in shared memory,
-//   3. builds every region pixel's 2x2 linear system in registers (data and
-//      gradient-constancy terms normalised, weights lagged at dU = 0),
-//   4. runs the red-black SOR sweeps on (du, dv) entirely in registers: a
-//      thread owns a 2-column x 4-row strip, so one of the two horizontal
-//      neighbours is its own and the other is a lane shuffle away, and the
-//      rows at strip ends are exchanged through shared memory once per half
-//      sweep,
-//   5. writes U + dU for its interior pixels.
-// The region border keeps du = 0.  After h half sweeps only pixels within
-// h - 1 px of that border differ from the whole-image red-black iteration,
-// and those lie in the discarded halo, so the interior is exactly the
-// whole-image iteration (up to floating-point rounding).
+// var_coeff_kernel, one thread per pixel: stages U and the warped image
+// I1(x + U) for a 32x16 tile plus 2 px in shared memory, builds derivatives
+// of the warped image and the smoothness weights, and writes every pixel's
+// 2x2 linear system (data and gradient-constancy terms normalised, weights
+// lagged at dU = 0): 1/a11, 1/a22, a12, b1, b2 and the four edge weights, as
+// nine planes.  Only the staging halo is shared between tiles.
+//
+// var_sor_kernel: one block owns a 64x64 region and refines the flow of its
+// (64 - 2R)^2 interior, R = 2 * sweeps - 1.  It loads the region's linear
+// systems into registers and runs the red-black SOR sweeps there: a thread
+// owns a 2-column x 4-row strip, so one horizontal neighbour is its own and
+// the other is a lane shuffle away, and the rows at strip ends are exchanged
+// through shared memory once per half sweep.  The region border keeps
+// du = 0; after h half sweeps only pixels within h - 1 px of that border
+// differ from the whole-image red-black iteration, and those lie in the
+// discarded halo, so the interior is exactly the whole-image iteration (up to
+// floating-point rounding).  It writes U + dU for its interior.
 #include "dev_common.cuh"
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
@@ -30,10 +30,12 @@ constexpr int kVR = 64;                  // region side
 constexpr int kVS = 4;                   // rows per thread strip
 constexpr int kVWarps = kVR / kVS;       // warps per block (stacked strips)
 constexpr int kVThreads = 32 * kVWarps;  // 512
-constexpr int kVE = kVR + 4;             // staging window: region + 2 px each side
-constexpr int kVD = kVR + 2;             // derivative window: region + 1 px each side
-constexpr size_t kVSmemFloats =
-    2 * kVE * kVE + kVE * kVE + 3 * kVD * kVD + 2 * 2 * kVWarps * 2 * 64;
+constexpr size_t kVSmemFloats = 2 * 2 * kVWarps * 2 * 64;  // strip-end exchange
+enum { kCI11 = 0, kCI22, kCA12, kCB1, kCB2, kCWL, kCWR, kCWU, kCWD, kCPlanes };
+
+constexpr int kAX = 32, kAY = 16;              // coefficient tile
+constexpr int kAEX = kAX + 4, kAEY = kAY + 4;  // staging window: tile + 2 px
+constexpr int kADX = kAX + 2, kADY = kAY + 2;  // derivative window: tile + 1 px
 constexpr unsigned kFull = 0xffffffffu;
 
 // One red-black half sweep of colour C on a thread's 2-column x kVS-row
@@ -126,91 +128,136 @@ __device__ __forceinline__ void sor_sweeps(float (&du)[kVS][2], float (&dv)[kVS]
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kVThreads, 1)
-var_fused_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
+__global__ void __launch_bounds__(kAX * kAY)
+var_coeff_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
                  const float *__restrict__ I0yb, const float *__restrict__ I1b, int w, int h,
-                 int pitch, size_t pfs, const float *__restrict__ Uinb, float *__restrict__ Uoutb,
-                 size_t ufs, size_t plane, int R, int tile, int n_half, float delta, float gamma,
-                 float alpha_s, float omega)
+                 int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs, size_t plane,
+                 float *__restrict__ coefb, size_t cfs, float delta, float gamma, float alpha_s)
 {
-    extern __shared__ float sm[];
-    float *sU = sm;
-    float *sV = sU + kVE * kVE;
-    float *sW = sV + kVE * kVE;
-    float *sIx = sW + kVE * kVE;
-    float *sIy = sIx + kVD * kVD;
-    float *sAs = sIy + kVD * kVD;
-    float *xch = sAs + kVD * kVD;  // strip-end exchange, two buffers
+    __shared__ float sU[kAEY][kAEX], sV[kAEY][kAEX], sW[kAEY][kAEX];
+    __shared__ float sIx[kADY][kADX], sIy[kADY][kADX], sAs[kADY][kADX];
+    const int f = blockIdx.z;
+    const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
+    const int ex0 = tx0 - 2, ey0 = ty0 - 2, dx0 = tx0 - 1, dy0 = ty0 - 1;
+    const size_t po = (size_t)f * pfs;
+    const float *I1 = I1b + po;
+    const float *U = Ub + (size_t)f * ufs;
+    const int tx = threadIdx.x, ty = threadIdx.y;
 
+    // staging window: thread (tx, ty) covers (tx + 32 i, ty + 16 j)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int lx = tx + kAX * i, ly = ty + kAY * j;
+            if (lx >= kAEX || ly >= kAEY) continue;
+            const int gx = ex0 + lx, gy = ey0 + ly;
+            float u = 0.0f, v = 0.0f;
+            if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+                const size_t p = (size_t)gy * pitch + gx;
+                u = U[p];
+                v = U[plane + p];
+            }
+            sU[ly][lx] = u;
+            sV[ly][lx] = v;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int lx = tx + kAX * i, ly = ty + kAY * j;
+            if (lx >= kAEX || ly >= kAEY) continue;
+            const int gx = ex0 + lx, gy = ey0 + ly;
+            float wv = 0.0f;
+            if (gx >= 0 && gx < w && gy >= 0 && gy < h)
+                wv = bilinear(I1, w, h, pitch, (float)gx + sU[ly][lx], (float)gy + sV[ly][lx]);
+            sW[ly][lx] = wv;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int lx = tx + kAX * i, ly = ty + kAY * j;
+            if (lx >= kADX || ly >= kADY) continue;
+            const int gx = dx0 + lx, gy = dy0 + ly;
+            float ix = 0.0f, iy = 0.0f, as = 0.0f;
+            if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+                const int xp = min(gx + 1, w - 1) - ex0, xm = max(gx - 1, 0) - ex0;
+                const int yp = min(gy + 1, h - 1) - ey0, ym = max(gy - 1, 0) - ey0;
+                const int ex = gx - ex0, ey = gy - ey0;
+                ix = 0.5f * (sW[ey][xp] - sW[ey][xm]);
+                iy = 0.5f * (sW[yp][ex] - sW[ym][ex]);
+                const float u = sU[ey][ex], v = sV[ey][ex];
+                const float ux = gx + 1 < w ? sU[ey][ex + 1] - u : 0.0f;
+                const float uy = gy + 1 < h ? sU[ey + 1][ex] - u : 0.0f;
+                const float vx = gx + 1 < w ? sV[ey][ex + 1] - v : 0.0f;
+                const float vy = gy + 1 < h ? sV[ey + 1][ex] - v : 0.0f;
+                as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
+            }
+            sIx[ly][lx] = ix;
+            sIy[ly][lx] = iy;
+            sAs[ly][lx] = as;
+        }
+    __syncthreads();
+
+    const int gx = tx0 + threadIdx.x, gy = ty0 + threadIdx.y;
+    if (gx >= w || gy >= h) return;
+    const int xp = min(gx + 1, w - 1) - dx0, xm = max(gx - 1, 0) - dx0;
+    const int yp = min(gy + 1, h - 1) - dy0, ym = max(gy - 1, 0) - dy0;
+    const int dx = gx - dx0, dy = gy - dy0, ex = gx - ex0, ey = gy - ey0;
+    const float Ix = sIx[dy][dx], Iy = sIy[dy][dx];
+    const float Ixx = 0.5f * (sIx[dy][xp] - sIx[dy][xm]);
+    const float Ixy = 0.5f * (sIx[yp][dx] - sIx[ym][dx]);
+    const float Iyy = 0.5f * (sIy[yp][dx] - sIy[ym][dx]);
+    const size_t p = (size_t)gy * pitch + gx;
+    const float Iz = sW[ey][ex] - I0b[po + p];
+    const float Ixz = Ix - I0xb[po + p], Iyz = Iy - I0yb[po + p];
+    const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
+    const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
+    float ad = delta * nd * psi_prime(nd * Iz * Iz);
+    float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
+    const float u = sU[ey][ex], v = sV[ey][ex];
+    const float wx = (float)gx + u, wy = (float)gy + v;
+    if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) {
+        ad = 0.0f;
+        ag = 0.0f;
+    }
+    const float asp = sAs[dy][dx];
+    const float cl = gx > 0 ? 0.5f * (asp + sAs[dy][dx - 1]) : 0.0f;
+    const float cr = gx + 1 < w ? 0.5f * (asp + sAs[dy][dx + 1]) : 0.0f;
+    const float cu = gy > 0 ? 0.5f * (asp + sAs[dy - 1][dx]) : 0.0f;
+    const float cd = gy + 1 < h ? 0.5f * (asp + sAs[dy + 1][dx]) : 0.0f;
+    const float sw = cl + cr + cu + cd;
+    const float su0 = cl * (sU[ey][ex - 1] - u) + cr * (sU[ey][ex + 1] - u) +
+                      cu * (sU[ey - 1][ex] - u) + cd * (sU[ey + 1][ex] - u);
+    const float sv0 = cl * (sV[ey][ex - 1] - v) + cr * (sV[ey][ex + 1] - v) +
+                      cu * (sV[ey - 1][ex] - v) + cd * (sV[ey + 1][ex] - v);
+    float *cf = coefb + (size_t)f * cfs + p;
+    cf[kCI11 * plane] = __fdividef(1.0f, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
+    cf[kCI22 * plane] = __fdividef(1.0f, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
+    cf[kCA12 * plane] = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
+    cf[kCB1 * plane] = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
+    cf[kCB2 * plane] = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
+    cf[kCWL * plane] = cl;
+    cf[kCWR * plane] = cr;
+    cf[kCWU * plane] = cu;
+    cf[kCWD * plane] = cd;
+}
+
+__global__ void __launch_bounds__(kVThreads, 1)
+var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
+               float *__restrict__ Uoutb, size_t ufs, size_t plane,
+               const float *__restrict__ coefb, size_t cfs, int R, int tile, int n_half,
+               float omega)
+{
+    extern __shared__ float xch[];  // strip-end exchange, two buffers
     const int f = blockIdx.z;
     const int rx0 = blockIdx.x * tile - R, ry0 = blockIdx.y * tile - R;
-    const int ex0 = rx0 - 2, ey0 = ry0 - 2;
-    const int dx0 = rx0 - 1, dy0 = ry0 - 1;
-    const size_t po = (size_t)f * pfs;
-    const float *I0 = I0b + po, *I0x = I0xb + po, *I0y = I0yb + po, *I1 = I1b + po;
     const float *Uin = Uinb + (size_t)f * ufs;
     float *Uout = Uoutb + (size_t)f * ufs;
-
-    // 1. flow on the staging window, then the warped image I1(x + U); the
-    // loops are unrolled so that each thread keeps all its loads in flight
-    const int t = threadIdx.x;
-    constexpr int kIt = (kVE * kVE + kVThreads - 1) / kVThreads;
-#pragma unroll
-    for (int it = 0; it < kIt; ++it) {
-        const int i = t + it * kVThreads;
-        if (i >= kVE * kVE) break;
-        const int gx = ex0 + i % kVE, gy = ey0 + i / kVE;
-        float u = 0.0f, v = 0.0f;
-        if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-            const size_t p = (size_t)gy * pitch + gx;
-            u = Uin[p];
-            v = Uin[plane + p];
-        }
-        sU[i] = u;
-        sV[i] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < kIt; ++it) {
-        const int i = t + it * kVThreads;
-        if (i >= kVE * kVE) break;
-        const int gx = ex0 + i % kVE, gy = ey0 + i / kVE;
-        float wv = 0.0f;
-        if (gx >= 0 && gx < w && gy >= 0 && gy < h)
-            wv = bilinear(I1, w, h, pitch, (float)gx + sU[i], (float)gy + sV[i]);
-        sW[i] = wv;
-    }
-    __syncthreads();
-
-    // 2. derivatives of the warped image and smoothness weights, region + 1
-    constexpr int kDIt = (kVD * kVD + kVThreads - 1) / kVThreads;
-#pragma unroll
-    for (int it = 0; it < kDIt; ++it) {
-        const int i = t + it * kVThreads;
-        if (i >= kVD * kVD) break;
-        const int gx = dx0 + i % kVD, gy = dy0 + i / kVD;
-        float ix = 0.0f, iy = 0.0f, as = 0.0f;
-        if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-            const int xp = min(gx + 1, w - 1), xm = max(gx - 1, 0);
-            const int yp = min(gy + 1, h - 1), ym = max(gy - 1, 0);
-            const int row = (gy - ey0) * kVE;
-            ix = 0.5f * (sW[row + xp - ex0] - sW[row + xm - ex0]);
-            iy = 0.5f * (sW[(yp - ey0) * kVE + gx - ex0] - sW[(ym - ey0) * kVE + gx - ex0]);
-            const int e = row + gx - ex0;
-            const float u = sU[e], v = sV[e];
-            const float ux = gx + 1 < w ? sU[e + 1] - u : 0.0f;
-            const float uy = gy + 1 < h ? sU[e + kVE] - u : 0.0f;
-            const float vx = gx + 1 < w ? sV[e + 1] - v : 0.0f;
-            const float vy = gy + 1 < h ? sV[e + kVE] - v : 0.0f;
-            as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
-        }
-        sIx[i] = ix;
-        sIy[i] = iy;
-        sAs[i] = as;
-    }
-    __syncthreads();
-
-    // 3. linear systems of this thread's 8 pixels
+    const float *cf = coefb + (size_t)f * cfs;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     float i11[kVS][2], i22[kVS][2], a12[kVS][2], b1[kVS][2], b2[kVS][2];
     float wl[kVS][2], wr[kVS][2], wu[kVS][2], wd[kVS][2];
@@ -219,63 +266,31 @@ var_fused_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
     for (int r = 0; r < kVS; ++r)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            du[r][q] = 0.0f; dv[r][q] = 0.0f;
-            i11[r][q] = 0.0f; i22[r][q] = 0.0f; a12[r][q] = 0.0f;
-            b1[r][q] = 0.0f; b2[r][q] = 0.0f;
-            wl[r][q] = 0.0f; wr[r][q] = 0.0f; wu[r][q] = 0.0f; wd[r][q] = 0.0f;
+            du[r][q] = 0.0f;
+            dv[r][q] = 0.0f;
             const int gx = rx0 + 2 * lane + q, gy = ry0 + wp * kVS + r;
-            if (gx < 0 || gx >= w || gy < 0 || gy >= h) continue;
-            const int xp = min(gx + 1, w - 1), xm = max(gx - 1, 0);
-            const int yp = min(gy + 1, h - 1), ym = max(gy - 1, 0);
-            const int d = (gy - dy0) * kVD + (gx - dx0);
-            const int drow = (gy - dy0) * kVD;
-            const float Ix = sIx[d], Iy = sIy[d];
-            const float Ixx = 0.5f * (sIx[drow + xp - dx0] - sIx[drow + xm - dx0]);
-            const float Ixy = 0.5f * (sIx[(yp - dy0) * kVD + gx - dx0] - sIx[(ym - dy0) * kVD + gx - dx0]);
-            const float Iyy = 0.5f * (sIy[(yp - dy0) * kVD + gx - dx0] - sIy[(ym - dy0) * kVD + gx - dx0]);
-            const size_t p = (size_t)gy * pitch + gx;
-            const int e = (gy - ey0) * kVE + (gx - ex0);
-            const float Iz = sW[e] - I0[p];
-            const float Ixz = Ix - I0x[p], Iyz = Iy - I0y[p];
-            const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
-            const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
-            float ad = delta * nd * psi_prime(nd * Iz * Iz);
-            float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
-            const float u = sU[e], v = sV[e];
-            const float wx = (float)gx + u, wy = (float)gy + v;
-            if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) {
-                ad = 0.0f;
-                ag = 0.0f;
-            }
-            const float asp = sAs[d];
-            const float cl = gx > 0 ? 0.5f * (asp + sAs[d - 1]) : 0.0f;
-            const float cr = gx + 1 < w ? 0.5f * (asp + sAs[d + 1]) : 0.0f;
-            const float cu = gy > 0 ? 0.5f * (asp + sAs[d - kVD]) : 0.0f;
-            const float cd = gy + 1 < h ? 0.5f * (asp + sAs[d + kVD]) : 0.0f;
-            const float sw = cl + cr + cu + cd;
-            const float su0 = cl * (sU[e - 1] - u) + cr * (sU[e + 1] - u) +
-                              cu * (sU[e - kVE] - u) + cd * (sU[e + kVE] - u);
-            const float sv0 = cl * (sV[e - 1] - v) + cr * (sV[e + 1] - v) +
-                              cu * (sV[e - kVE] - v) + cd * (sV[e + kVE] - v);
-            i11[r][q] = __fdividef(1.0f, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
-            i22[r][q] = __fdividef(1.0f, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
-            a12[r][q] = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
-            b1[r][q] = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
-            b2[r][q] = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
-            wl[r][q] = cl; wr[r][q] = cr; wu[r][q] = cu; wd[r][q] = cd;
+            const bool in = gx >= 0 && gx < w && gy >= 0 && gy < h;
+            const size_t p = in ? (size_t)gy * pitch + gx : 0;
+            i11[r][q] = in ? cf[kCI11 * plane + p] : 0.0f;
+            i22[r][q] = in ? cf[kCI22 * plane + p] : 0.0f;
+            a12[r][q] = in ? cf[kCA12 * plane + p] : 0.0f;
+            b1[r][q] = in ? cf[kCB1 * plane + p] : 0.0f;
+            b2[r][q] = in ? cf[kCB2 * plane + p] : 0.0f;
+            wl[r][q] = in ? cf[kCWL * plane + p] : 0.0f;
+            wr[r][q] = in ? cf[kCWR * plane + p] : 0.0f;
+            wu[r][q] = in ? cf[kCWU * plane + p] : 0.0f;
+            wd[r][q] = in ? cf[kCWD * plane + p] : 0.0f;
         }
 
-    // 4. red-black SOR; red = (x + y) even, first.  kVS is even, so the
-    // parity of (x + y) at a strip's first pixel is the same for every warp
-    // of the block, and the column of a given colour in a given row is a
+    // red-black SOR; red = (x + y) even, first.  kVS is even, so the parity
+    // of (x + y) at a strip's first pixel is the same for every warp of the
+    // block, and the column of a given colour in a given row is a
     // compile-time constant once that parity is fixed.
-    const int par = (rx0 + ry0) & 1;
-    if (par == 0)
+    if (((rx0 + ry0) & 1) == 0)
         sor_sweeps<0>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half, omega);
     else
         sor_sweeps<1>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half, omega);
 
-    // 5. U + dU on the interior
 #pragma unroll
     for (int r = 0; r < kVS; ++r)
 #pragma unroll
@@ -284,10 +299,9 @@ var_fused_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
             const int gx = rx0 + lx, gy = ry0 + ly;
             if (lx < R || lx >= R + tile || ly < R || ly >= R + tile || gx >= w || gy >= h)
                 continue;
-            const int e = (gy - ey0) * kVE + (gx - ex0);
             const size_t p = (size_t)gy * pitch + gx;
-            Uout[p] = sU[e] + du[r][q];
-            Uout[plane + p] = sV[e] + dv[r][q];
+            Uout[p] = Uin[p] + du[r][q];
+            Uout[plane + p] = Uin[plane + p] + dv[r][q];
         }
 }
 
@@ -299,27 +313,33 @@ bool var_fused_supported(int var_sor)
     return kVR - 2 * R >= 16;
 }
 
-void init_var_attributes()
-{
-    cudaFuncSetAttribute(var_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kVSmemFloats * sizeof(float)));
-}
+void init_var_attributes() {}
 
 float *launch_variational_fused(const float *I0, const float *I0x, const float *I0y,
                                 const float *I1, const Level &lv, size_t pyr_frame_stride,
-                                float *U, float *Utmp, size_t u_frame_stride, int frames,
-                                const FlowParams &fp, cudaStream_t st)
+                                float *U, float *Utmp, size_t u_frame_stride, float *coef,
+                                size_t coef_frame_stride, int frames, const FlowParams &fp,
+                                cudaStream_t st)
 {
     const int n_half = 2 * fp.var_sor;
     const int R = n_half > 0 ? n_half - 1 : 0;
     const int tile = kVR - 2 * R;
-    dim3 grd((lv.w + tile - 1) / tile, (lv.h + tile - 1) / tile, frames);
+    const dim3 cgrd((lv.w + kAX - 1) / kAX, (lv.h + kAY - 1) / kAY, frames);
+    const dim3 sgrd((lv.w + tile - 1) / tile, (lv.h + tile - 1) / tile, frames);
     float *a = U, *b = Utmp;
     for (int k = 0; k < fp.var_outer; ++k) {
-        StageScope sc(kStVarSor, 1, st);
-        var_fused_kernel<<<grd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
-            I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a, b, u_frame_stride,
-            lv.plane, R, tile, n_half, fp.delta, fp.gamma, fp.alpha_s, fp.omega);
+        {
+            StageScope sc(kStVarCoeff, 1, st);
+            var_coeff_kernel<<<cgrd, dim3(kAX, kAY), 0, st>>>(
+                I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a, u_frame_stride,
+                lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma, fp.alpha_s);
+        }
+        {
+            StageScope sc(kStVarSor, 1, st);
+            var_sor_kernel<<<sgrd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
+                lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef, coef_frame_stride, R,
+                tile, n_half, fp.omega);
+        }
         float *t = a;
         a = b;
         b = t;
