@@ -209,28 +209,31 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline
-def algorithmic_bytes(stage, geo_levels, n_events, P, frames):
-    """Algorithmic bytes of one stage over `frames` windows: each stage's
-    inputs read once and outputs written once (formulas in the design doc)."""
-    Pl = [w * h for (w, h, npx, npy) in geo_levels]
-    npl = [npx * npy for (w, h, npx, npy) in geo_levels]
-    L = len(geo_levels)
-    outer, sor = 5, 5
+def algorithmic_bytes_per_launch(stage, level, geo, n_events_per_window, P):
+    """Algorithmic bytes of ONE launch of a stage for one window: each
+    kernel's inputs read once and outputs written once (formulas in
+    DESIGN.md, "Kernels and their rooflines").  geo: [(w, h, npx, npy)]."""
+    if level >= 0:
+        w, h, npx, npy = geo[level]
+        Pl, npl = w * h, npx * npy
+        Pc = geo[level + 1][0] * geo[level + 1][1] if level + 1 < len(geo) else 0
     per = {
-        "scatter": 13 * n_events / frames,
-        "denoise_fill": 4 * P,
-        "edt_cols": 5 * P,
-        "edt_rows_surface": 8 * P,
-        "pyramid": sum(12 * Pl[l] for l in range(L)) + sum(20 * Pl[l] for l in range(1, L)),
-        "patch_search": sum(16 * Pl[l] + 16 * npl[l] for l in range(L)),
-        "densify": sum(16 * Pl[l] + 8 * npl[l] for l in range(L)),
-        "var_warp": outer * sum(16 * p for p in Pl),
-        "var_coeff": outer * sum(56 * p for p in Pl),
-        "var_sor": outer * 2 * sor * sum(34 * p for p in Pl),
-        "var_add": outer * sum(24 * p for p in Pl),
-        "flow_out": 16 * P,
+        "scatter": lambda: 13.0 * n_events_per_window,
+        "denoise_fill": lambda: 2.0 * P,          # per kernel: read one byte image, write one
+        "edt_cols": lambda: 5.0 * P,              # E_df bytes in, int32 g out
+        "edt_rows_surface": lambda: 8.0 * P,      # int32 g in, float intensity out
+        "pyramid": lambda: 12.0 * Pl,             # gradients: I in, Ix and Iy out
+        "patch_search": lambda: 16.0 * Pl + 8.0 * npl + 8.0 * Pc,
+        "densify": lambda: 16.0 * Pl + 8.0 * npl,
+        "var_coeff": lambda: 60.0 * Pl,           # U, I1, I0, I0x, I0y in; 9 planes out
+        "var_sor": lambda: 52.0 * Pl,             # 9 planes and U in, U out
+        "flow_out": lambda: 16.0 * P,
     }
-    return per.get(stage, 0.0) * frames
+    f = per.get(stage)
+    return float(f()) if f else 0.0
+
+
+PER_LEVEL = ("pyramid", "patch_search", "densify", "var_coeff", "var_sor")
 
 
 def geo_levels(p):
@@ -255,6 +258,48 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def dram_traffic(stage, level):
+    """DRAM bytes per launch of this stage at this level from the committed
+    ncu summary (profiles/dram_traffic.txt), or None when the kernel's source
+    file changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        f = ln.split()
+        if len(f) < 6 or f[1] != stage or int(f[2]) != level:
+            continue
+        src = os.path.join(ROOT, f[4])
+        try:
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        except OSError:
+            return None
+        return int(f[3]) if sha == f[5] else None
+    return None
+
+
+# ---------------------------------------------------------------- replicas
+def replica_seed(rank):
+    """Each rank runs its own camera stream (replicas, no data-path exchange)."""
+    return 1 + rank
+
+
+def combine_ranks(ms_local, frames_local, world, dist=None, device=None):
+    """Whole-job timing: the slowest rank's time, and the frames of all ranks
+    over it (weak scaling: every rank processes the same amount)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, frames_local * world / (ms / 1000.0)
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -276,7 +321,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    stream = synth.workload_1280x720(seed=1 + rank, n_windows=args.windows)
+    stream = synth.workload_1280x720(seed=replica_seed(rank), n_windows=args.windows)
     nwin = stream.n_windows
     frames_per_step = nwin - 1
     W, H = stream.width, stream.height
@@ -354,42 +399,39 @@ def main():
     lat += [evs_a[k].elapsed_time(evs_b[k]) for k in range(1, nwin)]
     launches = eb.ebof_kernel_launches() - launches0
     clocks = clk.stop()
-    ms = t_start.elapsed_time(t_end)
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms = float(tmax.item())
-    value = frames_per_step * args.steps * world / (ms / 1000.0)
+    ms, value = combine_ranks(t_start.elapsed_time(t_end), frames_per_step * args.steps, world,
+                              dist, dev)
 
     # stage profile over the same steps (events bracket each stage's launches)
     eb.check(eb.ebof_stream_set_profiling(s, True))
-    for _ in range(max(1, min(args.steps, 2))):
+    nprof = max(1, min(args.steps, 2))
+    for _ in range(nprof):
         step_plain()
     torch.cuda.synchronize(dev)
     pst, prof = eb.ebof_stream_get_profile(s)
     eb.check(pst)
+    _, prof0 = eb.ebof_stream_get_profile_level(s, 0)
+    _, profn = eb.ebof_stream_get_profile_level(s, -1)
     eb.ebof_stream_set_profiling(s, False)
-    prof_frames = (nwin) * max(1, min(args.steps, 2))
     total_ms = sum(v[0] for v in prof.values()) or 1.0
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
-    dom_ms, dom_launches = prof[dom]
+    level = 0 if dom in PER_LEVEL else -1
+    dom_ms, dom_launches = (prof0 if level == 0 else profn)[dom]
     gl = geo_levels(prm)
-    n_events = int(off[-1]) * max(1, min(args.steps, 2))
-    alg = algorithmic_bytes(dom, gl, n_events, P, prof_frames)
-    # the first window of each step has no previous surface: no flow stages
-    flow_stages = ("patch_search", "densify", "var_warp", "var_coeff", "var_sor", "var_add",
-                   "flow_out")
-    if dom in flow_stages:
-        alg = alg * (nwin - 1) / nwin
-    per_launch_bytes = alg / max(dom_launches, 1)
+    n_ev_win = int(off[-1]) / nwin
+    per_launch_bytes = algorithmic_bytes_per_launch(dom, level, gl, n_ev_win, P)
     per_launch_s = dom_ms / 1000.0 / max(dom_launches, 1)
     achieved = per_launch_bytes / per_launch_s / 1e9
     peak, peak_kind = load_peaks()
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_kind,
+    roofline = {"bound": "hbm", "kernel": dom,
+                "level": level, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": dram_traffic(dom, level),
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_launch": per_launch_bytes, "us_per_launch": per_launch_s * 1e6,
-                "stage_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items()}}
+                "launches_timed": int(dom_launches),
+                "stage_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items()},
+                "stage_ms_per_frame": {k: round(v[0] / (nwin * nprof), 4)
+                                       for k, v in prof.items() if v[1]}}
 
     # batched path: the same stream through ebof_process_windows
     batched = None
@@ -422,18 +464,15 @@ def main():
                 step_batched()
             e1.record(cs)
             barrier()
-            bms = e0.elapsed_time(e1)
-            tb_ = torch.tensor([bms], dtype=torch.float64, device=dev)
-            if world > 1:
-                dist.all_reduce(tb_, op=dist.ReduceOp.MAX)
-            bms = float(tb_.item())
+            bms, bval = combine_ranks(e0.elapsed_time(e1), frames_per_step * args.steps, world,
+                                      dist, dev)
             eb.check(eb.ebof_stream_set_profiling(sb, True))
             step_batched()
             torch.cuda.synchronize(dev)
             _, bprof = eb.ebof_stream_get_profile(sb)
             eb.ebof_stream_set_profiling(sb, False)
             btot = sum(v[0] for v in bprof.values()) or 1.0
-            batched = {"value": frames_per_step * args.steps * world / (bms / 1000.0),
+            batched = {"value": bval,
                        "unit": UNIT, "windows_per_call": B,
                        "ms_per_step": bms / args.steps,
                        "stage_ms_per_frame": {k: round(v[0] / frames_per_step, 4)
@@ -483,12 +522,9 @@ def main():
         for _ in range(args.steps):
             step_host()
         barrier()
-        hs = time.perf_counter() - h0
-        th = torch.tensor([hs], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(th, op=dist.ReduceOp.MAX)
-        hs = float(th.item())
-        e2e = {"value": frames_per_step * args.steps * world / hs, "unit": UNIT,
+        hms, hval = combine_ranks(1000.0 * (time.perf_counter() - h0),
+                                  frames_per_step * args.steps, world, dist, dev)
+        e2e = {"value": hval, "unit": UNIT,
                "h2d_bytes_per_step": int(off[-1]) * 12,
                "d2h_bytes_per_step": nwin * 2 * P * 4}
 

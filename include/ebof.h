@@ -216,6 +216,11 @@ ebof_status ebof_stream_set_profiling(ebof_stream *s, int32_t enable);
  * (either may be NULL; n <= EBOF_STAGE_COUNT). */
 ebof_status ebof_stream_get_profile(ebof_stream *s, double *ms, int64_t *launches, int32_t n);
 
+/* As ebof_stream_get_profile, for the launches of one pyramid level only
+ * (level -1: the stages that are not per level, e.g. the EDT). */
+ebof_status ebof_stream_get_profile_level(ebof_stream *s, int32_t level, double *ms,
+                                          int64_t *launches, int32_t n);
+
 /* Name of a stage ("scatter", "patch_search", ...). */
 const char *ebof_stage_name(int32_t stage);
 

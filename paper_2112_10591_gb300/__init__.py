@@ -12,5 +12,5 @@ from .binding import (  # noqa: F401
     ebof_process_windows, ebof_status_string, ebof_stream_create, ebof_stream_destroy,
     ebof_stream_reset, ebof_stream_sync, ebof_window_stats, library_path, load,
     EBOF_STAGE_COUNT, ebof_kernel_launches, ebof_stage_name, ebof_stream_get_profile,
-    ebof_stream_set_profiling, ebof_edt_static,
+    ebof_stream_set_profiling, ebof_edt_static, ebof_stream_get_profile_level,
 )

@@ -99,6 +99,7 @@ def _declare(L):
     L.ebof_edt_static.argtypes = [vp, i32, i32, vp, vp, f32, vp]
     L.ebof_stream_set_profiling.argtypes = [vp, i32]
     L.ebof_stream_get_profile.argtypes = [vp, P(ctypes.c_double), P(i64), i32]
+    L.ebof_stream_get_profile_level.argtypes = [vp, i32, P(ctypes.c_double), P(i64), i32]
     L.ebof_stage_name.argtypes = [i32]
     L.ebof_stage_name.restype = ctypes.c_char_p
     L.ebof_kernel_launches.argtypes = []
@@ -108,7 +109,8 @@ def _declare(L):
     for name in ("ebof_stream_create", "ebof_stream_destroy", "ebof_stream_reset",
                  "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
                  "ebof_process_window_host", "ebof_stream_sync", "ebof_edt",
-                 "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static"):
+                 "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static",
+                 "ebof_stream_get_profile_level"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -304,6 +306,15 @@ def ebof_stream_get_profile(stream: Stream):
     ms = (ctypes.c_double * EBOF_STAGE_COUNT)()
     ln = (ctypes.c_int64 * EBOF_STAGE_COUNT)()
     st = load().ebof_stream_get_profile(stream.handle, ms, ln, EBOF_STAGE_COUNT)
+    return st, {ebof_stage_name(i): (ms[i], ln[i]) for i in range(EBOF_STAGE_COUNT)}
+
+
+def ebof_stream_get_profile_level(stream: Stream, level: int):
+    """Returns (status, {stage name: (ms, launches)}) for one pyramid level."""
+    ms = (ctypes.c_double * EBOF_STAGE_COUNT)()
+    ln = (ctypes.c_int64 * EBOF_STAGE_COUNT)()
+    st = load().ebof_stream_get_profile_level(stream.handle, int(level), ms, ln,
+                                              EBOF_STAGE_COUNT)
     return st, {ebof_stage_name(i): (ms[i], ln[i]) for i in range(EBOF_STAGE_COUNT)}
 
 

@@ -99,8 +99,8 @@ struct DeviceGuard {
 };
 
 struct ProfScope {
-    explicit ProfScope(Profiler *p) { tl_prof = p; }
-    ~ProfScope() { tl_prof = nullptr; }
+    explicit ProfScope(Profiler *p) { tl_prof = p; tl_level = -1; }
+    ~ProfScope() { tl_prof = nullptr; tl_level = -1; }
 };
 
 struct BusyGuard {
@@ -211,6 +211,7 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
     // A5: pyramid and gradients of the current window(s)
     const int nlev = std::max(geo.levels, 1);
     for (int l = 0; l < nlev; ++l) {
+        tl_level = l;
         const Level &lv = geo.lv[l];
         float *I = I0cur + geo.pyr_off[l];
         if (l > 0) {
@@ -234,6 +235,7 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
         float *Ucur = nullptr, *Uc = nullptr;
         const Level *lvc = nullptr;
         for (int l = geo.levels - 1; l >= 0; --l) {
+            tl_level = l;
             const Level &lv = geo.lv[l];
             const float *I0 = s->pyr + (size_t)prev_first * s->pyr_fs + geo.pyr_off[l];
             const float *I1 = s->pyr + (size_t)curf_first * s->pyr_fs + geo.pyr_off[l];
@@ -248,6 +250,7 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
             Uc = Ucur;
             lvc = &lv;
         }
+        tl_level = -1;
         launch_flow_out(Ucur, W, H, s->pitch0, s->u_fs, d_flow + (size_t)ff * flow_frame, nf,
                         st);
     }
@@ -563,8 +566,28 @@ ebof_status ebof_stream_get_profile(ebof_stream *s, double *ms, int64_t *launche
     DeviceGuard dg(s->device);
     s->prof.flush();
     for (int i = 0; i < n; ++i) {
-        if (ms) ms[i] = s->prof.ms[i];
-        if (launches) launches[i] = s->prof.launches[i];
+        double t = 0.0;
+        long long c = 0;
+        for (int l = 0; l < kProfLevels; ++l) { t += s->prof.ms[i][l]; c += s->prof.launches[i][l]; }
+        if (ms) ms[i] = t;
+        if (launches) launches[i] = c;
+    }
+    return EBOF_OK;
+}
+
+ebof_status ebof_stream_get_profile_level(ebof_stream *s, int32_t level, double *ms,
+                                          int64_t *launches, int32_t n)
+{
+    if (!s || n < 0 || n > EBOF_STAGE_COUNT || level < -1 || level >= kProfLevels - 1)
+        return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    s->prof.flush();
+    const int l = level < 0 ? kProfLevels - 1 : level;
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = s->prof.ms[i][l];
+        if (launches) launches[i] = s->prof.launches[i][l];
     }
     return EBOF_OK;
 }

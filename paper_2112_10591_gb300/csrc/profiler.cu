@@ -4,6 +4,7 @@
 namespace ebof {
 
 thread_local Profiler *tl_prof = nullptr;
+thread_local int tl_level = -1;
 std::atomic<unsigned long long> g_launches{0};
 
 const char *stage_name(int s)
@@ -34,8 +35,8 @@ void Profiler::flush()
     for (const Rec &r : recs) {
         float t = 0.0f;
         if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
-            ms[r.stage] += t;
-            launches[r.stage] += r.launches;
+            ms[r.stage][r.level] += t;
+            launches[r.stage][r.level] += r.launches;
         }
     }
     recs.clear();
@@ -45,7 +46,8 @@ void Profiler::flush()
 void Profiler::reset()
 {
     flush();
-    for (int i = 0; i < kNumStages; ++i) { ms[i] = 0.0; launches[i] = 0; }
+    for (int i = 0; i < kNumStages; ++i)
+        for (int l = 0; l < kProfLevels; ++l) { ms[i][l] = 0.0; launches[i][l] = 0; }
 }
 
 }  // namespace ebof

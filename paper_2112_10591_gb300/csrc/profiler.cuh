@@ -27,26 +27,31 @@ enum Stage {
 
 const char *stage_name(int s);
 
+constexpr int kProfLevels = 9;  // pyramid levels 0..7, and 8 = not level-specific
+
 struct Profiler {
     bool on = false;
     struct Rec {
         int stage;
+        int level;
         int launches;
         cudaEvent_t a, b;
     };
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     std::vector<Rec> recs;
-    double ms[kNumStages] = {};
-    long long launches[kNumStages] = {};
+    double ms[kNumStages][kProfLevels] = {};
+    long long launches[kNumStages][kProfLevels] = {};
     ~Profiler();
     cudaEvent_t get();
     void flush();   // waits for recorded events, accumulates, recycles them
     void reset();
 };
 
-// The profiler of the stream whose call is running on this host thread.
+// The profiler of the stream whose call is running on this host thread, and
+// the pyramid level its launches belong to (-1: not level-specific).
 extern thread_local Profiler *tl_prof;
+extern thread_local int tl_level;
 extern std::atomic<unsigned long long> g_launches;
 
 // Brackets one stage's launches on `st` (no-ops when timing is off).
@@ -63,7 +68,8 @@ struct StageScope {
             cudaEvent_t a = p->get();
             b = p->get();
             cudaEventRecord(a, st);
-            p->recs.push_back({stage, n, a, b});
+            const int lv = (tl_level >= 0 && tl_level < kProfLevels - 1) ? tl_level : kProfLevels - 1;
+            p->recs.push_back({stage, lv, n, a, b});
         }
     }
     ~StageScope()
