@@ -485,16 +485,55 @@ def main():
 
     # EPE of the GPU flow against the oracle sample (same windows)
     epe = None
+    nchk = min(len(oracle_flows) if oracle_flows is not None else 8, nwin - 1)
+    step_plain()
+    torch.cuda.synchronize(dev)
+    flows32 = [flows[k + 1].cpu().numpy() for k in range(nchk)]
     if oracle_flows is not None:
-        step_plain()
-        torch.cuda.synchronize(dev)
-        es = []
-        for k, U in enumerate(oracle_flows):
-            g = flows[k + 1].cpu().numpy()
-            es.append(np.hypot(g[0] - U[0], g[1] - U[1]))
-        e = np.stack(es)
+        e = np.stack([np.hypot(g[0] - U[0], g[1] - U[1])
+                      for g, U in zip(flows32, oracle_flows[:nchk])])
         epe = {"mean_px": float(e.mean()), "p99_px": float(np.percentile(e, 99)),
-               "frames": len(es)}
+               "frames": len(flows32)}
+
+    # FP16 storage of surfaces, pyramid levels and gradients (same stream)
+    fp16 = None
+    p16 = eb.ebof_default_params(W, H)
+    p16.storage = eb.EBOF_STORAGE_FP16
+    st16, s16 = eb.ebof_stream_create(p16, local)
+    if st16 >= 0:
+        def step_plain16():
+            eb.check(lib.ebof_stream_reset(s16.handle), "reset")
+            for k in range(nwin):
+                a, b = off[k], off[k + 1]
+                r = lib.ebof_process_window(
+                    s16.handle, xs.data_ptr() + 2 * a, ys.data_ptr() + 2 * a,
+                    ts.data_ptr() + 8 * a, ps.data_ptr() + a, b - a, tb[k], tb[k] + stream.dt,
+                    flows[k].data_ptr(), None, None, None, handle)
+                if r < 0:
+                    raise eb.EbofError(r, "process_window fp16")
+        for _ in range(args.warmup):
+            step_plain16()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(cs)
+        for _ in range(args.steps):
+            step_plain16()
+        f1.record(cs)
+        barrier()
+        fms, fval = combine_ranks(f0.elapsed_time(f1), frames_per_step * args.steps, world,
+                                  dist, dev)
+        flows16 = [flows[k + 1].cpu().numpy() for k in range(nchk)]
+        e16 = np.stack([np.hypot(a[0] - b[0], a[1] - b[1]) for a, b in zip(flows16, flows32)])
+        fp16 = {"value": fval, "unit": UNIT, "ms_per_step": fms / args.steps,
+                "epe_vs_fp32_gpu": {"mean_px": float(e16.mean()),
+                                    "p99_px": float(np.percentile(e16, 99)), "frames": nchk}}
+        if oracle_flows is not None:
+            eo = np.stack([np.hypot(a[0] - U[0], a[1] - U[1])
+                           for a, U in zip(flows16, oracle_flows[:nchk])])
+            fp16["epe_vs_oracle"] = {"mean_px": float(eo.mean()),
+                                     "p99_px": float(np.percentile(eo, 99)), "frames": nchk}
+        s16.close()
 
     # end-to-end through the host-buffer call
     e2e = None
@@ -550,6 +589,7 @@ def main():
             "wall_s": wall,
             "batched": batched,
             "epe_vs_oracle": epe,
+            "fp16_storage": fp16,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

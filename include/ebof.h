@@ -75,7 +75,14 @@ typedef struct {
     float var_alpha;        /* smoothness weight */
     float sor_omega;        /* SOR relaxation, 0 < omega < 2 */
     int32_t max_batch;      /* most windows one ebof_process_windows call may take */
+    int32_t storage;        /* EBOF_STORAGE_FP32, or EBOF_STORAGE_FP16: surfaces, pyramid
+                               levels and gradients stored in FP16 (half the bytes) as the
+                               complement 255 (1 - d_exp), to which the flow is invariant;
+                               patch sums, densification and the variational refinement
+                               stay FP32 */
 } ebof_params;
+
+enum { EBOF_STORAGE_FP32 = 0, EBOF_STORAGE_FP16 = 1 };
 
 /* Counts of one processed window. */
 typedef struct {
@@ -95,7 +102,7 @@ typedef struct ebof_stream ebof_stream;
  * of 12x12 patches from 640 px, stride 4, 12 Gauss-Newton iterations with
  * damping 0.1, 5 x 5
  * variational iterations (delta 5, gamma 10, alpha 20, omega 1.6),
- * max_batch 1. */
+ * max_batch 1, FP32 storage. */
 void ebof_default_params(ebof_params *p, int32_t width, int32_t height);
 
 /* Eq. 2 with eps = 1/255 (Eq. 3): alpha = d_sat / ln(255). */

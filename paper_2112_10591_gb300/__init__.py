@@ -13,4 +13,5 @@ from .binding import (  # noqa: F401
     ebof_stream_reset, ebof_stream_sync, ebof_window_stats, library_path, load,
     EBOF_STAGE_COUNT, ebof_kernel_launches, ebof_stage_name, ebof_stream_get_profile,
     ebof_stream_set_profiling, ebof_edt_static, ebof_stream_get_profile_level,
+    EBOF_STORAGE_FP16, EBOF_STORAGE_FP32,
 )

@@ -42,7 +42,12 @@ class ebof_params(ctypes.Structure):
         ("var_delta", ctypes.c_float), ("var_gamma", ctypes.c_float),
         ("var_alpha", ctypes.c_float), ("sor_omega", ctypes.c_float),
         ("max_batch", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
     ]
+
+
+EBOF_STORAGE_FP32 = 0
+EBOF_STORAGE_FP16 = 1
 
 
 class ebof_window_stats(ctypes.Structure):

@@ -54,7 +54,8 @@ struct ebof_stream {
     size_t e_fs, g_fs, pyr_fs, up_fs, u_fs, work_fs;
     uint8_t *E = nullptr, *Ed = nullptr, *Edf = nullptr;
     int32_t *g = nullptr;
-    float *pyr = nullptr;
+    char *pyr = nullptr;  // pyramid slots, es bytes per element
+    size_t es = 4;
     int nslots = 0, head = 0;
     bool has_prev = false;
     float *up = nullptr, *Ua = nullptr, *Ub = nullptr, *work = nullptr;
@@ -136,6 +137,8 @@ ebof_status check_params(const ebof_params *p)
         return EBOF_ERR_INVALID_ARG;
     if (!(p->sor_omega > 0.0f && p->sor_omega < 2.0f)) return EBOF_ERR_INVALID_ARG;
     if (p->max_batch < 1 || p->max_batch > 4096) return EBOF_ERR_INVALID_ARG;
+    if (p->storage != EBOF_STORAGE_FP32 && p->storage != EBOF_STORAGE_FP16)
+        return EBOF_ERR_INVALID_ARG;
     if (p->patch < 4 || p->patch > kMaxPatch) return EBOF_ERR_UNSUPPORTED;
     return EBOF_OK;
 }
@@ -158,6 +161,7 @@ void free_all(ebof_stream *s)
 FlowParams flow_params(const ebof_params &p)
 {
     FlowParams fp;
+    fp.half = p.storage == EBOF_STORAGE_FP16;
     fp.ps = p.patch;
     fp.stride = p.stride;
     fp.gn_iters = p.gn_iters;
@@ -186,17 +190,19 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
 
     if (n > 1 && s->head + n >= s->nslots) {
         if (s->has_prev && s->head != 0)
-            cudaMemcpyAsync(s->pyr, s->pyr + (size_t)s->head * s->pyr_fs,
-                            s->pyr_fs * sizeof(float), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(s->pyr, s->pyr + (size_t)s->head * s->pyr_fs * s->es,
+                            s->pyr_fs * s->es, cudaMemcpyDeviceToDevice, st);
         s->head = 0;
     }
     const int cur_first = n == 1 ? (s->head + 1) % s->nslots : s->head + 1;
     cudaMemsetAsync(s->dstats, 0, sizeof(DevStats) * n, st);
     cudaMemsetAsync(s->d_dropped_time, 0, sizeof(unsigned long long), st);
-    float *I0cur = s->pyr + (size_t)cur_first * s->pyr_fs;
+    const bool half = p.storage == EBOF_STORAGE_FP16;
+    const size_t es = s->es;
+    char *I0cur = s->pyr + (size_t)cur_first * s->pyr_fs * es;
 
     if (surface_in) {
-        launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, st);
+        launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, half, st);
     } else {
         cudaMemsetAsync(s->E, 0, s->e_fs * n, st);
         launch_scatter(x, y, t, nev, t_begin, dt, n, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
@@ -205,7 +211,7 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
                             p.n_d, p.n_f, d_edge, s->dstats, st);
         launch_edt_columns(s->Edf, s->pitch0, s->e_fs, W, H, s->g, s->pitch0, s->g_fs, n, st);
         launch_edt_rows_surface(s->g, s->pitch0, s->g_fs, W, H, p.alpha, d_edt, d_surface,
-                                I0cur, s->pitch0, s->pyr_fs, n, st);
+                                I0cur, s->pitch0, s->pyr_fs, n, half, st);
     }
 
     // A5: pyramid and gradients of the current window(s)
@@ -213,14 +219,14 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
     for (int l = 0; l < nlev; ++l) {
         tl_level = l;
         const Level &lv = geo.lv[l];
-        float *I = I0cur + geo.pyr_off[l];
+        char *I = I0cur + geo.pyr_off[l] * es;
         if (l > 0) {
             const Level &lp = geo.lv[l - 1];
-            launch_downsample(I0cur + geo.pyr_off[l - 1], lp.w, lp.h, lp.pitch, I, lv.w, lv.h,
-                              lv.pitch, s->pyr_fs, n, st);
+            launch_downsample(I0cur + geo.pyr_off[l - 1] * es, lp.w, lp.h, lp.pitch, I, lv.w,
+                              lv.h, lv.pitch, s->pyr_fs, n, half, st);
         }
-        launch_gradients(I, I + lv.plane, I + 2 * lv.plane, lv.w, lv.h, lv.pitch, s->pyr_fs, n,
-                         st);
+        launch_gradients(I, I + lv.plane * es, I + 2 * lv.plane * es, lv.w, lv.h, lv.pitch,
+                         s->pyr_fs, n, half, st);
     }
 
     // A6-A9: flow for every window that has a previous one
@@ -237,16 +243,17 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
         for (int l = geo.levels - 1; l >= 0; --l) {
             tl_level = l;
             const Level &lv = geo.lv[l];
-            const float *I0 = s->pyr + (size_t)prev_first * s->pyr_fs + geo.pyr_off[l];
-            const float *I1 = s->pyr + (size_t)curf_first * s->pyr_fs + geo.pyr_off[l];
+            const char *I0 = s->pyr + ((size_t)prev_first * s->pyr_fs + geo.pyr_off[l]) * es;
+            const char *I1 = s->pyr + ((size_t)curf_first * s->pyr_fs + geo.pyr_off[l]) * es;
+            const char *I0x = I0 + lv.plane * es, *I0y = I0 + 2 * lv.plane * es;
             Ucur = (Uc == s->Ua) ? s->Ub : s->Ua;
-            launch_patch_search(I0, I0 + lv.plane, I0 + 2 * lv.plane, I1, lv, s->pyr_fs, Uc, lvc,
-                                s->u_fs, s->up, s->up_fs, nf, fp, s->d_err, st);
+            launch_patch_search(I0, I0x, I0y, I1, lv, s->pyr_fs, Uc, lvc, s->u_fs, s->up,
+                                s->up_fs, nf, fp, s->d_err, st);
             launch_densify(I0, I1, lv, s->pyr_fs, s->up, s->up_fs, Ucur, s->u_fs, nf, fp, st);
             // the coarser flow is consumed by the search: its buffer is free
             float *Utmp = (Ucur == s->Ua) ? s->Ub : s->Ua;
-            Ucur = launch_variational(I0, I0 + lv.plane, I0 + 2 * lv.plane, I1, lv, s->pyr_fs,
-                                      Ucur, Utmp, s->u_fs, s->work, s->work_fs, nf, fp, st);
+            Ucur = launch_variational(I0, I0x, I0y, I1, lv, s->pyr_fs, Ucur, Utmp, s->u_fs,
+                                      s->work, s->work_fs, nf, fp, st);
             Uc = Ucur;
             lvc = &lv;
         }
@@ -304,6 +311,7 @@ void ebof_default_params(ebof_params *p, int32_t width, int32_t height)
     p->var_alpha = 20.0f;
     p->sor_omega = 1.6f;
     p->max_batch = 1;
+    p->storage = EBOF_STORAGE_FP32;
 }
 
 float ebof_alpha_from_dsat(float d_sat) { return d_sat / std::log(255.0f); }
@@ -340,7 +348,8 @@ ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **o
     ok &= dmalloc(&s->Ed, s->e_fs * B) == cudaSuccess;
     ok &= dmalloc(&s->Edf, s->e_fs * B) == cudaSuccess;
     ok &= dmalloc(&s->g, sizeof(int32_t) * s->g_fs * B) == cudaSuccess;
-    ok &= dmalloc(&s->pyr, sizeof(float) * s->pyr_fs * s->nslots) == cudaSuccess;
+    s->es = p->storage == EBOF_STORAGE_FP16 ? 2 : 4;
+    ok &= dmalloc(&s->pyr, s->es * s->pyr_fs * s->nslots) == cudaSuccess;
     ok &= dmalloc(&s->up, sizeof(float) * s->up_fs * B) == cudaSuccess;
     ok &= dmalloc(&s->Ua, sizeof(float) * s->u_fs * B) == cudaSuccess;
     ok &= dmalloc(&s->Ub, sizeof(float) * s->u_fs * B) == cudaSuccess;
@@ -535,7 +544,7 @@ ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32
     const size_t plane = (size_t)width * height;
     launch_edt_columns(d_edge, width, plane, width, height, d_scratch, width, plane, 1, st);
     launch_edt_rows_surface(d_scratch, width, plane, width, height, alpha, d_edt, d_surface,
-                            nullptr, width, plane, 1, st);
+                            nullptr, width, plane, 1, false, st);
     return cudaGetLastError() == cudaSuccess ? EBOF_OK : EBOF_ERR_CUDA;
 }
 

@@ -1,14 +1,23 @@
 // dev_common.cuh -- small device helpers shared by the flow kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace ebof {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+// Pyramid storage: FP32, or FP16 with every load widened to FP32 and every
+// store rounded to nearest.
+__device__ __forceinline__ float ldp(const float *p) { return *p; }
+__device__ __forceinline__ float ldp(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ void stp(float *p, float v) { *p = v; }
+__device__ __forceinline__ void stp(__half *p, float v) { *p = __float2half_rn(v); }
+
 // Bilinear sample with the position clamped to [0, w-1] x [0, h-1].
-__device__ __forceinline__ float bilinear(const float *__restrict__ I, int w, int h, int pitch,
+template <typename T>
+__device__ __forceinline__ float bilinear(const T *__restrict__ I, int w, int h, int pitch,
                                           float x, float y)
 {
     x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
@@ -17,8 +26,8 @@ __device__ __forceinline__ float bilinear(const float *__restrict__ I, int w, in
     const int x0 = (int)xf, y0 = (int)yf;
     const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
     const float fx = x - xf, fy = y - yf;
-    const float a = I[(size_t)y0 * pitch + x0], b = I[(size_t)y0 * pitch + x1];
-    const float c = I[(size_t)y1 * pitch + x0], d = I[(size_t)y1 * pitch + x1];
+    const float a = ldp(&I[(size_t)y0 * pitch + x0]), b = ldp(&I[(size_t)y0 * pitch + x1]);
+    const float c = ldp(&I[(size_t)y1 * pitch + x0]), d = ldp(&I[(size_t)y1 * pitch + x1]);
     return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
 }
 

@@ -49,6 +49,7 @@ struct DevStats {
 // Kernel parameter bundles ---------------------------------------------------
 
 struct FlowParams {
+    bool half;  // pyramid stored as FP16 (loads widened to FP32)
     int ps, stride, gn_iters;
     float gn_damping;
     int var_outer, var_sor;
@@ -75,45 +76,46 @@ void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stri
 
 // A4: per-row lower envelope -> D, fused Eq. 1 surface and 255 * surface.
 void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
-                             float alpha, int32_t *D_dense, float *S_dense, float *I0,
-                             int i_pitch, size_t i_frame_stride, int frames, cudaStream_t st);
+                             float alpha, int32_t *D_dense, float *S_dense, void *I0,
+                             int i_pitch, size_t i_frame_stride, int frames, bool half,
+                             cudaStream_t st);
 
 // Per-device kernel attributes (opt-in shared memory); call with the device current.
 void init_front_attributes();
 void init_flow_attributes();
 
 // Surface given by the caller -> 255 * d_exp into the level-0 image.
-void launch_surface_to_intensity(const float *S, int W, int H, float *I0, int pitch,
+void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pitch, bool half,
                                  cudaStream_t st);
 
 // A5: gradients of level l, and downsample l -> l+1 (then its gradients).
-void launch_gradients(const float *I, float *Ix, float *Iy, int w, int h, int pitch,
-                      size_t frame_stride, int frames, cudaStream_t st);
-void launch_downsample(const float *I, int w, int h, int pitch, float *out, int wc, int hc,
-                       int pitch_c, size_t frame_stride, int frames, cudaStream_t st);
+void launch_gradients(const void *I, void *Ix, void *Iy, int w, int h, int pitch,
+                      size_t frame_stride, int frames, bool half, cudaStream_t st);
+void launch_downsample(const void *I, int w, int h, int pitch, void *out, int wc, int hc,
+                       int pitch_c, size_t frame_stride, int frames, bool half, cudaStream_t st);
 
 // A6: patch inverse search at one level.
-void launch_patch_search(const float *I0, const float *I0x, const float *I0y, const float *I1,
+void launch_patch_search(const void *I0, const void *I0x, const void *I0y, const void *I1,
                          const Level &lv, size_t pyr_frame_stride, const float *Uc,
                          const Level *lvc, size_t uc_frame_stride, float *up,
                          size_t up_frame_stride, int frames, const FlowParams &fp,
                          int *err, cudaStream_t st);
 
 // A7: densification.
-void launch_densify(const float *I0, const float *I1, const Level &lv, size_t pyr_frame_stride,
+void launch_densify(const void *I0, const void *I1, const Level &lv, size_t pyr_frame_stride,
                     const float *up, size_t up_frame_stride, float *U, size_t u_frame_stride,
                     int frames, const FlowParams &fp, cudaStream_t st);
 
 // A8: variational refinement of U.  Returns the buffer holding the result:
 // U itself, or Utmp (same shape as U) when the fused kernel ping-pongs.
-float *launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
+float *launch_variational(const void *I0, const void *I0x, const void *I0y, const void *I1,
                           const Level &lv, size_t pyr_frame_stride, float *U, float *Utmp,
                           size_t u_frame_stride, float *work, size_t work_frame_stride,
                           int frames, const FlowParams &fp, cudaStream_t st);
 bool var_fused_supported(int var_sor);
 void init_var_attributes();
-float *launch_variational_fused(const float *I0, const float *I0x, const float *I0y,
-                                const float *I1, const Level &lv, size_t pyr_frame_stride,
+float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y,
+                                const void *I1, const Level &lv, size_t pyr_frame_stride,
                                 float *U, float *Utmp, size_t u_frame_stride, float *coef,
                                 size_t coef_frame_stride, int frames, const FlowParams &fp,
                                 cudaStream_t st);

@@ -57,6 +57,6 @@ extern "C" ebof_status ebof_edt_static(const uint8_t *d_edge, int32_t width, int
     const size_t plane = (size_t)width * height;
     ebof::launch_edt_columns(d_edge, width, plane, width, height, scratch, width, plane, 1, st);
     ebof::launch_edt_rows_surface(scratch, width, plane, width, height, alpha, d_edt, d_surface,
-                                  nullptr, width, plane, 1, st);
+                                  nullptr, width, plane, 1, false, st);
     return cudaGetLastError() == cudaSuccess ? EBOF_OK : EBOF_ERR_CUDA;
 }

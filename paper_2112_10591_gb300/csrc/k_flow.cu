@@ -20,31 +20,33 @@ namespace ebof {
 namespace {
 
 // ---------------------------------------------------------------- A5
-__global__ void gradients_kernel(const float *__restrict__ I, float *__restrict__ Ix,
-                                 float *__restrict__ Iy, int w, int h, int pitch, size_t fs)
+template <typename T>
+__global__ void gradients_kernel(const T *__restrict__ I, T *__restrict__ Ix,
+                                 T *__restrict__ Iy, int w, int h, int pitch, size_t fs)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= w || y >= h) return;
     const size_t fo = (size_t)blockIdx.z * fs;
-    const float *im = I + fo;
+    const T *im = I + fo;
     const int xp = min(x + 1, w - 1), xm = max(x - 1, 0);
     const int yp = min(y + 1, h - 1), ym = max(y - 1, 0);
     const size_t p = (size_t)y * pitch + x;
-    Ix[fo + p] = 0.5f * (im[(size_t)y * pitch + xp] - im[(size_t)y * pitch + xm]);
-    Iy[fo + p] = 0.5f * (im[(size_t)yp * pitch + x] - im[(size_t)ym * pitch + x]);
+    stp(&Ix[fo + p], 0.5f * (ldp(&im[(size_t)y * pitch + xp]) - ldp(&im[(size_t)y * pitch + xm])));
+    stp(&Iy[fo + p], 0.5f * (ldp(&im[(size_t)yp * pitch + x]) - ldp(&im[(size_t)ym * pitch + x])));
 }
 
-__global__ void downsample_kernel(const float *__restrict__ I, int pitch, float *__restrict__ out,
+template <typename T>
+__global__ void downsample_kernel(const T *__restrict__ I, int pitch, T *__restrict__ out,
                                   int wc, int hc, int pitch_c, size_t fs)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= wc || y >= hc) return;
-    const float *im = I + (size_t)blockIdx.z * fs;
+    const T *im = I + (size_t)blockIdx.z * fs;
     const size_t r0 = (size_t)(2 * y) * pitch + 2 * x, r1 = r0 + pitch;
-    out[(size_t)blockIdx.z * fs + (size_t)y * pitch_c + x] =
-        0.25f * (im[r0] + im[r0 + 1] + im[r1] + im[r1 + 1]);
+    stp(&out[(size_t)blockIdx.z * fs + (size_t)y * pitch_c + x],
+        0.25f * (ldp(&im[r0]) + ldp(&im[r0 + 1]) + ldp(&im[r1]) + ldp(&im[r1 + 1])));
 }
 
 // ---------------------------------------------------------------- A6
@@ -62,10 +64,10 @@ __device__ __forceinline__ float group_sum(float v)
     return v;
 }
 
-template <int PS, int G>
+template <int PS, int G, typename T>
 __global__ void __launch_bounds__(128)
-patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
-                    const float *__restrict__ I0yb, const float *__restrict__ I1b, int w, int h,
+patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
+                    const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
                     int pitch, size_t pfs, int npx, int npy, const float *__restrict__ Ucb, int wc,
                     int hc, int pitch_c, size_t plane_c, size_t ucfs, float *__restrict__ upb,
                     size_t upfs, int stride, int iters, float kappa, int *err)
@@ -79,8 +81,8 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
     const int i = pid % npx, j = pid / npx;
     const int x0 = min(i * stride, w - PS), y0 = min(j * stride, h - PS);
     const bool active = c < PS;
-    const float *I0 = I0b + (size_t)f * pfs, *I0x = I0xb + (size_t)f * pfs;
-    const float *I0y = I0yb + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
+    const T *I0 = I0b + (size_t)f * pfs, *I0x = I0xb + (size_t)f * pfs;
+    const T *I0y = I0yb + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
     if (x0 < 0 || y0 < 0) {  // cannot happen when the level holds a patch
         if (real && c == 0) atomicOr(err, kErrBounds);
     }
@@ -96,15 +98,15 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
     }
 
     // F4: template, mean-normalised gradients, Hessian
-    float T[PS], GX[PS], GY[PS];
+    float Tm[PS], GX[PS], GY[PS];
     float sgx = 0.0f, sgy = 0.0f;
     const int xc = active ? x0 + c : x0;
 #pragma unroll
     for (int r = 0; r < PS; ++r) {
         const size_t p = (size_t)(y0 + r) * pitch + xc;
-        T[r] = active ? I0[p] : 0.0f;
-        GX[r] = active ? I0x[p] : 0.0f;
-        GY[r] = active ? I0y[p] : 0.0f;
+        Tm[r] = active ? ldp(&I0[p]) : 0.0f;
+        GX[r] = active ? ldp(&I0x[p]) : 0.0f;
+        GY[r] = active ? ldp(&I0y[p]) : 0.0f;
         sgx += GX[r]; sgy += GY[r];
     }
     constexpr float inv_n = 1.0f / (PS * PS);
@@ -142,13 +144,13 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
         float Wv[PS];
         if (fast) {
             if (active) {
-                const float *pp = I1 + (size_t)sy0 * pitch + sx0 + c;
-                float a = pp[0], b = pp[1];
+                const T *pp = I1 + (size_t)sy0 * pitch + sx0 + c;
+                float a = ldp(&pp[0]), b = ldp(&pp[1]);
                 float hp = a + ax * (b - a);
 #pragma unroll
                 for (int r = 0; r < PS; ++r) {
-                    const float *q = pp + (size_t)(r + 1) * pitch;
-                    const float c2 = q[0], d2 = q[1];
+                    const T *q = pp + (size_t)(r + 1) * pitch;
+                    const float c2 = ldp(&q[0]), d2 = ldp(&q[1]);
                     const float hn = c2 + ax * (d2 - c2);
                     Wv[r] = hp + ay * (hn - hp);
                     hp = hn;
@@ -169,7 +171,7 @@ patch_search_kernel(const float *__restrict__ I0b, const float *__restrict__ I0x
         float b1 = 0.0f, b2 = 0.0f;
 #pragma unroll
         for (int r = 0; r < PS; ++r) {
-            const float res = Wv[r] - T[r];
+            const float res = Wv[r] - Tm[r];
             b1 += GX[r] * res; b2 += GY[r] * res;
         }
         b1 = group_sum<G>(b1); b2 = group_sum<G>(b2);
@@ -196,7 +198,8 @@ __device__ __forceinline__ void cover_range(int x, int n, int ps, int stride, in
     last = x >= n - ps;
 }
 
-__global__ void densify_kernel(const float *__restrict__ I0b, const float *__restrict__ I1b,
+template <typename T>
+__global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ I1b,
                                int w, int h, int pitch, size_t pfs, const float *__restrict__ upb,
                                size_t upfs, int npx, int npy, float *__restrict__ Ub, size_t ufs,
                                size_t plane, int ps, int stride)
@@ -205,14 +208,14 @@ __global__ void densify_kernel(const float *__restrict__ I0b, const float *__res
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= w || y >= h) return;
     const int f = blockIdx.z;
-    const float *I0 = I0b + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
+    const T *I0 = I0b + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
     const float *up = upb + (size_t)f * upfs;
     const int np = npx * npy;
     int ilo, ihi, jlo, jhi;
     bool ilast, jlast;
     cover_range(x, w, ps, stride, npx, ilo, ihi, ilast);
     cover_range(y, h, ps, stride, npy, jlo, jhi, jlast);
-    const float i0 = I0[(size_t)y * pitch + x];
+    const float i0 = ldp(&I0[(size_t)y * pitch + x]);
     float nu = 0.0f, nv = 0.0f, den = 0.0f;
     for (int jj = jlo; jj <= jhi + 1; ++jj) {
         int j = jj;
@@ -237,7 +240,8 @@ __global__ void densify_kernel(const float *__restrict__ I0b, const float *__res
 // Work planes (each lv.plane floats) of one frame.
 enum { kW1 = 0, kA11, kA12, kA22, kB1, kB2, kAS, kDU, kDV, kWorkPlanes };
 
-__global__ void warp_kernel(const float *__restrict__ I1b, int w, int h, int pitch, size_t pfs,
+template <typename T>
+__global__ void warp_kernel(const T *__restrict__ I1b, int w, int h, int pitch, size_t pfs,
                             const float *__restrict__ Ub, size_t ufs, size_t plane,
                             float *__restrict__ workb, size_t wfs)
 {
@@ -251,8 +255,9 @@ __global__ void warp_kernel(const float *__restrict__ I1b, int w, int h, int pit
         bilinear(I1b + (size_t)f * pfs, w, h, pitch, (float)x + U[p], (float)y + U[plane + p]);
 }
 
-__global__ void coeff_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
-                             const float *__restrict__ I0yb, int w, int h, int pitch, size_t pfs,
+template <typename T>
+__global__ void coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
+                             const T *__restrict__ I0yb, int w, int h, int pitch, size_t pfs,
                              const float *__restrict__ Ub, size_t ufs, size_t plane,
                              float *__restrict__ workb, size_t wfs, float delta, float gamma,
                              float alpha_s)
@@ -279,9 +284,9 @@ __global__ void coeff_kernel(const float *__restrict__ I0b, const float *__restr
     const float Ixy = 0.5f * (dx(x, yp) - dx(x, ym));
     const float Iyy = 0.5f * (dy(x, yp) - dy(x, ym));
     const size_t fo = (size_t)f * pfs;
-    const float Iz = at(x, y) - I0b[fo + p];
-    const float Ixz = Ix - I0xb[fo + p];
-    const float Iyz = Iy - I0yb[fo + p];
+    const float Iz = at(x, y) - ldp(&I0b[fo + p]);
+    const float Ixz = Ix - ldp(&I0xb[fo + p]);
+    const float Iyz = Iy - ldp(&I0yb[fo + p]);
     const float nd = 1.0f / (Ix * Ix + Iy * Iy + kZeta2);
     const float ng = 1.0f / (Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
     float ad = delta * nd * psi_prime(nd * Iz * Iz);
@@ -367,8 +372,8 @@ __global__ void flow_out_kernel(const float *__restrict__ Ub, int W, int H, int 
     flow[o + (size_t)W * H] = U[plane + (size_t)y * pitch + x];
 }
 
-template <int PS>
-void search_ps(const float *I0, const float *I0x, const float *I0y, const float *I1,
+template <int PS, typename T>
+void search_ps(const T *I0, const T *I0x, const T *I0y, const T *I1,
                const Level &lv, size_t pfs, const float *Uc, const Level *lvc, size_t ucfs,
                float *up, size_t upfs, int frames, const FlowParams &fp, int *err, cudaStream_t st)
 {
@@ -376,7 +381,7 @@ void search_ps(const float *I0, const float *I0x, const float *I0y, const float 
     const int np = lv.npx * lv.npy;
     const int per_block = 128 / G;
     dim3 grd((np + per_block - 1) / per_block, frames);
-    patch_search_kernel<PS, G><<<grd, 128, 0, st>>>(
+    patch_search_kernel<PS, G, T><<<grd, 128, 0, st>>>(
         I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pfs, lv.npx, lv.npy, Uc, lvc ? lvc->w : 0,
         lvc ? lvc->h : 0, lvc ? lvc->pitch : 0, lvc ? lvc->plane : 0, ucfs, up, upfs, fp.stride,
         fp.gn_iters, fp.gn_damping, err);
@@ -391,37 +396,44 @@ dim3 grid2d(int w, int h, int frames, dim3 blk)
 
 void init_flow_attributes() { init_var_attributes(); }
 
-void launch_gradients(const float *I, float *Ix, float *Iy, int w, int h, int pitch,
-                      size_t frame_stride, int frames, cudaStream_t st)
+void launch_gradients(const void *I, void *Ix, void *Iy, int w, int h, int pitch,
+                      size_t frame_stride, int frames, bool half, cudaStream_t st)
 {
     StageScope sc(kStPyramid, 1, st);
     dim3 blk(32, 8);
-    gradients_kernel<<<grid2d(w, h, frames, blk), blk, 0, st>>>(I, Ix, Iy, w, h, pitch,
-                                                                frame_stride);
+    if (half)
+        gradients_kernel<__half><<<grid2d(w, h, frames, blk), blk, 0, st>>>(
+            (const __half *)I, (__half *)Ix, (__half *)Iy, w, h, pitch, frame_stride);
+    else
+        gradients_kernel<float><<<grid2d(w, h, frames, blk), blk, 0, st>>>(
+            (const float *)I, (float *)Ix, (float *)Iy, w, h, pitch, frame_stride);
 }
 
-void launch_downsample(const float *I, int w, int h, int pitch, float *out, int wc, int hc,
-                       int pitch_c, size_t frame_stride, int frames, cudaStream_t st)
+void launch_downsample(const void *I, int w, int h, int pitch, void *out, int wc, int hc,
+                       int pitch_c, size_t frame_stride, int frames, bool half, cudaStream_t st)
 {
     (void)w; (void)h;
     StageScope sc(kStPyramid, 1, st);
     dim3 blk(32, 8);
-    downsample_kernel<<<grid2d(wc, hc, frames, blk), blk, 0, st>>>(I, pitch, out, wc, hc,
-                                                                   pitch_c, frame_stride);
+    if (half)
+        downsample_kernel<__half><<<grid2d(wc, hc, frames, blk), blk, 0, st>>>(
+            (const __half *)I, pitch, (__half *)out, wc, hc, pitch_c, frame_stride);
+    else
+        downsample_kernel<float><<<grid2d(wc, hc, frames, blk), blk, 0, st>>>(
+            (const float *)I, pitch, (float *)out, wc, hc, pitch_c, frame_stride);
 }
 
-void launch_patch_search(const float *I0, const float *I0x, const float *I0y, const float *I1,
-                         const Level &lv, size_t pyr_frame_stride, const float *Uc,
-                         const Level *lvc, size_t uc_frame_stride, float *up,
-                         size_t up_frame_stride, int frames, const FlowParams &fp, int *err,
-                         cudaStream_t st)
+template <typename T>
+void launch_patch_search_t(const T *I0, const T *I0x, const T *I0y, const T *I1,
+                           const Level &lv, size_t pyr_frame_stride, const float *Uc,
+                           const Level *lvc, size_t uc_frame_stride, float *up,
+                           size_t up_frame_stride, int frames, const FlowParams &fp, int *err,
+                           cudaStream_t st)
 {
-    if (lv.npx * lv.npy <= 0) return;
-    StageScope sc(kStSearch, 1, st);
 #define EBOF_PS(N)                                                                              \
     case N:                                                                                     \
-        search_ps<N>(I0, I0x, I0y, I1, lv, pyr_frame_stride, Uc, lvc, uc_frame_stride, up,      \
-                     up_frame_stride, frames, fp, err, st);                                     \
+        search_ps<N, T>(I0, I0x, I0y, I1, lv, pyr_frame_stride, Uc, lvc, uc_frame_stride, up,   \
+                        up_frame_stride, frames, fp, err, st);                                  \
         break;
     switch (fp.ps) {
         EBOF_PS(4) EBOF_PS(5) EBOF_PS(6) EBOF_PS(7) EBOF_PS(8) EBOF_PS(9) EBOF_PS(10)
@@ -431,41 +443,61 @@ void launch_patch_search(const float *I0, const float *I0x, const float *I0y, co
 #undef EBOF_PS
 }
 
-void launch_densify(const float *I0, const float *I1, const Level &lv, size_t pyr_frame_stride,
+void launch_patch_search(const void *I0, const void *I0x, const void *I0y, const void *I1,
+                         const Level &lv, size_t pyr_frame_stride, const float *Uc,
+                         const Level *lvc, size_t uc_frame_stride, float *up,
+                         size_t up_frame_stride, int frames, const FlowParams &fp, int *err,
+                         cudaStream_t st)
+{
+    if (lv.npx * lv.npy <= 0) return;
+    StageScope sc(kStSearch, 1, st);
+    if (fp.half)
+        launch_patch_search_t((const __half *)I0, (const __half *)I0x, (const __half *)I0y,
+                              (const __half *)I1, lv, pyr_frame_stride, Uc, lvc, uc_frame_stride,
+                              up, up_frame_stride, frames, fp, err, st);
+    else
+        launch_patch_search_t((const float *)I0, (const float *)I0x, (const float *)I0y,
+                              (const float *)I1, lv, pyr_frame_stride, Uc, lvc, uc_frame_stride,
+                              up, up_frame_stride, frames, fp, err, st);
+}
+
+void launch_densify(const void *I0, const void *I1, const Level &lv, size_t pyr_frame_stride,
                     const float *up, size_t up_frame_stride, float *U, size_t u_frame_stride,
                     int frames, const FlowParams &fp, cudaStream_t st)
 {
     StageScope sc(kStDensify, 1, st);
     dim3 blk(32, 8);
-    densify_kernel<<<grid2d(lv.w, lv.h, frames, blk), blk, 0, st>>>(
-        I0, I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, up, up_frame_stride, lv.npx, lv.npy, U,
-        u_frame_stride, lv.plane, fp.ps, fp.stride);
+    if (fp.half)
+        densify_kernel<__half><<<grid2d(lv.w, lv.h, frames, blk), blk, 0, st>>>(
+            (const __half *)I0, (const __half *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, up,
+            up_frame_stride, lv.npx, lv.npy, U, u_frame_stride, lv.plane, fp.ps, fp.stride);
+    else
+        densify_kernel<float><<<grid2d(lv.w, lv.h, frames, blk), blk, 0, st>>>(
+            (const float *)I0, (const float *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, up,
+            up_frame_stride, lv.npx, lv.npy, U, u_frame_stride, lv.plane, fp.ps, fp.stride);
 }
 
-float *launch_variational(const float *I0, const float *I0x, const float *I0y, const float *I1,
-                          const Level &lv, size_t pyr_frame_stride, float *U, float *Utmp,
-                          size_t u_frame_stride, float *work, size_t work_frame_stride,
-                          int frames, const FlowParams &fp, cudaStream_t st)
+template <typename T>
+void variational_steps(const T *I0, const T *I0x, const T *I0y, const T *I1, const Level &lv,
+                       size_t pyr_frame_stride, float *U, size_t u_frame_stride, float *work,
+                       size_t work_frame_stride, int frames, const FlowParams &fp,
+                       cudaStream_t st)
 {
-    if (fp.var_outer <= 0) return U;
-    if (var_fused_supported(fp.var_sor))
-        return launch_variational_fused(I0, I0x, I0y, I1, lv, pyr_frame_stride, U, Utmp,
-                                        u_frame_stride, work, work_frame_stride, frames, fp, st);
-    // many sweeps: one launch per step, state in global memory
     dim3 blk(32, 8);
     const dim3 grd = grid2d(lv.w, lv.h, frames, blk);
     const dim3 grd_half = grid2d((lv.w + 1) / 2, lv.h, frames, blk);
     for (int k = 0; k < fp.var_outer; ++k) {
         {
             StageScope sc(kStVarWarp, 1, st);
-            warp_kernel<<<grd, blk, 0, st>>>(I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, U,
-                                             u_frame_stride, lv.plane, work, work_frame_stride);
+            warp_kernel<T><<<grd, blk, 0, st>>>(I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, U,
+                                                u_frame_stride, lv.plane, work, work_frame_stride);
         }
         {
             StageScope sc(kStVarCoeff, 1, st);
-            coeff_kernel<<<grd, blk, 0, st>>>(I0, I0x, I0y, lv.w, lv.h, lv.pitch,
-                                              pyr_frame_stride, U, u_frame_stride, lv.plane, work,
-                                              work_frame_stride, fp.delta, fp.gamma, fp.alpha_s);
+            coeff_kernel<T><<<grd, blk, 0, st>>>(I0, I0x, I0y, lv.w, lv.h, lv.pitch,
+                                                 pyr_frame_stride, U, u_frame_stride, lv.plane,
+                                                 work, work_frame_stride, fp.delta, fp.gamma,
+                                                 fp.alpha_s);
         }
         if (fp.var_sor > 0) {
             StageScope sc(kStVarSor, 2 * fp.var_sor, st);
@@ -481,6 +513,26 @@ float *launch_variational(const float *I0, const float *I0x, const float *I0y, c
                                             work, work_frame_stride);
         }
     }
+}
+
+float *launch_variational(const void *I0, const void *I0x, const void *I0y, const void *I1,
+                          const Level &lv, size_t pyr_frame_stride, float *U, float *Utmp,
+                          size_t u_frame_stride, float *work, size_t work_frame_stride,
+                          int frames, const FlowParams &fp, cudaStream_t st)
+{
+    if (fp.var_outer <= 0) return U;
+    if (var_fused_supported(fp.var_sor))
+        return launch_variational_fused(I0, I0x, I0y, I1, lv, pyr_frame_stride, U, Utmp,
+                                        u_frame_stride, work, work_frame_stride, frames, fp, st);
+    // many sweeps: one launch per step, state in global memory
+    if (fp.half)
+        variational_steps((const __half *)I0, (const __half *)I0x, (const __half *)I0y,
+                          (const __half *)I1, lv, pyr_frame_stride, U, u_frame_stride, work,
+                          work_frame_stride, frames, fp, st);
+    else
+        variational_steps((const float *)I0, (const float *)I0x, (const float *)I0y,
+                          (const float *)I1, lv, pyr_frame_stride, U, u_frame_stride, work,
+                          work_frame_stride, frames, fp, st);
     return U;
 }
 

@@ -8,6 +8,8 @@
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
 
+#include <cuda_fp16.h>
+
 namespace ebof {
 
 namespace {
@@ -233,11 +235,24 @@ __host__ __device__ __forceinline__ size_t rows_smem_words(int W, int wpr)
     return 3 * (size_t)W + 32 * (size_t)wpr + 1;
 }
 
-template <int WPR>
+// Level-0 intensity of the flow block.  FP32 storage keeps I = 255 d_exp.
+// FP16 storage keeps the complement C = 255 - I = 255 exp(-d / alpha): the
+// flow is the same for I and 255 - I (mean-normalised patches, squared
+// residuals and products of derivatives), and far from the edges, where I
+// saturates towards 255 and its variations are far below FP16's 0.125 step
+// there, C is small and keeps them at FP16's relative precision.
+__device__ __forceinline__ void st_int(float *p, float s, float c) { (void)c; *p = 255.0f * s; }
+__device__ __forceinline__ void st_int(__half *p, float s, float c)
+{
+    (void)s;
+    *p = __float2half_rn(255.0f * c);
+}
+
+template <int WPR, typename T>
 __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs,
                                         int W, int H, int rows_per_block, float alpha,
                                         int32_t *__restrict__ D_dense,
-                                        float *__restrict__ S_dense, float *__restrict__ I0,
+                                        float *__restrict__ S_dense, T *__restrict__ I0,
                                         int ipitch, size_t ifs)
 {
     constexpr int NB = 32 * WPR;
@@ -340,26 +355,31 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
     __syncthreads();
 
     if (!valid) return;
-    float *irow = I0 ? I0 + (size_t)f * ifs + (size_t)y * ipitch : nullptr;
+    T *irow = I0 ? I0 + (size_t)f * ifs + (size_t)y * ipitch : nullptr;
     const size_t dbase = (size_t)f * W * H + (size_t)y * W;
     for (int x = tr; x < W; x += NB) {
         const int32_t D = any ? res[x] : kInfD;
-        float S = 1.0f;
-        if (D != kInfD) S = 1.0f - expf(-sqrtf((float)D) / alpha);
-        if (irow) irow[x] = 255.0f * S;
+        float S = 1.0f, C = 0.0f;  // d_exp of Eq. 1 and its complement 1 - d_exp
+        if (D != kInfD) {
+            C = expf(-sqrtf((float)D) / alpha);
+            S = 1.0f - C;
+        }
+        if (irow) st_int(&irow[x], S, C);
         if (D_dense) D_dense[dbase + x] = D;
         if (S_dense) S_dense[dbase + x] = S;
     }
 }
 
 // Caller-given surface (dense, d_exp in [0, 1]) to the level-0 intensity.
+template <typename T>
 __global__ void surface_to_intensity_kernel(const float *__restrict__ S, int W, int H,
-                                            float *__restrict__ I0, int pitch)
+                                            T *__restrict__ I0, int pitch)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W) return;
-    I0[(size_t)y * pitch + x] = 255.0f * S[(size_t)y * W + x];
+    const float sv = S[(size_t)y * W + x];
+    st_int(&I0[(size_t)y * pitch + x], sv, 1.0f - sv);
 }
 
 inline unsigned grid1d(int64_t n, int block, int cap)
@@ -421,39 +441,60 @@ int edt_rows_per_block(int W)
     return rows;
 }
 
-void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
-                             float alpha, int32_t *D_dense, float *S_dense, float *I0,
-                             int i_pitch, size_t i_frame_stride, int frames, cudaStream_t st)
+template <typename T>
+void edt_rows_t(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H, float alpha,
+                int32_t *D_dense, float *S_dense, T *I0, int i_pitch, size_t i_frame_stride,
+                int frames, cudaStream_t st)
 {
     const int rows = edt_rows_per_block(W);
     const int wpr = edt_rows_wpr(W);
     const size_t smem = edt_rows_smem(W, rows);
-    StageScope sc(kStEdtRows, 1, st);
     dim3 grd((H + rows - 1) / rows, frames);
     if (wpr == 2)
-        edt_rows_surface_kernel<2><<<grd, 32 * 2 * rows, smem, st>>>(
+        edt_rows_surface_kernel<2, T><<<grd, 32 * 2 * rows, smem, st>>>(
             g, g_pitch, g_frame_stride, W, H, rows, alpha, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
     else
-        edt_rows_surface_kernel<1><<<grd, 32 * rows, smem, st>>>(
+        edt_rows_surface_kernel<1, T><<<grd, 32 * rows, smem, st>>>(
             g, g_pitch, g_frame_stride, W, H, rows, alpha, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
+}
+
+void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
+                             float alpha, int32_t *D_dense, float *S_dense, void *I0,
+                             int i_pitch, size_t i_frame_stride, int frames, bool half,
+                             cudaStream_t st)
+{
+    StageScope sc(kStEdtRows, 1, st);
+    if (half)
+        edt_rows_t(g, g_pitch, g_frame_stride, W, H, alpha, D_dense, S_dense, (__half *)I0,
+                   i_pitch, i_frame_stride, frames, st);
+    else
+        edt_rows_t(g, g_pitch, g_frame_stride, W, H, alpha, D_dense, S_dense, (float *)I0,
+                   i_pitch, i_frame_stride, frames, st);
 }
 
 void init_front_attributes()
 {
-    cudaFuncSetAttribute(edt_rows_surface_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         210 * 1024);
+    cudaFuncSetAttribute(edt_rows_surface_kernel<1, float>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(edt_rows_surface_kernel<2, float>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(edt_rows_surface_kernel<1, __half>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(edt_rows_surface_kernel<2, __half>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
 }
 
-void launch_surface_to_intensity(const float *S, int W, int H, float *I0, int pitch,
+void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pitch, bool half,
                                  cudaStream_t st)
 {
     StageScope sc(kStEdtRows, 1, st);
     dim3 grd((W + 255) / 256, H);
-    surface_to_intensity_kernel<<<grd, 256, 0, st>>>(S, W, H, I0, pitch);
+    if (half)
+        surface_to_intensity_kernel<__half><<<grd, 256, 0, st>>>(S, W, H, (__half *)I0, pitch);
+    else
+        surface_to_intensity_kernel<float><<<grd, 256, 0, st>>>(S, W, H, (float *)I0, pitch);
 }
 
 }  // namespace ebof

@@ -128,9 +128,10 @@ __device__ __forceinline__ void sor_sweeps(float (&du)[kVS][2], float (&dv)[kVS]
     __syncthreads();
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kAX * kAY)
-var_coeff_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
-                 const float *__restrict__ I0yb, const float *__restrict__ I1b, int w, int h,
+var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
+                 const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
                  int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs, size_t plane,
                  float *__restrict__ coefb, size_t cfs, float delta, float gamma, float alpha_s)
 {
@@ -140,66 +141,55 @@ var_coeff_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
     const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
     const int ex0 = tx0 - 2, ey0 = ty0 - 2, dx0 = tx0 - 1, dy0 = ty0 - 1;
     const size_t po = (size_t)f * pfs;
-    const float *I1 = I1b + po;
+    const T *I1 = I1b + po;
     const float *U = Ub + (size_t)f * ufs;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 16 threads, one per tile pixel
 
-    // staging window: thread (tx, ty) covers (tx + 32 i, ty + 16 j)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int lx = tx + kAX * i, ly = ty + kAY * j;
-            if (lx >= kAEX || ly >= kAEY) continue;
-            const int gx = ex0 + lx, gy = ey0 + ly;
-            float u = 0.0f, v = 0.0f;
-            if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-                const size_t p = (size_t)gy * pitch + gx;
-                u = U[p];
-                v = U[plane + p];
-            }
-            sU[ly][lx] = u;
-            sV[ly][lx] = v;
+    const int t = ty * kAX + tx;
+    constexpr int kN = kAX * kAY;
+    for (int i = t; i < kAEX * kAEY; i += kN) {
+        const int lx = i % kAEX, ly = i / kAEX;
+        const int gx = ex0 + lx, gy = ey0 + ly;
+        float u = 0.0f, v = 0.0f;
+        if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+            const size_t p = (size_t)gy * pitch + gx;
+            u = U[p];
+            v = U[plane + p];
         }
+        sU[ly][lx] = u;
+        sV[ly][lx] = v;
+    }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int lx = tx + kAX * i, ly = ty + kAY * j;
-            if (lx >= kAEX || ly >= kAEY) continue;
-            const int gx = ex0 + lx, gy = ey0 + ly;
-            float wv = 0.0f;
-            if (gx >= 0 && gx < w && gy >= 0 && gy < h)
-                wv = bilinear(I1, w, h, pitch, (float)gx + sU[ly][lx], (float)gy + sV[ly][lx]);
-            sW[ly][lx] = wv;
-        }
+    for (int i = t; i < kAEX * kAEY; i += kN) {
+        const int lx = i % kAEX, ly = i / kAEX;
+        const int gx = ex0 + lx, gy = ey0 + ly;
+        float wv = 0.0f;
+        if (gx >= 0 && gx < w && gy >= 0 && gy < h)
+            wv = bilinear(I1, w, h, pitch, (float)gx + sU[ly][lx], (float)gy + sV[ly][lx]);
+        sW[ly][lx] = wv;
+    }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int lx = tx + kAX * i, ly = ty + kAY * j;
-            if (lx >= kADX || ly >= kADY) continue;
-            const int gx = dx0 + lx, gy = dy0 + ly;
-            float ix = 0.0f, iy = 0.0f, as = 0.0f;
-            if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-                const int xp = min(gx + 1, w - 1) - ex0, xm = max(gx - 1, 0) - ex0;
-                const int yp = min(gy + 1, h - 1) - ey0, ym = max(gy - 1, 0) - ey0;
-                const int ex = gx - ex0, ey = gy - ey0;
-                ix = 0.5f * (sW[ey][xp] - sW[ey][xm]);
-                iy = 0.5f * (sW[yp][ex] - sW[ym][ex]);
-                const float u = sU[ey][ex], v = sV[ey][ex];
-                const float ux = gx + 1 < w ? sU[ey][ex + 1] - u : 0.0f;
-                const float uy = gy + 1 < h ? sU[ey + 1][ex] - u : 0.0f;
-                const float vx = gx + 1 < w ? sV[ey][ex + 1] - v : 0.0f;
-                const float vy = gy + 1 < h ? sV[ey + 1][ex] - v : 0.0f;
-                as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
-            }
-            sIx[ly][lx] = ix;
-            sIy[ly][lx] = iy;
-            sAs[ly][lx] = as;
+    for (int i = t; i < kADX * kADY; i += kN) {
+        const int lx = i % kADX, ly = i / kADX;
+        const int gx = dx0 + lx, gy = dy0 + ly;
+        float ix = 0.0f, iy = 0.0f, as = 0.0f;
+        if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+            const int xp = min(gx + 1, w - 1) - ex0, xm = max(gx - 1, 0) - ex0;
+            const int yp = min(gy + 1, h - 1) - ey0, ym = max(gy - 1, 0) - ey0;
+            const int ex = gx - ex0, ey = gy - ey0;
+            ix = 0.5f * (sW[ey][xp] - sW[ey][xm]);
+            iy = 0.5f * (sW[yp][ex] - sW[ym][ex]);
+            const float u = sU[ey][ex], v = sV[ey][ex];
+            const float ux = gx + 1 < w ? sU[ey][ex + 1] - u : 0.0f;
+            const float uy = gy + 1 < h ? sU[ey + 1][ex] - u : 0.0f;
+            const float vx = gx + 1 < w ? sV[ey][ex + 1] - v : 0.0f;
+            const float vy = gy + 1 < h ? sV[ey + 1][ex] - v : 0.0f;
+            as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
         }
+        sIx[ly][lx] = ix;
+        sIy[ly][lx] = iy;
+        sAs[ly][lx] = as;
+    }
     __syncthreads();
 
     const int gx = tx0 + threadIdx.x, gy = ty0 + threadIdx.y;
@@ -212,8 +202,8 @@ var_coeff_kernel(const float *__restrict__ I0b, const float *__restrict__ I0xb,
     const float Ixy = 0.5f * (sIx[yp][dx] - sIx[ym][dx]);
     const float Iyy = 0.5f * (sIy[yp][dx] - sIy[ym][dx]);
     const size_t p = (size_t)gy * pitch + gx;
-    const float Iz = sW[ey][ex] - I0b[po + p];
-    const float Ixz = Ix - I0xb[po + p], Iyz = Iy - I0yb[po + p];
+    const float Iz = sW[ey][ex] - ldp(&I0b[po + p]);
+    const float Ixz = Ix - ldp(&I0xb[po + p]), Iyz = Iy - ldp(&I0yb[po + p]);
     const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
     const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
     float ad = delta * nd * psi_prime(nd * Iz * Iz);
@@ -315,8 +305,8 @@ bool var_fused_supported(int var_sor)
 
 void init_var_attributes() {}
 
-float *launch_variational_fused(const float *I0, const float *I0x, const float *I0y,
-                                const float *I1, const Level &lv, size_t pyr_frame_stride,
+float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y,
+                                const void *I1, const Level &lv, size_t pyr_frame_stride,
                                 float *U, float *Utmp, size_t u_frame_stride, float *coef,
                                 size_t coef_frame_stride, int frames, const FlowParams &fp,
                                 cudaStream_t st)
@@ -330,9 +320,18 @@ float *launch_variational_fused(const float *I0, const float *I0x, const float *
     for (int k = 0; k < fp.var_outer; ++k) {
         {
             StageScope sc(kStVarCoeff, 1, st);
-            var_coeff_kernel<<<cgrd, dim3(kAX, kAY), 0, st>>>(
-                I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a, u_frame_stride,
-                lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma, fp.alpha_s);
+            if (fp.half)
+                var_coeff_kernel<__half><<<cgrd, dim3(kAX, kAY), 0, st>>>(
+                    (const __half *)I0, (const __half *)I0x, (const __half *)I0y,
+                    (const __half *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
+                    u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
+                    fp.alpha_s);
+            else
+                var_coeff_kernel<float><<<cgrd, dim3(kAX, kAY), 0, st>>>(
+                    (const float *)I0, (const float *)I0x, (const float *)I0y,
+                    (const float *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
+                    u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
+                    fp.alpha_s);
         }
         {
             StageScope sc(kStVarSor, 1, st);
