@@ -196,6 +196,48 @@ ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32
 ebof_status ebof_edt_static(const uint8_t *d_edge, int32_t width, int32_t height,
                             int32_t *d_edt, float *d_surface, float alpha, void *cuda_stream);
 
+/* ---- multi-stream groups -------------------------------------------------
+ * A group holds n camera streams of one resolution and steps them in
+ * lockstep: one ebof_group_process call takes one window of every stream
+ * and runs each stage once for all of them (every kernel gets the n windows
+ * in its grid), so small frames still fill the GPU.  From the second call
+ * on, the whole step is replayed as one CUDA graph per ping-pong parity
+ * (captured on first use); only the window descriptors are copied in
+ * before each replay.  Streams of other resolutions go in other groups,
+ * which may run concurrently on other CUDA streams.  Results per stream are
+ * bit-identical to an ebof_stream fed the same windows. */
+typedef struct {
+    const uint16_t *x;   /* device pointers, n_events each */
+    const uint16_t *y;
+    const int64_t *t;
+    int64_t n_events;
+    int64_t t_begin, t_end;  /* the window [t_begin, t_end) */
+} ebof_window_desc;
+
+typedef struct ebof_group ebof_group;
+
+/* Allocates the state of n_streams streams (1 .. 4096) with parameters p
+ * (p->max_batch is ignored) on `device`, including the group-owned flow
+ * buffer [n][2][H][W]. */
+ebof_status ebof_group_create(const ebof_params *p, int32_t n_streams, int device,
+                              ebof_group **out);
+ebof_status ebof_group_destroy(ebof_group *g);           /* NULL-safe; waits for work */
+ebof_status ebof_group_reset(ebof_group *g);             /* every stream forgets its window */
+
+/* One window per stream.  h_desc: HOST array of n_streams descriptors
+ * (copied during the call).  d_flow: optional device [n][2][H][W]; the flow
+ * also stays in the group's buffer (ebof_group_flow).  Returns
+ * EBOF_NO_PREVIOUS on the first step (flows zero). */
+ebof_status ebof_group_process(ebof_group *g, const ebof_window_desc *h_desc, float *d_flow,
+                               void *cuda_stream);
+
+/* Device pointer to stream k's flow of the last step ([2][H][W]); valid until
+ * the next ebof_group_process. */
+const float *ebof_group_flow(const ebof_group *g, int32_t k);
+
+/* As ebof_stream_sync, for the group's streams (out[k] = stream k). */
+ebof_status ebof_group_sync(ebof_group *g, ebof_window_stats *out, int32_t n_out);
+
 /* ---- tracing: per-stage CUDA-event timing (§IV Table VII reports per-block
  * times; these are the GPU equivalents).  Timing brackets each stage's
  * launches with cudaEvents on the caller's stream; it is off by default. */

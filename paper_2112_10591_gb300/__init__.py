@@ -13,5 +13,6 @@ from .binding import (  # noqa: F401
     ebof_stream_reset, ebof_stream_sync, ebof_window_stats, library_path, load,
     EBOF_STAGE_COUNT, ebof_kernel_launches, ebof_stage_name, ebof_stream_get_profile,
     ebof_stream_set_profiling, ebof_edt_static, ebof_stream_get_profile_level,
-    EBOF_STORAGE_FP16, EBOF_STORAGE_FP32,
+    EBOF_STORAGE_FP16, EBOF_STORAGE_FP32, Group, ebof_window_desc, ebof_group_create,
+    ebof_group_reset, ebof_group_process, ebof_group_flow, ebof_group_sync,
 )

@@ -59,6 +59,13 @@ class ebof_window_stats(ctypes.Structure):
     ]
 
 
+class ebof_window_desc(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("t", ctypes.c_void_p),
+        ("n_events", ctypes.c_int64), ("t_begin", ctypes.c_int64), ("t_end", ctypes.c_int64),
+    ]
+
+
 class EbofError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         super().__init__("%s: %s (%d)" % (what or "ebof", ebof_status_string(status), status))
@@ -102,6 +109,13 @@ def _declare(L):
     L.ebof_stream_sync.argtypes = [vp, P(ebof_window_stats), i32]
     L.ebof_edt.argtypes = [vp, i32, i32, vp, vp, vp, f32, vp]
     L.ebof_edt_static.argtypes = [vp, i32, i32, vp, vp, f32, vp]
+    L.ebof_group_create.argtypes = [P(ebof_params), i32, ctypes.c_int, P(vp)]
+    L.ebof_group_destroy.argtypes = [vp]
+    L.ebof_group_reset.argtypes = [vp]
+    L.ebof_group_process.argtypes = [vp, P(ebof_window_desc), vp, vp]
+    L.ebof_group_flow.argtypes = [vp, i32]
+    L.ebof_group_flow.restype = vp
+    L.ebof_group_sync.argtypes = [vp, P(ebof_window_stats), i32]
     L.ebof_stream_set_profiling.argtypes = [vp, i32]
     L.ebof_stream_get_profile.argtypes = [vp, P(ctypes.c_double), P(i64), i32]
     L.ebof_stream_get_profile_level.argtypes = [vp, i32, P(ctypes.c_double), P(i64), i32]
@@ -115,7 +129,8 @@ def _declare(L):
                  "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
                  "ebof_process_window_host", "ebof_stream_sync", "ebof_edt",
                  "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static",
-                 "ebof_stream_get_profile_level"):
+                 "ebof_stream_get_profile_level", "ebof_group_create", "ebof_group_destroy",
+                 "ebof_group_reset", "ebof_group_process", "ebof_group_sync"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -297,6 +312,74 @@ def ebof_edt_static(edge, width: int, height: int, edt, surface=None, alpha: flo
                                   _ptr(edt, torch.int32, n, "edt"),
                                   _ptr(surface, torch.float32, n, "surface"), float(alpha),
                                   _stream_handle(cuda_stream))
+
+
+class Group:
+    """Owner of an ``ebof_group*`` handle (n streams of one resolution)."""
+
+    def __init__(self, handle: int, params: ebof_params, n: int, device: int):
+        self.handle = handle
+        self.params = params
+        self.n = n
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().ebof_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ebof_group_create(params: ebof_params, n_streams: int, device: int = 0):
+    """Returns (status, Group or None)."""
+    h = ctypes.c_void_p()
+    st = load().ebof_group_create(ctypes.byref(params), int(n_streams), int(device),
+                                  ctypes.byref(h))
+    if st < 0:
+        return st, None
+    p = ebof_params()
+    ctypes.memmove(ctypes.byref(p), ctypes.byref(params), ctypes.sizeof(p))
+    return st, Group(h.value, p, int(n_streams), int(device))
+
+
+def ebof_group_reset(group: Group) -> int:
+    return load().ebof_group_reset(group.handle)
+
+
+def ebof_group_process(group: Group, windows, flow=None, cuda_stream=None) -> int:
+    """windows: n tuples (x, y, t, t_begin, t_end) of CUDA tensors and ints."""
+    import torch
+    if len(windows) != group.n:
+        raise ValueError("need %d windows, got %d" % (group.n, len(windows)))
+    arr = (ebof_window_desc * group.n)()
+    for k, (x, y, t, tb, te) in enumerate(windows):
+        n = x.numel()
+        arr[k].x = _ptr(x, torch.uint16, n, "x", group.device)
+        arr[k].y = _ptr(y, torch.uint16, n, "y", group.device)
+        arr[k].t = _ptr(t, torch.int64, n, "t", group.device)
+        arr[k].n_events = n
+        arr[k].t_begin = int(tb)
+        arr[k].t_end = int(te)
+    W, H = group.params.width, group.params.height
+    fp = _ptr(flow, torch.float32, group.n * 2 * W * H, "flow", group.device)
+    return load().ebof_group_process(group.handle, arr, fp, _stream_handle(cuda_stream))
+
+
+def ebof_group_flow(group: Group, k: int) -> int:
+    """Device address of stream k's flow of the last step ([2][H][W] float32)."""
+    return int(load().ebof_group_flow(group.handle, int(k)) or 0)
+
+
+def ebof_group_sync(group: Group, n_out: int = None):
+    n_out = group.n if n_out is None else n_out
+    arr = (ebof_window_stats * max(1, n_out))()
+    st = load().ebof_group_sync(group.handle, arr, int(n_out))
+    return st, [arr[i] for i in range(n_out)]
 
 
 EBOF_STAGE_COUNT = 12

@@ -76,6 +76,35 @@ struct ebof_stream {
     Profiler prof;
 };
 
+struct ebof_group {
+    ebof_params p;
+    int device = 0;
+    int n = 0;
+    Geometry geo;
+    int pitch0 = 0;
+    size_t e_fs = 0, g_fs = 0, pyr_fs = 0, up_fs = 0, u_fs = 0, work_fs = 0, es = 4;
+    uint8_t *E = nullptr, *Ed = nullptr, *Edf = nullptr;
+    int32_t *g = nullptr;
+    char *pyr = nullptr;  // two banks of n pyramid slots
+    float *up = nullptr, *Ua = nullptr, *Ub = nullptr, *work = nullptr;
+    float *flow = nullptr;  // [n][2][H][W]
+    DevStats *dstats = nullptr;
+    unsigned long long *d_dropped_time = nullptr;
+    int *d_err = nullptr;
+    ebof_window_desc *d_desc = nullptr;
+    int64_t *h_events = nullptr;  // events given per stream in the last step
+    int parity = 0;
+    bool has_prev = false, last_had_prev = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_kernels[2] = {0, 0};
+    cudaStream_t cap = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool have_last = false;
+    std::atomic<int> busy{0};
+    Profiler prof;
+};
+
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -276,6 +305,83 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
     s->have_last = true;
     if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
     return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
+}
+
+void free_group(ebof_group *g)
+{
+    for (int b = 0; b < 2; ++b)
+        if (g->graph[b]) cudaGraphExecDestroy(g->graph[b]);
+    cudaFree(g->E); cudaFree(g->Ed); cudaFree(g->Edf); cudaFree(g->g); cudaFree(g->pyr);
+    cudaFree(g->up); cudaFree(g->Ua); cudaFree(g->Ub); cudaFree(g->work); cudaFree(g->flow);
+    cudaFree(g->dstats); cudaFree(g->d_dropped_time); cudaFree(g->d_err); cudaFree(g->d_desc);
+    delete[] g->h_events;
+    if (g->cap) cudaStreamDestroy(g->cap);
+    if (g->done) cudaEventDestroy(g->done);
+}
+
+// One lockstep step of a group: every stage once for its n streams.  The
+// current windows go to bank `parity`, the previous ones are in the other
+// bank.  Enqueued on `st`; nothing here depends on host values that change
+// between steps of the same parity, so the sequence can be captured.
+void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
+{
+    const ebof_params &p = g->p;
+    const Geometry &geo = g->geo;
+    const int W = p.width, H = p.height, n = g->n;
+    const bool half = p.storage == EBOF_STORAGE_FP16;
+    const size_t es = g->es;
+    char *cur = g->pyr + (size_t)g->parity * n * g->pyr_fs * es;
+    char *prv = g->pyr + (size_t)(g->parity ^ 1) * n * g->pyr_fs * es;
+    tl_level = -1;
+    cudaMemsetAsync(g->dstats, 0, sizeof(DevStats) * n, st);
+    cudaMemsetAsync(g->d_dropped_time, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(g->E, 0, g->e_fs * n, st);
+    launch_scatter_desc(g->d_desc, n, W, H, g->pitch0, g->E, g->e_fs, g->dstats,
+                        g->d_dropped_time, st);
+    launch_denoise_fill(g->E, g->Ed, g->Edf, W, H, g->pitch0, g->e_fs, n, p.connectivity, p.n_d,
+                        p.n_f, nullptr, g->dstats, st);
+    launch_edt_columns(g->Edf, g->pitch0, g->e_fs, W, H, g->g, g->pitch0, g->g_fs, n, st);
+    launch_edt_rows_surface(g->g, g->pitch0, g->g_fs, W, H, p.alpha, nullptr, nullptr, cur,
+                            g->pitch0, g->pyr_fs, n, half, st);
+    const int nlev = std::max(geo.levels, 1);
+    for (int l = 0; l < nlev; ++l) {
+        tl_level = l;
+        const Level &lv = geo.lv[l];
+        char *I = cur + geo.pyr_off[l] * es;
+        if (l > 0) {
+            const Level &lp = geo.lv[l - 1];
+            launch_downsample(cur + geo.pyr_off[l - 1] * es, lp.w, lp.h, lp.pitch, I, lv.w, lv.h,
+                              lv.pitch, g->pyr_fs, n, half, st);
+        }
+        launch_gradients(I, I + lv.plane * es, I + 2 * lv.plane * es, lv.w, lv.h, lv.pitch,
+                         g->pyr_fs, n, half, st);
+    }
+    const size_t flow_frame = (size_t)2 * W * H;
+    if (with_flow && geo.levels > 0) {
+        const FlowParams fp = flow_params(p);
+        float *Ucur = nullptr, *Uc = nullptr;
+        const Level *lvc = nullptr;
+        for (int l = geo.levels - 1; l >= 0; --l) {
+            tl_level = l;
+            const Level &lv = geo.lv[l];
+            const char *I0 = prv + geo.pyr_off[l] * es;
+            const char *I1 = cur + geo.pyr_off[l] * es;
+            const char *I0x = I0 + lv.plane * es, *I0y = I0 + 2 * lv.plane * es;
+            Ucur = (Uc == g->Ua) ? g->Ub : g->Ua;
+            launch_patch_search(I0, I0x, I0y, I1, lv, g->pyr_fs, Uc, lvc, g->u_fs, g->up,
+                                g->up_fs, n, fp, g->d_err, st);
+            launch_densify(I0, I1, lv, g->pyr_fs, g->up, g->up_fs, Ucur, g->u_fs, n, fp, st);
+            float *Utmp = (Ucur == g->Ua) ? g->Ub : g->Ua;
+            Ucur = launch_variational(I0, I0x, I0y, I1, lv, g->pyr_fs, Ucur, Utmp, g->u_fs,
+                                      g->work, g->work_fs, n, fp, st);
+            Uc = Ucur;
+            lvc = &lv;
+        }
+        tl_level = -1;
+        launch_flow_out(Ucur, W, H, g->pitch0, g->u_fs, g->flow, n, st);
+    } else {
+        cudaMemsetAsync(g->flow, 0, sizeof(float) * flow_frame * n, st);
+    }
 }
 
 bool events_ok(const void *x, const void *y, const void *t, int64_t n)
@@ -546,6 +652,209 @@ ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32
     launch_edt_rows_surface(d_scratch, width, plane, width, height, alpha, d_edt, d_surface,
                             nullptr, width, plane, 1, false, st);
     return cudaGetLastError() == cudaSuccess ? EBOF_OK : EBOF_ERR_CUDA;
+}
+
+ebof_status ebof_group_create(const ebof_params *p, int32_t n_streams, int device,
+                              ebof_group **out)
+{
+    if (!out) return EBOF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_streams < 1 || n_streams > 4096) return EBOF_ERR_INVALID_ARG;
+    ebof_params q;
+    if (p) {
+        q = *p;
+        q.max_batch = 1;  // not used by groups; keeps the parameter check happy
+    }
+    const ebof_status ps = check_params(p ? &q : nullptr);
+    if (ps != EBOF_OK) return ps;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return device < 0 ? EBOF_ERR_INVALID_ARG : EBOF_ERR_CUDA;
+    DeviceGuard dg(device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    ebof_group *g = new (std::nothrow) ebof_group();
+    if (!g) return EBOF_ERR_OOM;
+    g->p = q;
+    g->device = device;
+    g->n = n_streams;
+    g->geo = make_geometry(q.width, q.height, q.levels, q.patch, q.stride);
+    const Geometry &geo = g->geo;
+    const int n = n_streams;
+    g->pitch0 = geo.lv[0].pitch;
+    const size_t plane0 = geo.lv[0].plane;
+    g->e_fs = plane0;
+    g->g_fs = plane0;
+    g->pyr_fs = geo.pyr_floats;
+    g->up_fs = (size_t)2 * std::max(geo.max_patches, 1);
+    g->u_fs = 2 * plane0;
+    g->work_fs = 9 * plane0;
+    g->es = q.storage == EBOF_STORAGE_FP16 ? 2 : 4;
+    g->h_events = new (std::nothrow) int64_t[n];
+    bool ok = g->h_events != nullptr;
+    ok &= dmalloc(&g->E, g->e_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->Ed, g->e_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->Edf, g->e_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->g, sizeof(int32_t) * g->g_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->pyr, g->es * g->pyr_fs * n * 2) == cudaSuccess;
+    ok &= dmalloc(&g->up, sizeof(float) * g->up_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->Ua, sizeof(float) * g->u_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->Ub, sizeof(float) * g->u_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->work, sizeof(float) * g->work_fs * n) == cudaSuccess;
+    ok &= dmalloc(&g->flow, sizeof(float) * 2 * (size_t)q.width * q.height * n) == cudaSuccess;
+    ok &= dmalloc(&g->dstats, sizeof(DevStats) * n) == cudaSuccess;
+    ok &= dmalloc(&g->d_dropped_time, sizeof(unsigned long long)) == cudaSuccess;
+    ok &= dmalloc(&g->d_err, sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&g->d_desc, sizeof(ebof_window_desc) * n) == cudaSuccess;
+    ok &= cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_group(g);
+        delete g;
+        return EBOF_ERR_OOM;
+    }
+    cudaMemset(g->d_err, 0, sizeof(int));
+    cudaMemset(g->flow, 0, sizeof(float) * 2 * (size_t)q.width * q.height * n);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_group(g);
+        delete g;
+        return EBOF_ERR_CUDA;
+    }
+    *out = g;
+    return EBOF_OK;
+}
+
+ebof_status ebof_group_destroy(ebof_group *g)
+{
+    if (!g) return EBOF_OK;
+    DeviceGuard dg(g->device);
+    if (g->have_last) cudaEventSynchronize(g->done);
+    free_group(g);
+    delete g;
+    return EBOF_OK;
+}
+
+ebof_status ebof_group_reset(ebof_group *g)
+{
+    if (!g) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(g->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(g->device);
+    if (g->have_last && cudaEventSynchronize(g->done) != cudaSuccess) return EBOF_ERR_CUDA;
+    g->has_prev = false;
+    g->parity = 0;
+    return EBOF_OK;
+}
+
+ebof_status ebof_group_process(ebof_group *g, const ebof_window_desc *h_desc, float *d_flow,
+                               void *cuda_stream)
+{
+    if (!g || !h_desc) return EBOF_ERR_INVALID_ARG;
+    for (int k = 0; k < g->n; ++k)
+        if (!events_ok(h_desc[k].x, h_desc[k].y, h_desc[k].t, h_desc[k].n_events) ||
+            h_desc[k].t_end < h_desc[k].t_begin)
+            return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(g->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaGetLastError();
+    if (g->have_last && g->last_stream != st) cudaStreamWaitEvent(st, g->done, 0);
+    for (int k = 0; k < g->n; ++k) g->h_events[k] = h_desc[k].n_events;
+    cudaMemcpyAsync(g->d_desc, h_desc, sizeof(ebof_window_desc) * g->n, cudaMemcpyHostToDevice,
+                    st);
+    const bool had_prev = g->has_prev;
+    ProfScope prof_scope(&g->prof);
+    if (!had_prev || g->prof.on) {
+        run_group(g, had_prev, st);  // first step, or timed stage by stage: no graph
+    } else {
+        const int b = g->parity;
+        if (!g->graph[b]) {
+            // capture this parity's step once; the capture stream starts after `st`
+            cudaEvent_t ready;
+            cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+            cudaEventRecord(ready, st);
+            cudaStreamWaitEvent(g->cap, ready, 0);
+            cudaEventDestroy(ready);
+            const unsigned long long before = g_launches.load();
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                tl_prof = nullptr;  // no event records inside a graph
+                run_group(g, true, g->cap);
+                cudaStreamEndCapture(g->cap, &graph);
+            }
+            if (graph && cudaGraphInstantiate(&g->graph[b], graph, 0) != cudaSuccess)
+                g->graph[b] = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+            g->graph_kernels[b] = (long long)(g_launches.load() - before);
+            g_launches.fetch_sub((unsigned long long)g->graph_kernels[b]);
+            if (!g->graph[b]) {
+                cudaGetLastError();
+                return EBOF_ERR_CUDA;
+            }
+        }
+        if (cudaGraphLaunch(g->graph[b], st) != cudaSuccess) return EBOF_ERR_CUDA;
+        g_launches.fetch_add((unsigned long long)g->graph_kernels[b]);
+    }
+    if (d_flow)
+        cudaMemcpyAsync(d_flow, g->flow, sizeof(float) * 2 * (size_t)g->p.width * g->p.height * g->n,
+                        cudaMemcpyDeviceToDevice, st);
+    g->parity ^= 1;
+    g->has_prev = true;
+    g->last_had_prev = had_prev;
+    cudaEventRecord(g->done, st);
+    g->last_stream = st;
+    g->have_last = true;
+    if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
+    return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
+}
+
+const float *ebof_group_flow(const ebof_group *g, int32_t k)
+{
+    if (!g || k < 0 || k >= g->n) return nullptr;
+    return g->flow + (size_t)k * 2 * g->p.width * g->p.height;
+}
+
+ebof_status ebof_group_sync(ebof_group *g, ebof_window_stats *out, int32_t n_out)
+{
+    if (!g || n_out < 0 || (n_out > 0 && !out)) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(g->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    if (g->have_last && cudaEventSynchronize(g->done) != cudaSuccess) return EBOF_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return EBOF_ERR_CUDA;
+    const int n = std::min<int>(n_out, g->n);
+    if (n > 0) {
+        DevStats hs[64];
+        unsigned long long dropped_time = 0;
+        cudaMemcpy(&dropped_time, g->d_dropped_time, sizeof(dropped_time),
+                   cudaMemcpyDeviceToHost);
+        for (int k0 = 0; k0 < n; k0 += 64) {
+            const int m = std::min(64, n - k0);
+            if (cudaMemcpy(hs, g->dstats + k0, sizeof(DevStats) * m, cudaMemcpyDeviceToHost) !=
+                cudaSuccess)
+                return EBOF_ERR_CUDA;
+            for (int k = 0; k < m; ++k) {
+                ebof_window_stats &o = out[k0 + k];
+                o.events = g->h_events[k0 + k];
+                o.in_window = (int64_t)hs[k].in_window;
+                o.dropped_time = (int64_t)dropped_time;
+                o.dropped_oob = (int64_t)hs[k].dropped_oob;
+                o.edge_px = (int64_t)hs[k].edge_px;
+                o.has_flow = g->last_had_prev ? 1 : 0;
+                o.levels_used = g->last_had_prev ? g->geo.levels : 0;
+            }
+        }
+    }
+    if (err) {
+        cudaMemset(g->d_err, 0, sizeof(int));
+        return EBOF_ERR_DEVICE_BOUNDS;
+    }
+    return EBOF_OK;
 }
 
 ebof_status ebof_stream_set_profiling(ebof_stream *s, int32_t enable)

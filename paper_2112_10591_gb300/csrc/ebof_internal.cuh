@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ebof.h"
+
 namespace ebof {
 
 constexpr int kMaxLevels = 8;
@@ -63,6 +65,11 @@ void launch_scatter(const uint16_t *x, const uint16_t *y, const int64_t *t, int6
                     int64_t t_begin, int64_t dt, int n_windows, int W, int H, int pitch,
                     uint8_t *E, size_t frame_stride, DevStats *stats,
                     unsigned long long *dropped_time, cudaStream_t st);
+
+// A1 for a group of streams: frame f scatters the events of desc[f] (device).
+void launch_scatter_desc(const ebof_window_desc *desc, int frames, int W, int H,
+                         int pitch, uint8_t *E, size_t frame_stride, DevStats *stats,
+                         unsigned long long *dropped_time, cudaStream_t st);
 
 // A2: Alg. 1 then Alg. 2; writes E_df (pitched) and optional dense export.
 void launch_denoise_fill(const uint8_t *E, uint8_t *Ed, uint8_t *Edf, int W, int H, int pitch,

@@ -5,6 +5,7 @@
 // distances (separable: a per-column pass, then a per-row lower envelope of
 // parabolas), fused with Eq. 1, d_exp = 1 - exp(-sqrt(D) / alpha), and the
 // 8-bit intensity scale 255 * d_exp the flow block runs on.
+#include "ebof.h"
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
 
@@ -55,6 +56,45 @@ __global__ void scatter_kernel(const uint16_t *__restrict__ x, const uint16_t *_
                 atomicAdd(dropped_time, (unsigned long long)__popc(peers));
             }
         }
+    }
+}
+
+// Scatter for a group of streams: frame f takes the events of descriptor f.
+__global__ void scatter_desc_kernel(const ebof_window_desc *__restrict__ desc, int W, int H,
+                                    int pitch, uint8_t *__restrict__ E, size_t fstride,
+                                    DevStats *stats, unsigned long long *dropped_time)
+{
+    const int f = blockIdx.y;
+    const ebof_window_desc d = desc[f];
+    const int lane = threadIdx.x & 31;
+    uint8_t *e = E + (size_t)f * fstride;
+    unsigned long long in_w = 0, oob = 0, out_t = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < d.n_events;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        if (i < d.n_events) {
+            const int64_t tt = d.t[i];
+            if (tt >= d.t_begin && tt < d.t_end) {
+                ++in_w;
+                const int xi = d.x[i], yi = d.y[i];
+                if (xi < W && yi < H) e[(size_t)yi * pitch + xi] = 1;
+                else ++oob;
+            } else {
+                ++out_t;
+            }
+        }
+    }
+    // warp sums, one atomic per warp and counter
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        in_w += __shfl_xor_sync(0xffffffffu, in_w, o);
+        oob += __shfl_xor_sync(0xffffffffu, oob, o);
+        out_t += __shfl_xor_sync(0xffffffffu, out_t, o);
+    }
+    if (lane == 0) {
+        if (in_w) atomicAdd(&stats[f].in_window, in_w);
+        if (oob) atomicAdd(&stats[f].dropped_oob, oob);
+        if (out_t) atomicAdd(dropped_time, out_t);
     }
 }
 
@@ -402,6 +442,16 @@ void launch_scatter(const uint16_t *x, const uint16_t *y, const int64_t *t, int6
     scatter_kernel<<<grid1d(n, 256, 152 * 16), 256, 0, st>>>(x, y, t, n, t_begin, dt, n_windows,
                                                              W, H, pitch, E, frame_stride, stats,
                                                              dropped_time);
+}
+
+void launch_scatter_desc(const ebof_window_desc *desc, int frames, int W, int H, int pitch,
+                         uint8_t *E, size_t frame_stride, DevStats *stats,
+                         unsigned long long *dropped_time, cudaStream_t st)
+{
+    StageScope sc(kStScatter, 1, st);
+    dim3 grd(64, frames);
+    scatter_desc_kernel<<<grd, 256, 0, st>>>(desc, W, H, pitch, E, frame_stride, stats,
+                                             dropped_time);
 }
 
 void launch_denoise_fill(const uint8_t *E, uint8_t *Ed, uint8_t *Edf, int W, int H, int pitch,
