@@ -128,7 +128,11 @@ ebof_status ebof_stream_reset(ebof_stream *s);
  * edge image (the paper's mask for restricting the flow, §III-D), d_edt
  * [H][W] squared distances (INT32_MAX when the window has no edge pixel),
  * d_surface [H][W] d_exp of Eq. 1.  Returns EBOF_NO_PREVIOUS (flow zero)
- * for the first window after create/reset, else EBOF_OK. */
+ * for the first window after create/reset, else EBOF_OK.
+ * With max_batch 1, no optional output and stage timing off, steady-state
+ * calls replay a CUDA graph of the whole window (one per ping-pong slot,
+ * captured on first use) after copying the call's pointers and counts to
+ * the device; the results are identical to the step-by-step launches. */
 ebof_status ebof_process_window(ebof_stream *s, const uint16_t *d_x, const uint16_t *d_y,
                                 const int64_t *d_t, const int8_t *d_p, int64_t n_events,
                                 int64_t t_begin, int64_t t_end, float *d_flow,

@@ -46,6 +46,12 @@ Geometry make_geometry(int width, int height, int levels, int ps, int stride)
 
 }  // namespace ebof
 
+// Per-call arguments of a single-window graph replay (copied to the device).
+struct StreamCall {
+    ebof_window_desc win;
+    float *flow;
+};
+
 struct ebof_stream {
     ebof_params p;
     int device;
@@ -74,6 +80,11 @@ struct ebof_stream {
     bool have_last = false;
     std::atomic<int> busy{0};
     Profiler prof;
+    // single-window graph replays (one graph per ping-pong slot)
+    StreamCall *d_args = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_kernels[2] = {0, 0};
+    cudaStream_t cap = nullptr;
 };
 
 struct ebof_group {
@@ -183,7 +194,10 @@ void free_all(ebof_stream *s)
     cudaFree(s->E); cudaFree(s->Ed); cudaFree(s->Edf); cudaFree(s->g); cudaFree(s->pyr);
     cudaFree(s->up); cudaFree(s->Ua); cudaFree(s->Ub); cudaFree(s->work);
     cudaFree(s->dstats); cudaFree(s->d_dropped_time); cudaFree(s->d_err);
-    cudaFree(s->flow_stage); cudaFree(s->ev_stage);
+    cudaFree(s->flow_stage); cudaFree(s->ev_stage); cudaFree(s->d_args);
+    for (int b = 0; b < 2; ++b)
+        if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+    if (s->cap) cudaStreamDestroy(s->cap);
     if (s->done) cudaEventDestroy(s->done);
 }
 
@@ -204,26 +218,20 @@ FlowParams flow_params(const ebof_params &p)
     return fp;
 }
 
-// The whole path for n consecutive windows (or one caller-given surface).
-ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const int64_t *t,
-                int64_t nev, int64_t t_begin, int64_t dt, const float *surface_in,
-                float *d_flow, uint8_t *d_edge, int32_t *d_edt, float *d_surface,
-                cudaStream_t st)
+// Enqueues the whole path for n consecutive windows (or one caller-given
+// surface) on `st`: the current windows go to slots cur_first.., the previous
+// ones are at prev_first.., and nothing of the stream's bookkeeping changes
+// (so the same sequence can be captured into a graph).  With `via_args` (one
+// window), the events and the flow destination are read from s->d_args.
+void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const int64_t *t,
+             int64_t nev, int64_t t_begin, int64_t dt, const float *surface_in, float *d_flow,
+             uint8_t *d_edge, int32_t *d_edt, float *d_surface, bool via_args, int cur_first,
+             int prev_first, bool had_prev, cudaStream_t st)
 {
     const ebof_params &p = s->p;
     const Geometry &geo = s->geo;
     const int W = p.width, H = p.height;
-    ProfScope prof_scope(&s->prof);
-    cudaGetLastError();  // start from a clean error state
-    if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
-
-    if (n > 1 && s->head + n >= s->nslots) {
-        if (s->has_prev && s->head != 0)
-            cudaMemcpyAsync(s->pyr, s->pyr + (size_t)s->head * s->pyr_fs * s->es,
-                            s->pyr_fs * s->es, cudaMemcpyDeviceToDevice, st);
-        s->head = 0;
-    }
-    const int cur_first = n == 1 ? (s->head + 1) % s->nslots : s->head + 1;
+    tl_level = -1;
     cudaMemsetAsync(s->dstats, 0, sizeof(DevStats) * n, st);
     cudaMemsetAsync(s->d_dropped_time, 0, sizeof(unsigned long long), st);
     const bool half = p.storage == EBOF_STORAGE_FP16;
@@ -234,8 +242,12 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
         launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, half, st);
     } else {
         cudaMemsetAsync(s->E, 0, s->e_fs * n, st);
-        launch_scatter(x, y, t, nev, t_begin, dt, n, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
-                       s->d_dropped_time, st);
+        if (via_args)
+            launch_scatter_desc(&s->d_args->win, 1, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
+                                s->d_dropped_time, st);
+        else
+            launch_scatter(x, y, t, nev, t_begin, dt, n, W, H, s->pitch0, s->E, s->e_fs,
+                           s->dstats, s->d_dropped_time, st);
         launch_denoise_fill(s->E, s->Ed, s->Edf, W, H, s->pitch0, s->e_fs, n, p.connectivity,
                             p.n_d, p.n_f, d_edge, s->dstats, st);
         launch_edt_columns(s->Edf, s->pitch0, s->e_fs, W, H, s->g, s->pitch0, s->g_fs, n, st);
@@ -259,13 +271,11 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
     }
 
     // A6-A9: flow for every window that has a previous one
-    const bool had_prev = s->has_prev;
     const int ff = had_prev ? 0 : 1;
     const int nf = n - ff;
     const size_t flow_frame = (size_t)2 * W * H;
     if (geo.levels > 0 && nf > 0) {
-        const int prev_first = n == 1 ? s->head : s->head + ff;
-        const int curf_first = n == 1 ? cur_first : s->head + 1 + ff;
+        const int curf_first = cur_first + ff;
         const FlowParams fp = flow_params(p);
         float *Ucur = nullptr, *Uc = nullptr;
         const Level *lvc = nullptr;
@@ -287,13 +297,85 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
             lvc = &lv;
         }
         tl_level = -1;
-        launch_flow_out(Ucur, W, H, s->pitch0, s->u_fs, d_flow + (size_t)ff * flow_frame, nf,
-                        st);
+        if (via_args)
+            launch_flow_out_ptr(Ucur, W, H, s->pitch0, &s->d_args->flow, st);
+        else
+            launch_flow_out(Ucur, W, H, s->pitch0, s->u_fs, d_flow + (size_t)ff * flow_frame,
+                            nf, st);
     }
-    if (geo.levels == 0)
-        cudaMemsetAsync(d_flow, 0, sizeof(float) * flow_frame * n, st);
-    else if (ff == 1)
-        cudaMemsetAsync(d_flow, 0, sizeof(float) * flow_frame, st);
+    if (!via_args) {
+        if (geo.levels == 0)
+            cudaMemsetAsync(d_flow, 0, sizeof(float) * flow_frame * n, st);
+        else if (ff == 1)
+            cudaMemsetAsync(d_flow, 0, sizeof(float) * flow_frame, st);
+    }
+}
+
+// One call: slot bookkeeping, then either a graph replay (single window in
+// steady state) or an eager enqueue.
+ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const int64_t *t,
+                int64_t nev, int64_t t_begin, int64_t dt, const float *surface_in,
+                float *d_flow, uint8_t *d_edge, int32_t *d_edt, float *d_surface,
+                cudaStream_t st)
+{
+    ProfScope prof_scope(&s->prof);
+    cudaGetLastError();  // start from a clean error state
+    if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
+
+    if (n > 1 && s->head + n >= s->nslots) {
+        if (s->has_prev && s->head != 0)
+            cudaMemcpyAsync(s->pyr, s->pyr + (size_t)s->head * s->pyr_fs * s->es,
+                            s->pyr_fs * s->es, cudaMemcpyDeviceToDevice, st);
+        s->head = 0;
+    }
+    const bool had_prev = s->has_prev;
+    const int cur_first = n == 1 ? (s->head + 1) % s->nslots : s->head + 1;
+    const int prev_first = n == 1 ? s->head : s->head + (had_prev ? 0 : 1);
+    const bool graph = n == 1 && had_prev && !surface_in && !d_edge && !d_edt && !d_surface &&
+                       !s->prof.on && s->nslots == 2;
+    if (graph) {
+        const int b = s->head;
+        StreamCall h;
+        h.win.x = x;
+        h.win.y = y;
+        h.win.t = t;
+        h.win.n_events = nev;
+        h.win.t_begin = t_begin;
+        h.win.t_end = t_begin + dt;
+        h.flow = d_flow;
+        cudaMemcpyAsync(s->d_args, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+        if (!s->graph[b]) {
+            cudaEvent_t ready;
+            cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+            cudaEventRecord(ready, st);
+            cudaStreamWaitEvent(s->cap, ready, 0);
+            cudaEventDestroy(ready);
+            const unsigned long long before = g_launches.load();
+            cudaGraph_t gr = nullptr;
+            if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                Profiler *keep = tl_prof;
+                tl_prof = nullptr;
+                enqueue(s, 1, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, true, cur_first, prev_first, true, s->cap);
+                tl_prof = keep;
+                cudaStreamEndCapture(s->cap, &gr);
+            }
+            if (gr && cudaGraphInstantiate(&s->graph[b], gr, 0) != cudaSuccess)
+                s->graph[b] = nullptr;
+            if (gr) cudaGraphDestroy(gr);
+            s->graph_kernels[b] = (long long)(g_launches.load() - before);
+            g_launches.fetch_sub((unsigned long long)s->graph_kernels[b]);
+            if (!s->graph[b]) {
+                cudaGetLastError();
+                return EBOF_ERR_CUDA;
+            }
+        }
+        if (cudaGraphLaunch(s->graph[b], st) != cudaSuccess) return EBOF_ERR_CUDA;
+        g_launches.fetch_add((unsigned long long)s->graph_kernels[b]);
+    } else {
+        enqueue(s, n, x, y, t, nev, t_begin, dt, surface_in, d_flow, d_edge, d_edt, d_surface,
+                false, cur_first, prev_first, had_prev, st);
+    }
 
     s->head = n == 1 ? cur_first : s->head + n;
     s->has_prev = true;
@@ -465,6 +547,8 @@ ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **o
     ok &= dmalloc(&s->d_err, sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&s->flow_stage, sizeof(float) * 2 * (size_t)p->width * p->height) == cudaSuccess;
     ok &= cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) == cudaSuccess;
+    ok &= dmalloc(&s->d_args, sizeof(StreamCall)) == cudaSuccess;
+    ok &= cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(s);

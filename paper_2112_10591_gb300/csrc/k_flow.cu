@@ -372,6 +372,20 @@ __global__ void flow_out_kernel(const float *__restrict__ Ub, int W, int H, int 
     flow[o + (size_t)W * H] = U[plane + (size_t)y * pitch + x];
 }
 
+// Same as flow_out_kernel, with the destination read from device memory (so
+// a captured graph can write each call's flow to the caller's buffer).
+__global__ void flow_out_ptr_kernel(const float *__restrict__ Ub, int W, int H, int pitch,
+                                    size_t plane, float *const *dst)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    float *flow = *dst;
+    const size_t o = (size_t)y * W + x;
+    flow[o] = Ub[(size_t)y * pitch + x];
+    flow[o + (size_t)W * H] = Ub[plane + (size_t)y * pitch + x];
+}
+
 template <int PS, typename T>
 void search_ps(const T *I0, const T *I0x, const T *I0y, const T *I1,
                const Level &lv, size_t pfs, const float *Uc, const Level *lvc, size_t ucfs,
@@ -534,6 +548,14 @@ float *launch_variational(const void *I0, const void *I0x, const void *I0y, cons
                           (const float *)I1, lv, pyr_frame_stride, U, u_frame_stride, work,
                           work_frame_stride, frames, fp, st);
     return U;
+}
+
+void launch_flow_out_ptr(const float *U, int W, int H, int pitch, float *const *dst,
+                         cudaStream_t st)
+{
+    StageScope sc(kStFlowOut, 1, st);
+    dim3 grd((W + 255) / 256, H);
+    flow_out_ptr_kernel<<<grd, 256, 0, st>>>(U, W, H, pitch, (size_t)pitch * H, dst);
 }
 
 void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,

@@ -297,3 +297,28 @@ def test_reset_interleave_host_and_errors(eb):
     assert g["stats"].edge_px == 0 and np.all(g["edt"] == 2147483647) and np.all(g["surf"] == 1.0)
     for h in (a, b, c):
         h.close()
+
+
+def test_graph_replay_equals_eager_launches(eb):
+    # without optional outputs, steady-state single windows replay a CUDA
+    # graph; with them, every stage is launched step by step
+    s_ = synth.translating_segments(n_windows=5, seed=13)
+    W, H = s_.width, s_.height
+    _, a = make_stream(eb, W, H)
+    _, b = make_stream(eb, W, H)
+    for k in range(5):
+        x, y, t, p, tb, te = s_.window(k)
+        fa = torch.empty((2, H, W), dtype=torch.float32, device="cuda:0")
+        fb = torch.empty((2, H, W), dtype=torch.float32, device="cuda:0")
+        edge = torch.empty((H, W), dtype=torch.uint8, device="cuda:0")
+        ra = eb.ebof_process_window(a, dev(x), dev(y), dev(t), None, tb, te, fa)
+        rb = eb.ebof_process_window(b, dev(x), dev(y), dev(t), None, tb, te, fb, edge)
+        assert ra == rb
+        torch.cuda.synchronize()
+        assert torch.equal(fa, fb), k
+        sa, st_a = eb.ebof_stream_sync(a, 1)
+        sb, st_b = eb.ebof_stream_sync(b, 1)
+        assert sa == sb == eb.EBOF_OK
+        assert (st_a[0].in_window, st_a[0].edge_px) == (st_b[0].in_window, st_b[0].edge_px)
+    a.close()
+    b.close()
