@@ -53,6 +53,15 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-multistream", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--sv-seconds", type=float, default=0.5,
+                    help="arrival span of each timed serving run")
+    ap.add_argument("--sv-warmup", type=float, default=0.3)
+    ap.add_argument("--sv-windows", type=int, default=12,
+                    help="generated windows per serving sequence")
+    ap.add_argument("--sv-workers", type=int, default=8)
+    ap.add_argument("--sv-scales", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[1.0, 0.35], help="arrival-rate scales of the serving runs")
     ap.add_argument("--ms-windows", type=int, default=11,
                     help="windows per stream in the multi-stream run")
     return ap.parse_args()
@@ -395,6 +404,149 @@ def run_multistream(args, eb, torch, dev, rank):
     return out
 
 
+def run_serving(args, eb, torch, dev, rank):
+    """64 camera streams served as their windows arrive: 32 at 346x260, 16 at
+    640x480 and 16 at 1280x720 (4:2:2).  Each stream delivers windows as a
+    Poisson process whose rate is drawn in [100, 250] Hz; window contents
+    follow the lognormal [5k, 500k] event counts and per-object affine motion
+    of the multi-stream workload, FP16 storage.  Every stream's state (its
+    previous pyramid and buffers for batches of up to 8 windows) is admitted
+    under a 40 GB budget and stays resident.  The client submits each window
+    at its arrival time through ebof_server_submit; the server's dispatcher
+    batches each stream's backlog into list calls on 8 worker CUDA streams.
+    Latency = completion seen by the dispatcher - arrival.  A run at a lower
+    rate scale shows the latency when the offered load is below capacity."""
+    import ctypes
+    from paper_2112_10591_gb300 import synth
+    lib = eb.load()
+    rng = np.random.default_rng(4242 + rank)
+    kinds = [(346, 260, 32, dict(n_objects=4, n_edges=60, radius=(15.0, 60.0),
+                                 extra_length=(5.0, 40.0))),
+             (640, 480, 16, dict(n_objects=8, n_edges=150, radius=(25.0, 110.0),
+                                 extra_length=(8.0, 80.0))),
+             (1280, 720, 16, {})]
+    n_seq, L = 4, max(4, args.sv_windows)
+    max_batch = 8
+    cfg = eb.ebof_server_default_config()
+    cfg.device = dev.index or 0
+    cfg.n_workers = args.sv_workers
+    st, server = eb.ebof_server_create(cfg)
+    eb.check(st, "ebof_server_create")
+    streams = []
+    keep = []
+    for ki, (W, H, n, kw) in enumerate(kinds):
+        pool = []
+        for q in range(n_seq):
+            ev = synth.rigid_objects(width=W, height=H, n_windows=L, events=(5000, 500000),
+                                     lognormal_counts=True,
+                                     seed=5000 * (rank + 1) + 100 * ki + q, **kw)
+            xs = torch.from_numpy(ev.x).to(dev)
+            ys = torch.from_numpy(ev.y).to(dev)
+            ts = torch.from_numpy(ev.t).to(dev)
+            keep.append((xs, ys, ts))
+            descs = []
+            for k in range(L):
+                a, b = int(ev.offsets[k]), int(ev.offsets[k + 1])
+                d = eb.ebof_window_desc()
+                d.x = xs.data_ptr() + 2 * a
+                d.y = ys.data_ptr() + 2 * a
+                d.t = ts.data_ptr() + 8 * a
+                d.n_events = b - a
+                d.t_begin = int(ev.t_begin[k])
+                d.t_end = int(ev.t_begin[k]) + ev.dt
+                descs.append(d)
+            pool.append(descs)
+        prm = eb.ebof_default_params(W, H)
+        prm.storage = eb.EBOF_STORAGE_FP16
+        prm.max_batch = max_batch
+        for i in range(n):
+            r, sid = eb.ebof_server_open_stream(server, prm)
+            eb.check(r, "ebof_server_open_stream")
+            ring = 2 * max_batch + 1  # flows of one stream complete in order
+            fl = torch.empty((ring, 2, H, W), dtype=torch.float32, device=dev)
+            keep.append(fl)
+            streams.append({"sid": sid, "W": W, "H": H, "seq": pool[i % n_seq],
+                            "pos": (i // n_seq) * 3 % L, "rate": float(rng.uniform(100, 250)),
+                            "flow": [fl[j].data_ptr() for j in range(ring)], "k": 0})
+    info0 = eb.ebof_server_get_info(server)
+    buf = (eb.ebof_completion * 4096)()
+
+    def run(seconds, scale):
+        sched = []
+        for si, sm in enumerate(streams):
+            t, lam = 0.0, sm["rate"] * scale
+            while True:
+                t += rng.exponential(1.0 / lam)
+                if t >= seconds:
+                    break
+                sched.append((t, si))
+        sched.sort()
+        t0 = int(lib.ebof_now_ns()) + 20_000_000
+        comps = []
+        for (toff, si) in sched:
+            sm = streams[si]
+            ta = t0 + int(toff * 1e9)
+            while lib.ebof_now_ns() < ta:
+                pass
+            k = sm["k"]
+            d = sm["seq"][(sm["pos"] + k) % L]
+            r = lib.ebof_server_submit(server.handle, sm["sid"], ctypes.byref(d),
+                                       sm["flow"][k % len(sm["flow"])], k, ta)
+            if r < 0:
+                raise eb.EbofError(r, "ebof_server_submit")
+            sm["k"] = k + 1
+        eb.check(lib.ebof_server_drain(server.handle, 600000), "ebof_server_drain")
+        while True:
+            n = lib.ebof_server_poll(server.handle, buf, 4096, 0)
+            if n <= 0:
+                break
+            comps += [(buf[i].stream_id, buf[i].status, buf[i].arrival_ns, buf[i].launch_ns,
+                       buf[i].done_ns, buf[i].batch) for i in range(n)]
+        return sched, t0, comps
+
+    # warm-up: first windows of every stream and the graphs of most batch sizes
+    run(args.sv_warmup, 1.0)
+    out = {"streams": {"%dx%d" % (W, H): n for (W, H, n, _) in kinds},
+           "storage": "fp16", "max_batch": max_batch, "workers": cfg.n_workers,
+           "memory_budget_gb": cfg.memory_budget / 1e9,
+           "memory_in_use_gb": info0.memory_in_use / 1e9,
+           "streams_admitted": info0.streams_admitted,
+           "arrivals": "Poisson, per-stream rate U[100, 250] Hz x scale",
+           "windows": "each stream cycles through %d generated windows of one of %d "
+                      "sequences per resolution" % (L, n_seq),
+           "runs": []}
+    for scale in args.sv_scales:
+        sched, t0, comps = run(args.sv_seconds, scale)
+        sid_px = {sm["sid"]: (sm["W"], sm["H"]) for sm in streams}
+        ok = [c for c in comps if c[1] >= 0]
+        lat = np.asarray([(c[4] - c[2]) / 1e6 for c in ok])
+        first = min(c[2] for c in comps)
+        last = max(c[4] for c in comps)
+        span = (last - first) / 1e9
+        px = sum(sid_px[c[0]][0] * sid_px[c[0]][1] for c in ok)
+        per_res = {}
+        for key in {"%dx%d" % v for v in sid_px.values()}:
+            lr = np.asarray([(c[4] - c[2]) / 1e6 for c in ok
+                             if "%dx%d" % sid_px[c[0]] == key])
+            per_res[key] = {"p50_ms": float(np.percentile(lr, 50)),
+                            "p99_ms": float(np.percentile(lr, 99)), "windows": int(len(lr))}
+        offered_px = sum(streams[si]["W"] * streams[si]["H"] for (_, si) in sched)
+        out["runs"].append({
+            "rate_scale": scale, "arrival_seconds": args.sv_seconds,
+            "windows": len(comps), "errors": len(comps) - len(ok),
+            "offered_windows_per_s": len(sched) / args.sv_seconds,
+            "offered_mpx_per_s": offered_px / args.sv_seconds / 1e6,
+            "frames_per_s": len(ok) / span, "mpx_per_s": px / span / 1e6,
+            "span_s": span, "p50_latency_ms": float(np.percentile(lat, 50)),
+            "p99_latency_ms": float(np.percentile(lat, 99)),
+            "max_latency_ms": float(lat.max()),
+            "mean_batch": float(np.mean([c[5] for c in comps])),
+            "latency_by_resolution": per_res})
+    server.close()
+    del keep
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -663,6 +815,7 @@ def main():
                "d2h_bytes_per_step": nwin * 2 * P * 4}
 
     multistream = None if args.no_multistream else run_multistream(args, eb, torch, dev, rank)
+    serving = None if args.no_serving else run_serving(args, eb, torch, dev, rank)
 
     if rank == 0:
         lat = np.asarray(lat)
@@ -688,6 +841,7 @@ def main():
             "epe_vs_oracle": epe,
             "fp16_storage": fp16,
             "multistream": multistream,
+            "serving": serving,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

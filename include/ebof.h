@@ -46,13 +46,15 @@ extern "C" {
 typedef enum {
     EBOF_OK = 0,
     EBOF_NO_PREVIOUS = 1,          /* first window: surface built, flow zero-filled */
+    EBOF_QUEUED = 2,               /* server: stream waits for memory to be admitted */
     EBOF_ERR_INVALID_ARG = -1,
     EBOF_ERR_OOM = -2,
     EBOF_ERR_CUDA = -3,
     EBOF_ERR_TIMEOUT = -4,
     EBOF_ERR_DEVICE_BOUNDS = -5,   /* a kernel's own bounds check fired */
     EBOF_ERR_UNSUPPORTED = -6,     /* parameter outside what the kernels support */
-    EBOF_ERR_BUSY = -7             /* stream used from two host threads */
+    EBOF_ERR_BUSY = -7,            /* stream used from two host threads */
+    EBOF_ERR_CANCELLED = -8        /* server: window dropped before it ran */
 } ebof_status;
 
 /* Method parameters.  Fill with ebof_default_params, then override. */
@@ -114,12 +116,28 @@ float ebof_alpha_from_dsat(float d_sat);
  * do not support.  *out is NULL on failure. */
 ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **out);
 
+/* Device bytes ebof_stream_create would allocate for these parameters (for
+ * admission control against a memory budget), or -1 if they are invalid.
+ * Allocates nothing. */
+int64_t ebof_stream_device_bytes(const ebof_params *p);
+
 /* Frees the stream after waiting for its work.  NULL is accepted. */
 ebof_status ebof_stream_destroy(ebof_stream *s);
 
 /* Forgets the previous window: the next call returns EBOF_NO_PREVIOUS.
  * Waits for work already enqueued on the stream. */
 ebof_status ebof_stream_reset(ebof_stream *s);
+
+/* One window of events, passed by descriptor (ebof_process_window_list,
+ * groups, the server).  Events outside [t_begin, t_end) or outside the
+ * image are counted and ignored, as in ebof_process_window. */
+typedef struct {
+    const uint16_t *x;   /* device pointers, n_events each */
+    const uint16_t *y;
+    const int64_t *t;
+    int64_t n_events;
+    int64_t t_begin, t_end;  /* the window [t_begin, t_end) */
+} ebof_window_desc;
 
 /* One window (§III-A..§III-D).  d_x, d_y, d_t: n_events events (SoA);
  * d_p (polarity) may be NULL and is never read (§III-A ignores polarity).
@@ -150,6 +168,21 @@ ebof_status ebof_process_windows(ebof_stream *s, int32_t n_windows, const uint16
                                  int64_t n_events, int64_t t_begin, int64_t dt,
                                  float *d_flow, uint8_t *d_edge, int32_t *d_edt,
                                  float *d_surface, void *cuda_stream);
+
+/* n_windows (1 <= n_windows <= max_batch) consecutive windows of one stream
+ * with arbitrary extents, in one call: windows[k] (HOST array, copied during
+ * the call) gives window k's device events and interval, d_flows[k] (HOST
+ * array of device pointers) its flow destination [2][H][W].  Flow k maps
+ * window k-1 to window k (window -1 = the stream's previous window); every
+ * stage runs once for all n windows.  In steady state (a previous window
+ * exists, stage timing off) the call replays a CUDA graph of the n-window
+ * sequence, one graph per n captured on first use, after copying the
+ * descriptors to the device and, if needed, moving the previous window's
+ * pyramid to the first slot.  Same results as n ebof_process_window calls.
+ * The event buffers must stay valid until the work completes. */
+ebof_status ebof_process_window_list(ebof_stream *s, int32_t n_windows,
+                                     const ebof_window_desc *windows, float *const *d_flows,
+                                     void *cuda_stream);
 
 /* Flow block only (§III-D) on a caller-given surface d_surface [H][W] with
  * values d_exp in [0, 1] (the flow runs on 255 * d_surface); it becomes the
@@ -210,14 +243,6 @@ ebof_status ebof_edt_static(const uint8_t *d_edge, int32_t width, int32_t height
  * before each replay.  Streams of other resolutions go in other groups,
  * which may run concurrently on other CUDA streams.  Results per stream are
  * bit-identical to an ebof_stream fed the same windows. */
-typedef struct {
-    const uint16_t *x;   /* device pointers, n_events each */
-    const uint16_t *y;
-    const int64_t *t;
-    int64_t n_events;
-    int64_t t_begin, t_end;  /* the window [t_begin, t_end) */
-} ebof_window_desc;
-
 typedef struct ebof_group ebof_group;
 
 /* Allocates the state of n_streams streams (1 .. 4096) with parameters p
@@ -241,6 +266,99 @@ const float *ebof_group_flow(const ebof_group *g, int32_t k);
 
 /* As ebof_stream_sync, for the group's streams (out[k] = stream k). */
 ebof_status ebof_group_sync(ebof_group *g, ebof_window_stats *out, int32_t n_out);
+
+/* ---- serving loop ---------------------------------------------------------
+ * A server runs many camera streams on one GPU as their windows arrive.
+ * §IV (Real-Time Compliance) runs one sensor per pipeline and counts a flow
+ * as real time when each window (4-13 ms of events) is processed before the
+ * next one ends; the server carries that setting to many sensors sharing a
+ * GPU.  It is a deployment layer with no counterpart in the paper's method.
+ *  - Admission: a stream's device state (ebof_stream_device_bytes of its
+ *    parameters, which include its batch limit max_batch) is allocated when
+ *    it is admitted and stays resident until it is closed.  Streams are
+ *    admitted in the order they were opened while the total fits the
+ *    memory budget; one that does not fit waits (EBOF_QUEUED) until closed
+ *    streams free enough memory.
+ *  - Submission: each window goes to its stream's FIFO with the caller's
+ *    tag and arrival time; its events and flow destination must stay valid
+ *    until its completion is reported.
+ *  - Continuous batching: a dispatcher thread keeps up to n_workers batches
+ *    in flight, each on its own CUDA stream.  When a worker frees up it takes
+ *    the stream whose oldest queued window arrived first and has no batch in
+ *    flight, and launches that stream's queued windows (up to its max_batch)
+ *    as one ebof_process_window_list call.  Batches grow with the backlog.
+ *  - Completion: one ebof_completion per window, in completion order.
+ * Every window's flow is bit-identical to feeding the same stream's windows
+ * to ebof_process_window one by one. */
+typedef struct ebof_server ebof_server;
+
+typedef struct {
+    int32_t struct_size;    /* sizeof(ebof_server_config) */
+    int32_t device;
+    int64_t memory_budget;  /* bytes of device state admitted streams may hold */
+    int32_t n_workers;      /* batches in flight at once, 1..64 */
+} ebof_server_config;
+
+typedef struct {
+    int32_t stream_id;
+    int32_t status;       /* EBOF_OK; EBOF_NO_PREVIOUS for a stream's first
+                             window (flow zero); EBOF_ERR_CANCELLED; or the
+                             error of the launch */
+    uint64_t tag;         /* as given to ebof_server_submit */
+    int64_t arrival_ns;   /* ebof_now_ns clock */
+    int64_t launch_ns;    /* the dispatcher launched its batch */
+    int64_t done_ns;      /* the dispatcher saw the batch complete */
+    int32_t batch;        /* windows in that batch */
+    int32_t index;        /* this window's position in it */
+} ebof_completion;
+
+typedef struct {
+    int32_t streams_admitted, streams_waiting;
+    int64_t memory_budget, memory_in_use;
+    int64_t windows_submitted, windows_completed, batches_launched;
+    int32_t batches_in_flight, max_batch_seen;
+} ebof_server_info;
+
+/* Monotonic clock (nanoseconds) of the arrival and completion times. */
+int64_t ebof_now_ns(void);
+
+/* device 0, a 40 GB (40e9 bytes) budget, 8 workers. */
+void ebof_server_default_config(ebof_server_config *c);
+
+/* Creates the server and its dispatcher thread and worker CUDA streams. */
+ebof_status ebof_server_create(const ebof_server_config *c, ebof_server **out);
+
+/* Drops queued windows (no completions), waits for the batches in flight,
+ * frees every stream.  NULL is accepted. */
+ebof_status ebof_server_destroy(ebof_server *v);
+
+/* Opens a stream with parameters p (validated as by ebof_stream_create) and
+ * returns its id.  EBOF_OK: admitted, state allocated.  EBOF_QUEUED: waits
+ * for memory; windows may be submitted meanwhile.  EBOF_ERR_OOM: its state
+ * is larger than the whole budget, or the allocation failed. */
+ebof_status ebof_server_open_stream(ebof_server *v, const ebof_params *p, int32_t *id);
+
+/* No further windows for the stream.  Its queued windows still run; then its
+ * state is freed and waiting streams are admitted.  A stream still waiting
+ * for admission is dropped and its windows complete as EBOF_ERR_CANCELLED. */
+ebof_status ebof_server_close_stream(ebof_server *v, int32_t id);
+
+/* Queues one window (descriptor copied; device pointers kept) whose flow
+ * [2][H][W] goes to d_flow.  arrival_ns: when the window became available
+ * (ebof_now_ns clock; 0 = now), the start of its latency. */
+ebof_status ebof_server_submit(ebof_server *v, int32_t id, const ebof_window_desc *w,
+                               float *d_flow, uint64_t tag, int64_t arrival_ns);
+
+/* Moves up to max_out completions into out, waiting up to wait_us
+ * microseconds for the first; returns how many (>= 0) or an error (< 0). */
+int32_t ebof_server_poll(ebof_server *v, ebof_completion *out, int32_t max_out,
+                         int32_t wait_us);
+
+/* Waits up to timeout_ms until every submitted window has completed
+ * (EBOF_ERR_TIMEOUT otherwise).  Completions stay queued for poll. */
+ebof_status ebof_server_drain(ebof_server *v, int32_t timeout_ms);
+
+ebof_status ebof_server_get_info(ebof_server *v, ebof_server_info *out);
 
 /* ---- tracing: per-stage CUDA-event timing (§IV Table VII reports per-block
  * times; these are the GPU equivalents).  Timing brackets each stage's

@@ -15,4 +15,9 @@ from .binding import (  # noqa: F401
     ebof_stream_set_profiling, ebof_edt_static, ebof_stream_get_profile_level,
     EBOF_STORAGE_FP16, EBOF_STORAGE_FP32, Group, ebof_window_desc, ebof_group_create,
     ebof_group_reset, ebof_group_process, ebof_group_flow, ebof_group_sync,
+    ebof_stream_device_bytes, ebof_process_window_list, EBOF_QUEUED, EBOF_ERR_CANCELLED,
+    Server, ebof_completion, ebof_now_ns, ebof_server_close_stream, ebof_server_config,
+    ebof_server_create, ebof_server_default_config, ebof_server_destroy, ebof_server_drain,
+    ebof_server_get_info, ebof_server_info, ebof_server_open_stream, ebof_server_poll,
+    ebof_server_submit,
 )

@@ -26,6 +26,8 @@ EBOF_ERR_TIMEOUT = -4
 EBOF_ERR_DEVICE_BOUNDS = -5
 EBOF_ERR_UNSUPPORTED = -6
 EBOF_ERR_BUSY = -7
+EBOF_QUEUED = 2
+EBOF_ERR_CANCELLED = -8
 
 
 class ebof_params(ctypes.Structure):
@@ -66,6 +68,26 @@ class ebof_window_desc(ctypes.Structure):
     ]
 
 
+class ebof_server_config(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("n_workers", ctypes.c_int32)]
+
+
+class ebof_completion(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("tag", ctypes.c_uint64), ("arrival_ns", ctypes.c_int64),
+                ("launch_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("batch", ctypes.c_int32), ("index", ctypes.c_int32)]
+
+
+class ebof_server_info(ctypes.Structure):
+    _fields_ = [("streams_admitted", ctypes.c_int32), ("streams_waiting", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("memory_in_use", ctypes.c_int64),
+                ("windows_submitted", ctypes.c_int64), ("windows_completed", ctypes.c_int64),
+                ("batches_launched", ctypes.c_int64), ("batches_in_flight", ctypes.c_int32),
+                ("max_batch_seen", ctypes.c_int32)]
+
+
 class EbofError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         super().__init__("%s: %s (%d)" % (what or "ebof", ebof_status_string(status), status))
@@ -101,10 +123,25 @@ def _declare(L):
     L.ebof_alpha_from_dsat.restype = f32
     L.ebof_stream_create.argtypes = [P(ebof_params), ctypes.c_int, P(vp)]
     L.ebof_stream_destroy.argtypes = [vp]
+    L.ebof_stream_device_bytes.argtypes = [P(ebof_params)]
+    L.ebof_stream_device_bytes.restype = ctypes.c_int64
     L.ebof_stream_reset.argtypes = [vp]
     L.ebof_process_window.argtypes = [vp, vp, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
     L.ebof_process_windows.argtypes = [vp, i32, vp, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
     L.ebof_process_surface.argtypes = [vp, vp, vp, vp]
+    L.ebof_process_window_list.argtypes = [vp, i32, P(ebof_window_desc), P(vp), vp]
+    L.ebof_now_ns.argtypes = []
+    L.ebof_now_ns.restype = i64
+    L.ebof_server_default_config.argtypes = [P(ebof_server_config)]
+    L.ebof_server_default_config.restype = None
+    L.ebof_server_create.argtypes = [P(ebof_server_config), P(vp)]
+    L.ebof_server_destroy.argtypes = [vp]
+    L.ebof_server_open_stream.argtypes = [vp, P(ebof_params), P(i32)]
+    L.ebof_server_close_stream.argtypes = [vp, i32]
+    L.ebof_server_submit.argtypes = [vp, i32, P(ebof_window_desc), vp, ctypes.c_uint64, i64]
+    L.ebof_server_poll.argtypes = [vp, P(ebof_completion), i32, i32]
+    L.ebof_server_drain.argtypes = [vp, i32]
+    L.ebof_server_get_info.argtypes = [vp, P(ebof_server_info)]
     L.ebof_process_window_host.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, vp]
     L.ebof_stream_sync.argtypes = [vp, P(ebof_window_stats), i32]
     L.ebof_edt.argtypes = [vp, i32, i32, vp, vp, vp, f32, vp]
@@ -130,7 +167,10 @@ def _declare(L):
                  "ebof_process_window_host", "ebof_stream_sync", "ebof_edt",
                  "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static",
                  "ebof_stream_get_profile_level", "ebof_group_create", "ebof_group_destroy",
-                 "ebof_group_reset", "ebof_group_process", "ebof_group_sync"):
+                 "ebof_group_reset", "ebof_group_process", "ebof_group_sync",
+                 "ebof_process_window_list", "ebof_server_create", "ebof_server_destroy",
+                 "ebof_server_open_stream", "ebof_server_close_stream", "ebof_server_submit",
+                 "ebof_server_poll", "ebof_server_drain", "ebof_server_get_info"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -228,6 +268,10 @@ def ebof_stream_create(params: ebof_params, device: int = 0):
     return st, Stream(h.value, p, int(device))
 
 
+def ebof_stream_device_bytes(params: ebof_params) -> int:
+    return int(load().ebof_stream_device_bytes(ctypes.byref(params)))
+
+
 def ebof_stream_destroy(stream: Stream) -> int:
     stream.close()
     return EBOF_OK
@@ -263,6 +307,38 @@ def ebof_process_windows(stream: Stream, n_windows: int, x, y, t, p, t_begin: in
         _ptr(edge, torch.uint8, k * W * H, "edge", dev),
         _ptr(edt, torch.int32, k * W * H, "edt", dev),
         _ptr(surface, torch.float32, k * W * H, "surface", dev), _stream_handle(cuda_stream))
+
+
+def _window_desc(w, device, out=None):
+    """(x, y, t, t_begin, t_end) of CUDA tensors and ints -> ebof_window_desc."""
+    import torch
+    x, y, t, tb, te = w
+    n = x.numel()
+    d = ebof_window_desc() if out is None else out
+    d.x = _ptr(x, torch.uint16, n, "x", device)
+    d.y = _ptr(y, torch.uint16, n, "y", device)
+    d.t = _ptr(t, torch.int64, n, "t", device)
+    d.n_events = n
+    d.t_begin = int(tb)
+    d.t_end = int(te)
+    return d
+
+
+def ebof_process_window_list(stream: Stream, windows, flows, cuda_stream=None) -> int:
+    """windows: n tuples (x, y, t, t_begin, t_end); flows: n CUDA float32
+    tensors of [2][H][W] elements each."""
+    import torch
+    n = len(windows)
+    if len(flows) != n:
+        raise ValueError("need one flow buffer per window")
+    arr = (ebof_window_desc * max(n, 1))()
+    dst = (ctypes.c_void_p * max(n, 1))()
+    W, H = stream.params.width, stream.params.height
+    for k in range(n):
+        _window_desc(windows[k], stream.device, arr[k])
+        dst[k] = _ptr(flows[k], torch.float32, 2 * W * H, "flow", stream.device)
+    return load().ebof_process_window_list(stream.handle, n, arr, dst,
+                                           _stream_handle(cuda_stream))
 
 
 def ebof_process_surface(stream: Stream, surface, flow, cuda_stream=None) -> int:
@@ -357,14 +433,8 @@ def ebof_group_process(group: Group, windows, flow=None, cuda_stream=None) -> in
     if len(windows) != group.n:
         raise ValueError("need %d windows, got %d" % (group.n, len(windows)))
     arr = (ebof_window_desc * group.n)()
-    for k, (x, y, t, tb, te) in enumerate(windows):
-        n = x.numel()
-        arr[k].x = _ptr(x, torch.uint16, n, "x", group.device)
-        arr[k].y = _ptr(y, torch.uint16, n, "y", group.device)
-        arr[k].t = _ptr(t, torch.int64, n, "t", group.device)
-        arr[k].n_events = n
-        arr[k].t_begin = int(tb)
-        arr[k].t_end = int(te)
+    for k in range(group.n):
+        _window_desc(windows[k], group.device, arr[k])
     W, H = group.params.width, group.params.height
     fp = _ptr(flow, torch.float32, group.n * 2 * W * H, "flow", group.device)
     return load().ebof_group_process(group.handle, arr, fp, _stream_handle(cuda_stream))
@@ -412,6 +482,99 @@ def ebof_stage_name(stage: int) -> str:
 
 def ebof_kernel_launches() -> int:
     return int(load().ebof_kernel_launches())
+
+
+# ---------------------------------------------------------------- serving loop
+def ebof_now_ns() -> int:
+    return int(load().ebof_now_ns())
+
+
+def ebof_server_default_config() -> ebof_server_config:
+    c = ebof_server_config()
+    load().ebof_server_default_config(ctypes.byref(c))
+    return c
+
+
+class Server:
+    """Owner of an ``ebof_server*`` handle."""
+
+    def __init__(self, handle: int, config: ebof_server_config):
+        self.handle = handle
+        self.config = config
+        self.params = {}  # stream id -> ebof_params
+
+    def close(self):
+        if self.handle:
+            load().ebof_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ebof_server_create(config: ebof_server_config = None):
+    """Returns (status, Server or None)."""
+    c = ebof_server_default_config() if config is None else config
+    h = ctypes.c_void_p()
+    st = load().ebof_server_create(ctypes.byref(c), ctypes.byref(h))
+    if st < 0:
+        return st, None
+    return st, Server(h.value, c)
+
+
+def ebof_server_destroy(server: Server) -> int:
+    server.close()
+    return EBOF_OK
+
+
+def ebof_server_open_stream(server: Server, params: ebof_params):
+    """Returns (status, stream id); status EBOF_QUEUED means waiting for memory."""
+    sid = ctypes.c_int32(-1)
+    st = load().ebof_server_open_stream(server.handle, ctypes.byref(params), ctypes.byref(sid))
+    if st >= 0:
+        p = ebof_params()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(params), ctypes.sizeof(p))
+        server.params[sid.value] = p
+    return st, sid.value
+
+
+def ebof_server_close_stream(server: Server, stream_id: int) -> int:
+    return load().ebof_server_close_stream(server.handle, int(stream_id))
+
+
+def ebof_server_submit(server: Server, stream_id: int, window, flow, tag: int,
+                       arrival_ns: int = 0) -> int:
+    """window: (x, y, t, t_begin, t_end); flow: CUDA float32 [2][H][W].  The
+    tensors must stay alive until the window's completion is polled."""
+    import torch
+    p = server.params.get(int(stream_id))
+    if p is None:
+        return EBOF_ERR_INVALID_ARG
+    d = _window_desc(window, server.config.device)
+    fp = _ptr(flow, torch.float32, 2 * p.width * p.height, "flow", server.config.device)
+    return load().ebof_server_submit(server.handle, int(stream_id), ctypes.byref(d), fp,
+                                     int(tag), int(arrival_ns))
+
+
+def ebof_server_poll(server: Server, max_out: int = 256, wait_us: int = 0):
+    """Returns a list of ebof_completion (raises EbofError on error)."""
+    arr = (ebof_completion * max(1, max_out))()
+    n = load().ebof_server_poll(server.handle, arr, int(max_out), int(wait_us))
+    check(n, "ebof_server_poll")
+    return [arr[i] for i in range(n)]
+
+
+def ebof_server_drain(server: Server, timeout_ms: int = 60000) -> int:
+    return load().ebof_server_drain(server.handle, int(timeout_ms))
+
+
+def ebof_server_get_info(server: Server) -> ebof_server_info:
+    info = ebof_server_info()
+    check(load().ebof_server_get_info(server.handle, ctypes.byref(info)), "ebof_server_get_info")
+    return info
 
 
 def check(status: int, what: str = "") -> int:

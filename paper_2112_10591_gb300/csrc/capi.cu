@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 using namespace ebof;
 
@@ -46,12 +47,6 @@ Geometry make_geometry(int width, int height, int levels, int ps, int stride)
 
 }  // namespace ebof
 
-// Per-call arguments of a single-window graph replay (copied to the device).
-struct StreamCall {
-    ebof_window_desc win;
-    float *flow;
-};
-
 struct ebof_stream {
     ebof_params p;
     int device;
@@ -80,10 +75,21 @@ struct ebof_stream {
     bool have_last = false;
     std::atomic<int> busy{0};
     Profiler prof;
+    // Per-call window descriptors and flow destinations, read on the device by
+    // the descriptor-driven paths: [max_batch] ebof_window_desc followed by
+    // [max_batch] float*, staged from h_call by one copy per call.
+    char *d_call = nullptr;
+    std::vector<char> h_call;
+    ebof_window_desc *d_wins = nullptr;
+    float **d_flows = nullptr;
     // single-window graph replays (one graph per ping-pong slot)
-    StreamCall *d_args = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_kernels[2] = {0, 0};
+    // list calls: graph [n] replays n windows with the previous one in slot 0
+    std::vector<cudaGraphExec_t> list_graph;
+    std::vector<long long> list_graph_kernels;
+    std::vector<int64_t> last_win_events;  // per window, after a list call
+    bool last_list = false;
     cudaStream_t cap = nullptr;
 };
 
@@ -194,9 +200,11 @@ void free_all(ebof_stream *s)
     cudaFree(s->E); cudaFree(s->Ed); cudaFree(s->Edf); cudaFree(s->g); cudaFree(s->pyr);
     cudaFree(s->up); cudaFree(s->Ua); cudaFree(s->Ub); cudaFree(s->work);
     cudaFree(s->dstats); cudaFree(s->d_dropped_time); cudaFree(s->d_err);
-    cudaFree(s->flow_stage); cudaFree(s->ev_stage); cudaFree(s->d_args);
+    cudaFree(s->flow_stage); cudaFree(s->ev_stage); cudaFree(s->d_call);
     for (int b = 0; b < 2; ++b)
         if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+    for (cudaGraphExec_t ge : s->list_graph)
+        if (ge) cudaGraphExecDestroy(ge);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->done) cudaEventDestroy(s->done);
 }
@@ -221,8 +229,9 @@ FlowParams flow_params(const ebof_params &p)
 // Enqueues the whole path for n consecutive windows (or one caller-given
 // surface) on `st`: the current windows go to slots cur_first.., the previous
 // ones are at prev_first.., and nothing of the stream's bookkeeping changes
-// (so the same sequence can be captured into a graph).  With `via_args` (one
-// window), the events and the flow destination are read from s->d_args.
+// (so the same sequence can be captured into a graph).  With `via_args`, the
+// events and flow destination of window k are read from s->d_wins[k] and
+// s->d_flows[k].
 void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const int64_t *t,
              int64_t nev, int64_t t_begin, int64_t dt, const float *surface_in, float *d_flow,
              uint8_t *d_edge, int32_t *d_edt, float *d_surface, bool via_args, int cur_first,
@@ -243,7 +252,7 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
     } else {
         cudaMemsetAsync(s->E, 0, s->e_fs * n, st);
         if (via_args)
-            launch_scatter_desc(&s->d_args->win, 1, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
+            launch_scatter_desc(s->d_wins, n, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
                                 s->d_dropped_time, st);
         else
             launch_scatter(x, y, t, nev, t_begin, dt, n, W, H, s->pitch0, s->E, s->e_fs,
@@ -298,7 +307,7 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
         }
         tl_level = -1;
         if (via_args)
-            launch_flow_out_ptr(Ucur, W, H, s->pitch0, &s->d_args->flow, st);
+            launch_flow_out_ptr(Ucur, W, H, s->pitch0, s->u_fs, s->d_flows + ff, nf, st);
         else
             launch_flow_out(Ucur, W, H, s->pitch0, s->u_fs, d_flow + (size_t)ff * flow_frame,
                             nf, st);
@@ -309,6 +318,99 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
         else if (ff == 1)
             cudaMemsetAsync(d_flow, 0, sizeof(float) * flow_frame, st);
     }
+}
+
+// Copies the descriptors and flow destinations of n windows to s->d_call.
+void stage_call(ebof_stream *s, int n, const ebof_window_desc *wins, float *const *flows,
+                cudaStream_t st)
+{
+    const int B = s->p.max_batch;
+    ebof_window_desc *hw = (ebof_window_desc *)s->h_call.data();
+    float **hf = (float **)(s->h_call.data() + sizeof(ebof_window_desc) * B);
+    for (int k = 0; k < n; ++k) {
+        hw[k] = wins[k];
+        hf[k] = flows[k];
+    }
+    cudaMemcpyAsync(s->d_call, s->h_call.data(), s->h_call.size(), cudaMemcpyHostToDevice, st);
+}
+
+// Captures enqueue(via_args) of n windows (current ones from slot cur_first,
+// previous from prev_first) into an executable graph on s->cap, after work
+// already queued on st.  Returns nullptr on failure; *kernels gets the number
+// of kernels in the graph.
+cudaGraphExec_t capture(ebof_stream *s, int n, int cur_first, int prev_first, cudaStream_t st,
+                        long long *kernels)
+{
+    cudaEvent_t ready;
+    cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    cudaEventRecord(ready, st);
+    cudaStreamWaitEvent(s->cap, ready, 0);
+    cudaEventDestroy(ready);
+    const unsigned long long before = g_launches.load();
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        Profiler *keep = tl_prof;
+        tl_prof = nullptr;
+        enqueue(s, n, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, nullptr,
+                nullptr, true, cur_first, prev_first, true, s->cap);
+        tl_prof = keep;
+        cudaStreamEndCapture(s->cap, &gr);
+    }
+    if (gr && cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess) ge = nullptr;
+    if (gr) cudaGraphDestroy(gr);
+    *kernels = (long long)(g_launches.load() - before);
+    g_launches.fetch_sub((unsigned long long)*kernels);
+    if (!ge) cudaGetLastError();
+    return ge;
+}
+
+// A list call: n windows of arbitrary extents.  With a previous window, that
+// window's pyramid is moved to slot 0 (if it is not there) and the current
+// windows go to slots 1..n, so the enqueued sequence depends on n alone and is
+// replayed from list_graph[n].
+ebof_status run_list(ebof_stream *s, int n, const ebof_window_desc *wins, float *const *flows,
+                     cudaStream_t st)
+{
+    ProfScope prof_scope(&s->prof);
+    cudaGetLastError();
+    if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
+    const bool had_prev = s->has_prev;
+    if (had_prev && s->head != 0)
+        cudaMemcpyAsync(s->pyr, s->pyr + (size_t)s->head * s->pyr_fs * s->es, s->pyr_fs * s->es,
+                        cudaMemcpyDeviceToDevice, st);
+    s->head = 0;
+    stage_call(s, n, wins, flows, st);
+    const size_t flow_bytes = sizeof(float) * 2 * (size_t)s->p.width * s->p.height;
+    if (had_prev && !s->prof.on && s->geo.levels > 0) {
+        if (!s->list_graph[n]) {
+            s->list_graph[n] = capture(s, n, 1, 0, st, &s->list_graph_kernels[n]);
+            if (!s->list_graph[n]) return EBOF_ERR_CUDA;
+        }
+        if (cudaGraphLaunch(s->list_graph[n], st) != cudaSuccess) return EBOF_ERR_CUDA;
+        g_launches.fetch_add((unsigned long long)s->list_graph_kernels[n]);
+    } else {
+        enqueue(s, n, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, nullptr,
+                nullptr, true, 1, had_prev ? 0 : 1, had_prev, st);
+        for (int k = 0; k < n; ++k)
+            if (s->geo.levels == 0 || (k == 0 && !had_prev))
+                cudaMemsetAsync(flows[k], 0, flow_bytes, st);
+    }
+    s->head = n;
+    s->has_prev = true;
+    s->last_n = n;
+    s->last_had_prev = had_prev;
+    s->last_list = true;
+    s->last_events = 0;
+    for (int k = 0; k < n; ++k) {
+        s->last_win_events[k] = wins[k].n_events;
+        s->last_events += wins[k].n_events;
+    }
+    cudaEventRecord(s->done, st);
+    s->last_stream = st;
+    s->have_last = true;
+    if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
+    return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
 }
 
 // One call: slot bookkeeping, then either a graph replay (single window in
@@ -332,43 +434,20 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
     const int cur_first = n == 1 ? (s->head + 1) % s->nslots : s->head + 1;
     const int prev_first = n == 1 ? s->head : s->head + (had_prev ? 0 : 1);
     const bool graph = n == 1 && had_prev && !surface_in && !d_edge && !d_edt && !d_surface &&
-                       !s->prof.on && s->nslots == 2;
+                       !s->prof.on && s->nslots == 2 && s->geo.levels > 0;
     if (graph) {
         const int b = s->head;
-        StreamCall h;
-        h.win.x = x;
-        h.win.y = y;
-        h.win.t = t;
-        h.win.n_events = nev;
-        h.win.t_begin = t_begin;
-        h.win.t_end = t_begin + dt;
-        h.flow = d_flow;
-        cudaMemcpyAsync(s->d_args, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+        ebof_window_desc w;
+        w.x = x;
+        w.y = y;
+        w.t = t;
+        w.n_events = nev;
+        w.t_begin = t_begin;
+        w.t_end = t_begin + dt;
+        stage_call(s, 1, &w, &d_flow, st);
         if (!s->graph[b]) {
-            cudaEvent_t ready;
-            cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-            cudaEventRecord(ready, st);
-            cudaStreamWaitEvent(s->cap, ready, 0);
-            cudaEventDestroy(ready);
-            const unsigned long long before = g_launches.load();
-            cudaGraph_t gr = nullptr;
-            if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                Profiler *keep = tl_prof;
-                tl_prof = nullptr;
-                enqueue(s, 1, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr,
-                        nullptr, nullptr, true, cur_first, prev_first, true, s->cap);
-                tl_prof = keep;
-                cudaStreamEndCapture(s->cap, &gr);
-            }
-            if (gr && cudaGraphInstantiate(&s->graph[b], gr, 0) != cudaSuccess)
-                s->graph[b] = nullptr;
-            if (gr) cudaGraphDestroy(gr);
-            s->graph_kernels[b] = (long long)(g_launches.load() - before);
-            g_launches.fetch_sub((unsigned long long)s->graph_kernels[b]);
-            if (!s->graph[b]) {
-                cudaGetLastError();
-                return EBOF_ERR_CUDA;
-            }
+            s->graph[b] = capture(s, 1, cur_first, prev_first, st, &s->graph_kernels[b]);
+            if (!s->graph[b]) return EBOF_ERR_CUDA;
         }
         if (cudaGraphLaunch(s->graph[b], st) != cudaSuccess) return EBOF_ERR_CUDA;
         g_launches.fetch_add((unsigned long long)s->graph_kernels[b]);
@@ -379,6 +458,7 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
 
     s->head = n == 1 ? cur_first : s->head + n;
     s->has_prev = true;
+    s->last_list = false;
     s->last_n = n;
     s->last_events = nev;
     s->last_had_prev = had_prev;
@@ -547,7 +627,14 @@ ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **o
     ok &= dmalloc(&s->d_err, sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&s->flow_stage, sizeof(float) * 2 * (size_t)p->width * p->height) == cudaSuccess;
     ok &= cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) == cudaSuccess;
-    ok &= dmalloc(&s->d_args, sizeof(StreamCall)) == cudaSuccess;
+    const size_t call_bytes = (sizeof(ebof_window_desc) + sizeof(float *)) * B;
+    ok &= dmalloc(&s->d_call, call_bytes) == cudaSuccess;
+    s->d_wins = (ebof_window_desc *)s->d_call;
+    s->d_flows = (float **)(s->d_call + sizeof(ebof_window_desc) * B);
+    s->h_call.assign(call_bytes, 0);
+    s->list_graph.assign(B + 1, nullptr);
+    s->list_graph_kernels.assign(B + 1, 0);
+    s->last_win_events.assign(B, 0);
     ok &= cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -565,6 +652,21 @@ ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **o
     }
     *out = s;
     return EBOF_OK;
+}
+
+int64_t ebof_stream_device_bytes(const ebof_params *p)
+{
+    if (check_params(p) != EBOF_OK) return -1;
+    const Geometry geo = make_geometry(p->width, p->height, p->levels, p->patch, p->stride);
+    const size_t B = (size_t)p->max_batch, plane0 = geo.lv[0].plane;
+    const size_t es = p->storage == EBOF_STORAGE_FP16 ? 2 : 4;
+    auto r = [](size_t b) { return std::max<size_t>(b, 256); };
+    size_t total = 3 * r(plane0 * B) + r(4 * plane0 * B) + r(es * geo.pyr_floats * (B + 1));
+    total += r(4 * 2 * (size_t)std::max(geo.max_patches, 1) * B);
+    total += 2 * r(4 * 2 * plane0 * B) + r(4 * 9 * plane0 * B);
+    total += r(sizeof(DevStats) * B) + 2 * 256 + r(4 * 2 * (size_t)p->width * p->height) +
+             r((sizeof(ebof_window_desc) + sizeof(float *)) * B);
+    return (int64_t)total;
 }
 
 ebof_status ebof_stream_destroy(ebof_stream *s)
@@ -620,6 +722,24 @@ ebof_status ebof_process_windows(ebof_stream *s, int32_t n_windows, const uint16
     if (!dg.ok) return EBOF_ERR_CUDA;
     return run(s, n_windows, d_x, d_y, d_t, n_events, t_begin, dt, nullptr, d_flow, d_edge,
                d_edt, d_surface, (cudaStream_t)cuda_stream);
+}
+
+ebof_status ebof_process_window_list(ebof_stream *s, int32_t n_windows,
+                                     const ebof_window_desc *windows, float *const *d_flows,
+                                     void *cuda_stream)
+{
+    if (!s || !windows || !d_flows || n_windows < 1 || n_windows > s->p.max_batch)
+        return EBOF_ERR_INVALID_ARG;
+    for (int k = 0; k < n_windows; ++k) {
+        const ebof_window_desc &w = windows[k];
+        if (!d_flows[k] || !events_ok(w.x, w.y, w.t, w.n_events) || w.t_end < w.t_begin)
+            return EBOF_ERR_INVALID_ARG;
+    }
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    return run_list(s, n_windows, windows, d_flows, (cudaStream_t)cuda_stream);
 }
 
 ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *d_flow,
@@ -702,7 +822,7 @@ ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_o
                 return EBOF_ERR_CUDA;
             for (int k = 0; k < m; ++k) {
                 ebof_window_stats &o = out[k0 + k];
-                o.events = s->last_events;
+                o.events = s->last_list ? s->last_win_events[k0 + k] : s->last_events;
                 o.in_window = (int64_t)hs[k].in_window;
                 o.dropped_time = (int64_t)dropped_time;
                 o.dropped_oob = (int64_t)hs[k].dropped_oob;
@@ -1010,6 +1130,8 @@ const char *ebof_status_string(ebof_status st)
     case EBOF_ERR_DEVICE_BOUNDS: return "device bounds check failed";
     case EBOF_ERR_UNSUPPORTED: return "unsupported parameter";
     case EBOF_ERR_BUSY: return "stream in use by another thread";
+    case EBOF_QUEUED: return "waiting for memory to be admitted";
+    case EBOF_ERR_CANCELLED: return "cancelled before it ran";
     }
     return "unknown status";
 }

@@ -128,8 +128,8 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
                                 cudaStream_t st);
 
 // A9 for one window, destination pointer read from device memory.
-void launch_flow_out_ptr(const float *U, int W, int H, int pitch, float *const *dst,
-                         cudaStream_t st);
+void launch_flow_out_ptr(const float *U, int W, int H, int pitch, size_t u_frame_stride,
+                         float *const *dst, int frames, cudaStream_t st);
 
 // A9: level-0 flow to the caller's dense planar layout.
 void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,

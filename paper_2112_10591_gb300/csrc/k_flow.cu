@@ -372,15 +372,17 @@ __global__ void flow_out_kernel(const float *__restrict__ Ub, int W, int H, int 
     flow[o + (size_t)W * H] = U[plane + (size_t)y * pitch + x];
 }
 
-// Same as flow_out_kernel, with the destination read from device memory (so
-// a captured graph can write each call's flow to the caller's buffer).
-__global__ void flow_out_ptr_kernel(const float *__restrict__ Ub, int W, int H, int pitch,
-                                    size_t plane, float *const *dst)
+// Same as flow_out_kernel, with frame f's destination read from dst[f] in
+// device memory (so a captured graph writes each call's flow to the caller's
+// buffers).
+__global__ void flow_out_ptr_kernel(const float *__restrict__ U, int W, int H, int pitch,
+                                    size_t plane, size_t u_frame_stride, float *const *dst)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W) return;
-    float *flow = *dst;
+    float *flow = dst[blockIdx.z];
+    const float *Ub = U + (size_t)blockIdx.z * u_frame_stride;
     const size_t o = (size_t)y * W + x;
     flow[o] = Ub[(size_t)y * pitch + x];
     flow[o + (size_t)W * H] = Ub[plane + (size_t)y * pitch + x];
@@ -550,12 +552,13 @@ float *launch_variational(const void *I0, const void *I0x, const void *I0y, cons
     return U;
 }
 
-void launch_flow_out_ptr(const float *U, int W, int H, int pitch, float *const *dst,
-                         cudaStream_t st)
+void launch_flow_out_ptr(const float *U, int W, int H, int pitch, size_t u_frame_stride,
+                         float *const *dst, int frames, cudaStream_t st)
 {
     StageScope sc(kStFlowOut, 1, st);
-    dim3 grd((W + 255) / 256, H);
-    flow_out_ptr_kernel<<<grd, 256, 0, st>>>(U, W, H, pitch, (size_t)pitch * H, dst);
+    dim3 grd((W + 255) / 256, H, frames);
+    flow_out_ptr_kernel<<<grd, 256, 0, st>>>(U, W, H, pitch, (size_t)pitch * H, u_frame_stride,
+                                             dst);
 }
 
 void launch_flow_out(const float *U, int W, int H, int pitch, size_t u_frame_stride,
