@@ -62,6 +62,11 @@ def _declare(L):
     L.orc_edt_brute.argtypes = [i32, i32, vp, vp]
     L.orc_edt_separable.argtypes = [i32, i32, vp, vp]
     L.orc_surface.argtypes = [i32, vp, f64, vp]
+    L.orc_surface_mode.argtypes = [i32, vp, i32, f64, f64, vp]
+    L.orc_iwe.argtypes = [i32, i32, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int64,
+                          ctypes.c_int64, vp, vp]
+    L.orc_fwl.argtypes = [i32, i32, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int64,
+                          ctypes.c_int64, vp, vp]
     L.orc_alpha_from_dsat.argtypes = [f64, f64]
     L.orc_alpha_from_dsat.restype = f64
     L.orc_downsample.argtypes = [i32, i32, vp, vp]
@@ -142,6 +147,60 @@ def surface(D, alpha=1.08):
     S = np.empty(D.shape, np.float64)
     lib().orc_surface(D.size, _p(D), float(alpha), _p(S))
     return S
+
+
+SURFACE_EXP, SURFACE_LINEAR, SURFACE_BOUNDED, SURFACE_LOG = 0, 1, 2, 3
+
+
+def surface_mode(D, mode=SURFACE_EXP, alpha=1.08, d_sat=6.0):
+    """Eq. 1 (mode 0) or one of the ablation surfaces of §IV-D: DS_L (1),
+    DS_LB (2, bounded at d_sat), DS_Log (3)."""
+    D = np.ascontiguousarray(D, np.int32)
+    Y = np.empty(D.shape, np.float64)
+    lib().orc_surface_mode(D.size, _p(D), int(mode), float(alpha), float(d_sat), _p(Y))
+    return Y
+
+
+def intensity_gain(mode=SURFACE_EXP, d_sat=6.0):
+    """Scale from a surface to the flow block's intensity (reading S2): Eq. 1
+    on the 8-bit scale, 255 d_exp (reading F0); each ablation surface scaled
+    so that its value at d_sat, the distance where Eq. 1 reaches 254 of 255
+    with alpha = d_sat / ln 255 (Eq. 3), maps to 255."""
+    if mode == SURFACE_EXP:
+        return 255.0
+    if mode in (SURFACE_LINEAR, SURFACE_BOUNDED):
+        return 255.0 / d_sat
+    return 255.0 / np.log(d_sat + 1.0)
+
+
+def _events(x, y, t, p):
+    x = np.ascontiguousarray(x, np.uint16)
+    y = np.ascontiguousarray(y, np.uint16)
+    t = np.ascontiguousarray(t, np.int64)
+    p = None if p is None else np.ascontiguousarray(p, np.int8)
+    return x, y, t, p
+
+
+def iwe(width, height, x, y, t, p, t_begin, t_end, U=None):
+    """§IV-C image of events moved back along the flow U (None: not moved),
+    readings W1-W3 of the C source."""
+    x, y, t, p = _events(x, y, t, p)
+    Ud = None if U is None else np.ascontiguousarray(U, np.float64)
+    img = np.empty((height, width), np.float64)
+    lib().orc_iwe(width, height, x.size, _p(x), _p(y), _p(t), None if p is None else _p(p),
+                  int(t_begin), int(t_end), None if Ud is None else _p(Ud), _p(img))
+    return img
+
+
+def fwl(width, height, x, y, t, p, t_begin, t_end, U):
+    """§IV-C Flow Warping Loss of flow U [2][H][W] on one window's events.
+    Returns (FWL, var(I_comp), var(I_uncomp))."""
+    x, y, t, p = _events(x, y, t, p)
+    Ud = np.ascontiguousarray(U, np.float64)
+    out = np.empty(3, np.float64)
+    lib().orc_fwl(width, height, x.size, _p(x), _p(y), _p(t), None if p is None else _p(p),
+                  int(t_begin), int(t_end), _p(Ud), _p(out))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def alpha_from_dsat(d_sat, eps=1.0 / 255.0):
@@ -231,27 +290,30 @@ def flow(I0, I1, levels=3, patch=8, stride=4, gn_iters=12, gn_damping=0.1, var_o
 
 
 def surface_from_events(width, height, x, y, t, t_begin, t_end,
-                        connectivity=8, n_d=1, n_f=9, alpha=1.08):
+                        connectivity=8, n_d=1, n_f=9, alpha=1.08, surface=SURFACE_EXP,
+                        d_sat=6.0):
     """§III-A to §III-C for one window: edge image, Alg. 1, Alg. 2, exact
-    EDT and Eq. 1.  Returns dict with E, Edf, D, S and the event counts."""
+    EDT and Eq. 1 (or an ablation surface of §IV-D).  Returns dict with E,
+    Edf, D, S (the surface) and the event counts."""
     E, st = edge_image(width, height, x, y, t, t_begin, t_end)
     Ed = denoise(E, connectivity, n_d)
     Edf = fill(Ed, connectivity, n_f)
     D = edt(Edf)
-    S = surface(D, alpha)
+    S = surface_mode(D, surface, alpha, d_sat)
     return dict(E=E, Edf=Edf, D=D, S=S, stats=st)
 
 
 def process_pair(width, height, win0, win1, connectivity=8, n_d=1, n_f=9,
-                 alpha=1.08, **flow_kw):
+                 alpha=1.08, surface=SURFACE_EXP, d_sat=6.0, **flow_kw):
     """Whole path for two consecutive windows ``(x, y, t, t_begin, t_end)``:
     surfaces of both, then the flow from the first to the second on the
-    8-bit intensity scale (reading F0)."""
+    intensity scale of readings F0 and S2."""
     s0 = surface_from_events(width, height, *win0, connectivity=connectivity,
-                             n_d=n_d, n_f=n_f, alpha=alpha)
+                             n_d=n_d, n_f=n_f, alpha=alpha, surface=surface, d_sat=d_sat)
     s1 = surface_from_events(width, height, *win1, connectivity=connectivity,
-                             n_d=n_d, n_f=n_f, alpha=alpha)
+                             n_d=n_d, n_f=n_f, alpha=alpha, surface=surface, d_sat=d_sat)
     kw = dict(FLOW_DEFAULTS)
     kw.update(flow_kw)
-    U = flow(255.0 * s0["S"], 255.0 * s1["S"], **kw)
+    g = intensity_gain(surface, d_sat)
+    U = flow(g * s0["S"], g * s1["S"], **kw)
     return s0, s1, U

@@ -195,6 +195,31 @@ void orc_surface(int n, const int32_t *D, double alpha, double *S)
     }
 }
 
+/* The distance surfaces compared in the ablations of §IV-D (plotted beside
+ * Eq. 1 in §III-C), as functions y(d) of the Euclidean distance d = sqrt(D):
+ *   mode 0  d_exp = 1 - exp(-d / alpha)             (Eq. 1, the proposal)
+ *   mode 1  DS_L   y = d                            (the plain distance)
+ *   mode 2  DS_LB  y = min(d, d_sat)                (bounded at d_sat)
+ *   mode 3  DS_Log y = ln(d + 1)
+ * Reading S1: an image without edge pixels (D = INT32_MAX) gives
+ * d_exp = 1 and, for the variants, y at the finite distance
+ * d = sqrt(INT32_MAX), so every surface is a constant image there. */
+void orc_surface_mode(int n, const int32_t *D, int mode, double alpha, double d_sat, double *Y)
+{
+    for (int i = 0; i < n; ++i) {
+        const double d = sqrt((double)D[i]);
+        if (mode == 0) {
+            orc_surface(1, &D[i], alpha, &Y[i]);
+        } else if (mode == 1) {
+            Y[i] = d;
+        } else if (mode == 2) {
+            Y[i] = (orc_mutation == 10) ? fmax(d, d_sat) : fmin(d, d_sat);
+        } else {
+            Y[i] = log(d + 1.0);
+        }
+    }
+}
+
 /* Eq. 2: alpha = -d_sat / ln(eps).  Eq. 3 is its value at eps = 1/255. */
 double orc_alpha_from_dsat(double d_sat, double eps) { return -d_sat / log(eps); }
 
@@ -569,4 +594,74 @@ int orc_flow(int W, int H, const double *I0, const double *I1, int levels,
     free(Uc);
     for (int l = 0; l < L; ++l) { free(A[l]); free(B[l]); free(Ax[l]); free(Ay[l]); }
     return L;
+}
+
+/* ---------------------------------------------------------------------------
+ * Flow Warping Loss (§IV-C): each event of the window is moved back along
+ * the flow to the window's start and accumulated with its polarity; the
+ * sharper the resulting image, the better the flow.  FWL = var(I_comp) /
+ * var(I_uncomp), the image variance taken over all W*H pixels.
+ * Readings:
+ *  W1  the flow U [2][H][W] is in pixels per window, so an event at time t
+ *      moves by -U(x, y) * (t - t_begin) / (t_end - t_begin), U read at the
+ *      event's own pixel; the reference time is t_begin;
+ *  W2  each moved event votes its polarity (+1 / -1; +1 for every event when
+ *      p is NULL) into the four pixels around its position with bilinear
+ *      weights; votes falling outside the image are dropped; I_uncomp is the
+ *      same image without moving the events (one vote at the event's pixel);
+ *  W3  only events with t_begin <= t < t_end and x < W, y < H take part;
+ *  W4  var(I) = mean(I^2) - mean(I)^2; FWL = 1 when var(I_uncomp) = 0.
+ * ------------------------------------------------------------------------- */
+void orc_iwe(int W, int H, int64_t n, const uint16_t *x, const uint16_t *y, const int64_t *t,
+             const int8_t *p, int64_t t_begin, int64_t t_end, const double *U, double *img)
+{
+    const size_t P = (size_t)W * H;
+    memset(img, 0, sizeof(double) * P);
+    const double span = (double)(t_end - t_begin);
+    for (int64_t i = 0; i < n; ++i) {
+        if (t[i] < t_begin || t[i] >= t_end || x[i] >= W || y[i] >= H) continue;
+        const double s = p ? (double)p[i] : 1.0;
+        double xw = x[i], yw = y[i];
+        if (U) {
+            const double tau = span > 0 ? (double)(t[i] - t_begin) / span : 0.0;
+            const size_t o = (size_t)y[i] * W + x[i];
+            const double sg = (orc_mutation == 11) ? 1.0 : -1.0;
+            xw += sg * U[o] * tau;
+            yw += sg * U[P + o] * tau;
+        }
+        const double fx0 = floor(xw), fy0 = floor(yw);
+        const double ax = xw - fx0, ay = yw - fy0;
+        const long X0 = (long)fx0, Y0 = (long)fy0;
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const long X = X0 + dx, Y = Y0 + dy;
+                if (X < 0 || Y < 0 || X >= W || Y >= H) continue;
+                const double w = (dx ? ax : 1.0 - ax) * (dy ? ay : 1.0 - ay);
+                img[(size_t)Y * W + X] += s * w;
+            }
+    }
+}
+
+static double orc_variance(size_t n, const double *a)
+{
+    double m = 0.0, q = 0.0;
+    for (size_t i = 0; i < n; ++i) { m += a[i]; q += a[i] * a[i]; }
+    m /= (double)n;
+    return q / (double)n - m * m;
+}
+
+/* out[0] = FWL, out[1] = var(I_comp), out[2] = var(I_uncomp). */
+void orc_fwl(int W, int H, int64_t n, const uint16_t *x, const uint16_t *y, const int64_t *t,
+             const int8_t *p, int64_t t_begin, int64_t t_end, const double *U, double *out)
+{
+    const size_t P = (size_t)W * H;
+    double *ic = (double *)malloc(sizeof(double) * P);
+    double *iu = (double *)malloc(sizeof(double) * P);
+    orc_iwe(W, H, n, x, y, t, p, t_begin, t_end, U, ic);
+    orc_iwe(W, H, n, x, y, t, p, t_begin, t_end, NULL, iu);
+    out[1] = orc_variance(P, ic);
+    out[2] = orc_variance(P, iu);
+    out[0] = out[2] > 0.0 ? out[1] / out[2] : 1.0;
+    free(ic);
+    free(iu);
 }

@@ -97,7 +97,7 @@ def _draw_window(rng, scene: _Scene, W: int, H: int, k: int, n_events: int,
     length = np.hypot(*(scene.p1 - scene.p0).T)
     cdf = np.cumsum(length / length.sum())
     cdf[-1] = 1.0
-    xs, ys, ts = [], [], []
+    xs, ys, ts, ss = [], [], [], []
     need = n_edge
     while need > 0:
         m = int(need * 1.3) + 64
@@ -113,16 +113,24 @@ def _draw_window(rng, scene: _Scene, W: int, H: int, k: int, n_events: int,
         xs.append(ix.astype(np.uint16))
         ys.append(iy.astype(np.uint16))
         ts.append(t)
+        ss.append(seg[ok][:need])
         need -= len(t)
     xs.append(rng.integers(0, W, size=n_noise).astype(np.uint16))
     ys.append(rng.integers(0, H, size=n_noise).astype(np.uint16))
     ts.append(rng.integers(t0, t0 + dt, size=n_noise, dtype=np.int64))
+    ss.append(np.full(n_noise, -1))
     x = np.concatenate(xs)
     y = np.concatenate(ys)
     t = np.concatenate(ts)
+    seg = np.concatenate(ss)[:n_events]
     order = np.argsort((t - t0).astype(np.uint32), kind="stable")
-    p = np.where(rng.random(n_events) < 0.5, 1, -1).astype(np.int8)
-    return x[order], y[order], t[order], p
+    # polarity: every edge has a contrast sign (alternating over the scene's
+    # segments) that 90 % of its events carry; noise events are +1 or -1
+    # with equal odds
+    u = rng.random(n_events)[np.argsort(order, kind="stable")]
+    sign = np.where(seg % 2 == 0, 1, -1)
+    p = np.where(seg < 0, np.where(u < 0.5, 1, -1), np.where(u < 0.9, sign, -sign))
+    return x[order], y[order], t[order], p[order].astype(np.int8)
 
 
 def _assemble(rng, scene, W, H, counts, noise_frac, dt, t_start=0):

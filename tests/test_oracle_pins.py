@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_2112_10591_gb300 import synth
 
 pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
 
@@ -146,6 +147,122 @@ def test_surface_closed_forms():
     assert np.all(np.diff(S) >= 0)                      # monotone in distance
     assert abs(S[4] - (1 - math.exp(-2.0 / 1.08))) < 1e-15
     assert abs(S[1] - (1 - math.exp(-1.0 / 1.08))) < 1e-15
+
+
+# ---------------------------------------------------------------- §IV-D ablation surfaces
+def test_ablation_surfaces_closed_forms():
+    D = np.array([0, 1, 4, 36, 49, 50, oracle.INF_D], np.int32)
+    lin = oracle.surface_mode(D, oracle.SURFACE_LINEAR)
+    lb = oracle.surface_mode(D, oracle.SURFACE_BOUNDED, d_sat=6.0)
+    lg = oracle.surface_mode(D, oracle.SURFACE_LOG)
+    assert lin[:6].tolist() == [0.0, 1.0, 2.0, 6.0, 7.0, 7.0710678118654755]
+    assert lb[:6].tolist() == [0.0, 1.0, 2.0, 6.0, 6.0, 6.0]          # the 6 px bound
+    assert abs(lg[1] - 0.6931471805599453) < 1e-15                    # ln 2
+    assert abs(lg[3] - 1.9459101490553132) < 1e-15                    # ln 7
+    assert abs(lg[4] - 2.0794415416798357) < 1e-15                    # ln 8
+    assert lg[0] == 0.0
+    # no edge pixel: a constant (finite) image for every surface
+    assert lin[6] == math.sqrt(2147483647.0) and lb[6] == 6.0 and np.isfinite(lg[6])
+    # mode 0 is Eq. 1 itself
+    Dd = np.arange(0, 400, dtype=np.int32)
+    assert np.array_equal(oracle.surface_mode(Dd, oracle.SURFACE_EXP, 1.08), oracle.surface(Dd))
+    # shapes of the plotted variants: DS_LB = min(DS_L, 6) <= DS_L, DS_Log <= DS_L
+    L = oracle.surface_mode(Dd, oracle.SURFACE_LINEAR)
+    B = oracle.surface_mode(Dd, oracle.SURFACE_BOUNDED)
+    G = oracle.surface_mode(Dd, oracle.SURFACE_LOG)
+    assert np.all(B <= L) and np.all(G <= L) and np.all(np.diff(G) > 0)
+    assert np.array_equal(B, np.minimum(L, 6.0))
+
+
+def test_ablation_intensity_scale():
+    # reading S2: every surface puts 255 at d_sat = 6 px, except Eq. 1 whose
+    # value there is 1 - 1/255 with alpha = 6 / ln 255 (Eq. 3), i.e. 254
+    a = oracle.alpha_from_dsat(6.0)
+    D = np.array([36], np.int32)
+    for mode in (oracle.SURFACE_LINEAR, oracle.SURFACE_BOUNDED, oracle.SURFACE_LOG):
+        v = oracle.intensity_gain(mode, 6.0) * oracle.surface_mode(D, mode, a, 6.0)[0]
+        assert abs(v - 255.0) < 1e-12, mode
+    v = oracle.intensity_gain(oracle.SURFACE_EXP) * oracle.surface_mode(D, 0, a)[0]
+    assert abs(v - 254.0) < 1e-9
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_ablation_surface_flow_recovers_shift(mode):
+    # the flow block on each ablation surface recovers an integer shift of an
+    # edge image on the edge pixels (the same scene as the Eq. 1 pin below)
+    rng = np.random.default_rng(11)
+    H, W = 120, 160
+    E = np.zeros((H, W), np.uint8)
+    for _ in range(300):
+        x, y = rng.integers(0, W - 2), rng.integers(0, H - 2)
+        E[y:y + 2, x:x + 2] = 1
+    E2 = np.zeros_like(E)
+    E2[0:H - 1, 3:W] = E[1:H, 0:W - 3]
+    g = oracle.intensity_gain(mode)
+    U = oracle.flow(g * oracle.surface_mode(oracle.edt(E), mode),
+                    g * oracle.surface_mode(oracle.edt(E2), mode))
+    m = E2.astype(bool)
+    m[:16] = m[-16:] = False
+    m[:, :16] = m[:, -16:] = False
+    e = np.hypot(U[0] - 3.0, U[1] + 1.0)[m]
+    assert e.mean() <= 0.1, e.mean()
+
+
+# ---------------------------------------------------------------- §IV-C FWL
+def _point_track():
+    # one point moving 4 px per window along x, seen at tau = 0, 1/4, 1/2, 3/4
+    # of a 100 us window: events at x = 2, 3, 4, 5 on row 5 of a 10 x 10 image
+    x = np.array([2, 3, 4, 5], np.uint16)
+    y = np.full(4, 5, np.uint16)
+    t = np.array([1000, 1025, 1050, 1075], np.int64)
+    return x, y, t
+
+
+def test_fwl_zero_flow_is_one():
+    x, y, t = _point_track()
+    U = np.zeros((2, 10, 10))
+    f, vc, vu = oracle.fwl(10, 10, x, y, t, None, 1000, 1100, U)
+    assert f == 1.0 and vc == vu
+
+
+def test_fwl_point_track_closed_form():
+    x, y, t = _point_track()
+    U = np.zeros((2, 10, 10))
+    U[0] = 4.0
+    img = oracle.iwe(10, 10, x, y, t, None, 1000, 1100, U)
+    assert img[5, 2] == 4.0 and img.sum() == 4.0        # all four land on x = 2
+    f, vc, vu = oracle.fwl(10, 10, x, y, t, None, 1000, 1100, U)
+    # 100 pixels: var_u = 4/100 - (4/100)^2, var_c = 16/100 - (4/100)^2
+    assert abs(vu - 0.0384) < 1e-15 and abs(vc - 0.1584) < 1e-15
+    assert abs(f - 4.125) < 1e-12
+
+
+def test_fwl_bilinear_split_polarity_and_bounds():
+    # an event half way through the window with flow (1, 0) lands between two
+    # pixels; a negative event votes -1; events outside the window or image,
+    # and votes moved outside the image, do not count
+    x = np.array([3, 6, 7, 0, 9], np.uint16)
+    y = np.array([2, 2, 2, 0, 12], np.uint16)
+    t = np.array([50, 0, 100, 50, 10], np.int64)
+    p = np.array([1, -1, 1, 1, 1], np.int8)
+    U = np.zeros((2, 10, 10))
+    U[0] = 1.0
+    img = oracle.iwe(10, 10, x, y, t, p, 0, 100, U)
+    want = np.zeros((10, 10))
+    want[2, 2] = want[2, 3] = 0.5      # x = 3 - 0.5
+    want[2, 6] = -1.0                  # tau = 0: not moved, polarity -1
+    want[0, 0] = 0.5                   # x = 0 - 0.5: the vote at x = -1 is dropped
+    assert np.array_equal(img, want)   # t = 100 is outside [0, 100); y = 12 outside
+
+
+def test_fwl_prefers_the_true_flow():
+    ev = synth.translating_segments(n_windows=1, seed=5, velocity=(3.0, -1.5), noise_frac=0.0)
+    x, y, t, p, tb, te = ev.window(0)
+    U = np.zeros((2, ev.height, ev.width))
+    U[0], U[1] = 3.0, -1.5
+    good = oracle.fwl(ev.width, ev.height, x, y, t, p, tb, te, U)[0]
+    bad = oracle.fwl(ev.width, ev.height, x, y, t, p, tb, te, -U)[0]
+    assert good > 1.0 > bad
 
 
 # ---------------------------------------------------------------- pyramid
@@ -379,6 +496,8 @@ def _pins_fail():
         lambda: me.test_denoise_fill_hand_cases(os.path.join(os.path.dirname(__file__), "golden")),
         me.test_edt_single_site_closed_form_and_empty,
         me.test_surface_closed_forms,
+        me.test_ablation_surfaces_closed_forms,
+        me.test_fwl_point_track_closed_form,
         me.test_downsample_and_gradients_closed_forms,
         lambda: me.test_flow_recovers_closed_form_translation((1.7, 0.9)),
         me.test_patch_search_recovers_translation,
@@ -396,7 +515,7 @@ def _pins_fail():
     return False
 
 
-@pytest.mark.parametrize("k", range(1, 10))
+@pytest.mark.parametrize("k", range(1, 12))
 def test_planted_mistakes_are_caught(k):
     try:
         oracle.set_mutation(k)
