@@ -742,6 +742,25 @@ def main():
         epe = {"mean_px": float(e.mean()), "p99_px": float(np.percentile(e, 99)),
                "frames": len(flows32)}
 
+    # flow quality without ground truth: the Flow Warping Loss (§IV-C) of
+    # every flow frame of the stream, on the events of its window
+    scr = torch.empty(eb.ebof_fwl_scratch_bytes(W, H), dtype=torch.uint8, device=dev)
+    fwl_out = torch.zeros((nwin, 3), dtype=torch.float64, device=dev)
+    for k in range(1, nwin):
+        a, b = off[k], off[k + 1]
+        eb.check(lib.ebof_fwl(xs.data_ptr() + 2 * a, ys.data_ptr() + 2 * a,
+                              ts.data_ptr() + 8 * a, ps.data_ptr() + a, b - a, tb[k],
+                              tb[k] + stream.dt, flows[k].data_ptr(), W, H, scr.data_ptr(),
+                              fwl_out[k].data_ptr(), handle), "ebof_fwl")
+    torch.cuda.synchronize(dev)
+    fw = fwl_out[1:, 0].cpu().numpy()
+    quality = {"fwl_mean": float(fw.mean()), "fwl_min": float(fw.min()),
+               "fwl_max": float(fw.max()), "frames_fwl_above_1": float((fw > 1.0).mean()),
+               "frames": int(len(fw)),
+               "note": "FWL = var(events moved back along the flow) / var(events unmoved), "
+                       "with polarity; > 1 beats the zero flow"}
+    del scr
+
     # FP16 storage of surfaces, pyramid levels and gradients (same stream)
     fp16 = None
     p16 = eb.ebof_default_params(W, H)
@@ -839,6 +858,7 @@ def main():
             "wall_s": wall,
             "batched": batched,
             "epe_vs_oracle": epe,
+            "flow_quality": quality,
             "fp16_storage": fp16,
             "multistream": multistream,
             "serving": serving,

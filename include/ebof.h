@@ -37,6 +37,7 @@
 #ifndef EBOF_H
 #define EBOF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -81,8 +82,22 @@ typedef struct {
                                levels and gradients stored in FP16 (half the bytes) as the
                                complement 255 (1 - d_exp), to which the flow is invariant;
                                patch sums, densification and the variational refinement
-                               stay FP32 */
+                               stay FP32 (the ablation surfaces are stored as they are) */
+    int32_t surface;        /* ebof_surface: Eq. 1, or an ablation surface of §IV-D */
+    float d_sat;            /* px: the bound of DS_LB, and the distance whose value
+                               maps to intensity 255 for every ablation surface */
 } ebof_params;
+
+/* Distance surface built from the EDT (§III-C) and handed to the flow block.
+ * The ablation surfaces of §IV-D replace Eq. 1 by y(d) of the distance d and
+ * are scaled to the flow's intensity by gain = 255 / y(d_sat); where a
+ * window has no edge pixel they take their value at d = sqrt(INT32_MAX). */
+typedef enum {
+    EBOF_SURFACE_EXP = 0,      /* Eq. 1: d_exp = 1 - exp(-d / alpha), intensity 255 d_exp */
+    EBOF_SURFACE_LINEAR = 1,   /* DS_L: y = d */
+    EBOF_SURFACE_BOUNDED = 2,  /* DS_LB: y = min(d, d_sat) */
+    EBOF_SURFACE_LOG = 3       /* DS_Log: y = ln(d + 1) */
+} ebof_surface;
 
 enum { EBOF_STORAGE_FP32 = 0, EBOF_STORAGE_FP16 = 1 };
 
@@ -100,7 +115,8 @@ typedef struct {
 typedef struct ebof_stream ebof_stream;
 
 /* Defaults for a width x height sensor: connectivity 8, n_d 1, filling off,
- * alpha 1.08 (§IV-A), 3 levels of 8x8 patches below 640 px width and 5 levels
+ * alpha 1.08 (§IV-A), the Eq. 1 surface with d_sat 6 px, 3 levels of 8x8
+ * patches below 640 px width and 5 levels
  * of 12x12 patches from 640 px, stride 4, 12 Gauss-Newton iterations with
  * damping 0.1, 5 x 5
  * variational iterations (delta 5, gamma 10, alpha 20, omega 1.6),
@@ -145,7 +161,8 @@ typedef struct {
  * Optional outputs (NULL to skip): d_edge [H][W] the denoised and filled
  * edge image (the paper's mask for restricting the flow, §III-D), d_edt
  * [H][W] squared distances (INT32_MAX when the window has no edge pixel),
- * d_surface [H][W] d_exp of Eq. 1.  Returns EBOF_NO_PREVIOUS (flow zero)
+ * d_surface [H][W] the surface (d_exp of Eq. 1, or y of the ablation
+ * surface p->surface).  Returns EBOF_NO_PREVIOUS (flow zero)
  * for the first window after create/reset, else EBOF_OK.
  * With max_batch 1, no optional output and stage timing off, steady-state
  * calls replay a CUDA graph of the whole window (one per ping-pong slot,
@@ -184,9 +201,11 @@ ebof_status ebof_process_window_list(ebof_stream *s, int32_t n_windows,
                                      const ebof_window_desc *windows, float *const *d_flows,
                                      void *cuda_stream);
 
-/* Flow block only (§III-D) on a caller-given surface d_surface [H][W] with
- * values d_exp in [0, 1] (the flow runs on 255 * d_surface); it becomes the
- * stream's previous window.  Same return values as ebof_process_window. */
+/* Flow block only (§III-D) on a caller-given surface d_surface [H][W] of the
+ * stream's surface kind: d_exp in [0, 1] for Eq. 1 (the flow runs on
+ * 255 * d_surface), y for an ablation surface (the flow runs on gain * y).
+ * It becomes the stream's previous window.  Same return values as
+ * ebof_process_window. */
 ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *d_flow,
                                  void *cuda_stream);
 
@@ -232,6 +251,28 @@ ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32
  * results. */
 ebof_status ebof_edt_static(const uint8_t *d_edge, int32_t width, int32_t height,
                             int32_t *d_edt, float *d_surface, float alpha, void *cuda_stream);
+
+/* ---- Flow Warping Loss (§IV-C) -------------------------------------------
+ * Quality of a flow without ground truth.  The window's events are moved
+ * back along the flow to t_begin and accumulated with their polarity into
+ * I_comp (bilinear votes; votes outside the image are dropped); I_uncomp
+ * accumulates the same events unmoved (one vote at their pixel).  FWL =
+ * var(I_comp) / var(I_uncomp), the variances over all width*height pixels;
+ * FWL = 1 when var(I_uncomp) = 0.  Above 1 the flow beats the zero flow.
+ * d_flow [2][H][W]: pixels per window as ebof_process_window returns it,
+ * read at each event's pixel; an event at time t moves by
+ * -flow * (t - t_begin) / (t_end - t_begin).  Only events with
+ * t_begin <= t < t_end inside the image count.  d_p: polarity per event
+ * (+1 / -1), or NULL to count every event as +1.  d_scratch: caller-owned
+ * device memory of ebof_fwl_scratch_bytes(width, height) bytes.  d_out:
+ * device double[3] = {FWL, var(I_comp), var(I_uncomp)}, written on
+ * cuda_stream (read it after synchronising).  Allocates nothing; I_comp is
+ * summed with float atomics, so its last bits depend on the vote order. */
+size_t ebof_fwl_scratch_bytes(int32_t width, int32_t height);
+ebof_status ebof_fwl(const uint16_t *d_x, const uint16_t *d_y, const int64_t *d_t,
+                     const int8_t *d_p, int64_t n_events, int64_t t_begin, int64_t t_end,
+                     const float *d_flow, int32_t width, int32_t height, void *d_scratch,
+                     double *d_out, void *cuda_stream);
 
 /* ---- multi-stream groups -------------------------------------------------
  * A group holds n camera streams of one resolution and steps them in

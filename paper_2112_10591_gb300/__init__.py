@@ -19,5 +19,6 @@ from .binding import (  # noqa: F401
     Server, ebof_completion, ebof_now_ns, ebof_server_close_stream, ebof_server_config,
     ebof_server_create, ebof_server_default_config, ebof_server_destroy, ebof_server_drain,
     ebof_server_get_info, ebof_server_info, ebof_server_open_stream, ebof_server_poll,
-    ebof_server_submit,
+    ebof_server_submit, EBOF_SURFACE_EXP, EBOF_SURFACE_LINEAR, EBOF_SURFACE_BOUNDED,
+    EBOF_SURFACE_LOG, ebof_fwl, ebof_fwl_scratch_bytes,
 )

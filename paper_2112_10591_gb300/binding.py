@@ -45,11 +45,14 @@ class ebof_params(ctypes.Structure):
         ("var_alpha", ctypes.c_float), ("sor_omega", ctypes.c_float),
         ("max_batch", ctypes.c_int32),
         ("storage", ctypes.c_int32),
+        ("surface", ctypes.c_int32),
+        ("d_sat", ctypes.c_float),
     ]
 
 
 EBOF_STORAGE_FP32 = 0
 EBOF_STORAGE_FP16 = 1
+EBOF_SURFACE_EXP, EBOF_SURFACE_LINEAR, EBOF_SURFACE_BOUNDED, EBOF_SURFACE_LOG = 0, 1, 2, 3
 
 
 class ebof_window_stats(ctypes.Structure):
@@ -130,6 +133,9 @@ def _declare(L):
     L.ebof_process_windows.argtypes = [vp, i32, vp, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
     L.ebof_process_surface.argtypes = [vp, vp, vp, vp]
     L.ebof_process_window_list.argtypes = [vp, i32, P(ebof_window_desc), P(vp), vp]
+    L.ebof_fwl_scratch_bytes.argtypes = [i32, i32]
+    L.ebof_fwl_scratch_bytes.restype = ctypes.c_size_t
+    L.ebof_fwl.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, i32, i32, vp, vp, vp]
     L.ebof_now_ns.argtypes = []
     L.ebof_now_ns.restype = i64
     L.ebof_server_default_config.argtypes = [P(ebof_server_config)]
@@ -168,7 +174,7 @@ def _declare(L):
                  "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static",
                  "ebof_stream_get_profile_level", "ebof_group_create", "ebof_group_destroy",
                  "ebof_group_reset", "ebof_group_process", "ebof_group_sync",
-                 "ebof_process_window_list", "ebof_server_create", "ebof_server_destroy",
+                 "ebof_process_window_list", "ebof_server_create", "ebof_fwl", "ebof_server_destroy",
                  "ebof_server_open_stream", "ebof_server_close_stream", "ebof_server_submit",
                  "ebof_server_poll", "ebof_server_drain", "ebof_server_get_info"):
         getattr(L, name).restype = ctypes.c_int
@@ -482,6 +488,39 @@ def ebof_stage_name(stage: int) -> str:
 
 def ebof_kernel_launches() -> int:
     return int(load().ebof_kernel_launches())
+
+
+# ---------------------------------------------------------------- FWL
+def ebof_fwl_scratch_bytes(width: int, height: int) -> int:
+    return int(load().ebof_fwl_scratch_bytes(int(width), int(height)))
+
+
+def ebof_fwl(x, y, t, p, t_begin: int, t_end: int, flow, width: int, height: int,
+             scratch=None, out=None, cuda_stream=None):
+    """Flow Warping Loss of one window (§IV-C).  x, y, t, p: CUDA event
+    tensors (p int8 polarity or None); flow: CUDA float32 [2][H][W].
+    scratch: CUDA uint8 tensor of ebof_fwl_scratch_bytes bytes (allocated
+    here if None); out: CUDA float64 tensor of 3 (allocated if None).
+    Returns (status, out) with out = [FWL, var(I_comp), var(I_uncomp)]
+    written on the stream."""
+    import torch
+    n = x.numel()
+    dev = flow.device.index
+    if scratch is None:
+        scratch = torch.empty(ebof_fwl_scratch_bytes(width, height), dtype=torch.uint8,
+                              device=flow.device)
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=flow.device)
+    st = load().ebof_fwl(_ptr(x, torch.uint16, n, "x", dev), _ptr(y, torch.uint16, n, "y", dev),
+                         _ptr(t, torch.int64, n, "t", dev),
+                         _ptr(p, torch.int8, n, "p", dev) if p is not None else None,
+                         n, int(t_begin), int(t_end),
+                         _ptr(flow, torch.float32, 2 * width * height, "flow", dev),
+                         int(width), int(height),
+                         _ptr(scratch, torch.uint8, ebof_fwl_scratch_bytes(width, height),
+                              "scratch", dev),
+                         _ptr(out, torch.float64, 3, "out", dev), _stream_handle(cuda_stream))
+    return st, out
 
 
 # ---------------------------------------------------------------- serving loop

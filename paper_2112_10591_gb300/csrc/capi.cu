@@ -185,6 +185,8 @@ ebof_status check_params(const ebof_params *p)
     if (p->max_batch < 1 || p->max_batch > 4096) return EBOF_ERR_INVALID_ARG;
     if (p->storage != EBOF_STORAGE_FP32 && p->storage != EBOF_STORAGE_FP16)
         return EBOF_ERR_INVALID_ARG;
+    if (p->surface < EBOF_SURFACE_EXP || p->surface > EBOF_SURFACE_LOG) return EBOF_ERR_INVALID_ARG;
+    if (!(std::isfinite(p->d_sat) && p->d_sat > 0.0f)) return EBOF_ERR_INVALID_ARG;
     if (p->patch < 4 || p->patch > kMaxPatch) return EBOF_ERR_UNSUPPORTED;
     return EBOF_OK;
 }
@@ -207,6 +209,21 @@ void free_all(ebof_stream *s)
         if (ge) cudaGraphExecDestroy(ge);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->done) cudaEventDestroy(s->done);
+}
+
+SurfaceMap surface_map(const ebof_params &p)
+{
+    SurfaceMap m;
+    m.mode = p.surface;
+    m.alpha = p.alpha;
+    m.d_sat = p.d_sat;
+    if (p.surface == EBOF_SURFACE_EXP)
+        m.gain = 255.0f;
+    else if (p.surface == EBOF_SURFACE_LOG)
+        m.gain = (float)(255.0 / std::log1p((double)p.d_sat));
+    else
+        m.gain = (float)(255.0 / (double)p.d_sat);
+    return m;
 }
 
 FlowParams flow_params(const ebof_params &p)
@@ -248,7 +265,8 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
     char *I0cur = s->pyr + (size_t)cur_first * s->pyr_fs * es;
 
     if (surface_in) {
-        launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, half, st);
+        launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, half,
+                                    surface_map(p), st);
     } else {
         cudaMemsetAsync(s->E, 0, s->e_fs * n, st);
         if (via_args)
@@ -260,7 +278,7 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
         launch_denoise_fill(s->E, s->Ed, s->Edf, W, H, s->pitch0, s->e_fs, n, p.connectivity,
                             p.n_d, p.n_f, d_edge, s->dstats, st);
         launch_edt_columns(s->Edf, s->pitch0, s->e_fs, W, H, s->g, s->pitch0, s->g_fs, n, st);
-        launch_edt_rows_surface(s->g, s->pitch0, s->g_fs, W, H, p.alpha, d_edt, d_surface,
+        launch_edt_rows_surface(s->g, s->pitch0, s->g_fs, W, H, surface_map(p), d_edt, d_surface,
                                 I0cur, s->pitch0, s->pyr_fs, n, half, st);
     }
 
@@ -503,7 +521,7 @@ void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
     launch_denoise_fill(g->E, g->Ed, g->Edf, W, H, g->pitch0, g->e_fs, n, p.connectivity, p.n_d,
                         p.n_f, nullptr, g->dstats, st);
     launch_edt_columns(g->Edf, g->pitch0, g->e_fs, W, H, g->g, g->pitch0, g->g_fs, n, st);
-    launch_edt_rows_surface(g->g, g->pitch0, g->g_fs, W, H, p.alpha, nullptr, nullptr, cur,
+    launch_edt_rows_surface(g->g, g->pitch0, g->g_fs, W, H, surface_map(p), nullptr, nullptr, cur,
                             g->pitch0, g->pyr_fs, n, half, st);
     const int nlev = std::max(geo.levels, 1);
     for (int l = 0; l < nlev; ++l) {
@@ -580,6 +598,8 @@ void ebof_default_params(ebof_params *p, int32_t width, int32_t height)
     p->sor_omega = 1.6f;
     p->max_batch = 1;
     p->storage = EBOF_STORAGE_FP32;
+    p->surface = EBOF_SURFACE_EXP;
+    p->d_sat = 6.0f;
 }
 
 float ebof_alpha_from_dsat(float d_sat) { return d_sat / std::log(255.0f); }

@@ -50,6 +50,18 @@ struct DevStats {
 
 // Kernel parameter bundles ---------------------------------------------------
 
+// Distance to surface value y(d), d = sqrt(D), and surface to level-0
+// intensity: Eq. 1 (mode EBOF_SURFACE_EXP, intensity 255 y) or an ablation
+// surface of §IV-D (intensity gain * y, gain = 255 / y(d_sat)).
+struct SurfaceMap {
+    int mode;
+    float alpha;  // Eq. 1
+    float d_sat;  // bound of DS_LB
+    float gain;   // intensity scale of the ablation surfaces
+};
+
+inline SurfaceMap exp_surface(float alpha) { return SurfaceMap{0, alpha, 6.0f, 255.0f}; }
+
 struct FlowParams {
     bool half;  // pyramid stored as FP16 (loads widened to FP32)
     int ps, stride, gn_iters;
@@ -81,7 +93,13 @@ void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stri
                         int H, int32_t *g, int g_pitch, size_t g_frame_stride, int frames,
                         cudaStream_t st);
 
-// A4: per-row lower envelope -> D, fused Eq. 1 surface and 255 * surface.
+// A4: per-row lower envelope -> D, fused surface (Eq. 1 or an ablation
+// surface) and level-0 intensity.
+void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
+                             const SurfaceMap &sm, int32_t *D_dense, float *S_dense, void *I0,
+                             int i_pitch, size_t i_frame_stride, int frames, bool half,
+                             cudaStream_t st);
+// The same with the Eq. 1 surface.
 void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
                              float alpha, int32_t *D_dense, float *S_dense, void *I0,
                              int i_pitch, size_t i_frame_stride, int frames, bool half,
@@ -91,9 +109,9 @@ void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_strid
 void init_front_attributes();
 void init_flow_attributes();
 
-// Surface given by the caller -> 255 * d_exp into the level-0 image.
+// Surface given by the caller -> level-0 intensity (255 d_exp, or gain * y).
 void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pitch, bool half,
-                                 cudaStream_t st);
+                                 const SurfaceMap &sm, cudaStream_t st);
 
 // A5: gradients of level l, and downsample l -> l+1 (then its gradients).
 void launch_gradients(const void *I, void *Ix, void *Iy, int w, int h, int pitch,

@@ -288,9 +288,24 @@ __device__ __forceinline__ void st_int(__half *p, float s, float c)
     *p = __float2half_rn(255.0f * c);
 }
 
+// The ablation surfaces are stored as gain * y itself (no complement); FP16
+// clamps at its largest finite value, so distances beyond 65504 / gain
+// (about 1540 px for DS_L) read as one plateau.
+__device__ __forceinline__ void st_lin(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_lin(__half *p, float v)
+{
+    *p = __float2half_rn(fminf(v, 65504.0f));
+}
+
+// y(d) of the ablation surfaces of §IV-D (mode 1 DS_L, 2 DS_LB, 3 DS_Log).
+__device__ __forceinline__ float ablation_surface(const SurfaceMap &sm, float d)
+{
+    return sm.mode == 1 ? d : (sm.mode == 2 ? fminf(d, sm.d_sat) : log1pf(d));
+}
+
 template <int WPR, typename T>
 __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs,
-                                        int W, int H, int rows_per_block, float alpha,
+                                        int W, int H, int rows_per_block, SurfaceMap sm,
                                         int32_t *__restrict__ D_dense,
                                         float *__restrict__ S_dense, T *__restrict__ I0,
                                         int ipitch, size_t ifs)
@@ -400,11 +415,17 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
     for (int x = tr; x < W; x += NB) {
         const int32_t D = any ? res[x] : kInfD;
         float S = 1.0f, C = 0.0f;  // d_exp of Eq. 1 and its complement 1 - d_exp
-        if (D != kInfD) {
-            C = expf(-sqrtf((float)D) / alpha);
-            S = 1.0f - C;
+        if (sm.mode == 0) {
+            if (D != kInfD) {
+                C = expf(-sqrtf((float)D) / sm.alpha);
+                S = 1.0f - C;
+            }
+            if (irow) st_int(&irow[x], S, C);
+        } else {
+            // no edge pixel (kInfD): y at the finite d = sqrt(INT32_MAX)
+            S = ablation_surface(sm, sqrtf((float)D));
+            if (irow) st_lin(&irow[x], sm.gain * S);
         }
-        if (irow) st_int(&irow[x], S, C);
         if (D_dense) D_dense[dbase + x] = D;
         if (S_dense) S_dense[dbase + x] = S;
     }
@@ -413,13 +434,16 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
 // Caller-given surface (dense, d_exp in [0, 1]) to the level-0 intensity.
 template <typename T>
 __global__ void surface_to_intensity_kernel(const float *__restrict__ S, int W, int H,
-                                            T *__restrict__ I0, int pitch)
+                                            T *__restrict__ I0, int pitch, SurfaceMap sm)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W) return;
     const float sv = S[(size_t)y * W + x];
-    st_int(&I0[(size_t)y * pitch + x], sv, 1.0f - sv);
+    if (sm.mode == 0)
+        st_int(&I0[(size_t)y * pitch + x], sv, 1.0f - sv);
+    else
+        st_lin(&I0[(size_t)y * pitch + x], sm.gain * sv);
 }
 
 inline unsigned grid1d(int64_t n, int block, int cap)
@@ -492,8 +516,8 @@ int edt_rows_per_block(int W)
 }
 
 template <typename T>
-void edt_rows_t(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H, float alpha,
-                int32_t *D_dense, float *S_dense, T *I0, int i_pitch, size_t i_frame_stride,
+void edt_rows_t(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
+                const SurfaceMap &sm, int32_t *D_dense, float *S_dense, T *I0, int i_pitch, size_t i_frame_stride,
                 int frames, cudaStream_t st)
 {
     const int rows = edt_rows_per_block(W);
@@ -502,12 +526,26 @@ void edt_rows_t(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int
     dim3 grd((H + rows - 1) / rows, frames);
     if (wpr == 2)
         edt_rows_surface_kernel<2, T><<<grd, 32 * 2 * rows, smem, st>>>(
-            g, g_pitch, g_frame_stride, W, H, rows, alpha, D_dense, S_dense, I0, i_pitch,
+            g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
     else
         edt_rows_surface_kernel<1, T><<<grd, 32 * rows, smem, st>>>(
-            g, g_pitch, g_frame_stride, W, H, rows, alpha, D_dense, S_dense, I0, i_pitch,
+            g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
+}
+
+void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
+                             const SurfaceMap &sm, int32_t *D_dense, float *S_dense, void *I0,
+                             int i_pitch, size_t i_frame_stride, int frames, bool half,
+                             cudaStream_t st)
+{
+    StageScope sc(kStEdtRows, 1, st);
+    if (half)
+        edt_rows_t(g, g_pitch, g_frame_stride, W, H, sm, D_dense, S_dense, (__half *)I0,
+                   i_pitch, i_frame_stride, frames, st);
+    else
+        edt_rows_t(g, g_pitch, g_frame_stride, W, H, sm, D_dense, S_dense, (float *)I0,
+                   i_pitch, i_frame_stride, frames, st);
 }
 
 void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
@@ -515,13 +553,8 @@ void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_strid
                              int i_pitch, size_t i_frame_stride, int frames, bool half,
                              cudaStream_t st)
 {
-    StageScope sc(kStEdtRows, 1, st);
-    if (half)
-        edt_rows_t(g, g_pitch, g_frame_stride, W, H, alpha, D_dense, S_dense, (__half *)I0,
-                   i_pitch, i_frame_stride, frames, st);
-    else
-        edt_rows_t(g, g_pitch, g_frame_stride, W, H, alpha, D_dense, S_dense, (float *)I0,
-                   i_pitch, i_frame_stride, frames, st);
+    launch_edt_rows_surface(g, g_pitch, g_frame_stride, W, H, exp_surface(alpha), D_dense,
+                            S_dense, I0, i_pitch, i_frame_stride, frames, half, st);
 }
 
 void init_front_attributes()
@@ -537,14 +570,15 @@ void init_front_attributes()
 }
 
 void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pitch, bool half,
-                                 cudaStream_t st)
+                                 const SurfaceMap &sm, cudaStream_t st)
 {
     StageScope sc(kStEdtRows, 1, st);
     dim3 grd((W + 255) / 256, H);
     if (half)
-        surface_to_intensity_kernel<__half><<<grd, 256, 0, st>>>(S, W, H, (__half *)I0, pitch);
+        surface_to_intensity_kernel<__half>
+            <<<grd, 256, 0, st>>>(S, W, H, (__half *)I0, pitch, sm);
     else
-        surface_to_intensity_kernel<float><<<grd, 256, 0, st>>>(S, W, H, (float *)I0, pitch);
+        surface_to_intensity_kernel<float><<<grd, 256, 0, st>>>(S, W, H, (float *)I0, pitch, sm);
 }
 
 }  // namespace ebof

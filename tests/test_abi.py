@@ -52,7 +52,9 @@ def test_create_rejects_bad_params_before_touching_a_device():
     bad = []
     for field, val in (("width", 0), ("height", 20000), ("connectivity", 6), ("n_d", -1),
                        ("alpha", 0.0), ("levels", 0), ("stride", 0), ("sor_omega", 2.0),
-                       ("max_batch", 0), ("struct_size", 4)):
+                       ("max_batch", 0), ("struct_size", 4), ("surface", 4),
+                       ("surface", -1), ("d_sat", 0.0), ("d_sat", float("nan")),
+                       ("storage", 2)):
         p = eb.ebof_default_params(64, 48)
         setattr(p, field, val)
         st, s = eb.ebof_stream_create(p, 0)
@@ -62,3 +64,8 @@ def test_create_rejects_bad_params_before_touching_a_device():
     p = eb.ebof_default_params(64, 48)
     p.patch = 20
     assert eb.ebof_stream_create(p, 0)[0] == eb.EBOF_ERR_UNSUPPORTED
+    p = eb.ebof_default_params(64, 48)
+    p.surface = 4
+    assert eb.ebof_stream_device_bytes(p) == -1
+    p.surface = eb.EBOF_SURFACE_LOG
+    assert eb.ebof_stream_device_bytes(p) > 0
