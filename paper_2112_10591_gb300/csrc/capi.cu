@@ -283,19 +283,8 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
     }
 
     // A5: pyramid and gradients of the current window(s)
-    const int nlev = std::max(geo.levels, 1);
-    for (int l = 0; l < nlev; ++l) {
-        tl_level = l;
-        const Level &lv = geo.lv[l];
-        char *I = I0cur + geo.pyr_off[l] * es;
-        if (l > 0) {
-            const Level &lp = geo.lv[l - 1];
-            launch_downsample(I0cur + geo.pyr_off[l - 1] * es, lp.w, lp.h, lp.pitch, I, lv.w,
-                              lv.h, lv.pitch, s->pyr_fs, n, half, st);
-        }
-        launch_gradients(I, I + lv.plane * es, I + 2 * lv.plane * es, lv.w, lv.h, lv.pitch,
-                         s->pyr_fs, n, half, st);
-    }
+    tl_level = 0;
+    launch_pyramid(I0cur, geo, s->pyr_fs, n, half, st);
 
     // A6-A9: flow for every window that has a previous one
     const int ff = had_prev ? 0 : 1;
@@ -523,19 +512,8 @@ void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
     launch_edt_columns(g->Edf, g->pitch0, g->e_fs, W, H, g->g, g->pitch0, g->g_fs, n, st);
     launch_edt_rows_surface(g->g, g->pitch0, g->g_fs, W, H, surface_map(p), nullptr, nullptr, cur,
                             g->pitch0, g->pyr_fs, n, half, st);
-    const int nlev = std::max(geo.levels, 1);
-    for (int l = 0; l < nlev; ++l) {
-        tl_level = l;
-        const Level &lv = geo.lv[l];
-        char *I = cur + geo.pyr_off[l] * es;
-        if (l > 0) {
-            const Level &lp = geo.lv[l - 1];
-            launch_downsample(cur + geo.pyr_off[l - 1] * es, lp.w, lp.h, lp.pitch, I, lv.w, lv.h,
-                              lv.pitch, g->pyr_fs, n, half, st);
-        }
-        launch_gradients(I, I + lv.plane * es, I + 2 * lv.plane * es, lv.w, lv.h, lv.pitch,
-                         g->pyr_fs, n, half, st);
-    }
+    tl_level = 0;
+    launch_pyramid(cur, geo, g->pyr_fs, n, half, st);
     const size_t flow_frame = (size_t)2 * W * H;
     if (with_flow && geo.levels > 0) {
         const FlowParams fp = flow_params(p);

@@ -40,6 +40,15 @@ struct Geometry {
 
 Geometry make_geometry(int width, int height, int levels, int ps, int stride);
 
+// The pyramid of one slot as the fused pyramid kernels see it.
+struct PyrDesc {
+    int levels;
+    int w[kMaxLevels], h[kMaxLevels], pitch[kMaxLevels];
+    size_t off[kMaxLevels];    // element offset of level l's I in a slot
+    size_t plane[kMaxLevels];  // Ix and Iy follow I at one and two planes
+    int blk0[kMaxLevels + 1];  // first block of level l in the gradient launch
+};
+
 // Per-window event counters kept on the device (one per batch slot).
 struct DevStats {
     unsigned long long in_window;
@@ -113,11 +122,10 @@ void init_flow_attributes();
 void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pitch, bool half,
                                  const SurfaceMap &sm, cudaStream_t st);
 
-// A5: gradients of level l, and downsample l -> l+1 (then its gradients).
-void launch_gradients(const void *I, void *Ix, void *Iy, int w, int h, int pitch,
-                      size_t frame_stride, int frames, bool half, cudaStream_t st);
-void launch_downsample(const void *I, int w, int h, int pitch, void *out, int wc, int hc,
-                       int pitch_c, size_t frame_stride, int frames, bool half, cudaStream_t st);
+// A5: every box-mean level and every level's gradients of `frames` slots
+// starting at `slots` (level 0 must be in place), in two launches.
+void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int frames, bool half,
+                    cudaStream_t st);
 
 // A6: patch inverse search at one level.
 void launch_patch_search(const void *I0, const void *I0x, const void *I0y, const void *I1,

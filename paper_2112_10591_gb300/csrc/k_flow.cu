@@ -21,22 +21,6 @@ namespace {
 
 // ---------------------------------------------------------------- A5
 template <typename T>
-__global__ void gradients_kernel(const T *__restrict__ I, T *__restrict__ Ix,
-                                 T *__restrict__ Iy, int w, int h, int pitch, size_t fs)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= w || y >= h) return;
-    const size_t fo = (size_t)blockIdx.z * fs;
-    const T *im = I + fo;
-    const int xp = min(x + 1, w - 1), xm = max(x - 1, 0);
-    const int yp = min(y + 1, h - 1), ym = max(y - 1, 0);
-    const size_t p = (size_t)y * pitch + x;
-    stp(&Ix[fo + p], 0.5f * (ldp(&im[(size_t)y * pitch + xp]) - ldp(&im[(size_t)y * pitch + xm])));
-    stp(&Iy[fo + p], 0.5f * (ldp(&im[(size_t)yp * pitch + x]) - ldp(&im[(size_t)ym * pitch + x])));
-}
-
-template <typename T>
 __global__ void downsample_kernel(const T *__restrict__ I, int pitch, T *__restrict__ out,
                                   int wc, int hc, int pitch_c, size_t fs)
 {
@@ -47,6 +31,93 @@ __global__ void downsample_kernel(const T *__restrict__ I, int pitch, T *__restr
     const size_t r0 = (size_t)(2 * y) * pitch + 2 * x, r1 = r0 + pitch;
     stp(&out[(size_t)blockIdx.z * fs + (size_t)y * pitch_c + x],
         0.25f * (ldp(&im[r0]) + ldp(&im[r0 + 1]) + ldp(&im[r1]) + ldp(&im[r1 + 1])));
+}
+
+// Value as stored in T (the next level is built from the stored values).
+__device__ __forceinline__ float as_stored(float v, const float *) { return v; }
+__device__ __forceinline__ float as_stored(float v, const __half *)
+{
+    return __half2float(__float2half_rn(v));
+}
+
+// Box-mean levels 1 .. min(levels, kPyrFused) - 1 of a slot in one launch:
+// a block owns a 32 x 32 tile of level 1 (a 64 x 64 region of level 0) and
+// halves it in shared memory down to 2 x 2 at level 5.  Same sums in the same
+// order as downsample_kernel, so the levels are identical.
+constexpr int kPyrTile = 32;
+constexpr int kPyrFused = 6;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+pyramid_means_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
+{
+    __shared__ float ta[kPyrTile][kPyrTile + 1];
+    __shared__ float tb[kPyrTile / 2][kPyrTile / 2 + 1];
+    T *slot = slots + (size_t)blockIdx.z * fs;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int x1b = blockIdx.x * kPyrTile, y1b = blockIdx.y * kPyrTile;
+    {
+        const T *I0 = slot + d.off[0];
+        T *I1 = slot + d.off[1];
+        const int p0 = d.pitch[0];
+#pragma unroll
+        for (int i = 0; i < kPyrTile / 8; ++i) {
+            const int ly = ty + 8 * i, x = x1b + tx, y = y1b + ly;
+            float v = 0.0f;
+            if (x < d.w[1] && y < d.h[1]) {
+                const size_t r0 = (size_t)(2 * y) * p0 + 2 * x, r1 = r0 + p0;
+                v = 0.25f * (ldp(&I0[r0]) + ldp(&I0[r0 + 1]) + ldp(&I0[r1]) + ldp(&I0[r1 + 1]));
+                stp(&I1[(size_t)y * d.pitch[1] + x], v);
+                v = as_stored(v, I1);
+            }
+            ta[ly][tx] = v;
+        }
+    }
+    __syncthreads();
+    const int t = ty * 32 + tx;
+    int side = kPyrTile / 2;
+    for (int l = 2; l < d.levels && l < kPyrFused; ++l, side >>= 1) {
+        // level l - 1 is in ta for even l, in tb for odd l
+        const bool from_a = (l & 1) == 0;
+        const int lx = t % side, ly = t / side;
+        const int x = (x1b >> (l - 1)) + lx, y = (y1b >> (l - 1)) + ly;
+        if (t < side * side) {
+            float v = 0.0f;
+            if (x < d.w[l] && y < d.h[l]) {
+                const int sx = 2 * lx, sy = 2 * ly;
+                v = from_a ? 0.25f * (ta[sy][sx] + ta[sy][sx + 1] + ta[sy + 1][sx] + ta[sy + 1][sx + 1])
+                           : 0.25f * (tb[sy][sx] + tb[sy][sx + 1] + tb[sy + 1][sx] + tb[sy + 1][sx + 1]);
+                T *Il = slot + d.off[l];
+                stp(&Il[(size_t)y * d.pitch[l] + x], v);
+                v = as_stored(v, Il);
+            }
+            if (from_a) tb[ly][lx] = v;
+            else ta[ly][lx] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Central differences of every level of a slot in one launch: the blocks of
+// level l are blk0[l] .. blk0[l + 1] - 1 (32 x 8 pixels each).
+template <typename T>
+__global__ void __launch_bounds__(256)
+pyramid_gradients_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
+{
+    int l = 0;
+    while (l + 1 < d.levels && (int)blockIdx.x >= d.blk0[l + 1]) ++l;
+    const int b = blockIdx.x - d.blk0[l];
+    const int w = d.w[l], h = d.h[l], pitch = d.pitch[l];
+    const int nbx = (w + 31) / 32;
+    const int x = (b % nbx) * 32 + threadIdx.x, y = (b / nbx) * 8 + threadIdx.y;
+    if (x >= w || y >= h) return;
+    T *im = slots + (size_t)blockIdx.z * fs + d.off[l];
+    T *Ix = im + d.plane[l], *Iy = im + 2 * d.plane[l];
+    const int xp = min(x + 1, w - 1), xm = max(x - 1, 0);
+    const int yp = min(y + 1, h - 1), ym = max(y - 1, 0);
+    const size_t p = (size_t)y * pitch + x;
+    stp(&Ix[p], 0.5f * (ldp(&im[(size_t)y * pitch + xp]) - ldp(&im[(size_t)y * pitch + xm])));
+    stp(&Iy[p], 0.5f * (ldp(&im[(size_t)yp * pitch + x]) - ldp(&im[(size_t)ym * pitch + x])));
 }
 
 // ---------------------------------------------------------------- A6
@@ -412,31 +483,52 @@ dim3 grid2d(int w, int h, int frames, dim3 blk)
 
 void init_flow_attributes() { init_var_attributes(); }
 
-void launch_gradients(const void *I, void *Ix, void *Iy, int w, int h, int pitch,
-                      size_t frame_stride, int frames, bool half, cudaStream_t st)
+void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int frames, bool half,
+                    cudaStream_t st)
 {
-    StageScope sc(kStPyramid, 1, st);
-    dim3 blk(32, 8);
+    PyrDesc d;
+    d.levels = std::max(geo.levels, 1);
+    int nb = 0;
+    for (int l = 0; l < d.levels; ++l) {
+        const Level &lv = geo.lv[l];
+        d.w[l] = lv.w;
+        d.h[l] = lv.h;
+        d.pitch[l] = lv.pitch;
+        d.off[l] = geo.pyr_off[l];
+        d.plane[l] = lv.plane;
+        d.blk0[l] = nb;
+        nb += ((lv.w + 31) / 32) * ((lv.h + 7) / 8);
+    }
+    d.blk0[d.levels] = nb;
+    const int extra = std::max(0, d.levels - kPyrFused);
+    StageScope sc(kStPyramid, 1 + (d.levels > 1 ? 1 : 0) + extra, st);
+    const dim3 blk(32, 8);
+    const size_t es = half ? 2 : 4;
+    if (d.levels > 1) {
+        const dim3 grd((d.w[1] + kPyrTile - 1) / kPyrTile, (d.h[1] + kPyrTile - 1) / kPyrTile,
+                       frames);
+        if (half)
+            pyramid_means_kernel<__half><<<grd, blk, 0, st>>>((__half *)slots, frame_stride, d);
+        else
+            pyramid_means_kernel<float><<<grd, blk, 0, st>>>((float *)slots, frame_stride, d);
+    }
+    for (int l = kPyrFused; l < d.levels; ++l) {  // levels beyond the fused tile
+        char *base = (char *)slots;
+        const dim3 grd = grid2d(d.w[l], d.h[l], frames, blk);
+        if (half)
+            downsample_kernel<__half><<<grd, blk, 0, st>>>(
+                (const __half *)(base + d.off[l - 1] * es), d.pitch[l - 1],
+                (__half *)(base + d.off[l] * es), d.w[l], d.h[l], d.pitch[l], frame_stride);
+        else
+            downsample_kernel<float><<<grd, blk, 0, st>>>(
+                (const float *)(base + d.off[l - 1] * es), d.pitch[l - 1],
+                (float *)(base + d.off[l] * es), d.w[l], d.h[l], d.pitch[l], frame_stride);
+    }
+    const dim3 ggrd(nb, 1, frames);
     if (half)
-        gradients_kernel<__half><<<grid2d(w, h, frames, blk), blk, 0, st>>>(
-            (const __half *)I, (__half *)Ix, (__half *)Iy, w, h, pitch, frame_stride);
+        pyramid_gradients_kernel<__half><<<ggrd, blk, 0, st>>>((__half *)slots, frame_stride, d);
     else
-        gradients_kernel<float><<<grid2d(w, h, frames, blk), blk, 0, st>>>(
-            (const float *)I, (float *)Ix, (float *)Iy, w, h, pitch, frame_stride);
-}
-
-void launch_downsample(const void *I, int w, int h, int pitch, void *out, int wc, int hc,
-                       int pitch_c, size_t frame_stride, int frames, bool half, cudaStream_t st)
-{
-    (void)w; (void)h;
-    StageScope sc(kStPyramid, 1, st);
-    dim3 blk(32, 8);
-    if (half)
-        downsample_kernel<__half><<<grid2d(wc, hc, frames, blk), blk, 0, st>>>(
-            (const __half *)I, pitch, (__half *)out, wc, hc, pitch_c, frame_stride);
-    else
-        downsample_kernel<float><<<grid2d(wc, hc, frames, blk), blk, 0, st>>>(
-            (const float *)I, pitch, (float *)out, wc, hc, pitch_c, frame_stride);
+        pyramid_gradients_kernel<float><<<ggrd, blk, 0, st>>>((float *)slots, frame_stride, d);
 }
 
 template <typename T>

@@ -11,6 +11,8 @@
 
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 namespace ebof {
 
 namespace {
@@ -99,56 +101,54 @@ __global__ void scatter_desc_kernel(const ebof_window_desc *__restrict__ desc, i
 }
 
 // ---------------------------------------------------------------- A2
-__device__ __forceinline__ int count_neighbours(const uint8_t *img, int W, int H, int pitch,
-                                                int x, int y, int conn)
+// Alg. 1 then Alg. 2 in one pass: a block stages E for its 32 x 8 tile plus
+// a 2-pixel halo in shared memory, denoises the tile plus 1 pixel there
+// (counts in E), then fills the tile (counts in the denoised image).
+// Neighbours outside the image count as non-edge in both, as in
+// count_neighbours, so the result equals denoise_kernel then fill_kernel.
+constexpr int kDfX = 32, kDfY = 8;
+
+__device__ __forceinline__ int count_tile(const uint8_t (*t)[kDfX + 4], int lx, int ly, int conn)
 {
-    int c = 0;
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dy == 0) continue;
-            if (conn == 4 && dx != 0 && dy != 0) continue;
-            const int qx = x + dx, qy = y + dy;
-            if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
-            c += img[(size_t)qy * pitch + qx] ? 1 : 0;
-        }
+    int c = t[ly - 1][lx] + t[ly + 1][lx] + t[ly][lx - 1] + t[ly][lx + 1];
+    if (conn == 8) c += t[ly - 1][lx - 1] + t[ly - 1][lx + 1] + t[ly + 1][lx - 1] + t[ly + 1][lx + 1];
     return c;
 }
 
-// Alg. 1: an edge pixel with fewer than n_d edge neighbours (counted in E)
-// stops being an edge pixel.
-__global__ void denoise_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Ed, int W,
-                               int H, int pitch, size_t fstride, int conn, int n_d)
+__global__ void __launch_bounds__(kDfX * kDfY)
+denoise_fill_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Edf, int W, int H,
+                    int pitch, size_t fstride, int conn, int n_d, int n_f,
+                    uint8_t *__restrict__ export_dense, DevStats *stats)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const uint8_t *e = E + (size_t)blockIdx.z * fstride;
-    const size_t p = (size_t)y * pitch + x;
-    uint8_t v = e[p] ? 1 : 0;
-    if (v && count_neighbours(e, W, H, pitch, x, y, conn) < n_d) v = 0;
-    Ed[(size_t)blockIdx.z * fstride + p] = v;
-}
-
-// Alg. 2 on the denoised image: a non-edge pixel with at least n_f edge
-// neighbours (counted in E_d) becomes an edge pixel.  Also counts the edge
-// pixels of E_df and writes the optional dense export.
-__global__ void fill_kernel(const uint8_t *__restrict__ Ed, uint8_t *__restrict__ Edf, int W,
-                            int H, int pitch, size_t fstride, int conn, int n_f,
-                            uint8_t *__restrict__ export_dense, DevStats *stats)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    __shared__ uint8_t sE[kDfY + 4][kDfX + 4];
+    __shared__ uint8_t sD[kDfY + 4][kDfX + 4];  // denoised, 1-pixel ring inside a 2-pixel frame
     const int f = blockIdx.z;
+    const uint8_t *e = E + (size_t)f * fstride;
+    const int x0 = blockIdx.x * kDfX - 2, y0 = blockIdx.y * kDfY - 2;
+    const int t = threadIdx.y * kDfX + threadIdx.x;
+    for (int i = t; i < (kDfX + 4) * (kDfY + 4); i += kDfX * kDfY) {
+        const int lx = i % (kDfX + 4), ly = i / (kDfX + 4);
+        const int gx = x0 + lx, gy = y0 + ly;
+        uint8_t v = 0;
+        if (gx >= 0 && gy >= 0 && gx < W && gy < H) v = e[(size_t)gy * pitch + gx] ? 1 : 0;
+        sE[ly][lx] = v;
+        sD[ly][lx] = 0;
+    }
+    __syncthreads();
+    for (int i = t; i < (kDfX + 2) * (kDfY + 2); i += kDfX * kDfY) {
+        const int lx = 1 + i % (kDfX + 2), ly = 1 + i / (kDfX + 2);
+        uint8_t v = sE[ly][lx];
+        if (v && count_tile(sE, lx, ly, conn) < n_d) v = 0;
+        sD[ly][lx] = v;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * kDfX + threadIdx.x, y = blockIdx.y * kDfY + threadIdx.y;
     uint8_t v = 0;
-    const bool in = x < W && y < H;
-    if (in) {
-        const uint8_t *e = Ed + (size_t)f * fstride;
-        const size_t p = (size_t)y * pitch + x;
-        v = e[p] ? 1 : 0;
-        if (!v && count_neighbours(e, W, H, pitch, x, y, conn) >= n_f) v = 1;
-        Edf[(size_t)f * fstride + p] = v;
+    if (x < W && y < H) {
+        const int lx = threadIdx.x + 2, ly = threadIdx.y + 2;
+        v = sD[ly][lx];
+        if (!v && count_tile(sD, lx, ly, conn) >= n_f) v = 1;
+        Edf[(size_t)f * fstride + (size_t)y * pitch + x] = v;
         if (export_dense) export_dense[(size_t)f * W * H + (size_t)y * W + x] = v;
     }
     const unsigned m = __ballot_sync(0xffffffffu, v != 0);
@@ -473,7 +473,9 @@ void launch_scatter_desc(const ebof_window_desc *desc, int frames, int W, int H,
                          unsigned long long *dropped_time, cudaStream_t st)
 {
     StageScope sc(kStScatter, 1, st);
-    dim3 grd(64, frames);
+    // the event counts are read on the device: size the grid for the largest
+    // windows (about 4 blocks per SM in all), blocks past a window's end exit
+    dim3 grd(std::max(64, 608 / std::max(frames, 1)), frames);
     scatter_desc_kernel<<<grd, 256, 0, st>>>(desc, W, H, pitch, E, frame_stride, stats,
                                              dropped_time);
 }
@@ -482,11 +484,11 @@ void launch_denoise_fill(const uint8_t *E, uint8_t *Ed, uint8_t *Edf, int W, int
                          size_t frame_stride, int frames, int conn, int n_d, int n_f,
                          uint8_t *export_dense, DevStats *stats, cudaStream_t st)
 {
-    StageScope sc(kStDenoiseFill, 2, st);
-    dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8, frames);
-    denoise_kernel<<<grd, blk, 0, st>>>(E, Ed, W, H, pitch, frame_stride, conn, n_d);
-    fill_kernel<<<grd, blk, 0, st>>>(Ed, Edf, W, H, pitch, frame_stride, conn, n_f,
-                                     export_dense, stats);
+    (void)Ed;  // the denoised image stays in shared memory
+    StageScope sc(kStDenoiseFill, 1, st);
+    dim3 blk(kDfX, kDfY), grd((W + kDfX - 1) / kDfX, (H + kDfY - 1) / kDfY, frames);
+    denoise_fill_kernel<<<grd, blk, 0, st>>>(E, Edf, W, H, pitch, frame_stride, conn, n_d, n_f,
+                                             export_dense, stats);
 }
 
 void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stride, int W,

@@ -13,7 +13,8 @@
 // systems into registers and runs the red-black SOR sweeps there: a thread
 // owns a 2-column x 4-row strip, so one horizontal neighbour is its own and
 // the other is a lane shuffle away, and the rows at strip ends are exchanged
-// through shared memory once per half sweep.  The region border keeps
+// through shared memory once per half sweep.  (A 2 x 2 strip with 1024
+// threads, twice the resident warps, measured no faster.)  The region border keeps
 // du = 0; after h half sweeps only pixels within h - 1 px of that border
 // differ from the whole-image red-black iteration, and those lie in the
 // discarded halo, so the interior is exactly the whole-image iteration (up to
@@ -128,6 +129,79 @@ __device__ __forceinline__ void sor_sweeps(float (&du)[kVS][2], float (&dv)[kVS]
     __syncthreads();
 }
 
+// Derivatives of the warped image and the smoothness weight at a pixel of a
+// staging window (row stride ES; (e) the pixel, at image position gx, gy).
+__device__ __forceinline__ void stage_derivs(const float *sW, const float *sU, const float *sV,
+                                             int ES, int e, int ex0, int ey0, int gx, int gy,
+                                             int w, int h, float alpha_s, float &ix, float &iy,
+                                             float &as)
+{
+    const int xp = min(gx + 1, w - 1) - ex0, xm = max(gx - 1, 0) - ex0;
+    const int yp = min(gy + 1, h - 1) - ey0, ym = max(gy - 1, 0) - ey0;
+    const int ex = gx - ex0, ey = gy - ey0;
+    ix = 0.5f * (sW[ey * ES + xp] - sW[ey * ES + xm]);
+    iy = 0.5f * (sW[yp * ES + ex] - sW[ym * ES + ex]);
+    const float u = sU[e], v = sV[e];
+    const float ux = gx + 1 < w ? sU[e + 1] - u : 0.0f;
+    const float uy = gy + 1 < h ? sU[e + ES] - u : 0.0f;
+    const float vx = gx + 1 < w ? sV[e + 1] - v : 0.0f;
+    const float vy = gy + 1 < h ? sV[e + ES] - v : 0.0f;
+    as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
+}
+
+struct PixelSystem {
+    float i11, i22, a12, b1, b2, cl, cr, cu, cd;
+};
+
+// The 2x2 system of pixel (gx, gy): d indexes the derivative window (row
+// stride DS, origin dx0, dy0), e the staging window (row stride ES); I0, I0x,
+// I0y at the pixel are given.
+__device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const float *sIy,
+                                                    const float *sAs, int DS, int dx0, int dy0,
+                                                    const float *sW, const float *sU,
+                                                    const float *sV, int ES, int e, int gx,
+                                                    int gy, int w, int h, float i0, float i0x,
+                                                    float i0y, float delta, float gamma)
+{
+    const int xp = min(gx + 1, w - 1) - dx0, xm = max(gx - 1, 0) - dx0;
+    const int yp = min(gy + 1, h - 1) - dy0, ym = max(gy - 1, 0) - dy0;
+    const int dx = gx - dx0, dy = gy - dy0;
+    const int d = dy * DS + dx;
+    const float Ix = sIx[d], Iy = sIy[d];
+    const float Ixx = 0.5f * (sIx[dy * DS + xp] - sIx[dy * DS + xm]);
+    const float Ixy = 0.5f * (sIx[yp * DS + dx] - sIx[ym * DS + dx]);
+    const float Iyy = 0.5f * (sIy[yp * DS + dx] - sIy[ym * DS + dx]);
+    const float Iz = sW[e] - i0;
+    const float Ixz = Ix - i0x, Iyz = Iy - i0y;
+    const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
+    const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
+    float ad = delta * nd * psi_prime(nd * Iz * Iz);
+    float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
+    const float u = sU[e], v = sV[e];
+    const float wx = (float)gx + u, wy = (float)gy + v;
+    if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) {
+        ad = 0.0f;
+        ag = 0.0f;
+    }
+    const float asp = sAs[d];
+    PixelSystem ps;
+    ps.cl = gx > 0 ? 0.5f * (asp + sAs[d - 1]) : 0.0f;
+    ps.cr = gx + 1 < w ? 0.5f * (asp + sAs[d + 1]) : 0.0f;
+    ps.cu = gy > 0 ? 0.5f * (asp + sAs[d - DS]) : 0.0f;
+    ps.cd = gy + 1 < h ? 0.5f * (asp + sAs[d + DS]) : 0.0f;
+    const float sw = ps.cl + ps.cr + ps.cu + ps.cd;
+    const float su0 = ps.cl * (sU[e - 1] - u) + ps.cr * (sU[e + 1] - u) +
+                      ps.cu * (sU[e - ES] - u) + ps.cd * (sU[e + ES] - u);
+    const float sv0 = ps.cl * (sV[e - 1] - v) + ps.cr * (sV[e + 1] - v) +
+                      ps.cu * (sV[e - ES] - v) + ps.cd * (sV[e + ES] - v);
+    ps.i11 = __fdividef(1.0f, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
+    ps.i22 = __fdividef(1.0f, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
+    ps.a12 = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
+    ps.b1 = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
+    ps.b2 = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
+    return ps;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kAX * kAY)
 var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
@@ -173,19 +247,9 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         const int lx = i % kADX, ly = i / kADX;
         const int gx = dx0 + lx, gy = dy0 + ly;
         float ix = 0.0f, iy = 0.0f, as = 0.0f;
-        if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-            const int xp = min(gx + 1, w - 1) - ex0, xm = max(gx - 1, 0) - ex0;
-            const int yp = min(gy + 1, h - 1) - ey0, ym = max(gy - 1, 0) - ey0;
-            const int ex = gx - ex0, ey = gy - ey0;
-            ix = 0.5f * (sW[ey][xp] - sW[ey][xm]);
-            iy = 0.5f * (sW[yp][ex] - sW[ym][ex]);
-            const float u = sU[ey][ex], v = sV[ey][ex];
-            const float ux = gx + 1 < w ? sU[ey][ex + 1] - u : 0.0f;
-            const float uy = gy + 1 < h ? sU[ey + 1][ex] - u : 0.0f;
-            const float vx = gx + 1 < w ? sV[ey][ex + 1] - v : 0.0f;
-            const float vy = gy + 1 < h ? sV[ey + 1][ex] - v : 0.0f;
-            as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
-        }
+        if (gx >= 0 && gx < w && gy >= 0 && gy < h)
+            stage_derivs(&sW[0][0], &sU[0][0], &sV[0][0], kAEX, (gy - ey0) * kAEX + (gx - ex0),
+                         ex0, ey0, gx, gy, w, h, alpha_s, ix, iy, as);
         sIx[ly][lx] = ix;
         sIy[ly][lx] = iy;
         sAs[ly][lx] = as;
@@ -194,46 +258,21 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
 
     const int gx = tx0 + threadIdx.x, gy = ty0 + threadIdx.y;
     if (gx >= w || gy >= h) return;
-    const int xp = min(gx + 1, w - 1) - dx0, xm = max(gx - 1, 0) - dx0;
-    const int yp = min(gy + 1, h - 1) - dy0, ym = max(gy - 1, 0) - dy0;
-    const int dx = gx - dx0, dy = gy - dy0, ex = gx - ex0, ey = gy - ey0;
-    const float Ix = sIx[dy][dx], Iy = sIy[dy][dx];
-    const float Ixx = 0.5f * (sIx[dy][xp] - sIx[dy][xm]);
-    const float Ixy = 0.5f * (sIx[yp][dx] - sIx[ym][dx]);
-    const float Iyy = 0.5f * (sIy[yp][dx] - sIy[ym][dx]);
     const size_t p = (size_t)gy * pitch + gx;
-    const float Iz = sW[ey][ex] - ldp(&I0b[po + p]);
-    const float Ixz = Ix - ldp(&I0xb[po + p]), Iyz = Iy - ldp(&I0yb[po + p]);
-    const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
-    const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
-    float ad = delta * nd * psi_prime(nd * Iz * Iz);
-    float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
-    const float u = sU[ey][ex], v = sV[ey][ex];
-    const float wx = (float)gx + u, wy = (float)gy + v;
-    if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) {
-        ad = 0.0f;
-        ag = 0.0f;
-    }
-    const float asp = sAs[dy][dx];
-    const float cl = gx > 0 ? 0.5f * (asp + sAs[dy][dx - 1]) : 0.0f;
-    const float cr = gx + 1 < w ? 0.5f * (asp + sAs[dy][dx + 1]) : 0.0f;
-    const float cu = gy > 0 ? 0.5f * (asp + sAs[dy - 1][dx]) : 0.0f;
-    const float cd = gy + 1 < h ? 0.5f * (asp + sAs[dy + 1][dx]) : 0.0f;
-    const float sw = cl + cr + cu + cd;
-    const float su0 = cl * (sU[ey][ex - 1] - u) + cr * (sU[ey][ex + 1] - u) +
-                      cu * (sU[ey - 1][ex] - u) + cd * (sU[ey + 1][ex] - u);
-    const float sv0 = cl * (sV[ey][ex - 1] - v) + cr * (sV[ey][ex + 1] - v) +
-                      cu * (sV[ey - 1][ex] - v) + cd * (sV[ey + 1][ex] - v);
+    const PixelSystem ps = pixel_system(
+        &sIx[0][0], &sIy[0][0], &sAs[0][0], kADX, dx0, dy0, &sW[0][0], &sU[0][0], &sV[0][0], kAEX,
+        (gy - ey0) * kAEX + (gx - ex0), gx, gy, w, h, ldp(&I0b[po + p]), ldp(&I0xb[po + p]),
+        ldp(&I0yb[po + p]), delta, gamma);
     float *cf = coefb + (size_t)f * cfs + p;
-    cf[kCI11 * plane] = __fdividef(1.0f, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
-    cf[kCI22 * plane] = __fdividef(1.0f, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
-    cf[kCA12 * plane] = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
-    cf[kCB1 * plane] = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
-    cf[kCB2 * plane] = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
-    cf[kCWL * plane] = cl;
-    cf[kCWR * plane] = cr;
-    cf[kCWU * plane] = cu;
-    cf[kCWD * plane] = cd;
+    cf[kCI11 * plane] = ps.i11;
+    cf[kCI22 * plane] = ps.i22;
+    cf[kCA12 * plane] = ps.a12;
+    cf[kCB1 * plane] = ps.b1;
+    cf[kCB2 * plane] = ps.b2;
+    cf[kCWL * plane] = ps.cl;
+    cf[kCWR * plane] = ps.cr;
+    cf[kCWU * plane] = ps.cu;
+    cf[kCWD * plane] = ps.cd;
 }
 
 __global__ void __launch_bounds__(kVThreads, 1)
