@@ -121,12 +121,14 @@ pyramid_gradients_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
 }
 
 // ---------------------------------------------------------------- A6
-// Group of G lanes per patch (G = 8 for ps <= 8, else 16); lane c < ps owns
-// patch column c and keeps its template, gradients and warped samples in
-// registers.  Patch sums are reduced over the group with xor shuffles, so a
-// warp serves 32 / G patches.  Every lane of a warp runs the same number of
-// iterations (guarded patches iterate on a dummy determinant and are
-// discarded), so the shuffles never diverge.
+// Group of G lanes per patch; lane c owns the CPL adjacent patch columns
+// c * CPL .. c * CPL + CPL - 1 (those below ps) and keeps their template,
+// gradients and running samples in registers.  The lane count and CPL are
+// chosen so that few lanes idle: ps <= 8: 8 lanes x 1 column; ps 9..12: 4
+// lanes x 3 columns; ps 13..16: 8 lanes x 2 columns.  Patch sums are reduced
+// over the group with xor shuffles, so a warp serves 32 / G patches.  Every
+// lane of a warp runs the same number of iterations (guarded patches iterate
+// on a dummy determinant and are discarded), so the shuffles never diverge.
 template <int G>
 __device__ __forceinline__ float group_sum(float v)
 {
@@ -134,6 +136,20 @@ __device__ __forceinline__ float group_sum(float v)
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// Lanes per patch.  Wide: fewest idle lanes and fewest instructions per
+// patch (ps 9..12: 4 lanes x 3 columns), for levels with enough patches to
+// fill the GPU.  Narrow: one column per lane (ps 9..16: 16 lanes), a third of
+// the serial work per lane, for levels with few patches where latency
+// matters.  The choice depends on the level's patch count only, never on the
+// number of frames in a launch, so batched and single-window results agree
+// bit for bit.
+template <int PS>
+struct SearchShape {
+    static constexpr int kWide = PS <= 8 ? 8 : (PS <= 12 ? 4 : 8);
+    static constexpr int kNarrow = PS <= 8 ? 8 : 16;
+};
+constexpr int kWideSearchPatches = 32768;
 
 template <int PS, int G, typename T>
 __global__ void __launch_bounds__(128)
@@ -143,6 +159,7 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     int hc, int pitch_c, size_t plane_c, size_t ucfs, float *__restrict__ upb,
                     size_t upfs, int stride, int iters, float kappa, int *err)
 {
+    constexpr int CPL = (PS + G - 1) / G;
     const int f = blockIdx.y;
     const int c = threadIdx.x % G;
     const int np = npx * npy;
@@ -151,7 +168,7 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     const int pid = real ? pid_raw : np - 1;
     const int i = pid % npx, j = pid / npx;
     const int x0 = min(i * stride, w - PS), y0 = min(j * stride, h - PS);
-    const bool active = c < PS;
+    const int c0 = c * CPL;  // first column of this lane
     const T *I0 = I0b + (size_t)f * pfs, *I0x = I0xb + (size_t)f * pfs;
     const T *I0y = I0yb + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
     if (x0 < 0 || y0 < 0) {  // cannot happen when the level holds a patch
@@ -169,26 +186,31 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     }
 
     // F4: template, mean-normalised gradients, Hessian
-    float Tm[PS], GX[PS], GY[PS];
+    float Tm[PS][CPL], GX[PS][CPL], GY[PS][CPL];
     float sgx = 0.0f, sgy = 0.0f;
-    const int xc = active ? x0 + c : x0;
 #pragma unroll
-    for (int r = 0; r < PS; ++r) {
-        const size_t p = (size_t)(y0 + r) * pitch + xc;
-        Tm[r] = active ? ldp(&I0[p]) : 0.0f;
-        GX[r] = active ? ldp(&I0x[p]) : 0.0f;
-        GY[r] = active ? ldp(&I0y[p]) : 0.0f;
-        sgx += GX[r]; sgy += GY[r];
-    }
+    for (int r = 0; r < PS; ++r)
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const bool act = c0 + k < PS;
+            const size_t p = (size_t)(y0 + r) * pitch + x0 + (act ? c0 + k : 0);
+            Tm[r][k] = act ? ldp(&I0[p]) : 0.0f;
+            GX[r][k] = act ? ldp(&I0x[p]) : 0.0f;
+            GY[r][k] = act ? ldp(&I0y[p]) : 0.0f;
+            sgx += GX[r][k];
+            sgy += GY[r][k];
+        }
     constexpr float inv_n = 1.0f / (PS * PS);
     sgx = group_sum<G>(sgx); sgy = group_sum<G>(sgy);
     const float mgx = sgx * inv_n, mgy = sgy * inv_n;
     float h11 = 0.0f, h12 = 0.0f, h22 = 0.0f;
 #pragma unroll
-    for (int r = 0; r < PS; ++r) {
-        if (active) { GX[r] -= mgx; GY[r] -= mgy; }
-        h11 += GX[r] * GX[r]; h12 += GX[r] * GY[r]; h22 += GY[r] * GY[r];
-    }
+    for (int r = 0; r < PS; ++r)
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            if (c0 + k < PS) { GX[r][k] -= mgx; GY[r][k] -= mgy; }
+            h11 += GX[r][k] * GX[r][k]; h12 += GX[r][k] * GY[r][k]; h22 += GY[r][k] * GY[r][k];
+        }
     h11 = group_sum<G>(h11); h12 = group_sum<G>(h12); h22 = group_sum<G>(h22);
     const float det = h11 * h22 - h12 * h12;
     const bool guard = !(det > 1e-6f * (float)(PS * PS) * (float)(PS * PS));
@@ -197,14 +219,17 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     const float a11 = h11 + mu, a22 = h22 + mu;
     const float inv_det = guard ? 0.0f : __fdividef(1.0f, a11 * a22 - h12 * h12);
 
-
     float u = u0, v = v0;
     const float lim = (float)(w + h);
     for (int it = 0; it < iters; ++it) {
+        // b = sum g ((w - mean w) - (T - mean T)); the mean-normalised
+        // gradients sum to zero, so both means drop out of b: b = sum g (w - T)
+        // (exactly zero when the warped patch equals the template)
+        float b1 = 0.0f, b2 = 0.0f;
         // The displacement is the same for the whole patch: when every
         // sample of the patch and its right/lower neighbour lies inside the
         // image, the clamped bilinear sample reduces to fixed weights on a
-        // fixed (PS+1) x (PS+1) window, and each row's horizontal lerp serves
+        // fixed (PS+1) x (PS+1) window, and each row's horizontal lerps serve
         // two output rows.
         const float uc = fminf(fmaxf(u, -lim), lim), vc = fminf(fmaxf(v, -lim), lim);
         const float fu = floorf(uc), fv = floorf(vc);
@@ -212,38 +237,46 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         const float ax = uc - fu, ay = vc - fv;
         const bool fast = sx0 >= 0 && sy0 >= 0 && sx0 + PS <= w - 1 && sy0 + PS <= h - 1 &&
                           uc == u && vc == v;
-        float Wv[PS];
         if (fast) {
-            if (active) {
-                const T *pp = I1 + (size_t)sy0 * pitch + sx0 + c;
-                float a = ldp(&pp[0]), b = ldp(&pp[1]);
-                float hp = a + ax * (b - a);
+            // columns c0 .. c0 + CPL of the window (the last one only as the
+            // right neighbour); a column beyond PS is never read
+            const T *pp = I1 + (size_t)sy0 * pitch + sx0 + c0;
+            float hp[CPL];
+            {
+                float s[CPL + 1];
 #pragma unroll
-                for (int r = 0; r < PS; ++r) {
-                    const T *q = pp + (size_t)(r + 1) * pitch;
-                    const float c2 = ldp(&q[0]), d2 = ldp(&q[1]);
-                    const float hn = c2 + ax * (d2 - c2);
-                    Wv[r] = hp + ay * (hn - hp);
-                    hp = hn;
+                for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS ? ldp(&pp[k]) : 0.0f;
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) hp[k] = s[k] + ax * (s[k + 1] - s[k]);
+            }
+#pragma unroll
+            for (int r = 0; r < PS; ++r) {
+                const T *q = pp + (size_t)(r + 1) * pitch;
+                float s[CPL + 1];
+#pragma unroll
+                for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS ? ldp(&q[k]) : 0.0f;
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    const float hn = s[k] + ax * (s[k + 1] - s[k]);
+                    const float wv = hp[k] + ay * (hn - hp[k]);
+                    hp[k] = hn;
+                    const float res = wv - Tm[r][k];
+                    b1 += GX[r][k] * res;
+                    b2 += GY[r][k] * res;
                 }
-            } else {
-#pragma unroll
-                for (int r = 0; r < PS; ++r) Wv[r] = 0.0f;
             }
         } else {
-            const float xs = (float)xc + u;
 #pragma unroll
             for (int r = 0; r < PS; ++r)
-                Wv[r] = active ? bilinear(I1, w, h, pitch, xs, (float)(y0 + r) + v) : 0.0f;
-        }
-        // b = sum g ((w - mean w) - (T - mean T)); the mean-normalised
-        // gradients sum to zero, so both means drop out of b: b = sum g (w - T)
-        // (exactly zero when the warped patch equals the template)
-        float b1 = 0.0f, b2 = 0.0f;
 #pragma unroll
-        for (int r = 0; r < PS; ++r) {
-            const float res = Wv[r] - Tm[r];
-            b1 += GX[r] * res; b2 += GY[r] * res;
+                for (int k = 0; k < CPL; ++k) {
+                    if (c0 + k >= PS) continue;
+                    const float wv = bilinear(I1, w, h, pitch, (float)(x0 + c0 + k) + u,
+                                              (float)(y0 + r) + v);
+                    const float res = wv - Tm[r][k];
+                    b1 += GX[r][k] * res;
+                    b2 += GY[r][k] * res;
+                }
         }
         b1 = group_sum<G>(b1); b2 = group_sum<G>(b2);
         u -= (a22 * b1 - h12 * b2) * inv_det;
@@ -464,11 +497,14 @@ void search_ps(const T *I0, const T *I0x, const T *I0y, const T *I1,
                const Level &lv, size_t pfs, const float *Uc, const Level *lvc, size_t ucfs,
                float *up, size_t upfs, int frames, const FlowParams &fp, int *err, cudaStream_t st)
 {
-    constexpr int G = PS <= 8 ? 8 : 16;
     const int np = lv.npx * lv.npy;
+    const bool wide = np >= kWideSearchPatches;
+    const int G = wide ? SearchShape<PS>::kWide : SearchShape<PS>::kNarrow;
     const int per_block = 128 / G;
     dim3 grd((np + per_block - 1) / per_block, frames);
-    patch_search_kernel<PS, G, T><<<grd, 128, 0, st>>>(
+    auto kern = wide ? patch_search_kernel<PS, SearchShape<PS>::kWide, T>
+                     : patch_search_kernel<PS, SearchShape<PS>::kNarrow, T>;
+    kern<<<grd, 128, 0, st>>>(
         I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pfs, lv.npx, lv.npy, Uc, lvc ? lvc->w : 0,
         lvc ? lvc->h : 0, lvc ? lvc->pitch : 0, lvc ? lvc->plane : 0, ucfs, up, upfs, fp.stride,
         fp.gn_iters, fp.gn_damping, err);
