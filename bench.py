@@ -659,6 +659,11 @@ def main():
     eb.check(pst)
     _, prof0 = eb.ebof_stream_get_profile_level(s, 0)
     _, profn = eb.ebof_stream_get_profile_level(s, -1)
+    by_level = {}
+    for lvl in [-1] + list(range(prm.levels)):
+        _, pl = eb.ebof_stream_get_profile_level(s, lvl)
+        by_level["all" if lvl < 0 else str(lvl)] = {
+            k: round(v[0] / (nwin * nprof), 4) for k, v in pl.items() if v[1]}
     eb.ebof_stream_set_profiling(s, False)
     total_ms = sum(v[0] for v in prof.values()) or 1.0
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
@@ -678,7 +683,10 @@ def main():
                 "launches_timed": int(dom_launches),
                 "stage_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items()},
                 "stage_ms_per_frame": {k: round(v[0] / (nwin * nprof), 4)
-                                       for k, v in prof.items() if v[1]}}
+                                       for k, v in prof.items() if v[1]},
+                "stage_ms_per_frame_by_level": by_level,
+                "stage_timing": "CUDA events around each stage's launches on the "
+                                "caller's stream (eager launches, gaps included)"}
 
     # batched path: the same stream through ebof_process_windows
     batched = None

@@ -91,6 +91,7 @@ struct ebof_stream {
     std::vector<int64_t> last_win_events;  // per window, after a list call
     bool last_list = false;
     cudaStream_t cap = nullptr;
+    CoefMaps cmaps;  // tensor maps of the variational coefficient planes per level
 };
 
 struct ebof_group {
@@ -120,6 +121,7 @@ struct ebof_group {
     bool have_last = false;
     std::atomic<int> busy{0};
     Profiler prof;
+    CoefMaps cmaps;
 };
 
 namespace {
@@ -308,7 +310,8 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
             // the coarser flow is consumed by the search: its buffer is free
             float *Utmp = (Ucur == s->Ua) ? s->Ub : s->Ua;
             Ucur = launch_variational(I0, I0x, I0y, I1, lv, s->pyr_fs, Ucur, Utmp, s->u_fs,
-                                      s->work, s->work_fs, nf, fp, st);
+                                      s->work, s->work_fs, nf, fp,
+                                      s->cmaps.ok[l] ? &s->cmaps.map[l] : nullptr, s->d_err, st);
             Uc = Ucur;
             lvc = &lv;
         }
@@ -531,7 +534,8 @@ void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
             launch_densify(I0, I1, lv, g->pyr_fs, g->up, g->up_fs, Ucur, g->u_fs, n, fp, st);
             float *Utmp = (Ucur == g->Ua) ? g->Ub : g->Ua;
             Ucur = launch_variational(I0, I0x, I0y, I1, lv, g->pyr_fs, Ucur, Utmp, g->u_fs,
-                                      g->work, g->work_fs, n, fp, st);
+                                      g->work, g->work_fs, n, fp,
+                                      g->cmaps.ok[l] ? &g->cmaps.map[l] : nullptr, g->d_err, st);
             Uc = Ucur;
             lvc = &lv;
         }
@@ -642,6 +646,7 @@ ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **o
     }
     cudaMemset(s->d_err, 0, sizeof(int));
     cudaMemset(s->dstats, 0, sizeof(DevStats) * B);
+    make_coef_maps(s->work, s->geo, B, &s->cmaps);
     cudaMemset(s->d_dropped_time, 0, sizeof(unsigned long long));
     if (cudaDeviceSynchronize() != cudaSuccess) {
         free_all(s);
@@ -833,7 +838,7 @@ ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_o
     }
     if (err) {
         cudaMemset(s->d_err, 0, sizeof(int));
-        return EBOF_ERR_DEVICE_BOUNDS;
+        return (err & kErrTimeout) ? EBOF_ERR_TIMEOUT : EBOF_ERR_DEVICE_BOUNDS;
     }
     return EBOF_OK;
 }
@@ -917,6 +922,7 @@ ebof_status ebof_group_create(const ebof_params *p, int32_t n_streams, int devic
     }
     cudaMemset(g->d_err, 0, sizeof(int));
     cudaMemset(g->flow, 0, sizeof(float) * 2 * (size_t)q.width * q.height * n);
+    make_coef_maps(g->work, g->geo, n, &g->cmaps);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         free_group(g);
         delete g;
@@ -1054,7 +1060,7 @@ ebof_status ebof_group_sync(ebof_group *g, ebof_window_stats *out, int32_t n_out
     }
     if (err) {
         cudaMemset(g->d_err, 0, sizeof(int));
-        return EBOF_ERR_DEVICE_BOUNDS;
+        return (err & kErrTimeout) ? EBOF_ERR_TIMEOUT : EBOF_ERR_DEVICE_BOUNDS;
     }
     return EBOF_OK;
 }

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only; the driver is reached through the runtime)
 #include <cuda_runtime.h>
 
 #include "ebof.h"
@@ -17,6 +18,7 @@ constexpr int32_t kInfD = 2147483647;  // squared distance with no edge pixel
 
 // Device error bits, latched in StreamState::d_err.
 constexpr int kErrBounds = 1;
+constexpr int kErrTimeout = 2;  // a bounded wait on an asynchronous copy ran out
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -139,19 +141,33 @@ void launch_densify(const void *I0, const void *I1, const Level &lv, size_t pyr_
                     const float *up, size_t up_frame_stride, float *U, size_t u_frame_stride,
                     int frames, const FlowParams &fp, cudaStream_t st);
 
+// Tensor maps (TMA descriptors) of the variational coefficient planes of
+// each pyramid level in a stream's or group's work buffer: level l holds
+// frames x 9 planes of pitch_l x h_l floats, frame stride 9 planes.
+struct CoefMaps {
+    bool ok[kMaxLevels];
+    CUtensorMap map[kMaxLevels];
+};
+// Fills m for `frames` frames of `work`; levels whose map cannot be encoded
+// are marked not ok (their SOR sweeps then load the planes directly).
+void make_coef_maps(float *work, const Geometry &geo, int frames, CoefMaps *m);
+
 // A8: variational refinement of U.  Returns the buffer holding the result:
 // U itself, or Utmp (same shape as U) when the fused kernel ping-pongs.
+// coef_map: the level's coefficient tensor map, or nullptr; err: device
+// error word (kErrTimeout if a bounded wait runs out).
 float *launch_variational(const void *I0, const void *I0x, const void *I0y, const void *I1,
                           const Level &lv, size_t pyr_frame_stride, float *U, float *Utmp,
                           size_t u_frame_stride, float *work, size_t work_frame_stride,
-                          int frames, const FlowParams &fp, cudaStream_t st);
+                          int frames, const FlowParams &fp, const CUtensorMap *coef_map,
+                          int *err, cudaStream_t st);
 bool var_fused_supported(int var_sor);
 void init_var_attributes();
 float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y,
                                 const void *I1, const Level &lv, size_t pyr_frame_stride,
                                 float *U, float *Utmp, size_t u_frame_stride, float *coef,
-                                size_t coef_frame_stride, int frames, const FlowParams &fp,
-                                cudaStream_t st);
+                                int frames, const FlowParams &fp, const CUtensorMap *coef_map,
+                                int *err, cudaStream_t st);
 
 // A9 for one window, destination pointer read from device memory.
 void launch_flow_out_ptr(const float *U, int W, int H, int pitch, size_t u_frame_stride,

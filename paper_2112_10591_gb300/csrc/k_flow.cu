@@ -662,12 +662,13 @@ void variational_steps(const T *I0, const T *I0x, const T *I0y, const T *I1, con
 float *launch_variational(const void *I0, const void *I0x, const void *I0y, const void *I1,
                           const Level &lv, size_t pyr_frame_stride, float *U, float *Utmp,
                           size_t u_frame_stride, float *work, size_t work_frame_stride,
-                          int frames, const FlowParams &fp, cudaStream_t st)
+                          int frames, const FlowParams &fp, const CUtensorMap *coef_map,
+                          int *err, cudaStream_t st)
 {
     if (fp.var_outer <= 0) return U;
     if (var_fused_supported(fp.var_sor))
         return launch_variational_fused(I0, I0x, I0y, I1, lv, pyr_frame_stride, U, Utmp,
-                                        u_frame_stride, work, work_frame_stride, frames, fp, st);
+                                        u_frame_stride, work, frames, fp, coef_map, err, st);
     // many sweeps: one launch per step, state in global memory
     if (fp.half)
         variational_steps((const __half *)I0, (const __half *)I0x, (const __half *)I0y,

@@ -19,9 +19,21 @@
 // differ from the whole-image red-black iteration, and those lie in the
 // discarded halo, so the interior is exactly the whole-image iteration (up to
 // floating-point rounding).  It writes U + dU for its interior.
+//
+// var_sor_tma_kernel: the same sweeps in a persistent grid (one block per
+// SM) that walks over the regions, for grids of at least four regions per SM.  One thread loads each region's nine
+// coefficient planes into shared memory with a single TMA tensor copy
+// (cp.async.bulk.tensor, completion on an mbarrier); once every thread has
+// moved its values into registers, the copy of the block's next region is
+// issued and runs during the sweeps.  The box starts at the region's first
+// column rounded down to a multiple of 4 (the 16-byte rule of tensor
+// copies) and is 4 columns wider; elements outside the level are filled
+// with zero, as the direct loads do, so both kernels give the same result.
 #include "dev_common.cuh"
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
+
+#include <mutex>
 
 namespace ebof {
 
@@ -34,6 +46,12 @@ constexpr int kVThreads = 32 * kVWarps;  // 512
 constexpr size_t kVSmemFloats = 2 * 2 * kVWarps * 2 * 64;  // strip-end exchange
 enum { kCI11 = 0, kCI22, kCA12, kCB1, kCB2, kCWL, kCWR, kCWU, kCWD, kCPlanes };
 
+constexpr int kTmaBoxW = kVR + 4;  // region columns + the rounding of the box start
+constexpr size_t kTmaCoefFloats = (size_t)kCPlanes * kVR * kTmaBoxW;
+constexpr size_t kTmaSmemBytes = (kTmaCoefFloats + kVSmemFloats) * sizeof(float);
+constexpr long kTmaSpinLimit = 1L << 22;  // bounded wait on a tensor copy
+constexpr int kMaxDevs = 64;
+int g_num_sms[kMaxDevs];
 constexpr int kAX = 32, kAY = 16;              // coefficient tile
 constexpr int kAEX = kAX + 4, kAEY = kAY + 4;  // staging window: tile + 2 px
 constexpr int kADX = kAX + 2, kADY = kAY + 2;  // derivative window: tile + 1 px
@@ -334,7 +352,173 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
         }
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Bounded wait for the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long it = 0; it < kTmaSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kVThreads, 1)
+var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int pitch,
+                   const float *__restrict__ Uinb, float *__restrict__ Uoutb, size_t ufs,
+                   size_t plane, int R, int tile, int nrx, int nry, int total, int n_half,
+                   float omega, int *err)
+{
+    extern __shared__ __align__(1024) float tsm[];
+    float *cbuf = tsm;                  // [kCPlanes][kVR][kTmaBoxW]
+    float *xch = tsm + kTmaCoefFloats;  // strip-end exchange, two buffers
+    __shared__ __align__(8) unsigned long long mbar_s;
+    const uint32_t mbar = smem_u32(&mbar_s);
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    const int per_frame = nrx * nry;
+    const unsigned long long map_addr = (unsigned long long)&cmap;
+    const uint32_t dst = smem_u32(cbuf);
+
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int r) {  // thread 0: the tensor copy of region r
+        const int f = r / per_frame, rem = r - f * per_frame;
+        const int ry = rem / nrx, rx = rem - ry * nrx;
+        const int bx0 = (rx * tile - R) & ~3;
+        const int by0 = ry * tile - R;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+                     "r"((unsigned)(kTmaCoefFloats * sizeof(float)))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+            "l"(map_addr), "r"(bx0), "r"(by0), "r"(0), "r"(f), "r"(mbar)
+            : "memory");
+    };
+    int r = blockIdx.x;
+    if (t == 0 && r < total) issue(r);
+    uint32_t parity = 0;
+    for (; r < total; r += gridDim.x) {
+        const bool ok = mbar_wait(mbar, parity);
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                atomicOr(err, kErrTimeout);
+                mbar_wait(mbar, parity);  // let the copy in flight land (bounded)
+            }
+            return;
+        }
+        parity ^= 1u;
+        const int f = r / per_frame, rem = r - f * per_frame;
+        const int ry = rem / nrx, rx = rem - ry * nrx;
+        const int rx0 = rx * tile - R, ry0 = ry * tile - R;
+        const int ox = rx0 - (rx0 & ~3);  // region column 0 within the box
+        float i11[kVS][2], i22[kVS][2], a12[kVS][2], b1[kVS][2], b2[kVS][2];
+        float wl[kVS][2], wr[kVS][2], wu[kVS][2], wd[kVS][2];
+        float du[kVS][2], dv[kVS][2];
+#pragma unroll
+        for (int rr = 0; rr < kVS; ++rr)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                du[rr][q] = 0.0f;
+                dv[rr][q] = 0.0f;
+                const float *c = cbuf + (wp * kVS + rr) * kTmaBoxW + ox + 2 * lane + q;
+                constexpr int P = kVR * kTmaBoxW;
+                i11[rr][q] = c[kCI11 * P];
+                i22[rr][q] = c[kCI22 * P];
+                a12[rr][q] = c[kCA12 * P];
+                b1[rr][q] = c[kCB1 * P];
+                b2[rr][q] = c[kCB2 * P];
+                wl[rr][q] = c[kCWL * P];
+                wr[rr][q] = c[kCWR * P];
+                wu[rr][q] = c[kCWU * P];
+                wd[rr][q] = c[kCWD * P];
+            }
+        __syncthreads();  // every thread holds its coefficients: the buffer is free
+        if (t == 0 && r + (int)gridDim.x < total) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(r + gridDim.x);
+        }
+        const float *Uin = Uinb + (size_t)f * ufs;
+        float *Uout = Uoutb + (size_t)f * ufs;
+        if (((rx0 + ry0) & 1) == 0)
+            sor_sweeps<0>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half,
+                          omega);
+        else
+            sor_sweeps<1>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half,
+                          omega);
+#pragma unroll
+        for (int rr = 0; rr < kVS; ++rr)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int lx = 2 * lane + q, ly = wp * kVS + rr;
+                const int gx = rx0 + lx, gy = ry0 + ly;
+                if (lx < R || lx >= R + tile || ly < R || ly >= R + tile || gx >= w || gy >= h)
+                    continue;
+                const size_t p = (size_t)gy * pitch + gx;
+                Uout[p] = Uin[p] + du[rr][q];
+                Uout[plane + p] = Uin[plane + p] + dv[rr][q];
+            }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
 }  // namespace
+
+void make_coef_maps(float *work, const Geometry &geo, int frames, CoefMaps *m)
+{
+    for (int l = 0; l < kMaxLevels; ++l) m->ok[l] = false;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || !work) return;
+    for (int l = 0; l < geo.levels; ++l) {
+        const Level &lv = geo.lv[l];
+        const cuuint64_t dims[4] = {(cuuint64_t)lv.w, (cuuint64_t)lv.h, (cuuint64_t)kCPlanes,
+                                    (cuuint64_t)frames};
+        const cuuint64_t strides[3] = {(cuuint64_t)lv.pitch * sizeof(float),
+                                       (cuuint64_t)lv.plane * sizeof(float),
+                                       (cuuint64_t)kCPlanes * lv.plane * sizeof(float)};
+        const cuuint32_t box[4] = {(cuuint32_t)kTmaBoxW, (cuuint32_t)kVR, (cuuint32_t)kCPlanes,
+                                   1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        m->ok[l] = enc(&m->map[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, work, dims, strides, box,
+                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+}
 
 bool var_fused_supported(int var_sor)
 {
@@ -342,14 +526,29 @@ bool var_fused_supported(int var_sor)
     return kVR - 2 * R >= 16;
 }
 
-void init_var_attributes() {}
+void init_var_attributes()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevs) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        g_num_sms[dev] = n;
+    }
+    cudaFuncSetAttribute(var_sor_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTmaSmemBytes);
+}
 
 float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y,
                                 const void *I1, const Level &lv, size_t pyr_frame_stride,
                                 float *U, float *Utmp, size_t u_frame_stride, float *coef,
-                                size_t coef_frame_stride, int frames, const FlowParams &fp,
-                                cudaStream_t st)
+                                int frames, const FlowParams &fp, const CUtensorMap *coef_map,
+                                int *err, cudaStream_t st)
 {
+    // the level's planes are packed: frame stride 9 planes of this level
+    const size_t coef_frame_stride = (size_t)kCPlanes * lv.plane;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int nsm = (dev >= 0 && dev < kMaxDevs && g_num_sms[dev] > 0) ? g_num_sms[dev] : 0;
     const int n_half = 2 * fp.var_sor;
     const int R = n_half > 0 ? n_half - 1 : 0;
     const int tile = kVR - 2 * R;
@@ -374,9 +573,19 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
         }
         {
             StageScope sc(kStVarSor, 1, st);
-            var_sor_kernel<<<sgrd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
-                lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef, coef_frame_stride, R,
-                tile, n_half, fp.omega);
+            const int total = (int)(sgrd.x * sgrd.y * sgrd.z);
+            // the persistent copy-ahead kernel pays off once every SM has
+            // several regions to walk (batched and grouped windows); both
+            // kernels see the same coefficients, so the choice never changes
+            // the result
+            if (coef_map && nsm > 0 && total >= 4 * nsm)
+                var_sor_tma_kernel<<<nsm, kVThreads, kTmaSmemBytes, st>>>(
+                    *coef_map, lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, R, tile,
+                    (int)sgrd.x, (int)sgrd.y, total, n_half, fp.omega, err);
+            else
+                var_sor_kernel<<<sgrd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
+                    lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
+                    coef_frame_stride, R, tile, n_half, fp.omega);
         }
         float *t = a;
         a = b;
