@@ -404,6 +404,46 @@ def run_multistream(args, eb, torch, dev, rank):
     return out
 
 
+def ground_truth_quality(eb, torch, dev, local):
+    """§IV-C's AEE and outlier share (error > 3 px and > 5 % of the motion)
+    of the GPU flow against the generator's ground truth at the previous
+    window's event pixels: the 346x260 workload pair, and 20 flow frames of
+    a 21-window copy of the 1280x720 workload (its own draws: the motion of
+    a stream is drawn for its length).  Sanity figures: the 1280x720 scene
+    moves up to 20 px and 2 degrees per 10 ms window, so its edges smear
+    into bands as wide as the motion."""
+    from paper_2112_10591_gb300 import synth
+    out = {}
+    for name, ev in (("346x260", synth.translating_segments(keep_truth=True)),
+                     ("1280x720", synth.workload_1280x720(n_windows=21, keep_truth=True))):
+        prm = eb.ebof_default_params(ev.width, ev.height)
+        st, s = eb.ebof_stream_create(prm, local)
+        eb.check(st, "ebof_stream_create")
+        W, H = ev.width, ev.height
+        flows = []
+        for k in range(ev.n_windows):
+            x, y, t, _, tb, te = ev.window(k)
+            fl = torch.empty((2, H, W), dtype=torch.float32, device=dev)
+            eb.check(eb.ebof_process_window(s, torch.from_numpy(x).to(dev),
+                                            torch.from_numpy(y).to(dev),
+                                            torch.from_numpy(t).to(dev), None, tb, te, fl))
+            flows.append(fl)
+        torch.cuda.synchronize(dev)
+        errs, outl, zero = [], [], []
+        for k in range(1, ev.n_windows):
+            U = flows[k].cpu().numpy().astype(np.float64)
+            G, m = ev.true_flow(k)
+            e = np.hypot(U[0] - G[0], U[1] - G[1])[m]
+            mag = np.hypot(G[0], G[1])[m]
+            errs.append(e.mean())
+            outl.append(((e > 3.0) & (e > 0.05 * mag)).mean())
+            zero.append(mag.mean())
+        s.close()
+        out[name] = {"aee_px": float(np.mean(errs)), "outliers_pct": 100 * float(np.mean(outl)),
+                     "zero_flow_aee_px": float(np.mean(zero)), "frames": ev.n_windows - 1}
+    return out
+
+
 def run_serving(args, eb, torch, dev, rank):
     """64 camera streams served as their windows arrive: 32 at 346x260, 16 at
     640x480 and 16 at 1280x720 (4:2:2).  Each stream delivers windows as a
@@ -768,6 +808,7 @@ def main():
                "note": "FWL = var(events moved back along the flow) / var(events unmoved), "
                        "with polarity; > 1 beats the zero flow"}
     del scr
+    quality["vs_ground_truth"] = ground_truth_quality(eb, torch, dev, local)
 
     # FP16 storage of surfaces, pyramid levels and gradients (same stream)
     fp16 = None

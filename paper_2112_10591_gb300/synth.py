@@ -19,8 +19,14 @@ Recipe (one line per knob):
     tau = k + (t - t_k) / dt, rounded with floor(v + 0.5); events that land
     off the image are drawn again;
   * noise events are uniform over the image and the window;
-  * polarity is +1 or -1 with equal probability (the method ignores it);
+  * polarity: every edge has a contrast sign (alternating over the scene's
+    segments) that 90 % of its events carry; noise events are +1 or -1 with
+    equal odds (the method ignores polarity; the FWL metric uses it);
   * events of one window are sorted by timestamp, as a sensor emits them.
+
+With ``keep_truth`` a stream also keeps, per event, the segment and the
+point on it that produced the event, from which ``true_flow`` gives the
+ground-truth displacement of every edge pixel between two windows.
 """
 from __future__ import annotations
 
@@ -49,6 +55,9 @@ class EventStream:
     offsets: np.ndarray    # int64  [n_windows + 1]
     t_begin: np.ndarray    # int64  [n_windows]
     dt: int
+    seg: np.ndarray = None     # int32 [N] producing segment, -1 for noise (keep_truth)
+    frac: np.ndarray = None    # float64 [N] point on the segment (keep_truth)
+    scene: "_Scene" = None     # the moving scene (keep_truth)
 
     @property
     def n_windows(self) -> int:
@@ -59,6 +68,35 @@ class EventStream:
         tb = int(self.t_begin[k])
         return (self.x[a:b], self.y[a:b], self.t[a:b], self.p[a:b],
                 tb, tb + self.dt)
+
+    def true_flow(self, k: int):
+        """Ground truth of the flow from window k - 1 to window k (k >= 1):
+        at every pixel where window k - 1 has an edge event, the mean over
+        those events of how far the scene point that produced the event
+        moves in one window (its position at the same phase of window k
+        minus its position at the event).  Returns (flow [2][H][W] float64,
+        mask [H][W] bool); flow is 0 where mask is False.  Needs a stream
+        made with keep_truth."""
+        if self.seg is None or k < 1:
+            raise ValueError("true_flow needs keep_truth and k >= 1")
+        a, b = int(self.offsets[k - 1]), int(self.offsets[k])
+        seg = self.seg[a:b]
+        m = seg >= 0
+        seg = seg[m].astype(np.int64)
+        frac = self.frac[a:b][m]
+        f = (self.t[a:b][m] - self.t_begin[k - 1]) / self.dt
+        x0, y0 = _place(self.scene, seg, frac, k - 1, f)
+        x1, y1 = _place(self.scene, seg, frac, k, f)
+        W, H = self.width, self.height
+        pix = self.y[a:b][m].astype(np.int64) * W + self.x[a:b][m].astype(np.int64)
+        cnt = np.bincount(pix, minlength=W * H)
+        u = np.bincount(pix, weights=x1 - x0, minlength=W * H)
+        v = np.bincount(pix, weights=y1 - y0, minlength=W * H)
+        mask = cnt > 0
+        flow = np.zeros((2, W * H))
+        flow[0, mask] = u[mask] / cnt[mask]
+        flow[1, mask] = v[mask] / cnt[mask]
+        return flow.reshape(2, H, W), mask.reshape(H, W)
 
 
 @dataclasses.dataclass
@@ -97,7 +135,7 @@ def _draw_window(rng, scene: _Scene, W: int, H: int, k: int, n_events: int,
     length = np.hypot(*(scene.p1 - scene.p0).T)
     cdf = np.cumsum(length / length.sum())
     cdf[-1] = 1.0
-    xs, ys, ts, ss = [], [], [], []
+    xs, ys, ts, ss, fs = [], [], [], [], []
     need = n_edge
     while need > 0:
         m = int(need * 1.3) + 64
@@ -114,15 +152,18 @@ def _draw_window(rng, scene: _Scene, W: int, H: int, k: int, n_events: int,
         ys.append(iy.astype(np.uint16))
         ts.append(t)
         ss.append(seg[ok][:need])
+        fs.append(s[ok][:need])
         need -= len(t)
     xs.append(rng.integers(0, W, size=n_noise).astype(np.uint16))
     ys.append(rng.integers(0, H, size=n_noise).astype(np.uint16))
     ts.append(rng.integers(t0, t0 + dt, size=n_noise, dtype=np.int64))
     ss.append(np.full(n_noise, -1))
+    fs.append(np.zeros(n_noise))
     x = np.concatenate(xs)
     y = np.concatenate(ys)
     t = np.concatenate(ts)
     seg = np.concatenate(ss)[:n_events]
+    frac = np.concatenate(fs)[:n_events]
     order = np.argsort((t - t0).astype(np.uint32), kind="stable")
     # polarity: every edge has a contrast sign (alternating over the scene's
     # segments) that 90 % of its events carry; noise events are +1 or -1
@@ -130,29 +171,37 @@ def _draw_window(rng, scene: _Scene, W: int, H: int, k: int, n_events: int,
     u = rng.random(n_events)[np.argsort(order, kind="stable")]
     sign = np.where(seg % 2 == 0, 1, -1)
     p = np.where(seg < 0, np.where(u < 0.5, 1, -1), np.where(u < 0.9, sign, -sign))
-    return x[order], y[order], t[order], p[order].astype(np.int8)
+    return (x[order], y[order], t[order], p[order].astype(np.int8), seg[order].astype(np.int32),
+            frac[order])
 
 
-def _assemble(rng, scene, W, H, counts, noise_frac, dt, t_start=0):
-    xs, ys, ts, ps = [], [], [], []
+def _assemble(rng, scene, W, H, counts, noise_frac, dt, t_start=0, keep_truth=False):
+    xs, ys, ts, ps, ss, fs = [], [], [], [], [], []
     offsets = [0]
     t_begin = []
     for k, n in enumerate(counts):
         t0 = t_start + k * dt
-        x, y, t, p = _draw_window(rng, scene, W, H, k, int(n), noise_frac, t0, dt)
+        x, y, t, p, sg, fr = _draw_window(rng, scene, W, H, k, int(n), noise_frac, t0, dt)
         xs.append(x); ys.append(y); ts.append(t); ps.append(p)
+        if keep_truth:
+            ss.append(sg); fs.append(fr)
         offsets.append(offsets[-1] + len(x))
         t_begin.append(t0)
-    return EventStream(W, H, np.concatenate(xs), np.concatenate(ys),
-                       np.concatenate(ts), np.concatenate(ps),
-                       np.asarray(offsets, np.int64),
-                       np.asarray(t_begin, np.int64), dt)
+    ev = EventStream(W, H, np.concatenate(xs), np.concatenate(ys),
+                     np.concatenate(ts), np.concatenate(ps),
+                     np.asarray(offsets, np.int64),
+                     np.asarray(t_begin, np.int64), dt)
+    if keep_truth:
+        ev.seg = np.concatenate(ss)
+        ev.frac = np.concatenate(fs)
+        ev.scene = scene
+    return ev
 
 
 def translating_segments(width=346, height=260, n_windows=2, n_segments=40,
                          length=(10.0, 60.0), velocity=(3.0, -1.5),
                          events_per_window=20_000, noise_frac=0.05, seed=0,
-                         dt=WINDOW_US) -> EventStream:
+                         dt=WINDOW_US, keep_truth=False) -> EventStream:
     """Low-resolution stream: line segments translating at one velocity.
 
     Default arguments give the 346x260 single-window workload: two windows of
@@ -171,14 +220,14 @@ def translating_segments(width=346, height=260, n_windows=2, n_segments=40,
     scene = _Scene(start, end, np.zeros(n_segments, np.int64),
                    np.zeros((1, 2)), theta, shift)
     return _assemble(rng, scene, width, height, [events_per_window] * K,
-                     noise_frac, dt)
+                     noise_frac, dt, keep_truth=keep_truth)
 
 
 def rigid_objects(width=1280, height=720, n_windows=201, n_objects=12,
                   n_edges=300, radius=(40.0, 200.0), extra_length=(10.0, 120.0),
                   max_rot_deg=2.0, max_shift=20.0, events=(150_000, 400_000),
                   noise_frac=0.03, seed=1, dt=WINDOW_US,
-                  lognormal_counts=False) -> EventStream:
+                  lognormal_counts=False, keep_truth=False) -> EventStream:
     """High-resolution stream: rigid objects with their own affine motion.
 
     Default arguments give the 1280x720 stream workload: 201 windows (200
@@ -237,7 +286,7 @@ def rigid_objects(width=1280, height=720, n_windows=201, n_objects=12,
         counts = np.clip(np.round(rng.lognormal(mu, sig, K)), lo, hi).astype(np.int64)
     else:
         counts = rng.integers(events[0], events[1] + 1, size=K)
-    return _assemble(rng, scene, width, height, counts, noise_frac, dt)
+    return _assemble(rng, scene, width, height, counts, noise_frac, dt, keep_truth=keep_truth)
 
 
 def workload_346x260(seed=0) -> EventStream:
@@ -245,9 +294,9 @@ def workload_346x260(seed=0) -> EventStream:
     return translating_segments(seed=seed)
 
 
-def workload_1280x720(seed=1, n_windows=201) -> EventStream:
+def workload_1280x720(seed=1, n_windows=201, keep_truth=False) -> EventStream:
     """1280x720, 201 windows of 150k-400k events: 200 flow frames."""
-    return rigid_objects(seed=seed, n_windows=n_windows)
+    return rigid_objects(seed=seed, n_windows=n_windows, keep_truth=keep_truth)
 
 
 def random_edge_events(rng, width, height, n, t_begin=0, dt=WINDOW_US,

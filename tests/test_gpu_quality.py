@@ -1,0 +1,66 @@
+"""Flow quality against the generator's ground truth (§IV-C's AEE and
+outlier share) on the GPU, beside the FP64 oracle's on the same windows.
+Sanity checks: the GPU's figures follow the oracle's (parity), the flow beats
+the zero flow, and on the translating 346x260 scene it recovers the motion
+to well under a pixel."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_10591_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def eb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_10591_gb300 as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _aee(U, G, m):
+    e = np.hypot(U[0] - G[0], U[1] - G[1])[m]
+    mag = np.hypot(G[0], G[1])[m]
+    return float(e.mean()), float(((e > 3.0) & (e > 0.05 * mag)).mean())
+
+
+@pytest.mark.parametrize("which", ["346x260", "1280x720"])
+def test_aee_against_ground_truth(eb, which):
+    if which == "346x260":
+        ev = synth.translating_segments(keep_truth=True)
+    else:
+        ev = synth.workload_1280x720(n_windows=2, keep_truth=True)
+    prm = eb.ebof_default_params(ev.width, ev.height)
+    st, s = eb.ebof_stream_create(prm, 0)
+    eb.check(st)
+    W, H = ev.width, ev.height
+    flow = torch.empty((2, H, W), device="cuda:0")
+    for k in range(2):
+        x, y, t, _, tb, te = ev.window(k)
+        eb.ebof_process_window(s, dev(x), dev(y), dev(t), None, tb, te, flow)
+    torch.cuda.synchronize()
+    s.close()
+    Ug = flow.cpu().numpy().astype(np.float64)
+    w0, w1 = ev.window(0), ev.window(1)
+    _, _, Uo = oracle.process_pair(W, H, (w0[0], w0[1], w0[2], w0[4], w0[5]),
+                                   (w1[0], w1[1], w1[2], w1[4], w1[5]), levels=prm.levels,
+                                   patch=prm.patch, stride=prm.stride)
+    G, m = ev.true_flow(1)
+    ag, og = _aee(Ug, G, m)
+    ao, oo = _aee(Uo, G, m)
+    zero, _ = _aee(np.zeros_like(Ug), G, m)
+    print("%s: AEE GPU %.3f oracle %.3f zero %.3f; outliers GPU %.3f oracle %.3f"
+          % (which, ag, ao, zero, og, oo))
+    assert abs(ag - ao) <= 0.05 and abs(og - oo) <= 0.01
+    assert ag < zero
+    if which == "346x260":
+        assert ag <= 0.6 and og == 0.0

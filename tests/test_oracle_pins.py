@@ -265,6 +265,28 @@ def test_fwl_prefers_the_true_flow():
     assert good > 1.0 > bad
 
 
+# ---------------------------------------------------------------- §IV-C AEE vs ground truth
+def _aee(U, G, m):
+    e = np.hypot(U[0] - G[0], U[1] - G[1])[m]
+    mag = np.hypot(G[0], G[1])[m]
+    return e.mean(), ((e > 3.0) & (e > 0.05 * mag)).mean()
+
+
+def test_flow_recovers_generator_motion_on_translating_scene():
+    # the whole path on the 346x260 workload against the generator's own
+    # motion at the previous window's event pixels: AEE (§IV-C) well below
+    # the zero flow's and no outliers (error > 3 px and > 5 % of the motion)
+    ev = synth.translating_segments(keep_truth=True)
+    w0, w1 = ev.window(0), ev.window(1)
+    _, _, U = oracle.process_pair(ev.width, ev.height, (w0[0], w0[1], w0[2], w0[4], w0[5]),
+                                  (w1[0], w1[1], w1[2], w1[4], w1[5]))
+    G, m = ev.true_flow(1)
+    assert np.allclose(G[0][m], 3.0) and np.allclose(G[1][m], -1.5)
+    aee, out = _aee(U, G, m)
+    zero, _ = _aee(np.zeros_like(U), G, m)
+    assert aee <= 0.6 and out == 0.0 and zero > 3.0, (aee, out, zero)
+
+
 # ---------------------------------------------------------------- pyramid
 def test_downsample_and_gradients_closed_forms():
     I = np.arange(30, dtype=np.float64).reshape(5, 6)
