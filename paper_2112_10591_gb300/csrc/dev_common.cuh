@@ -31,6 +31,23 @@ __device__ __forceinline__ float bilinear(const T *__restrict__ I, int w, int h,
     return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
 }
 
+// The same sample with 32-bit offsets (images of at most 2^31 elements).
+template <typename T>
+__device__ __forceinline__ float bilinear_i(const T *__restrict__ I, int w, int h, int pitch,
+                                            float x, float y)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
+    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
+    const float xf = floorf(x), yf = floorf(y);
+    const int x0 = (int)xf, y0 = (int)yf;
+    const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+    const float fx = x - xf, fy = y - yf;
+    const T *r0 = I + y0 * pitch, *r1 = I + y1 * pitch;
+    const float a = ldp(&r0[x0]), b = ldp(&r0[x1]);
+    const float c = ldp(&r1[x0]), d = ldp(&r1[x1]);
+    return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
+}
+
 // Robust penaliser derivative Psi'(s^2) = 1 / (2 sqrt(s^2 + eps^2)), eps = 1e-3.
 __device__ __forceinline__ float psi_prime(float s2) { return 0.5f * rsqrtf(s2 + 1e-6f); }
 

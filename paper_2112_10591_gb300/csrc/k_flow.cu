@@ -193,7 +193,7 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             const bool act = c0 + k < PS;
-            const size_t p = (size_t)(y0 + r) * pitch + x0 + (act ? c0 + k : 0);
+            const int p = (y0 + r) * pitch + x0 + (act ? c0 + k : 0);
             Tm[r][k] = act ? ldp(&I0[p]) : 0.0f;
             GX[r][k] = act ? ldp(&I0x[p]) : 0.0f;
             GY[r][k] = act ? ldp(&I0y[p]) : 0.0f;
@@ -240,7 +240,7 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         if (fast) {
             // columns c0 .. c0 + CPL of the window (the last one only as the
             // right neighbour); a column beyond PS is never read
-            const T *pp = I1 + (size_t)sy0 * pitch + sx0 + c0;
+            const T *pp = I1 + sy0 * pitch + sx0 + c0;
             float hp[CPL];
             {
                 float s[CPL + 1];
@@ -251,7 +251,7 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
             }
 #pragma unroll
             for (int r = 0; r < PS; ++r) {
-                const T *q = pp + (size_t)(r + 1) * pitch;
+                const T *q = pp + (r + 1) * pitch;
                 float s[CPL + 1];
 #pragma unroll
                 for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS ? ldp(&q[k]) : 0.0f;
@@ -271,8 +271,8 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     if (c0 + k >= PS) continue;
-                    const float wv = bilinear(I1, w, h, pitch, (float)(x0 + c0 + k) + u,
-                                              (float)(y0 + r) + v);
+                    const float wv = bilinear_i(I1, w, h, pitch, (float)(x0 + c0 + k) + u,
+                                                (float)(y0 + r) + v);
                     const float res = wv - Tm[r][k];
                     b1 += GX[r][k] * res;
                     b2 += GY[r][k] * res;
@@ -315,11 +315,12 @@ __global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ 
     const T *I0 = I0b + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
     const float *up = upb + (size_t)f * upfs;
     const int np = npx * npy;
+    const float *vp = up + np;
     int ilo, ihi, jlo, jhi;
     bool ilast, jlast;
     cover_range(x, w, ps, stride, npx, ilo, ihi, ilast);
     cover_range(y, h, ps, stride, npy, jlo, jhi, jlast);
-    const float i0 = ldp(&I0[(size_t)y * pitch + x]);
+    const float i0 = ldp(&I0[y * pitch + x]);
     float nu = 0.0f, nv = 0.0f, den = 0.0f;
     for (int jj = jlo; jj <= jhi + 1; ++jj) {
         int j = jj;
@@ -328,16 +329,16 @@ __global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ 
             int i = ii;
             if (ii == ihi + 1) { if (!ilast) break; i = npx - 1; }
             const int id = j * npx + i;
-            const float u = up[id], v = up[(size_t)np + id];
-            const float r = bilinear(I1, w, h, pitch, (float)x + u, (float)y + v) - i0;
+            const float u = up[id], v = vp[id];
+            const float r = bilinear_i(I1, w, h, pitch, (float)x + u, (float)y + v) - i0;
             const float lam = 1.0f / fmaxf(1.0f, fabsf(r));
             nu += lam * u; nv += lam * v; den += lam;
         }
     }
     float *U = Ub + (size_t)f * ufs;
-    const size_t p = (size_t)y * pitch + x;
+    const int p = y * pitch + x;
     U[p] = den > 0.0f ? nu / den : 0.0f;
-    U[plane + p] = den > 0.0f ? nv / den : 0.0f;
+    (U + plane)[p] = den > 0.0f ? nv / den : 0.0f;
 }
 
 // ---------------------------------------------------------------- A8

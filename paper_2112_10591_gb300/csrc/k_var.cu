@@ -232,9 +232,11 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     const int f = blockIdx.z;
     const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
     const int ex0 = tx0 - 2, ey0 = ty0 - 2, dx0 = tx0 - 1, dy0 = ty0 - 1;
+    // frame base pointers once; offsets within a frame fit in 32 bits
     const size_t po = (size_t)f * pfs;
     const T *I1 = I1b + po;
     const float *U = Ub + (size_t)f * ufs;
+    const float *V = U + plane;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 16 threads, one per tile pixel
 
     const int t = ty * kAX + tx;
@@ -244,9 +246,9 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         const int gx = ex0 + lx, gy = ey0 + ly;
         float u = 0.0f, v = 0.0f;
         if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-            const size_t p = (size_t)gy * pitch + gx;
+            const int p = gy * pitch + gx;
             u = U[p];
-            v = U[plane + p];
+            v = V[p];
         }
         sU[ly][lx] = u;
         sV[ly][lx] = v;
@@ -257,7 +259,7 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         const int gx = ex0 + lx, gy = ey0 + ly;
         float wv = 0.0f;
         if (gx >= 0 && gx < w && gy >= 0 && gy < h)
-            wv = bilinear(I1, w, h, pitch, (float)gx + sU[ly][lx], (float)gy + sV[ly][lx]);
+            wv = bilinear_i(I1, w, h, pitch, (float)gx + sU[ly][lx], (float)gy + sV[ly][lx]);
         sW[ly][lx] = wv;
     }
     __syncthreads();
@@ -276,21 +278,22 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
 
     const int gx = tx0 + threadIdx.x, gy = ty0 + threadIdx.y;
     if (gx >= w || gy >= h) return;
-    const size_t p = (size_t)gy * pitch + gx;
+    const int p = gy * pitch + gx;
     const PixelSystem ps = pixel_system(
         &sIx[0][0], &sIy[0][0], &sAs[0][0], kADX, dx0, dy0, &sW[0][0], &sU[0][0], &sV[0][0], kAEX,
-        (gy - ey0) * kAEX + (gx - ex0), gx, gy, w, h, ldp(&I0b[po + p]), ldp(&I0xb[po + p]),
-        ldp(&I0yb[po + p]), delta, gamma);
+        (gy - ey0) * kAEX + (gx - ex0), gx, gy, w, h, ldp(&(I0b + po)[p]), ldp(&(I0xb + po)[p]),
+        ldp(&(I0yb + po)[p]), delta, gamma);
+    const int pl = (int)plane;
     float *cf = coefb + (size_t)f * cfs + p;
-    cf[kCI11 * plane] = ps.i11;
-    cf[kCI22 * plane] = ps.i22;
-    cf[kCA12 * plane] = ps.a12;
-    cf[kCB1 * plane] = ps.b1;
-    cf[kCB2 * plane] = ps.b2;
-    cf[kCWL * plane] = ps.cl;
-    cf[kCWR * plane] = ps.cr;
-    cf[kCWU * plane] = ps.cu;
-    cf[kCWD * plane] = ps.cd;
+    cf[kCI11 * pl] = ps.i11;
+    cf[kCI22 * pl] = ps.i22;
+    cf[kCA12 * pl] = ps.a12;
+    cf[kCB1 * pl] = ps.b1;
+    cf[kCB2 * pl] = ps.b2;
+    cf[kCWL * pl] = ps.cl;
+    cf[kCWR * pl] = ps.cr;
+    cf[kCWU * pl] = ps.cu;
+    cf[kCWD * pl] = ps.cd;
 }
 
 __global__ void __launch_bounds__(kVThreads, 1)
@@ -305,6 +308,7 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
     const float *Uin = Uinb + (size_t)f * ufs;
     float *Uout = Uoutb + (size_t)f * ufs;
     const float *cf = coefb + (size_t)f * cfs;
+    const int pl = (int)plane;  // offsets within a frame fit in 32 bits
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     float i11[kVS][2], i22[kVS][2], a12[kVS][2], b1[kVS][2], b2[kVS][2];
     float wl[kVS][2], wr[kVS][2], wu[kVS][2], wd[kVS][2];
@@ -317,16 +321,16 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
             dv[r][q] = 0.0f;
             const int gx = rx0 + 2 * lane + q, gy = ry0 + wp * kVS + r;
             const bool in = gx >= 0 && gx < w && gy >= 0 && gy < h;
-            const size_t p = in ? (size_t)gy * pitch + gx : 0;
-            i11[r][q] = in ? cf[kCI11 * plane + p] : 0.0f;
-            i22[r][q] = in ? cf[kCI22 * plane + p] : 0.0f;
-            a12[r][q] = in ? cf[kCA12 * plane + p] : 0.0f;
-            b1[r][q] = in ? cf[kCB1 * plane + p] : 0.0f;
-            b2[r][q] = in ? cf[kCB2 * plane + p] : 0.0f;
-            wl[r][q] = in ? cf[kCWL * plane + p] : 0.0f;
-            wr[r][q] = in ? cf[kCWR * plane + p] : 0.0f;
-            wu[r][q] = in ? cf[kCWU * plane + p] : 0.0f;
-            wd[r][q] = in ? cf[kCWD * plane + p] : 0.0f;
+            const float *c = cf + (in ? gy * pitch + gx : 0);
+            i11[r][q] = in ? c[kCI11 * pl] : 0.0f;
+            i22[r][q] = in ? c[kCI22 * pl] : 0.0f;
+            a12[r][q] = in ? c[kCA12 * pl] : 0.0f;
+            b1[r][q] = in ? c[kCB1 * pl] : 0.0f;
+            b2[r][q] = in ? c[kCB2 * pl] : 0.0f;
+            wl[r][q] = in ? c[kCWL * pl] : 0.0f;
+            wr[r][q] = in ? c[kCWR * pl] : 0.0f;
+            wu[r][q] = in ? c[kCWU * pl] : 0.0f;
+            wd[r][q] = in ? c[kCWD * pl] : 0.0f;
         }
 
     // red-black SOR; red = (x + y) even, first.  kVS is even, so the parity
@@ -346,9 +350,9 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
             const int gx = rx0 + lx, gy = ry0 + ly;
             if (lx < R || lx >= R + tile || ly < R || ly >= R + tile || gx >= w || gy >= h)
                 continue;
-            const size_t p = (size_t)gy * pitch + gx;
+            const int p = gy * pitch + gx;
             Uout[p] = Uin[p] + du[r][q];
-            Uout[plane + p] = Uin[plane + p] + dv[r][q];
+            (Uout + plane)[p] = (Uin + plane)[p] + dv[r][q];
         }
 }
 
@@ -468,9 +472,9 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
                 const int gx = rx0 + lx, gy = ry0 + ly;
                 if (lx < R || lx >= R + tile || ly < R || ly >= R + tile || gx >= w || gy >= h)
                     continue;
-                const size_t p = (size_t)gy * pitch + gx;
+                const int p = gy * pitch + gx;
                 Uout[p] = Uin[p] + du[rr][q];
-                Uout[plane + p] = Uin[plane + p] + dv[rr][q];
+                (Uout + plane)[p] = (Uin + plane)[p] + dv[rr][q];
             }
     }
 }
