@@ -244,22 +244,15 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     for (int i = t; i < kAEX * kAEY; i += kN) {
         const int lx = i % kAEX, ly = i / kAEX;
         const int gx = ex0 + lx, gy = ey0 + ly;
-        float u = 0.0f, v = 0.0f;
+        float u = 0.0f, v = 0.0f, wv = 0.0f;
         if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
             const int p = gy * pitch + gx;
             u = U[p];
             v = V[p];
+            wv = bilinear_i(I1, w, h, pitch, (float)gx + u, (float)gy + v);
         }
         sU[ly][lx] = u;
         sV[ly][lx] = v;
-    }
-    __syncthreads();
-    for (int i = t; i < kAEX * kAEY; i += kN) {
-        const int lx = i % kAEX, ly = i / kAEX;
-        const int gx = ex0 + lx, gy = ey0 + ly;
-        float wv = 0.0f;
-        if (gx >= 0 && gx < w && gy >= 0 && gy < h)
-            wv = bilinear_i(I1, w, h, pitch, (float)gx + sU[ly][lx], (float)gy + sV[ly][lx]);
         sW[ly][lx] = wv;
     }
     __syncthreads();
