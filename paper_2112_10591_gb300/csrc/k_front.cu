@@ -272,7 +272,7 @@ __device__ __forceinline__ int para(int x, int site, const int32_t *h)
 
 __host__ __device__ __forceinline__ size_t rows_smem_words(int W, int wpr)
 {
-    return 3 * (size_t)W + 32 * (size_t)wpr + 1;
+    return 3 * (size_t)W + 2 * 32 * (size_t)wpr + 1;
 }
 
 // Level-0 intensity of the flow block.  FP32 storage keeps I = 255 d_exp.
@@ -321,7 +321,8 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
     int32_t *stk = h + W;       // envelope sites, per band
     int32_t *res = stk + W;     // D per pixel of the row
     int32_t *cnts = res + W;    // envelope size per band
-    int32_t *anyf = cnts + NB;  // row has an edge pixel
+    int32_t *minh = cnts + NB;  // smallest h of the band's sites (a lower bound of its parabolas)
+    int32_t *anyf = minh + NB;  // row has an edge pixel
     const int tr = sub * 32 + lane;  // thread index within the row
     const int ginf = W + H;
     if (tr == 0) *anyf = 0;
@@ -342,15 +343,19 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
     const int B = (W + NB - 1) / NB;
     const int bi = tr;  // this lane's band
     const int a = min(W, bi * B), b = min(W, a + B);
-    int cnt = 0;
+    int cnt = 0, mh = 0x7fffffff;
     if (any) {
         for (int q = a; q < b; ++q) {
             if (h[q] < 0) continue;
+            mh = min(mh, h[q]);
             while (cnt >= 2 && hidden(stk[a + cnt - 2], stk[a + cnt - 1], q, h)) --cnt;
             stk[a + cnt++] = q;
         }
     }
-    if (valid) cnts[bi] = cnt;
+    if (valid) {
+        cnts[bi] = cnt;
+        minh[bi] = mh;
+    }
     __syncthreads();
 
     if (any) {
@@ -367,7 +372,8 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
                 const int cM = cnts[M];
                 if (cM == 0) continue;
                 const int gap = M < bi ? x - (mb - 1) : (M > bi ? ma - x : 0);
-                if (M != bi && gap * gap >= best) continue;
+                // no parabola of band M is below gap^2 + its smallest h
+                if (M != bi && gap * gap + minh[M] >= best) continue;
                 const int32_t *sl = stk + ma;
                 int pk = ptr[k];
                 int cur = para(x, sl[pk], h);
@@ -388,11 +394,11 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
                     if (M < 0 || M >= NB) continue;
                     const int ma = min(W, M * B), mb = min(W, ma + B);
                     if (ma >= mb) continue;
-                    const long long gap = side ? (long long)(ma - x) : (long long)(x - (mb - 1));
+                    const int gap = side ? ma - x : x - (mb - 1);  // < 2^14: gap^2 fits
                     if (gap * gap >= best) continue;
                     progress = true;
                     const int cM = cnts[M];
-                    if (cM == 0) continue;
+                    if (cM == 0 || gap * gap + minh[M] >= best) continue;
                     const int32_t *sl = stk + ma;
                     int lo = 0, hi = cM - 1;
                     while (lo < hi) {
