@@ -44,6 +44,7 @@ constexpr int kVS = 4;                   // rows per thread strip
 constexpr int kVWarps = kVR / kVS;       // warps per block (stacked strips)
 constexpr int kVThreads = 32 * kVWarps;  // 512
 constexpr size_t kVSmemFloats = 2 * 2 * kVWarps * 2 * 64;  // strip-end exchange
+constexpr size_t kVSmemFloats2 = 2 * 2 * 32 * 2 * 64;       // the same for 32 warps
 enum { kCI11 = 0, kCI22, kCA12, kCB1, kCB2, kCWL, kCWR, kCWU, kCWD, kCPlanes };
 
 constexpr int kTmaBoxW = kVR + 4;  // region columns + the rounding of the box start
@@ -57,23 +58,24 @@ constexpr int kAEX = kAX + 4, kAEY = kAY + 4;  // staging window: tile + 2 px
 constexpr int kADX = kAX + 2, kADY = kAY + 2;  // derivative window: tile + 1 px
 constexpr unsigned kFull = 0xffffffffu;
 
-// One red-black half sweep of colour C on a thread's 2-column x kVS-row
+// One red-black half sweep of colour C on a thread's 2-column x VS-row
 // strip; P is the parity of (x + y) at the strip's first pixel.  Pixel
 // (row r, column q) has colour (P + r + q) & 1.  The strip's first and last
 // rows are read by the warps above and below from xch (double-buffered by
-// half sweep, so one barrier per half sweep suffices).
-template <int P, int C>
-__device__ __forceinline__ void sor_half(float (&du)[kVS][2], float (&dv)[kVS][2],
-                                         const float (&i11)[kVS][2], const float (&i22)[kVS][2],
-                                         const float (&a12)[kVS][2], const float (&b1)[kVS][2],
-                                         const float (&b2)[kVS][2], const float (&wl)[kVS][2],
-                                         const float (&wr)[kVS][2], const float (&wu)[kVS][2],
-                                         const float (&wd)[kVS][2], const float *xtop,
+// half sweep, so one barrier per half sweep suffices).  WARPS strips are
+// stacked in a block.
+template <int VS, int WARPS, int P, int C>
+__device__ __forceinline__ void sor_half(float (&du)[VS][2], float (&dv)[VS][2],
+                                         const float (&i11)[VS][2], const float (&i22)[VS][2],
+                                         const float (&a12)[VS][2], const float (&b1)[VS][2],
+                                         const float (&b2)[VS][2], const float (&wl)[VS][2],
+                                         const float (&wr)[VS][2], const float (&wu)[VS][2],
+                                         const float (&wd)[VS][2], const float *xtop,
                                          const float *xbot, int lane, int wp, float omega)
 {
     const float om1 = 1.0f - omega;
 #pragma unroll
-    for (int r = 0; r < kVS; ++r) {
+    for (int r = 0; r < VS; ++r) {
         const int q = (C + P + r) & 1;  // compile-time after unrolling
         float lu, lv, ru, rv;
         if (q == 0) {
@@ -100,12 +102,12 @@ __device__ __forceinline__ void sor_half(float (&du)[kVS][2], float (&dv)[kVS][2
             uu = wp > 0 ? xbot[((wp - 1) * 2 + 0) * 64 + col] : 0.0f;
             uv = wp > 0 ? xbot[((wp - 1) * 2 + 1) * 64 + col] : 0.0f;
         }
-        if (r < kVS - 1) {
+        if (r < VS - 1) {
             dnu = du[r + 1][q];
             dnv = dv[r + 1][q];
         } else {
-            dnu = wp < kVWarps - 1 ? xtop[((wp + 1) * 2 + 0) * 64 + col] : 0.0f;
-            dnv = wp < kVWarps - 1 ? xtop[((wp + 1) * 2 + 1) * 64 + col] : 0.0f;
+            dnu = wp < WARPS - 1 ? xtop[((wp + 1) * 2 + 0) * 64 + col] : 0.0f;
+            dnv = wp < WARPS - 1 ? xtop[((wp + 1) * 2 + 1) * 64 + col] : 0.0f;
         }
         const float nu = om1 * du[r][q] +
                          omega * (b1[r][q] + wl[r][q] * lu + wr[r][q] * ru + wu[r][q] * uu +
@@ -118,31 +120,45 @@ __device__ __forceinline__ void sor_half(float (&du)[kVS][2], float (&dv)[kVS][2
     }
 }
 
-template <int P>
-__device__ __forceinline__ void sor_sweeps(float (&du)[kVS][2], float (&dv)[kVS][2],
-                                           const float (&i11)[kVS][2], const float (&i22)[kVS][2],
-                                           const float (&a12)[kVS][2], const float (&b1)[kVS][2],
-                                           const float (&b2)[kVS][2], const float (&wl)[kVS][2],
-                                           const float (&wr)[kVS][2], const float (&wu)[kVS][2],
-                                           const float (&wd)[kVS][2], float *xch, int lane, int wp,
-                                           int n_half, float omega)
+// n_half half sweeps, red first.  pw = parity of (x + y) at this warp's
+// strip start (block-uniform when VS is even, alternating per warp when VS
+// is odd); the branch on it is warp-uniform and every barrier is outside it.
+template <int VS, int WARPS>
+__device__ __forceinline__ void sor_sweeps(float (&du)[VS][2], float (&dv)[VS][2],
+                                           const float (&i11)[VS][2], const float (&i22)[VS][2],
+                                           const float (&a12)[VS][2], const float (&b1)[VS][2],
+                                           const float (&b2)[VS][2], const float (&wl)[VS][2],
+                                           const float (&wr)[VS][2], const float (&wu)[VS][2],
+                                           const float (&wd)[VS][2], float *xch, int lane, int wp,
+                                           int pw, int n_half, float omega)
 {
     for (int hs = 0; hs < n_half; ++hs) {
         // exchange buffer of this half sweep: [top|bottom][warp][du|dv][64]
-        float *xb = xch + (hs & 1) * (2 * kVWarps * 2 * 64);
-        float *xtop = xb, *xbot = xb + kVWarps * 2 * 64;
+        float *xb = xch + (hs & 1) * (2 * WARPS * 2 * 64);
+        float *xtop = xb, *xbot = xb + WARPS * 2 * 64;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             xtop[(wp * 2 + 0) * 64 + 2 * lane + q] = du[0][q];
             xtop[(wp * 2 + 1) * 64 + 2 * lane + q] = dv[0][q];
-            xbot[(wp * 2 + 0) * 64 + 2 * lane + q] = du[kVS - 1][q];
-            xbot[(wp * 2 + 1) * 64 + 2 * lane + q] = dv[kVS - 1][q];
+            xbot[(wp * 2 + 0) * 64 + 2 * lane + q] = du[VS - 1][q];
+            xbot[(wp * 2 + 1) * 64 + 2 * lane + q] = dv[VS - 1][q];
         }
         __syncthreads();
-        if ((hs & 1) == 0)
-            sor_half<P, 0>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xtop, xbot, lane, wp, omega);
-        else
-            sor_half<P, 1>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xtop, xbot, lane, wp, omega);
+        if (pw == 0) {
+            if ((hs & 1) == 0)
+                sor_half<VS, WARPS, 0, 0>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xtop,
+                                          xbot, lane, wp, omega);
+            else
+                sor_half<VS, WARPS, 0, 1>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xtop,
+                                          xbot, lane, wp, omega);
+        } else {
+            if ((hs & 1) == 0)
+                sor_half<VS, WARPS, 1, 0>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xtop,
+                                          xbot, lane, wp, omega);
+            else
+                sor_half<VS, WARPS, 1, 1>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xtop,
+                                          xbot, lane, wp, omega);
+        }
     }
     __syncthreads();
 }
@@ -289,30 +305,33 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     cf[kCWD * pl] = ps.cd;
 }
 
-__global__ void __launch_bounds__(kVThreads, 1)
+// Region of 64 columns x RH rows, strips of VS rows: RH / VS warps.
+template <int VS, int RH>
+__global__ void __launch_bounds__(32 * (RH / VS), 1)
 var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
                float *__restrict__ Uoutb, size_t ufs, size_t plane,
-               const float *__restrict__ coefb, size_t cfs, int R, int tile, int n_half,
-               float omega)
+               const float *__restrict__ coefb, size_t cfs, int R, int n_half, float omega)
 {
+    constexpr int WARPS = RH / VS;
     extern __shared__ float xch[];  // strip-end exchange, two buffers
     const int f = blockIdx.z;
-    const int rx0 = blockIdx.x * tile - R, ry0 = blockIdx.y * tile - R;
+    const int tile_x = kVR - 2 * R, tile_y = RH - 2 * R;
+    const int rx0 = blockIdx.x * tile_x - R, ry0 = blockIdx.y * tile_y - R;
     const float *Uin = Uinb + (size_t)f * ufs;
     float *Uout = Uoutb + (size_t)f * ufs;
     const float *cf = coefb + (size_t)f * cfs;
     const int pl = (int)plane;  // offsets within a frame fit in 32 bits
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    float i11[kVS][2], i22[kVS][2], a12[kVS][2], b1[kVS][2], b2[kVS][2];
-    float wl[kVS][2], wr[kVS][2], wu[kVS][2], wd[kVS][2];
-    float du[kVS][2], dv[kVS][2];
+    float i11[VS][2], i22[VS][2], a12[VS][2], b1[VS][2], b2[VS][2];
+    float wl[VS][2], wr[VS][2], wu[VS][2], wd[VS][2];
+    float du[VS][2], dv[VS][2];
 #pragma unroll
-    for (int r = 0; r < kVS; ++r)
+    for (int r = 0; r < VS; ++r)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             du[r][q] = 0.0f;
             dv[r][q] = 0.0f;
-            const int gx = rx0 + 2 * lane + q, gy = ry0 + wp * kVS + r;
+            const int gx = rx0 + 2 * lane + q, gy = ry0 + wp * VS + r;
             const bool in = gx >= 0 && gx < w && gy >= 0 && gy < h;
             const float *c = cf + (in ? gy * pitch + gx : 0);
             i11[r][q] = in ? c[kCI11 * pl] : 0.0f;
@@ -326,22 +345,19 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
             wd[r][q] = in ? c[kCWD * pl] : 0.0f;
         }
 
-    // red-black SOR; red = (x + y) even, first.  kVS is even, so the parity
-    // of (x + y) at a strip's first pixel is the same for every warp of the
-    // block, and the column of a given colour in a given row is a
-    // compile-time constant once that parity is fixed.
-    if (((rx0 + ry0) & 1) == 0)
-        sor_sweeps<0>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half, omega);
-    else
-        sor_sweeps<1>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half, omega);
+    // red-black SOR; red = (x + y) even, first.  Given the parity of (x + y)
+    // at a strip's first pixel, the column of a given colour in a given row
+    // is a compile-time constant.
+    sor_sweeps<VS, WARPS>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp,
+                          (rx0 + ry0 + wp * VS) & 1, n_half, omega);
 
 #pragma unroll
-    for (int r = 0; r < kVS; ++r)
+    for (int r = 0; r < VS; ++r)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int lx = 2 * lane + q, ly = wp * kVS + r;
+            const int lx = 2 * lane + q, ly = wp * VS + r;
             const int gx = rx0 + lx, gy = ry0 + ly;
-            if (lx < R || lx >= R + tile || ly < R || ly >= R + tile || gx >= w || gy >= h)
+            if (lx < R || lx >= R + tile_x || ly < R || ly >= R + tile_y || gx >= w || gy >= h)
                 continue;
             const int p = gy * pitch + gx;
             Uout[p] = Uin[p] + du[r][q];
@@ -451,12 +467,8 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
         }
         const float *Uin = Uinb + (size_t)f * ufs;
         float *Uout = Uoutb + (size_t)f * ufs;
-        if (((rx0 + ry0) & 1) == 0)
-            sor_sweeps<0>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half,
-                          omega);
-        else
-            sor_sweeps<1>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp, n_half,
-                          omega);
+        sor_sweeps<kVS, kVWarps>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp,
+                                 (rx0 + ry0) & 1, n_half, omega);
 #pragma unroll
         for (int rr = 0; rr < kVS; ++rr)
 #pragma unroll
@@ -533,6 +545,9 @@ void init_var_attributes()
     }
     cudaFuncSetAttribute(var_sor_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kTmaSmemBytes);
+    cudaFuncSetAttribute(var_sor_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kVSmemFloats2 * sizeof(float)));
+
 }
 
 float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y,
@@ -575,14 +590,26 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
             // several regions to walk (batched and grouped windows); both
             // kernels see the same coefficients, so the choice never changes
             // the result
+            // grids of under one wave are latency bound: where 64 x 32
+            // regions of 1-row strips (1024 threads, one pixel update each
+            // per half sweep) still fit in one wave, they replace the 4-row
+            // strips.  Every layout computes the interior's whole-image
+            // iteration, so the choice never changes the result.
+            const dim3 g1((lv.w + tile - 1) / tile, (lv.h + (32 - 2 * R) - 1) / (32 - 2 * R),
+                          frames);
+            const bool small = nsm > 0 && total < nsm;
             if (coef_map && nsm > 0 && total >= 4 * nsm)
                 var_sor_tma_kernel<<<nsm, kVThreads, kTmaSmemBytes, st>>>(
                     *coef_map, lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, R, tile,
                     (int)sgrd.x, (int)sgrd.y, total, n_half, fp.omega, err);
-            else
-                var_sor_kernel<<<sgrd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
+            else if (small && 32 - 2 * R >= 8 && (int)(g1.x * g1.y * g1.z) <= nsm)
+                var_sor_kernel<1, 32><<<g1, 32 * 32, kVSmemFloats2 * sizeof(float), st>>>(
                     lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
-                    coef_frame_stride, R, tile, n_half, fp.omega);
+                    coef_frame_stride, R, n_half, fp.omega);
+            else
+                var_sor_kernel<kVS, kVR><<<sgrd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
+                    lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
+                    coef_frame_stride, R, n_half, fp.omega);
         }
         float *t = a;
         a = b;
