@@ -121,14 +121,13 @@ pyramid_gradients_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
 }
 
 // ---------------------------------------------------------------- A6
-// Group of G lanes per patch; lane c owns the CPL adjacent patch columns
-// c * CPL .. c * CPL + CPL - 1 (those below ps) and keeps their template,
-// gradients and running samples in registers.  The lane count and CPL are
-// chosen so that few lanes idle: ps <= 8: 8 lanes x 1 column; ps 9..12: 4
-// lanes x 3 columns; ps 13..16: 8 lanes x 2 columns.  Patch sums are reduced
-// over the group with xor shuffles, so a warp serves 32 / G patches.  Every
-// lane of a warp runs the same number of iterations (guarded patches iterate
-// on a dummy determinant and are discarded), so the shuffles never diverge.
+// Group of G = CG x RG lanes per patch: lane c owns the CPL adjacent patch
+// columns of column group c % CG (those below ps) over the RPL rows of row
+// group c / CG, and keeps their template, gradients and running samples in
+// registers.  Patch sums are reduced over the group with xor shuffles, so a
+// warp serves 32 / G patches.  Every lane of a warp runs the same number of
+// iterations (guarded patches iterate on a dummy determinant and are
+// discarded), so the shuffles never diverge.
 template <int G>
 __device__ __forceinline__ float group_sum(float v)
 {
@@ -137,21 +136,22 @@ __device__ __forceinline__ float group_sum(float v)
     return v;
 }
 
-// Lanes per patch.  Wide: fewest idle lanes and fewest instructions per
-// patch (ps 9..12: 4 lanes x 3 columns), for levels with enough patches to
-// fill the GPU.  Narrow: one column per lane (ps 9..16: 16 lanes), a third of
-// the serial work per lane, for levels with few patches where latency
-// matters.  The choice depends on the level's patch count only, never on the
-// number of frames in a launch, so batched and single-window results agree
-// bit for bit.
+// Lane layouts per patch size.  Wide: fewest idle lanes and fewest
+// instructions per patch (ps 9..12: 4 lanes x 3 columns), for levels with
+// enough patches to fill the GPU.  Narrow: one column per lane, split into
+// two row halves (32 lanes for ps 9..16), the shortest serial work per lane,
+// for levels with few patches where latency matters.  The choice depends on
+// the level's patch count only, never on the number of frames in a launch,
+// so batched and single-window results agree bit for bit.
 template <int PS>
 struct SearchShape {
-    static constexpr int kWide = PS <= 8 ? 8 : (PS <= 12 ? 4 : 8);
-    static constexpr int kNarrow = PS <= 8 ? 8 : 16;
+    static constexpr int kWideCG = PS <= 8 ? 8 : (PS <= 12 ? 4 : 8);
+    static constexpr int kNarrowCG = PS <= 8 ? 8 : 16;
+    static constexpr int kNarrowRG = PS <= 8 ? 1 : 2;
 };
-constexpr int kWideSearchPatches = 32768;
+constexpr int kWideSearchPatches = 8192;
 
-template <int PS, int G, typename T>
+template <int PS, int CG, int RG, typename T>
 __global__ void __launch_bounds__(128)
 patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
@@ -159,7 +159,9 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     int hc, int pitch_c, size_t plane_c, size_t ucfs, float *__restrict__ upb,
                     size_t upfs, int stride, int iters, float kappa, int *err)
 {
-    constexpr int CPL = (PS + G - 1) / G;
+    constexpr int G = CG * RG;
+    constexpr int CPL = (PS + CG - 1) / CG;
+    constexpr int RPL = (PS + RG - 1) / RG;
     const int f = blockIdx.y;
     const int c = threadIdx.x % G;
     const int np = npx * npy;
@@ -168,7 +170,8 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     const int pid = real ? pid_raw : np - 1;
     const int i = pid % npx, j = pid / npx;
     const int x0 = min(i * stride, w - PS), y0 = min(j * stride, h - PS);
-    const int c0 = c * CPL;  // first column of this lane
+    const int c0 = (c % CG) * CPL;  // first column of this lane
+    const int r0 = (c / CG) * RPL;  // first row of this lane
     const T *I0 = I0b + (size_t)f * pfs, *I0x = I0xb + (size_t)f * pfs;
     const T *I0y = I0yb + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
     if (x0 < 0 || y0 < 0) {  // cannot happen when the level holds a patch
@@ -186,14 +189,14 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     }
 
     // F4: template, mean-normalised gradients, Hessian
-    float Tm[PS][CPL], GX[PS][CPL], GY[PS][CPL];
+    float Tm[RPL][CPL], GX[RPL][CPL], GY[RPL][CPL];
     float sgx = 0.0f, sgy = 0.0f;
 #pragma unroll
-    for (int r = 0; r < PS; ++r)
+    for (int r = 0; r < RPL; ++r)
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
-            const bool act = c0 + k < PS;
-            const int p = (y0 + r) * pitch + x0 + (act ? c0 + k : 0);
+            const bool act = c0 + k < PS && r0 + r < PS;
+            const int p = (y0 + (act ? r0 + r : 0)) * pitch + x0 + (act ? c0 + k : 0);
             Tm[r][k] = act ? ldp(&I0[p]) : 0.0f;
             GX[r][k] = act ? ldp(&I0x[p]) : 0.0f;
             GY[r][k] = act ? ldp(&I0y[p]) : 0.0f;
@@ -205,10 +208,10 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     const float mgx = sgx * inv_n, mgy = sgy * inv_n;
     float h11 = 0.0f, h12 = 0.0f, h22 = 0.0f;
 #pragma unroll
-    for (int r = 0; r < PS; ++r)
+    for (int r = 0; r < RPL; ++r)
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
-            if (c0 + k < PS) { GX[r][k] -= mgx; GY[r][k] -= mgy; }
+            if (c0 + k < PS && r0 + r < PS) { GX[r][k] -= mgx; GY[r][k] -= mgy; }
             h11 += GX[r][k] * GX[r][k]; h12 += GX[r][k] * GY[r][k]; h22 += GY[r][k] * GY[r][k];
         }
     h11 = group_sum<G>(h11); h12 = group_sum<G>(h12); h22 = group_sum<G>(h22);
@@ -238,23 +241,26 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         const bool fast = sx0 >= 0 && sy0 >= 0 && sx0 + PS <= w - 1 && sy0 + PS <= h - 1 &&
                           uc == u && vc == v;
         if (fast) {
-            // columns c0 .. c0 + CPL of the window (the last one only as the
-            // right neighbour); a column beyond PS is never read
-            const T *pp = I1 + sy0 * pitch + sx0 + c0;
+            // columns c0 .. c0 + CPL and rows r0 .. r0 + RPL of the window
+            // (the last of each only as the right / lower neighbour); no
+            // column or row beyond PS is read
+            const T *pp = I1 + (sy0 + r0) * pitch + sx0 + c0;
             float hp[CPL];
             {
                 float s[CPL + 1];
 #pragma unroll
-                for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS ? ldp(&pp[k]) : 0.0f;
+                for (int k = 0; k <= CPL; ++k)
+                    s[k] = c0 + k <= PS && r0 <= PS ? ldp(&pp[k]) : 0.0f;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) hp[k] = s[k] + ax * (s[k + 1] - s[k]);
             }
 #pragma unroll
-            for (int r = 0; r < PS; ++r) {
+            for (int r = 0; r < RPL; ++r) {
                 const T *q = pp + (r + 1) * pitch;
+                const bool rin = r0 + r + 1 <= PS;
                 float s[CPL + 1];
 #pragma unroll
-                for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS ? ldp(&q[k]) : 0.0f;
+                for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS && rin ? ldp(&q[k]) : 0.0f;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     const float hn = s[k] + ax * (s[k + 1] - s[k]);
@@ -267,12 +273,12 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < PS; ++r)
+            for (int r = 0; r < RPL; ++r)
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
-                    if (c0 + k >= PS) continue;
+                    if (c0 + k >= PS || r0 + r >= PS) continue;
                     const float wv = bilinear_i(I1, w, h, pitch, (float)(x0 + c0 + k) + u,
-                                                (float)(y0 + r) + v);
+                                                (float)(y0 + r0 + r) + v);
                     const float res = wv - Tm[r][k];
                     b1 += GX[r][k] * res;
                     b2 += GY[r][k] * res;
@@ -498,13 +504,14 @@ void search_ps(const T *I0, const T *I0x, const T *I0y, const T *I1,
                const Level &lv, size_t pfs, const float *Uc, const Level *lvc, size_t ucfs,
                float *up, size_t upfs, int frames, const FlowParams &fp, int *err, cudaStream_t st)
 {
+    using SS = SearchShape<PS>;
     const int np = lv.npx * lv.npy;
     const bool wide = np >= kWideSearchPatches;
-    const int G = wide ? SearchShape<PS>::kWide : SearchShape<PS>::kNarrow;
+    const int G = wide ? SS::kWideCG : SS::kNarrowCG * SS::kNarrowRG;
     const int per_block = 128 / G;
     dim3 grd((np + per_block - 1) / per_block, frames);
-    auto kern = wide ? patch_search_kernel<PS, SearchShape<PS>::kWide, T>
-                     : patch_search_kernel<PS, SearchShape<PS>::kNarrow, T>;
+    auto kern = wide ? patch_search_kernel<PS, SS::kWideCG, 1, T>
+                     : patch_search_kernel<PS, SS::kNarrowCG, SS::kNarrowRG, T>;
     kern<<<grd, 128, 0, st>>>(
         I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pfs, lv.npx, lv.npy, Uc, lvc ? lvc->w : 0,
         lvc ? lvc->h : 0, lvc ? lvc->pitch : 0, lvc ? lvc->plane : 0, ucfs, up, upfs, fp.stride,
