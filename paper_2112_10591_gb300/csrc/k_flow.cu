@@ -308,7 +308,10 @@ __device__ __forceinline__ void cover_range(int x, int n, int ps, int stride, in
     last = x >= n - ps;
 }
 
-template <typename T>
+// MAXC > 0: at most MAXC covering patches per axis, loops unrolled and
+// predicated so that the patches' loads are in flight together; 0: runtime
+// loops.  The patches are summed in the same order either way.
+template <typename T, int MAXC>
 __global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ I1b,
                                int w, int h, int pitch, size_t pfs, const float *__restrict__ upb,
                                size_t upfs, int npx, int npy, float *__restrict__ Ub, size_t ufs,
@@ -328,17 +331,35 @@ __global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ 
     cover_range(y, h, ps, stride, npy, jlo, jhi, jlast);
     const float i0 = ldp(&I0[y * pitch + x]);
     float nu = 0.0f, nv = 0.0f, den = 0.0f;
-    for (int jj = jlo; jj <= jhi + 1; ++jj) {
-        int j = jj;
-        if (jj == jhi + 1) { if (!jlast) break; j = npy - 1; }
-        for (int ii = ilo; ii <= ihi + 1; ++ii) {
-            int i = ii;
-            if (ii == ihi + 1) { if (!ilast) break; i = npx - 1; }
-            const int id = j * npx + i;
-            const float u = up[id], v = vp[id];
-            const float r = bilinear_i(I1, w, h, pitch, (float)x + u, (float)y + v) - i0;
-            const float lam = 1.0f / fmaxf(1.0f, fabsf(r));
-            nu += lam * u; nv += lam * v; den += lam;
+    auto add = [&](int id) {
+        const float u = up[id], v = vp[id];
+        const float r = bilinear_i(I1, w, h, pitch, (float)x + u, (float)y + v) - i0;
+        const float lam = 1.0f / fmaxf(1.0f, fabsf(r));
+        nu += lam * u; nv += lam * v; den += lam;
+    };
+    if (MAXC > 0) {
+#pragma unroll
+        for (int dj = 0; dj < (MAXC > 0 ? MAXC : 1); ++dj) {
+            const int jj = jlo + dj;
+            const bool vj = jj <= jhi || (jj == jhi + 1 && jlast);
+            const int j = jj <= jhi ? jj : npy - 1;
+#pragma unroll
+            for (int di = 0; di < (MAXC > 0 ? MAXC : 1); ++di) {
+                const int ii = ilo + di;
+                const bool vi = ii <= ihi || (ii == ihi + 1 && ilast);
+                const int i = ii <= ihi ? ii : npx - 1;
+                if (vj && vi) add(j * npx + i);
+            }
+        }
+    } else {
+        for (int jj = jlo; jj <= jhi + 1; ++jj) {
+            int j = jj;
+            if (jj == jhi + 1) { if (!jlast) break; j = npy - 1; }
+            for (int ii = ilo; ii <= ihi + 1; ++ii) {
+                int i = ii;
+                if (ii == ihi + 1) { if (!ilast) break; i = npx - 1; }
+                add(j * npx + i);
+            }
         }
     }
     float *U = Ub + (size_t)f * ufs;
@@ -619,14 +640,20 @@ void launch_densify(const void *I0, const void *I1, const Level &lv, size_t pyr_
 {
     StageScope sc(kStDensify, 1, st);
     dim3 blk(32, 8);
-    if (fp.half)
-        densify_kernel<__half><<<grid2d(lv.w, lv.h, frames, blk), blk, 0, st>>>(
-            (const __half *)I0, (const __half *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, up,
-            up_frame_stride, lv.npx, lv.npy, U, u_frame_stride, lv.plane, fp.ps, fp.stride);
-    else
-        densify_kernel<float><<<grid2d(lv.w, lv.h, frames, blk), blk, 0, st>>>(
-            (const float *)I0, (const float *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, up,
-            up_frame_stride, lv.npx, lv.npy, U, u_frame_stride, lv.plane, fp.ps, fp.stride);
+    // covering patches per axis: at most ceil(ps / stride) regular ones + the last
+    const bool unrolled = (fp.ps + fp.stride - 1) / fp.stride + 1 <= 4;
+    const dim3 grd = grid2d(lv.w, lv.h, frames, blk);
+    if (fp.half) {
+        auto k = unrolled ? densify_kernel<__half, 4> : densify_kernel<__half, 0>;
+        k<<<grd, blk, 0, st>>>((const __half *)I0, (const __half *)I1, lv.w, lv.h, lv.pitch,
+                               pyr_frame_stride, up, up_frame_stride, lv.npx, lv.npy, U,
+                               u_frame_stride, lv.plane, fp.ps, fp.stride);
+    } else {
+        auto k = unrolled ? densify_kernel<float, 4> : densify_kernel<float, 0>;
+        k<<<grd, blk, 0, st>>>((const float *)I0, (const float *)I1, lv.w, lv.h, lv.pitch,
+                               pyr_frame_stride, up, up_frame_stride, lv.npx, lv.npy, U,
+                               u_frame_stride, lv.plane, fp.ps, fp.stride);
+    }
 }
 
 template <typename T>
