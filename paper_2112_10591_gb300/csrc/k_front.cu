@@ -242,15 +242,16 @@ edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, in
 //     construction of the separable exact EDT; breakpoints compared exactly
 //     in 64-bit integers).
 //  3. Each lane walks its band's pixels left to right.  For every band within
-//     kRowNear bands it keeps a pointer into that band's envelope and moves it
+//     NEAR bands it keeps a pointer into that band's envelope and moves it
 //     forward while the next parabola is not higher at x; since the owner of x
 //     within one envelope never moves left as x grows, the walk costs O(1) per
 //     pixel on average.  Farther bands are visited (nearest first, binary
 //     search for the owner) only while their distance^2 is below the best
 //     value so far.
 //  4. Eq. 1 and the 8-bit scale, with coalesced stores.
-// Every step is an exact integer minimum, so D is bit-identical to any exact EDT.
-constexpr int kRowNear = 2;
+// Every step is an exact integer minimum, so D is bit-identical to any exact
+// EDT, whatever WPR and NEAR: single windows use twice the warps per row
+// (half the pixels per lane) to cut latency, batches the narrower layout.
 
 // With sites a < b < c on an envelope, is b hidden once c arrives?
 // Breakpoint s(p, q) = ((h_q + q^2) - (h_p + p^2)) / (2 (q - p)) for p < q;
@@ -303,7 +304,7 @@ __device__ __forceinline__ float ablation_surface(const SurfaceMap &sm, float d)
     return sm.mode == 1 ? d : (sm.mode == 2 ? fminf(d, sm.d_sat) : log1pf(d));
 }
 
-template <int WPR, typename T>
+template <int WPR, int NEAR, typename T>
 __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs,
                                         int W, int H, int rows_per_block, SurfaceMap sm,
                                         int32_t *__restrict__ D_dense,
@@ -359,14 +360,14 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
     __syncthreads();
 
     if (any) {
-        int ptr[2 * kRowNear + 1];
+        int ptr[2 * NEAR + 1];
 #pragma unroll
-        for (int k = 0; k <= 2 * kRowNear; ++k) ptr[k] = 0;
+        for (int k = 0; k <= 2 * NEAR; ++k) ptr[k] = 0;
         for (int x = a; x < b; ++x) {
             int best = 0x7fffffff;
 #pragma unroll
-            for (int k = 0; k <= 2 * kRowNear; ++k) {
-                const int M = bi + k - kRowNear;
+            for (int k = 0; k <= 2 * NEAR; ++k) {
+                const int M = bi + k - NEAR;
                 if (M < 0 || M >= NB) continue;
                 const int ma = min(W, M * B), mb = min(W, ma + B);
                 const int cM = cnts[M];
@@ -386,7 +387,7 @@ __global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitc
                 ptr[k] = pk;
                 best = min(best, cur);
             }
-            for (int dist = kRowNear + 1; dist < NB; ++dist) {
+            for (int dist = NEAR + 1; dist < NB; ++dist) {
                 bool progress = false;
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
@@ -512,32 +513,35 @@ void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stri
                                          g_frame_stride, CH);
 }
 
-int edt_rows_wpr(int W) { return W >= 640 ? 2 : 1; }
-
-size_t edt_rows_smem(int W, int rows) { return (size_t)rows * rows_smem_words(W, edt_rows_wpr(W)) * 4; }
-
-int edt_rows_per_block(int W)
+// Warps per row: one below 640 px, two above; single windows (one or two
+// frames per launch) of rows from 1024 px use four, with a window of four
+// near bands each side (two otherwise).
+int edt_rows_wpr(int W, int frames)
 {
-    int rows = edt_rows_wpr(W) == 2 ? 2 : 4;
-    while (rows > 1 && edt_rows_smem(W, rows) > 200 * 1024) --rows;
-    return rows;
+    const int wpr = W >= 640 ? 2 : 1;
+    return (wpr == 2 && W >= 1024 && frames <= 2) ? 4 : wpr;
 }
 
 template <typename T>
 void edt_rows_t(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int H,
-                const SurfaceMap &sm, int32_t *D_dense, float *S_dense, T *I0, int i_pitch, size_t i_frame_stride,
-                int frames, cudaStream_t st)
+                const SurfaceMap &sm, int32_t *D_dense, float *S_dense, T *I0, int i_pitch,
+                size_t i_frame_stride, int frames, cudaStream_t st)
 {
-    const int rows = edt_rows_per_block(W);
-    const int wpr = edt_rows_wpr(W);
-    const size_t smem = edt_rows_smem(W, rows);
+    const int wpr = edt_rows_wpr(W, frames);
+    int rows = wpr == 1 ? 4 : 2;
+    while (rows > 1 && (size_t)rows * rows_smem_words(W, wpr) * 4 > 200 * 1024) --rows;
+    const size_t smem = (size_t)rows * rows_smem_words(W, wpr) * 4;
     dim3 grd((H + rows - 1) / rows, frames);
-    if (wpr == 2)
-        edt_rows_surface_kernel<2, T><<<grd, 32 * 2 * rows, smem, st>>>(
+    if (wpr == 4)
+        edt_rows_surface_kernel<4, 4, T><<<grd, 32 * 4 * rows, smem, st>>>(
+            g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
+            i_frame_stride);
+    else if (wpr == 2)
+        edt_rows_surface_kernel<2, 2, T><<<grd, 32 * 2 * rows, smem, st>>>(
             g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
     else
-        edt_rows_surface_kernel<1, T><<<grd, 32 * rows, smem, st>>>(
+        edt_rows_surface_kernel<1, 2, T><<<grd, 32 * rows, smem, st>>>(
             g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
 }
@@ -567,13 +571,17 @@ void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_strid
 
 void init_front_attributes()
 {
-    cudaFuncSetAttribute(edt_rows_surface_kernel<1, float>,
+    cudaFuncSetAttribute(edt_rows_surface_kernel<1, 2, float>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<2, float>,
+    cudaFuncSetAttribute(edt_rows_surface_kernel<2, 2, float>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<1, __half>,
+    cudaFuncSetAttribute(edt_rows_surface_kernel<4, 4, float>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<2, __half>,
+    cudaFuncSetAttribute(edt_rows_surface_kernel<1, 2, __half>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(edt_rows_surface_kernel<2, 2, __half>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(edt_rows_surface_kernel<4, 4, __half>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
 }
 
