@@ -215,6 +215,17 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
             h11 += GX[r][k] * GX[r][k]; h12 += GX[r][k] * GY[r][k]; h22 += GY[r][k] * GY[r][k];
         }
     h11 = group_sum<G>(h11); h12 = group_sum<G>(h12); h22 = group_sum<G>(h22);
+    // this lane's share of sum g T, accumulated in the order the iterations
+    // accumulate sum g w, so that b = sum g w - sum g T is exactly zero
+    // wherever the warped patch equals the template
+    float tb1 = 0.0f, tb2 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r)
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            tb1 += GX[r][k] * Tm[r][k];
+            tb2 += GY[r][k] * Tm[r][k];
+        }
     const float det = h11 * h22 - h12 * h12;
     const bool guard = !(det > 1e-6f * (float)(PS * PS) * (float)(PS * PS));
     // damped step (H + mu Id)^-1 b, mu = kappa * trace(H)
@@ -226,7 +237,7 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     const float lim = (float)(w + h);
     for (int it = 0; it < iters; ++it) {
         // b = sum g ((w - mean w) - (T - mean T)); the mean-normalised
-        // gradients sum to zero, so both means drop out of b: b = sum g (w - T)
+        // gradients sum to zero, so both means drop out: b = sum g w - sum g T
         // (exactly zero when the warped patch equals the template)
         float b1 = 0.0f, b2 = 0.0f;
         // The displacement is the same for the whole patch: when every
@@ -266,9 +277,8 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     const float hn = s[k] + ax * (s[k + 1] - s[k]);
                     const float wv = hp[k] + ay * (hn - hp[k]);
                     hp[k] = hn;
-                    const float res = wv - Tm[r][k];
-                    b1 += GX[r][k] * res;
-                    b2 += GY[r][k] * res;
+                    b1 += GX[r][k] * wv;
+                    b2 += GY[r][k] * wv;
                 }
             }
         } else {
@@ -279,12 +289,11 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     if (c0 + k >= PS || r0 + r >= PS) continue;
                     const float wv = bilinear_i(I1, w, h, pitch, (float)(x0 + c0 + k) + u,
                                                 (float)(y0 + r0 + r) + v);
-                    const float res = wv - Tm[r][k];
-                    b1 += GX[r][k] * res;
-                    b2 += GY[r][k] * res;
+                    b1 += GX[r][k] * wv;
+                    b2 += GY[r][k] * wv;
                 }
         }
-        b1 = group_sum<G>(b1); b2 = group_sum<G>(b2);
+        b1 = group_sum<G>(b1 - tb1); b2 = group_sum<G>(b2 - tb2);
         u -= (a22 * b1 - h12 * b2) * inv_det;
         v -= (a11 * b2 - h12 * b1) * inv_det;
     }
