@@ -305,8 +305,33 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     cf[kCWD * pl] = ps.cd;
 }
 
-// Region of 64 columns x RH rows, strips of VS rows: RH / VS warps.
-template <int VS, int RH>
+// Left and right halo of a region in columns: R rounded up to even, so that
+// every region starts on an even column and a lane's two columns are one
+// aligned 8-byte pair in every plane (pitches and plane sizes are even).
+__host__ __device__ __forceinline__ int sor_halo_x(int R) { return R + (R & 1); }
+
+// Interior output of a lane's pair (columns gx0, gx0 + 1 of row gy; the
+// pair is interior or not as a whole): U + dU, as pairs where both columns
+// are in the level.
+__device__ __forceinline__ void store_pair(const float *Uin, float *Uout, size_t plane, int p,
+                                           int gx0, int w, float du0, float du1, float dv0,
+                                           float dv1)
+{
+    if (gx0 + 1 < w) {
+        const float2 u = *reinterpret_cast<const float2 *>(Uin + p);
+        const float2 v = *reinterpret_cast<const float2 *>(Uin + plane + p);
+        *reinterpret_cast<float2 *>(Uout + p) = make_float2(u.x + du0, u.y + du1);
+        *reinterpret_cast<float2 *>(Uout + plane + p) = make_float2(v.x + dv0, v.y + dv1);
+    } else if (gx0 < w) {
+        Uout[p] = Uin[p] + du0;
+        (Uout + plane)[p] = (Uin + plane)[p] + dv0;
+    }
+}
+
+// Region of 64 columns x RH rows, strips of VS rows: RH / VS warps.  EVEN:
+// column halo rounded up to even (pairs loaded and stored as 8 bytes); else
+// a halo of R columns (narrower halo, scalar accesses).
+template <int VS, int RH, bool EVEN>
 __global__ void __launch_bounds__(32 * (RH / VS), 1)
 var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
                float *__restrict__ Uoutb, size_t ufs, size_t plane,
@@ -315,8 +340,9 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
     constexpr int WARPS = RH / VS;
     extern __shared__ float xch[];  // strip-end exchange, two buffers
     const int f = blockIdx.z;
-    const int tile_x = kVR - 2 * R, tile_y = RH - 2 * R;
-    const int rx0 = blockIdx.x * tile_x - R, ry0 = blockIdx.y * tile_y - R;
+    const int hx = EVEN ? sor_halo_x(R) : R;
+    const int tile_x = kVR - 2 * hx, tile_y = RH - 2 * R;
+    const int rx0 = blockIdx.x * tile_x - hx, ry0 = blockIdx.y * tile_y - R;
     const float *Uin = Uinb + (size_t)f * ufs;
     float *Uout = Uoutb + (size_t)f * ufs;
     const float *cf = coefb + (size_t)f * cfs;
@@ -325,25 +351,55 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
     float i11[VS][2], i22[VS][2], a12[VS][2], b1[VS][2], b2[VS][2];
     float wl[VS][2], wr[VS][2], wu[VS][2], wd[VS][2];
     float du[VS][2], dv[VS][2];
+    const int gx0 = rx0 + 2 * lane;  // the lane's pair of columns (even when EVEN)
 #pragma unroll
-    for (int r = 0; r < VS; ++r)
+    for (int r = 0; r < VS; ++r) {
+        const int gy = ry0 + wp * VS + r;
+        if (!EVEN) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                du[r][q] = 0.0f;
+                dv[r][q] = 0.0f;
+                const int gx = gx0 + q;
+                const bool in = gx >= 0 && gx < w && gy >= 0 && gy < h;
+                const float *c = cf + (in ? gy * pitch + gx : 0);
+                i11[r][q] = in ? c[kCI11 * pl] : 0.0f;
+                i22[r][q] = in ? c[kCI22 * pl] : 0.0f;
+                a12[r][q] = in ? c[kCA12 * pl] : 0.0f;
+                b1[r][q] = in ? c[kCB1 * pl] : 0.0f;
+                b2[r][q] = in ? c[kCB2 * pl] : 0.0f;
+                wl[r][q] = in ? c[kCWL * pl] : 0.0f;
+                wr[r][q] = in ? c[kCWR * pl] : 0.0f;
+                wu[r][q] = in ? c[kCWU * pl] : 0.0f;
+                wd[r][q] = in ? c[kCWD * pl] : 0.0f;
+            }
+            continue;
+        }
+        // gx0 >= 0 implies both columns >= 0; the second may be w (odd w),
+        // still inside the row's pitch: loaded and masked
+        const bool in0 = gx0 >= 0 && gx0 < w && gy >= 0 && gy < h;
+        const bool in1 = in0 && gx0 + 1 < w;
+        const float *c = cf + (in0 ? gy * pitch + gx0 : 0);
+        float2 v[kCPlanes];
+#pragma unroll
+        for (int k = 0; k < kCPlanes; ++k)
+            v[k] = in0 ? *reinterpret_cast<const float2 *>(c + k * pl) : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
+            const bool in = q ? in1 : in0;
             du[r][q] = 0.0f;
             dv[r][q] = 0.0f;
-            const int gx = rx0 + 2 * lane + q, gy = ry0 + wp * VS + r;
-            const bool in = gx >= 0 && gx < w && gy >= 0 && gy < h;
-            const float *c = cf + (in ? gy * pitch + gx : 0);
-            i11[r][q] = in ? c[kCI11 * pl] : 0.0f;
-            i22[r][q] = in ? c[kCI22 * pl] : 0.0f;
-            a12[r][q] = in ? c[kCA12 * pl] : 0.0f;
-            b1[r][q] = in ? c[kCB1 * pl] : 0.0f;
-            b2[r][q] = in ? c[kCB2 * pl] : 0.0f;
-            wl[r][q] = in ? c[kCWL * pl] : 0.0f;
-            wr[r][q] = in ? c[kCWR * pl] : 0.0f;
-            wu[r][q] = in ? c[kCWU * pl] : 0.0f;
-            wd[r][q] = in ? c[kCWD * pl] : 0.0f;
+            i11[r][q] = in ? (q ? v[kCI11].y : v[kCI11].x) : 0.0f;
+            i22[r][q] = in ? (q ? v[kCI22].y : v[kCI22].x) : 0.0f;
+            a12[r][q] = in ? (q ? v[kCA12].y : v[kCA12].x) : 0.0f;
+            b1[r][q] = in ? (q ? v[kCB1].y : v[kCB1].x) : 0.0f;
+            b2[r][q] = in ? (q ? v[kCB2].y : v[kCB2].x) : 0.0f;
+            wl[r][q] = in ? (q ? v[kCWL].y : v[kCWL].x) : 0.0f;
+            wr[r][q] = in ? (q ? v[kCWR].y : v[kCWR].x) : 0.0f;
+            wu[r][q] = in ? (q ? v[kCWU].y : v[kCWU].x) : 0.0f;
+            wd[r][q] = in ? (q ? v[kCWD].y : v[kCWD].x) : 0.0f;
         }
+    }
 
     // red-black SOR; red = (x + y) even, first.  Given the parity of (x + y)
     // at a strip's first pixel, the column of a given colour in a given row
@@ -351,18 +407,32 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
     sor_sweeps<VS, WARPS>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp,
                           (rx0 + ry0 + wp * VS) & 1, n_half, omega);
 
+    if (!EVEN) {
 #pragma unroll
-    for (int r = 0; r < VS; ++r)
+        for (int r = 0; r < VS; ++r)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int lx = 2 * lane + q, ly = wp * VS + r;
-            const int gx = rx0 + lx, gy = ry0 + ly;
-            if (lx < R || lx >= R + tile_x || ly < R || ly >= R + tile_y || gx >= w || gy >= h)
-                continue;
-            const int p = gy * pitch + gx;
-            Uout[p] = Uin[p] + du[r][q];
-            (Uout + plane)[p] = (Uin + plane)[p] + dv[r][q];
+            for (int q = 0; q < 2; ++q) {
+                const int lx = 2 * lane + q, ly = wp * VS + r;
+                const int gx = rx0 + lx, gy = ry0 + ly;
+                if (lx < hx || lx >= hx + tile_x || ly < R || ly >= R + tile_y || gx >= w ||
+                    gy >= h)
+                    continue;
+                const int p = gy * pitch + gx;
+                Uout[p] = Uin[p] + du[r][q];
+                (Uout + plane)[p] = (Uin + plane)[p] + dv[r][q];
+            }
+        return;
+    }
+    const int lx0 = 2 * lane;
+    if (lx0 >= hx && lx0 < hx + tile_x) {
+#pragma unroll
+        for (int r = 0; r < VS; ++r) {
+            const int ly = wp * VS + r, gy = ry0 + ly;
+            if (ly < R || ly >= R + tile_y || gy >= h) continue;
+            store_pair(Uin, Uout, plane, gy * pitch + gx0, gx0, w, du[r][0], du[r][1], dv[r][0],
+                       dv[r][1]);
         }
+    }
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -408,10 +478,11 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const int hx = sor_halo_x(R), tile_x = kVR - 2 * hx;
     auto issue = [&](int r) {  // thread 0: the tensor copy of region r
         const int f = r / per_frame, rem = r - f * per_frame;
         const int ry = rem / nrx, rx = rem - ry * nrx;
-        const int bx0 = (rx * tile - R) & ~3;
+        const int bx0 = (rx * tile_x - hx) & ~3;
         const int by0 = ry * tile - R;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
                      "r"((unsigned)(kTmaCoefFloats * sizeof(float)))
@@ -437,29 +508,33 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
         parity ^= 1u;
         const int f = r / per_frame, rem = r - f * per_frame;
         const int ry = rem / nrx, rx = rem - ry * nrx;
-        const int rx0 = rx * tile - R, ry0 = ry * tile - R;
-        const int ox = rx0 - (rx0 & ~3);  // region column 0 within the box
+        const int rx0 = rx * tile_x - hx, ry0 = ry * tile - R;
+        const int ox = rx0 - (rx0 & ~3);  // region column 0 within the box: 0 or 2
         float i11[kVS][2], i22[kVS][2], a12[kVS][2], b1[kVS][2], b2[kVS][2];
         float wl[kVS][2], wr[kVS][2], wu[kVS][2], wd[kVS][2];
         float du[kVS][2], dv[kVS][2];
 #pragma unroll
-        for (int rr = 0; rr < kVS; ++rr)
+        for (int rr = 0; rr < kVS; ++rr) {
+            const float *c = cbuf + (wp * kVS + rr) * kTmaBoxW + ox + 2 * lane;
+            constexpr int P = kVR * kTmaBoxW;
+            float2 v[kCPlanes];
+#pragma unroll
+            for (int k = 0; k < kCPlanes; ++k) v[k] = *reinterpret_cast<const float2 *>(c + k * P);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 du[rr][q] = 0.0f;
                 dv[rr][q] = 0.0f;
-                const float *c = cbuf + (wp * kVS + rr) * kTmaBoxW + ox + 2 * lane + q;
-                constexpr int P = kVR * kTmaBoxW;
-                i11[rr][q] = c[kCI11 * P];
-                i22[rr][q] = c[kCI22 * P];
-                a12[rr][q] = c[kCA12 * P];
-                b1[rr][q] = c[kCB1 * P];
-                b2[rr][q] = c[kCB2 * P];
-                wl[rr][q] = c[kCWL * P];
-                wr[rr][q] = c[kCWR * P];
-                wu[rr][q] = c[kCWU * P];
-                wd[rr][q] = c[kCWD * P];
+                i11[rr][q] = q ? v[kCI11].y : v[kCI11].x;
+                i22[rr][q] = q ? v[kCI22].y : v[kCI22].x;
+                a12[rr][q] = q ? v[kCA12].y : v[kCA12].x;
+                b1[rr][q] = q ? v[kCB1].y : v[kCB1].x;
+                b2[rr][q] = q ? v[kCB2].y : v[kCB2].x;
+                wl[rr][q] = q ? v[kCWL].y : v[kCWL].x;
+                wr[rr][q] = q ? v[kCWR].y : v[kCWR].x;
+                wu[rr][q] = q ? v[kCWU].y : v[kCWU].x;
+                wd[rr][q] = q ? v[kCWD].y : v[kCWD].x;
             }
+        }
         __syncthreads();  // every thread holds its coefficients: the buffer is free
         if (t == 0 && r + (int)gridDim.x < total) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -469,18 +544,16 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
         float *Uout = Uoutb + (size_t)f * ufs;
         sor_sweeps<kVS, kVWarps>(du, dv, i11, i22, a12, b1, b2, wl, wr, wu, wd, xch, lane, wp,
                                  (rx0 + ry0) & 1, n_half, omega);
+        const int lx0 = 2 * lane, gx0 = rx0 + lx0;
+        if (lx0 >= hx && lx0 < hx + tile_x) {
 #pragma unroll
-        for (int rr = 0; rr < kVS; ++rr)
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int lx = 2 * lane + q, ly = wp * kVS + rr;
-                const int gx = rx0 + lx, gy = ry0 + ly;
-                if (lx < R || lx >= R + tile || ly < R || ly >= R + tile || gx >= w || gy >= h)
-                    continue;
-                const int p = gy * pitch + gx;
-                Uout[p] = Uin[p] + du[rr][q];
-                (Uout + plane)[p] = (Uin + plane)[p] + dv[rr][q];
+            for (int rr = 0; rr < kVS; ++rr) {
+                const int ly = wp * kVS + rr, gy = ry0 + ly;
+                if (ly < R || ly >= R + tile || gy >= h) continue;
+                store_pair(Uin, Uout, plane, gy * pitch + gx0, gx0, w, du[rr][0], du[rr][1],
+                           dv[rr][0], dv[rr][1]);
             }
+        }
     }
 }
 
@@ -532,7 +605,7 @@ void make_coef_maps(float *work, const Geometry &geo, int frames, CoefMaps *m)
 bool var_fused_supported(int var_sor)
 {
     const int R = var_sor > 0 ? 2 * var_sor - 1 : 0;
-    return kVR - 2 * R >= 16;
+    return kVR - 2 * sor_halo_x(R) >= 16;
 }
 
 void init_var_attributes()
@@ -545,7 +618,7 @@ void init_var_attributes()
     }
     cudaFuncSetAttribute(var_sor_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kTmaSmemBytes);
-    cudaFuncSetAttribute(var_sor_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(var_sor_kernel<1, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(kVSmemFloats2 * sizeof(float)));
 
 }
@@ -563,9 +636,10 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
     const int nsm = (dev >= 0 && dev < kMaxDevs && g_num_sms[dev] > 0) ? g_num_sms[dev] : 0;
     const int n_half = 2 * fp.var_sor;
     const int R = n_half > 0 ? n_half - 1 : 0;
-    const int tile = kVR - 2 * R;
+    const int tile = kVR - 2 * R;                    // interior rows of a 64-row region
+    const int tile_x = kVR - 2 * sor_halo_x(R);      // interior columns
     const dim3 cgrd((lv.w + kAX - 1) / kAX, (lv.h + kAY - 1) / kAY, frames);
-    const dim3 sgrd((lv.w + tile - 1) / tile, (lv.h + tile - 1) / tile, frames);
+    const dim3 sgrd((lv.w + tile_x - 1) / tile_x, (lv.h + tile - 1) / tile, frames);
     float *a = U, *b = Utmp;
     for (int k = 0; k < fp.var_outer; ++k) {
         {
@@ -595,21 +669,34 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
             // per half sweep) still fit in one wave, they replace the 4-row
             // strips.  Every layout computes the interior's whole-image
             // iteration, so the choice never changes the result.
-            const dim3 g1((lv.w + tile - 1) / tile, (lv.h + (32 - 2 * R) - 1) / (32 - 2 * R),
-                          frames);
+            const dim3 g1((lv.w + tile_x - 1) / tile_x,
+                          (lv.h + (32 - 2 * R) - 1) / (32 - 2 * R), frames);
             const bool small = nsm > 0 && total < nsm;
+            // even-halo regions (8-byte pairs) unless they take more waves
+            // than regions with an R-column halo
+            const int todd = kVR - 2 * R;
+            const dim3 godd((lv.w + todd - 1) / todd, sgrd.y, frames);
+            const int wave = nsm > 0 ? nsm : 1;
+            const bool even = (total + wave - 1) / wave <=
+                              ((int)(godd.x * godd.y * godd.z) + wave - 1) / wave;
             if (coef_map && nsm > 0 && total >= 4 * nsm)
                 var_sor_tma_kernel<<<nsm, kVThreads, kTmaSmemBytes, st>>>(
                     *coef_map, lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, R, tile,
                     (int)sgrd.x, (int)sgrd.y, total, n_half, fp.omega, err);
             else if (small && 32 - 2 * R >= 8 && (int)(g1.x * g1.y * g1.z) <= nsm)
-                var_sor_kernel<1, 32><<<g1, 32 * 32, kVSmemFloats2 * sizeof(float), st>>>(
+                var_sor_kernel<1, 32, true><<<g1, 32 * 32, kVSmemFloats2 * sizeof(float), st>>>(
                     lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
                     coef_frame_stride, R, n_half, fp.omega);
+            else if (even)
+                var_sor_kernel<kVS, kVR, true>
+                    <<<sgrd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
+                        lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
+                        coef_frame_stride, R, n_half, fp.omega);
             else
-                var_sor_kernel<kVS, kVR><<<sgrd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
-                    lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
-                    coef_frame_stride, R, n_half, fp.omega);
+                var_sor_kernel<kVS, kVR, false>
+                    <<<godd, kVThreads, kVSmemFloats * sizeof(float), st>>>(
+                        lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
+                        coef_frame_stride, R, n_half, fp.omega);
         }
         float *t = a;
         a = b;
