@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--sv-windows", type=int, default=12,
                     help="generated windows per serving sequence")
     ap.add_argument("--sv-workers", type=int, default=8)
+    ap.add_argument("--sv-max-batch", type=int, default=16,
+                    help="windows of one stream the server may batch into one launch")
     ap.add_argument("--sv-scales", type=lambda v: [float(x) for x in v.split(",")],
                     default=[1.0, 0.35], help="arrival-rate scales of the serving runs")
     ap.add_argument("--ms-windows", type=int, default=11,
@@ -450,10 +452,10 @@ def run_serving(args, eb, torch, dev, rank):
     Poisson process whose rate is drawn in [100, 250] Hz; window contents
     follow the lognormal [5k, 500k] event counts and per-object affine motion
     of the multi-stream workload, FP16 storage.  Every stream's state (its
-    previous pyramid and buffers for batches of up to 8 windows) is admitted
+    previous pyramid and buffers for its largest batch) is admitted
     under a 40 GB budget and stays resident.  The client submits each window
     at its arrival time through ebof_server_submit; the server's dispatcher
-    batches each stream's backlog into list calls on 8 worker CUDA streams.
+    batches each stream's backlog into list calls on the worker CUDA streams.
     Latency = completion seen by the dispatcher - arrival.  A run at a lower
     rate scale shows the latency when the offered load is below capacity."""
     import ctypes
@@ -466,7 +468,7 @@ def run_serving(args, eb, torch, dev, rank):
                                  extra_length=(8.0, 80.0))),
              (1280, 720, 16, {})]
     n_seq, L = 4, max(4, args.sv_windows)
-    max_batch = 8
+    max_batch = args.sv_max_batch
     cfg = eb.ebof_server_default_config()
     cfg.device = dev.index or 0
     cfg.n_workers = args.sv_workers
@@ -509,6 +511,11 @@ def run_serving(args, eb, torch, dev, rank):
                             "pos": (i // n_seq) * 3 % L, "rate": float(rng.uniform(100, 250)),
                             "flow": [fl[j].data_ptr() for j in range(ring)], "k": 0})
     info0 = eb.ebof_server_get_info(server)
+    if info0.streams_waiting:
+        server.close()
+        raise RuntimeError("serving: %d of %d streams do not fit the %.0f GB budget with "
+                           "batches of %d windows" % (info0.streams_waiting, len(streams),
+                                                      cfg.memory_budget / 1e9, max_batch))
     buf = (eb.ebof_completion * 4096)()
 
     def run(seconds, scale):
@@ -535,7 +542,7 @@ def run_serving(args, eb, torch, dev, rank):
             if r < 0:
                 raise eb.EbofError(r, "ebof_server_submit")
             sm["k"] = k + 1
-        eb.check(lib.ebof_server_drain(server.handle, 600000), "ebof_server_drain")
+        eb.check(lib.ebof_server_drain(server.handle, 120000), "ebof_server_drain")
         while True:
             n = lib.ebof_server_poll(server.handle, buf, 4096, 0)
             if n <= 0:
