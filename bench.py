@@ -399,6 +399,7 @@ def run_multistream(args, eb, torch, dev, rank):
                      "CUDA streams",
            "autotune": {"%dx%d" % (gr["W"], gr["H"]): {"patch": gr["prm"].patch,
                                                       "stride": gr["prm"].stride,
+                                                      "levels": gr["prm"].levels,
                                                       "candidates": gr["table"]}
                         for gr in groups}}
     for gr in groups:

@@ -1,11 +1,12 @@
-"""Per-resolution choice of the patch grid for multi-stream groups.
+"""Per-resolution choice of the patch grid and pyramid depth for
+multi-stream groups.
 
 For one sensor resolution the tuner times a group step for a few candidate
-(patch size, stride) pairs on calibration windows and keeps the fastest
-candidate whose flow stays within ``tol_px`` mean endpoint error of the flow
-computed with the library's default parameters on the same windows.  Every
-measurement goes through the C ABI (ebof_group_*); the tuner itself only
-orchestrates and compares.
+(patch size, stride, levels) triples on calibration windows and keeps the
+fastest candidate whose flow stays within ``tol_px`` mean endpoint error of
+the flow computed with the library's default parameters on the same windows.
+Every measurement goes through the C ABI (ebof_group_*); the tuner itself
+only orchestrates and compares.
 """
 from __future__ import annotations
 
@@ -31,22 +32,26 @@ def tune(width, height, calib, storage=eb.EBOF_STORAGE_FP32, candidates=None, to
     base = eb.ebof_default_params(width, height)
     base.storage = storage
     if candidates is None:
-        candidates = [(base.patch, base.stride), (base.patch, base.stride + 2),
-                      (8, 4), (8, 6), (12, 4), (12, 6)]
+        L = base.levels
+        candidates = [(base.patch, base.stride, L), (base.patch, base.stride + 2, L),
+                      (base.patch, base.stride, L - 1), (8, 4, L), (8, 6, L), (12, 4, L),
+                      (12, 6, L)]
     seen, cands = set(), []
     for c in candidates:
-        if c not in seen and min(width, height) >= c[0]:
+        c = tuple(c) if len(c) == 3 else (c[0], c[1], base.levels)
+        if c not in seen and min(width, height) >= c[0] and c[2] >= 1:
             seen.add(c)
             cands.append(c)
     n = len(calib)
     ref_flow = None
     table = []
-    for ps, st in cands:
+    for ps, st, lv in cands:
         prm = _copy_params(base)
-        prm.patch, prm.stride = ps, st
+        prm.patch, prm.stride, prm.levels = ps, st, lv
         rc, g = eb.ebof_group_create(prm, n, device)
         if rc < 0:
-            table.append({"patch": ps, "stride": st, "status": eb.ebof_status_string(rc)})
+            table.append({"patch": ps, "stride": st, "levels": lv,
+                          "status": eb.ebof_status_string(rc)})
             continue
         flow = torch.empty((n, 2, height, width), dtype=torch.float32, device="cuda")
         w0 = [c[0] for c in calib]
@@ -67,10 +72,11 @@ def tune(width, height, calib, storage=eb.EBOF_STORAGE_FP32, candidates=None, to
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / repeats
-        table.append({"patch": ps, "stride": st, "ms_per_step": ms, "epe_vs_default_px": epe})
+        table.append({"patch": ps, "stride": st, "levels": lv, "ms_per_step": ms,
+                      "epe_vs_default_px": epe})
         g.close()
     ok = [r for r in table if "ms_per_step" in r and r["epe_vs_default_px"] <= tol_px]
     best = min(ok, key=lambda r: r["ms_per_step"]) if ok else table[0]
     out = _copy_params(base)
-    out.patch, out.stride = best["patch"], best["stride"]
+    out.patch, out.stride, out.levels = best["patch"], best["stride"], best["levels"]
     return out, table
