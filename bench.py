@@ -250,6 +250,39 @@ def algorithmic_bytes_per_launch(stage, level, geo, n_events_per_window, P):
 PER_LEVEL = ("pyramid", "patch_search", "densify", "var_coeff", "var_sor")
 
 
+def stage_hbm_fractions(ms_per_frame, P, n_events, n_levels, var_outer, peak):
+    """HBM fraction of each hot-path stage with the stage's algorithmic bytes
+    per flow frame: its own inputs read once and outputs written once, the
+    variational stage once per outer iteration (I0, I1, U in, U out: 24 B per
+    pixel of every level) with its SOR sweeps on chip; c_L = sum of 4^-l over
+    the levels.  ms_per_frame: stage times per frame from the stage profile."""
+    cL = sum(4.0 ** -l for l in range(n_levels))
+    rows = (
+        ("A1 scatter", 12.0 * n_events + P + n_events, ("scatter",)),
+        ("A2 denoise_fill", 2.0 * P, ("denoise_fill",)),
+        ("A3+A4 edt_surface", 17.0 * P, ("edt_cols", "edt_rows_surface")),
+        ("A5 pyramid", 22.0 * P, ("pyramid",)),
+        ("A6 patch_search", 17.0 * P * cL, ("patch_search",)),
+        ("A7 densify", 16.0 * P * cL, ("densify",)),
+        ("A8 variational", var_outer * 24.0 * P * cL, ("var_coeff", "var_sor")),
+    )
+    out, tb, tt = {}, 0.0, 0.0
+    for name, nbytes, stages in rows:
+        t = sum(ms_per_frame.get(k, 0.0) for k in stages)
+        if t <= 0.0:
+            continue
+        gbs = nbytes / (t / 1000.0) / 1e9
+        out[name] = {"bytes_per_frame": nbytes, "ms_per_frame": t,
+                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+        tb += nbytes
+        tt += t
+    if tt > 0.0:
+        gbs = tb / (tt / 1000.0) / 1e9
+        out["all stages"] = {"bytes_per_frame": tb, "ms_per_frame": tt,
+                             "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    return out
+
+
 def geo_levels(p):
     out = []
     for l in range(p.levels):
@@ -782,6 +815,9 @@ def main():
                                               for k, v in bprof.items() if v[1]},
                        "stage_share": {k: round(v[0] / btot, 4) for k, v in bprof.items()
                                        if v[1]}}
+            batched["stage_roofline"] = stage_hbm_fractions(
+                {k: v[0] / frames_per_step for k, v in bprof.items() if v[1]}, P, n_ev_win,
+                len(gl), prm.var_outer, peak)
             sb.close()
         else:
             batched = {"unavailable": eb.ebof_status_string(stb)}

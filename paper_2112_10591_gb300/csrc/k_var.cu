@@ -165,21 +165,26 @@ __device__ __forceinline__ void sor_sweeps(float (&du)[VS][2], float (&dv)[VS][2
 
 // Derivatives of the warped image and the smoothness weight at a pixel of a
 // staging window (row stride ES; (e) the pixel, at image position gx, gy).
+// IN: the pixel and its neighbours lie inside the level, so the clamps and
+// border tests are known to pass and are left out (same values).
+template <bool IN>
 __device__ __forceinline__ void stage_derivs(const float *sW, const float *sU, const float *sV,
                                              int ES, int e, int ex0, int ey0, int gx, int gy,
                                              int w, int h, float alpha_s, float &ix, float &iy,
                                              float &as)
 {
-    const int xp = min(gx + 1, w - 1) - ex0, xm = max(gx - 1, 0) - ex0;
-    const int yp = min(gy + 1, h - 1) - ey0, ym = max(gy - 1, 0) - ey0;
+    const int xp = (IN ? gx + 1 : min(gx + 1, w - 1)) - ex0;
+    const int xm = (IN ? gx - 1 : max(gx - 1, 0)) - ex0;
+    const int yp = (IN ? gy + 1 : min(gy + 1, h - 1)) - ey0;
+    const int ym = (IN ? gy - 1 : max(gy - 1, 0)) - ey0;
     const int ex = gx - ex0, ey = gy - ey0;
     ix = 0.5f * (sW[ey * ES + xp] - sW[ey * ES + xm]);
     iy = 0.5f * (sW[yp * ES + ex] - sW[ym * ES + ex]);
     const float u = sU[e], v = sV[e];
-    const float ux = gx + 1 < w ? sU[e + 1] - u : 0.0f;
-    const float uy = gy + 1 < h ? sU[e + ES] - u : 0.0f;
-    const float vx = gx + 1 < w ? sV[e + 1] - v : 0.0f;
-    const float vy = gy + 1 < h ? sV[e + ES] - v : 0.0f;
+    const float ux = IN || gx + 1 < w ? sU[e + 1] - u : 0.0f;
+    const float uy = IN || gy + 1 < h ? sU[e + ES] - u : 0.0f;
+    const float vx = IN || gx + 1 < w ? sV[e + 1] - v : 0.0f;
+    const float vy = IN || gy + 1 < h ? sV[e + ES] - v : 0.0f;
     as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
 }
 
@@ -189,7 +194,8 @@ struct PixelSystem {
 
 // The 2x2 system of pixel (gx, gy): d indexes the derivative window (row
 // stride DS, origin dx0, dy0), e the staging window (row stride ES); I0, I0x,
-// I0y at the pixel are given.
+// I0y at the pixel are given.  IN as in stage_derivs.
+template <bool IN>
 __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const float *sIy,
                                                     const float *sAs, int DS, int dx0, int dy0,
                                                     const float *sW, const float *sU,
@@ -197,8 +203,10 @@ __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const floa
                                                     int gy, int w, int h, float i0, float i0x,
                                                     float i0y, float delta, float gamma)
 {
-    const int xp = min(gx + 1, w - 1) - dx0, xm = max(gx - 1, 0) - dx0;
-    const int yp = min(gy + 1, h - 1) - dy0, ym = max(gy - 1, 0) - dy0;
+    const int xp = (IN ? gx + 1 : min(gx + 1, w - 1)) - dx0;
+    const int xm = (IN ? gx - 1 : max(gx - 1, 0)) - dx0;
+    const int yp = (IN ? gy + 1 : min(gy + 1, h - 1)) - dy0;
+    const int ym = (IN ? gy - 1 : max(gy - 1, 0)) - dy0;
     const int dx = gx - dx0, dy = gy - dy0;
     const int d = dy * DS + dx;
     const float Ix = sIx[d], Iy = sIy[d];
@@ -219,10 +227,10 @@ __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const floa
     }
     const float asp = sAs[d];
     PixelSystem ps;
-    ps.cl = gx > 0 ? 0.5f * (asp + sAs[d - 1]) : 0.0f;
-    ps.cr = gx + 1 < w ? 0.5f * (asp + sAs[d + 1]) : 0.0f;
-    ps.cu = gy > 0 ? 0.5f * (asp + sAs[d - DS]) : 0.0f;
-    ps.cd = gy + 1 < h ? 0.5f * (asp + sAs[d + DS]) : 0.0f;
+    ps.cl = IN || gx > 0 ? 0.5f * (asp + sAs[d - 1]) : 0.0f;
+    ps.cr = IN || gx + 1 < w ? 0.5f * (asp + sAs[d + 1]) : 0.0f;
+    ps.cu = IN || gy > 0 ? 0.5f * (asp + sAs[d - DS]) : 0.0f;
+    ps.cd = IN || gy + 1 < h ? 0.5f * (asp + sAs[d + DS]) : 0.0f;
     const float sw = ps.cl + ps.cr + ps.cu + ps.cd;
     const float su0 = ps.cl * (sU[e - 1] - u) + ps.cr * (sU[e + 1] - u) +
                       ps.cu * (sU[e - ES] - u) + ps.cd * (sU[e + ES] - u);
@@ -236,15 +244,17 @@ __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const floa
     return ps;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kAX * kAY)
-var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
-                 const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
-                 int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs, size_t plane,
-                 float *__restrict__ coefb, size_t cfs, float delta, float gamma, float alpha_s)
+// One coefficient tile.  IN: the tile's staging window (tile + 2 px) lies
+// inside the level, so no load or neighbour needs a bounds test.
+template <bool IN, typename T>
+__device__ __forceinline__ void coeff_tile(
+    float (&sU)[kAEY][kAEX], float (&sV)[kAEY][kAEX], float (&sW)[kAEY][kAEX],
+    float (&sIx)[kADY][kADX], float (&sIy)[kADY][kADX], float (&sAs)[kADY][kADX],
+    const T *__restrict__ I0b, const T *__restrict__ I0xb, const T *__restrict__ I0yb,
+    const T *__restrict__ I1b, int w, int h, int pitch, size_t pfs, const float *__restrict__ Ub,
+    size_t ufs, size_t plane, float *__restrict__ coefb, size_t cfs, float delta, float gamma,
+    float alpha_s)
 {
-    __shared__ float sU[kAEY][kAEX], sV[kAEY][kAEX], sW[kAEY][kAEX];
-    __shared__ float sIx[kADY][kADX], sIy[kADY][kADX], sAs[kADY][kADX];
     const int f = blockIdx.z;
     const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
     const int ex0 = tx0 - 2, ey0 = ty0 - 2, dx0 = tx0 - 1, dy0 = ty0 - 1;
@@ -261,7 +271,7 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         const int lx = i % kAEX, ly = i / kAEX;
         const int gx = ex0 + lx, gy = ey0 + ly;
         float u = 0.0f, v = 0.0f, wv = 0.0f;
-        if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+        if (IN || (gx >= 0 && gx < w && gy >= 0 && gy < h)) {
             const int p = gy * pitch + gx;
             u = U[p];
             v = V[p];
@@ -276,9 +286,10 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
         const int lx = i % kADX, ly = i / kADX;
         const int gx = dx0 + lx, gy = dy0 + ly;
         float ix = 0.0f, iy = 0.0f, as = 0.0f;
-        if (gx >= 0 && gx < w && gy >= 0 && gy < h)
-            stage_derivs(&sW[0][0], &sU[0][0], &sV[0][0], kAEX, (gy - ey0) * kAEX + (gx - ex0),
-                         ex0, ey0, gx, gy, w, h, alpha_s, ix, iy, as);
+        if (IN || (gx >= 0 && gx < w && gy >= 0 && gy < h))
+            stage_derivs<IN>(&sW[0][0], &sU[0][0], &sV[0][0], kAEX,
+                             (gy - ey0) * kAEX + (gx - ex0), ex0, ey0, gx, gy, w, h, alpha_s,
+                             ix, iy, as);
         sIx[ly][lx] = ix;
         sIy[ly][lx] = iy;
         sAs[ly][lx] = as;
@@ -286,9 +297,9 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     __syncthreads();
 
     const int gx = tx0 + threadIdx.x, gy = ty0 + threadIdx.y;
-    if (gx >= w || gy >= h) return;
+    if (!IN && (gx >= w || gy >= h)) return;
     const int p = gy * pitch + gx;
-    const PixelSystem ps = pixel_system(
+    const PixelSystem ps = pixel_system<IN>(
         &sIx[0][0], &sIy[0][0], &sAs[0][0], kADX, dx0, dy0, &sW[0][0], &sU[0][0], &sV[0][0], kAEX,
         (gy - ey0) * kAEX + (gx - ex0), gx, gy, w, h, ldp(&(I0b + po)[p]), ldp(&(I0xb + po)[p]),
         ldp(&(I0yb + po)[p]), delta, gamma);
@@ -303,6 +314,24 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     cf[kCWR * pl] = ps.cr;
     cf[kCWU * pl] = ps.cu;
     cf[kCWD * pl] = ps.cd;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAX * kAY)
+var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
+                 const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
+                 int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs, size_t plane,
+                 float *__restrict__ coefb, size_t cfs, float delta, float gamma, float alpha_s)
+{
+    __shared__ float sU[kAEY][kAEX], sV[kAEY][kAEX], sW[kAEY][kAEX];
+    __shared__ float sIx[kADY][kADX], sIy[kADY][kADX], sAs[kADY][kADX];
+    const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
+    if (tx0 >= 2 && ty0 >= 2 && tx0 + kAX + 2 <= w && ty0 + kAY + 2 <= h)
+        coeff_tile<true>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
+                         ufs, plane, coefb, cfs, delta, gamma, alpha_s);
+    else
+        coeff_tile<false>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
+                          ufs, plane, coefb, cfs, delta, gamma, alpha_s);
 }
 
 // Left and right halo of a region in columns: R rounded up to even, so that
