@@ -357,6 +357,21 @@ __device__ __forceinline__ void store_pair(const float *Uin, float *Uout, size_t
     }
 }
 
+// A lane's two adjacent values of one plane (c: the first); EVEN: one
+// aligned 8-byte load.
+template <bool EVEN>
+__device__ __forceinline__ void set_pair(float (&a)[2], const float *c)
+{
+    if (EVEN) {
+        const float2 v = *reinterpret_cast<const float2 *>(c);
+        a[0] = v.x;
+        a[1] = v.y;
+    } else {
+        a[0] = c[0];
+        a[1] = c[1];
+    }
+}
+
 // Region of 64 columns x RH rows, strips of VS rows: RH / VS warps.  EVEN:
 // column halo rounded up to even (pairs loaded and stored as 8 bytes); else
 // a halo of R columns (narrower halo, scalar accesses).
@@ -381,9 +396,26 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
     float wl[VS][2], wr[VS][2], wu[VS][2], wd[VS][2];
     float du[VS][2], dv[VS][2];
     const int gx0 = rx0 + 2 * lane;  // the lane's pair of columns (even when EVEN)
+    const bool inside = rx0 >= 0 && ry0 >= 0 && rx0 + kVR <= w && ry0 + RH <= h;  // block-uniform
 #pragma unroll
     for (int r = 0; r < VS; ++r) {
         const int gy = ry0 + wp * VS + r;
+        if (inside) {
+            // the whole region lies in the level: loads without bounds tests
+            du[r][0] = du[r][1] = 0.0f;
+            dv[r][0] = dv[r][1] = 0.0f;
+            const float *c = cf + gy * pitch + gx0;
+            set_pair<EVEN>(i11[r], c + kCI11 * pl);
+            set_pair<EVEN>(i22[r], c + kCI22 * pl);
+            set_pair<EVEN>(a12[r], c + kCA12 * pl);
+            set_pair<EVEN>(b1[r], c + kCB1 * pl);
+            set_pair<EVEN>(b2[r], c + kCB2 * pl);
+            set_pair<EVEN>(wl[r], c + kCWL * pl);
+            set_pair<EVEN>(wr[r], c + kCWR * pl);
+            set_pair<EVEN>(wu[r], c + kCWU * pl);
+            set_pair<EVEN>(wd[r], c + kCWD * pl);
+            continue;
+        }
         if (!EVEN) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
