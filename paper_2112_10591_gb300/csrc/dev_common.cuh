@@ -31,7 +31,43 @@ __device__ __forceinline__ float bilinear(const T *__restrict__ I, int w, int h,
     return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
 }
 
-// The same sample with 32-bit offsets (images of at most 2^31 elements).
+// The four samples around a clamped position and its fractional offsets.
+struct BilTaps {
+    float a, b, c, d, fx, fy;
+};
+
+// Taps of the sample below with 32-bit offsets (images of at most 2^31
+// elements); split from the interpolation so that callers can issue the
+// loads ahead of their use.
+template <typename T>
+__device__ __forceinline__ BilTaps bil_taps_i(const T *__restrict__ I, int w, int h, int pitch,
+                                              float x, float y)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
+    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
+    const float xf = floorf(x), yf = floorf(y);
+    const int x0 = (int)xf, y0 = (int)yf;
+    const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+    const T *r0 = I + y0 * pitch, *r1 = I + y1 * pitch;
+    BilTaps t;
+    t.fx = x - xf;
+    t.fy = y - yf;
+    t.a = ldp(&r0[x0]);
+    t.b = ldp(&r0[x1]);
+    t.c = ldp(&r1[x0]);
+    t.d = ldp(&r1[x1]);
+    return t;
+}
+
+__device__ __forceinline__ float bil_lerp(const BilTaps &t)
+{
+    return (1.0f - t.fy) * ((1.0f - t.fx) * t.a + t.fx * t.b) +
+           t.fy * ((1.0f - t.fx) * t.c + t.fx * t.d);
+}
+
+// The bilinear sample with 32-bit offsets (the same arithmetic as
+// bil_lerp(bil_taps_i(...)), written out whole for the search and
+// densification kernels).
 template <typename T>
 __device__ __forceinline__ float bilinear_i(const T *__restrict__ I, int w, int h, int pitch,
                                             float x, float y)

@@ -163,6 +163,21 @@ __device__ __forceinline__ void sor_sweeps(float (&du)[VS][2], float (&dv)[VS][2
     __syncthreads();
 }
 
+// Smoothness weight alpha_s Psi'(|grad u|^2 + |grad v|^2) with forward
+// differences (ur, ud: U to the right and below; hx, hy: those neighbours are
+// in the level, else the difference is 0).
+__device__ __forceinline__ float smooth_weight(float u, float ur, float ud, float v, float vr,
+                                               float vd, bool hx, bool hy, float alpha_s)
+{
+    const float ux = hx ? ur - u : 0.0f;
+    const float uy = hy ? ud - u : 0.0f;
+    const float vx = hx ? vr - v : 0.0f;
+    const float vy = hy ? vd - v : 0.0f;
+    return alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
+}
+
+__device__ __forceinline__ float cdiff(float hi, float lo) { return 0.5f * (hi - lo); }
+
 // Derivatives of the warped image and the smoothness weight at a pixel of a
 // staging window (row stride ES; (e) the pixel, at image position gx, gy).
 // IN: the pixel and its neighbours lie inside the level, so the clamps and
@@ -178,23 +193,65 @@ __device__ __forceinline__ void stage_derivs(const float *sW, const float *sU, c
     const int yp = (IN ? gy + 1 : min(gy + 1, h - 1)) - ey0;
     const int ym = (IN ? gy - 1 : max(gy - 1, 0)) - ey0;
     const int ex = gx - ex0, ey = gy - ey0;
-    ix = 0.5f * (sW[ey * ES + xp] - sW[ey * ES + xm]);
-    iy = 0.5f * (sW[yp * ES + ex] - sW[ym * ES + ex]);
-    const float u = sU[e], v = sV[e];
-    const float ux = IN || gx + 1 < w ? sU[e + 1] - u : 0.0f;
-    const float uy = IN || gy + 1 < h ? sU[e + ES] - u : 0.0f;
-    const float vx = IN || gx + 1 < w ? sV[e + 1] - v : 0.0f;
-    const float vy = IN || gy + 1 < h ? sV[e + ES] - v : 0.0f;
-    as = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
+    ix = cdiff(sW[ey * ES + xp], sW[ey * ES + xm]);
+    iy = cdiff(sW[yp * ES + ex], sW[ym * ES + ex]);
+    as = smooth_weight(sU[e], sU[e + 1], sU[e + ES], sV[e], sV[e + 1], sV[e + ES],
+                       IN || gx + 1 < w, IN || gy + 1 < h, alpha_s);
 }
 
 struct PixelSystem {
     float i11, i22, a12, b1, b2, cl, cr, cu, cd;
 };
 
-// The 2x2 system of pixel (gx, gy): d indexes the derivative window (row
-// stride DS, origin dx0, dy0), e the staging window (row stride ES); I0, I0x,
-// I0y at the pixel are given.  IN as in stage_derivs.
+// The 2x2 system of pixel (gx, gy) from its neighbourhood.  ix, iy: the
+// warped image's derivatives at the pixel; ixl, ixr: Ix at the clamped left
+// and right neighbours, ixu, ixd and iyu, iyd: Ix and Iy at the clamped upper
+// and lower ones; iw: the warped sample; as*: smoothness weights at the pixel
+// and its four neighbours, used only where that neighbour is in the level
+// (bl, br, bu, bd); u*, v*: the flow at the pixel and its four neighbours (0
+// outside the level); i0, i0x, i0y: the template image and its gradient.
+__device__ __forceinline__ PixelSystem pixel_system_vals(
+    float ix, float iy, float ixl, float ixr, float ixu, float ixd, float iyu, float iyd,
+    float iw, float asp, float asl, float asr, float asu, float asd, float u, float ul, float ur,
+    float uu, float ud, float v, float vl, float vr, float vu, float vd, bool bl, bool br,
+    bool bu, bool bd, int gx, int gy, int w, int h, float i0, float i0x, float i0y, float delta,
+    float gamma)
+{
+    const float Ix = ix, Iy = iy;
+    const float Ixx = cdiff(ixr, ixl);
+    const float Ixy = cdiff(ixd, ixu);
+    const float Iyy = cdiff(iyd, iyu);
+    const float Iz = iw - i0;
+    const float Ixz = Ix - i0x, Iyz = Iy - i0y;
+    const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
+    const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
+    float ad = delta * nd * psi_prime(nd * Iz * Iz);
+    float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
+    const float wx = (float)gx + u, wy = (float)gy + v;
+    if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) {
+        ad = 0.0f;
+        ag = 0.0f;
+    }
+    PixelSystem ps;
+    ps.cl = bl ? 0.5f * (asp + asl) : 0.0f;
+    ps.cr = br ? 0.5f * (asp + asr) : 0.0f;
+    ps.cu = bu ? 0.5f * (asp + asu) : 0.0f;
+    ps.cd = bd ? 0.5f * (asp + asd) : 0.0f;
+    const float sw = ps.cl + ps.cr + ps.cu + ps.cd;
+    const float su0 = ps.cl * (ul - u) + ps.cr * (ur - u) + ps.cu * (uu - u) + ps.cd * (ud - u);
+    const float sv0 = ps.cl * (vl - v) + ps.cr * (vr - v) + ps.cu * (vu - v) + ps.cd * (vd - v);
+    ps.i11 = __fdividef(1.0f, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
+    ps.i22 = __fdividef(1.0f, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
+    ps.a12 = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
+    ps.b1 = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
+    ps.b2 = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
+    return ps;
+}
+
+// The same system read from the staging and derivative windows: d indexes
+// the derivative window (row stride DS, origin dx0, dy0), e the staging
+// window (row stride ES).  Every index read lies in the windows (their rings
+// hold 0 outside the level).  IN as in stage_derivs.
 template <bool IN>
 __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const float *sIy,
                                                     const float *sAs, int DS, int dx0, int dy0,
@@ -209,39 +266,13 @@ __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const floa
     const int ym = (IN ? gy - 1 : max(gy - 1, 0)) - dy0;
     const int dx = gx - dx0, dy = gy - dy0;
     const int d = dy * DS + dx;
-    const float Ix = sIx[d], Iy = sIy[d];
-    const float Ixx = 0.5f * (sIx[dy * DS + xp] - sIx[dy * DS + xm]);
-    const float Ixy = 0.5f * (sIx[yp * DS + dx] - sIx[ym * DS + dx]);
-    const float Iyy = 0.5f * (sIy[yp * DS + dx] - sIy[ym * DS + dx]);
-    const float Iz = sW[e] - i0;
-    const float Ixz = Ix - i0x, Iyz = Iy - i0y;
-    const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
-    const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
-    float ad = delta * nd * psi_prime(nd * Iz * Iz);
-    float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
-    const float u = sU[e], v = sV[e];
-    const float wx = (float)gx + u, wy = (float)gy + v;
-    if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) {
-        ad = 0.0f;
-        ag = 0.0f;
-    }
-    const float asp = sAs[d];
-    PixelSystem ps;
-    ps.cl = IN || gx > 0 ? 0.5f * (asp + sAs[d - 1]) : 0.0f;
-    ps.cr = IN || gx + 1 < w ? 0.5f * (asp + sAs[d + 1]) : 0.0f;
-    ps.cu = IN || gy > 0 ? 0.5f * (asp + sAs[d - DS]) : 0.0f;
-    ps.cd = IN || gy + 1 < h ? 0.5f * (asp + sAs[d + DS]) : 0.0f;
-    const float sw = ps.cl + ps.cr + ps.cu + ps.cd;
-    const float su0 = ps.cl * (sU[e - 1] - u) + ps.cr * (sU[e + 1] - u) +
-                      ps.cu * (sU[e - ES] - u) + ps.cd * (sU[e + ES] - u);
-    const float sv0 = ps.cl * (sV[e - 1] - v) + ps.cr * (sV[e + 1] - v) +
-                      ps.cu * (sV[e - ES] - v) + ps.cd * (sV[e + ES] - v);
-    ps.i11 = __fdividef(1.0f, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
-    ps.i22 = __fdividef(1.0f, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
-    ps.a12 = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
-    ps.b1 = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
-    ps.b2 = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
-    return ps;
+    return pixel_system_vals(
+        sIx[d], sIy[d], sIx[dy * DS + xm], sIx[dy * DS + xp], sIx[ym * DS + dx],
+        sIx[yp * DS + dx], sIy[ym * DS + dx], sIy[yp * DS + dx], sW[e], sAs[d], sAs[d - 1],
+        sAs[d + 1], sAs[d - DS], sAs[d + DS], sU[e], sU[e - 1], sU[e + 1], sU[e - ES],
+        sU[e + ES], sV[e], sV[e - 1], sV[e + 1], sV[e - ES], sV[e + ES], IN || gx > 0,
+        IN || gx + 1 < w, IN || gy > 0, IN || gy + 1 < h, gx, gy, w, h, i0, i0x, i0y, delta,
+        gamma);
 }
 
 // One coefficient tile.  IN: the tile's staging window (tile + 2 px) lies
@@ -332,6 +363,164 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     else
         coeff_tile<false>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
                           ufs, plane, coefb, cfs, delta, gamma, alpha_s);
+}
+
+// Column-walk form of the same kernel.  A warp owns 28 output columns: lane
+// l holds column x = x0 - 2 + l, lanes 2..29 are outputs and lanes 0, 1, 30,
+// 31 the halo that the central differences and the forward differences of
+// the smoothness term need.  The warp walks R output rows down and keeps
+// the rows it needs in registers: W (the warped sample I1(x + U)) of rows
+// y .. y + 2, Ix, Iy and the smoothness weight of rows y - 1 .. y + 1, U and
+// V of rows y - 1 .. y + 2; horizontal neighbours come from lane shuffles.
+// Each row's U, V loads are issued two iterations and its bilinear taps one
+// iteration before their use.  Values of positions outside the level are 0,
+// as in the staging windows of coeff_tile, and every clamp and border test
+// is the tile form's, so both forms write the same coefficients.
+constexpr int kCWOut = 28;   // output columns per warp
+constexpr int kCWWarps = 4;  // warps per block, row strips stacked
+constexpr int kCWRows = 8;   // output rows per warp
+
+template <int R, bool IN, typename T>
+__device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *__restrict__ I0x,
+                                            const T *__restrict__ I0y, const T *__restrict__ I1,
+                                            int w, int h, int pitch, const float *__restrict__ U,
+                                            const float *__restrict__ V, float *__restrict__ cf,
+                                            int pl, int x, int y0, bool out_lane, float delta,
+                                            float gamma, float alpha_s)
+{
+    const bool xin = IN || (x >= 0 && x < w);
+    const bool hx = IN || x + 1 < w;
+    const bool bl = IN || x > 0;
+    const int ylast = y0 + R + 1;  // last row whose W, U and V are read
+    auto row_in = [&](int r) { return IN || (r >= 0 && r < h); };
+    auto load_uv = [&](int r, float &u, float &v) {
+        u = 0.0f;
+        v = 0.0f;
+        if (row_in(r) && xin) {
+            const int p = r * pitch + x;
+            u = U[p];
+            v = V[p];
+        }
+    };
+    auto taps = [&](int r, float u, float v) {
+        BilTaps t = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (row_in(r) && xin) t = bil_taps_i(I1, w, h, pitch, (float)x + u, (float)r + v);
+        return t;
+    };
+    // neighbour in x with the clamp of the central differences
+    auto right = [&](float c) {
+        const float n = __shfl_down_sync(kFull, c, 1);
+        return (IN || x + 1 < w) ? n : c;
+    };
+    auto left = [&](float c) {
+        const float n = __shfl_up_sync(kFull, c, 1);
+        return (IN || x > 0) ? n : c;
+    };
+    // Ix, Iy and the smoothness weight of row r from W of rows r - 1 .. r + 1
+    // and U, V of rows r, r + 1
+    auto derive = [&](int r, float wm, float w0, float wp, float u0, float u1, float v0,
+                      float v1, float &ix, float &iy, float &as) {
+        ix = cdiff(right(w0), left(w0));
+        iy = cdiff((IN || r + 1 < h) ? wp : w0, (IN || r > 0) ? wm : w0);
+        as = smooth_weight(u0, __shfl_down_sync(kFull, u0, 1), u1, v0,
+                           __shfl_down_sync(kFull, v0, 1), v1, hx, IN || r + 1 < h, alpha_s);
+    };
+
+    // prologue: U, V of rows y0 - 2 .. y0 + 3, W of rows y0 - 2 .. y0 + 1,
+    // the derivatives of rows y0 - 1 and y0, the taps of row y0 + 2
+    float ua, va, ub, vb, uc, vc, ud, vd, u2, v2, u3, v3;
+    load_uv(y0 - 2, ua, va);
+    load_uv(y0 - 1, ub, vb);
+    load_uv(y0, uc, vc);
+    load_uv(y0 + 1, ud, vd);
+    load_uv(y0 + 2, u2, v2);
+    load_uv(y0 + 3, u3, v3);
+    const float wa = bil_lerp(taps(y0 - 2, ua, va));
+    const float wb = bil_lerp(taps(y0 - 1, ub, vb));
+    float wc = bil_lerp(taps(y0, uc, vc));
+    float wd = bil_lerp(taps(y0 + 1, ud, vd));
+    BilTaps t2 = taps(y0 + 2, u2, v2);
+    float ixm, iym, asm_, ix0, iy0, as0;
+    derive(y0 - 1, wa, wb, wc, ub, uc, vb, vc, ixm, iym, asm_);
+    derive(y0, wb, wc, wd, uc, ud, vc, vd, ix0, iy0, as0);
+    auto ld_t = [&](const T *a, int p) { return ldp(&a[p]); };
+    int p = y0 * pitch + x;
+    const bool pin = row_in(y0) && xin;
+    float i0 = pin ? ld_t(I0, p) : 0.0f, i0x = pin ? ld_t(I0x, p) : 0.0f;
+    float i0y = pin ? ld_t(I0y, p) : 0.0f;
+
+#pragma unroll 1
+    for (int y = y0; y < y0 + R; ++y) {
+        if (!IN && y >= h) break;
+        // W, derivatives of row y + 1
+        const float we = bil_lerp(t2);
+        float ixp, iyp, asp_;
+        derive(y + 1, wc, wd, we, ud, u2, vd, v2, ixp, iyp, asp_);
+        // loads for the next iterations
+        BilTaps t3 = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (y + 3 <= ylast) t3 = taps(y + 3, u3, v3);
+        float u4 = 0.0f, v4 = 0.0f;
+        if (y + 4 <= ylast) load_uv(y + 4, u4, v4);
+        const int pn = p + pitch;
+        const bool nin = y + 1 < y0 + R && row_in(y + 1) && xin;
+        const float n_i0 = nin ? ld_t(I0, pn) : 0.0f, n_i0x = nin ? ld_t(I0x, pn) : 0.0f;
+        const float n_i0y = nin ? ld_t(I0y, pn) : 0.0f;
+        // the system of row y
+        const PixelSystem ps = pixel_system_vals(
+            ix0, iy0, left(ix0), right(ix0), (IN || y > 0) ? ixm : ix0,
+            (IN || y + 1 < h) ? ixp : ix0, (IN || y > 0) ? iym : iy0,
+            (IN || y + 1 < h) ? iyp : iy0, wc, as0, __shfl_up_sync(kFull, as0, 1),
+            __shfl_down_sync(kFull, as0, 1), asm_, asp_, uc, __shfl_up_sync(kFull, uc, 1),
+            __shfl_down_sync(kFull, uc, 1), ub, ud, vc, __shfl_up_sync(kFull, vc, 1),
+            __shfl_down_sync(kFull, vc, 1), vb, vd, bl, hx, IN || y > 0, IN || y + 1 < h, x, y,
+            w, h, i0, i0x, i0y, delta, gamma);
+        if (out_lane && xin) {
+            float *c = cf + p;
+            c[kCI11 * pl] = ps.i11;
+            c[kCI22 * pl] = ps.i22;
+            c[kCA12 * pl] = ps.a12;
+            c[kCB1 * pl] = ps.b1;
+            c[kCB2 * pl] = ps.b2;
+            c[kCWL * pl] = ps.cl;
+            c[kCWR * pl] = ps.cr;
+            c[kCWU * pl] = ps.cu;
+            c[kCWD * pl] = ps.cd;
+        }
+        // move the windows down one row
+        ixm = ix0; iym = iy0; asm_ = as0;
+        ix0 = ixp; iy0 = iyp; as0 = asp_;
+        wc = wd; wd = we;
+        ub = uc; vb = vc; uc = ud; vc = vd; ud = u2; vd = v2; u2 = u3; v2 = v3; u3 = u4; v3 = v4;
+        t2 = t3;
+        p = pn;
+        i0 = n_i0; i0x = n_i0x; i0y = n_i0y;
+    }
+}
+
+template <int R, typename T>
+__global__ void __launch_bounds__(32 * kCWWarps)
+var_coeff_cw_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
+                    const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
+                    int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs,
+                    size_t plane, float *__restrict__ coefb, size_t cfs, float delta,
+                    float gamma, float alpha_s)
+{
+    const int lane = threadIdx.x;
+    const int y0 = (blockIdx.y * kCWWarps + threadIdx.y) * R;
+    if (y0 >= h) return;  // the whole warp
+    const int f = blockIdx.z;
+    const int cx0 = blockIdx.x * kCWOut - 2;  // column of lane 0
+    const size_t po = (size_t)f * pfs;
+    const float *U = Ub + (size_t)f * ufs;
+    const bool out_lane = lane >= 2 && lane < 2 + kCWOut;
+    if (cx0 >= 0 && cx0 + 31 < w && y0 >= 2 && y0 + R + 1 < h)
+        coeff_strip<R, true>(I0b + po, I0xb + po, I0yb + po, I1b + po, w, h, pitch, U, U + plane,
+                             coefb + (size_t)f * cfs, (int)plane, cx0 + lane, y0, out_lane,
+                             delta, gamma, alpha_s);
+    else
+        coeff_strip<R, false>(I0b + po, I0xb + po, I0yb + po, I1b + po, w, h, pitch, U,
+                              U + plane, coefb + (size_t)f * cfs, (int)plane, cx0 + lane, y0,
+                              out_lane, delta, gamma, alpha_s);
 }
 
 // Left and right halo of a region in columns: R rounded up to even, so that
@@ -700,10 +889,32 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
     const int tile = kVR - 2 * R;                    // interior rows of a 64-row region
     const int tile_x = kVR - 2 * sor_halo_x(R);      // interior columns
     const dim3 cgrd((lv.w + kAX - 1) / kAX, (lv.h + kAY - 1) / kAY, frames);
+    // the coefficient kernel's form depends on the level's geometry and the
+    // storage type only, so single, batched and grouped windows of a level
+    // always run the same one (and give the same coefficients): the column
+    // walk from 1024 px wide (the finest level of 1280 x 720 frames), where
+    // it is the faster; smaller levels keep the tile form
+    const bool column_walk = lv.w >= 1024;
+    const dim3 wgrd((lv.w + kCWOut - 1) / kCWOut,
+                    ((lv.h + kCWRows - 1) / kCWRows + kCWWarps - 1) / kCWWarps, frames);
     const dim3 sgrd((lv.w + tile_x - 1) / tile_x, (lv.h + tile - 1) / tile, frames);
     float *a = U, *b = Utmp;
     for (int k = 0; k < fp.var_outer; ++k) {
-        {
+        if (column_walk) {
+            StageScope sc(kStVarCoeff, 1, st);
+            if (fp.half)
+                var_coeff_cw_kernel<kCWRows, __half><<<wgrd, dim3(32, kCWWarps), 0, st>>>(
+                    (const __half *)I0, (const __half *)I0x, (const __half *)I0y,
+                    (const __half *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
+                    u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
+                    fp.alpha_s);
+            else
+                var_coeff_cw_kernel<kCWRows, float><<<wgrd, dim3(32, kCWWarps), 0, st>>>(
+                    (const float *)I0, (const float *)I0x, (const float *)I0y,
+                    (const float *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
+                    u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
+                    fp.alpha_s);
+        } else {
             StageScope sc(kStVarCoeff, 1, st);
             if (fp.half)
                 var_coeff_kernel<__half><<<cgrd, dim3(kAX, kAY), 0, st>>>(
