@@ -239,8 +239,8 @@ def algorithmic_bytes_per_launch(stage, level, geo, n_events_per_window, P):
         "pyramid": lambda: 12.0 * Pl,             # gradients: I in, Ix and Iy out
         "patch_search": lambda: 16.0 * Pl + 8.0 * npl + 8.0 * Pc,
         "densify": lambda: 16.0 * Pl + 8.0 * npl,
-        "var_coeff": lambda: 60.0 * Pl,           # U, I1, I0, I0x, I0y in; 9 planes out
-        "var_sor": lambda: 52.0 * Pl,             # 9 planes and U in, U out
+        "var_coeff": lambda: 52.0 * Pl,           # U, I1, I0, I0x, I0y in; 7 planes out
+        "var_sor": lambda: 44.0 * Pl,             # 7 planes and U in, U out
         "flow_out": lambda: 16.0 * P,
     }
     f = per.get(stage)

@@ -5,8 +5,11 @@
 // I1(x + U) for a 32x16 tile plus 2 px in shared memory, builds derivatives
 // of the warped image and the smoothness weights, and writes every pixel's
 // 2x2 linear system (data and gradient-constancy terms normalised, weights
-// lagged at dU = 0): 1/a11, 1/a22, a12, b1, b2 and the four edge weights, as
-// nine planes.  Only the staging halo is shared between tiles.
+// lagged at dU = 0): 1/a11, 1/a22, a12, b1, b2 and the left and upper edge
+// weights, as seven planes (the right and lower weights are the neighbours'
+// left and upper ones).  Only the staging halo is shared between tiles.  On
+// levels from 1024 px wide the same systems come from var_coeff_cw_kernel,
+// a column walk with the rows in registers.
 //
 // var_sor_kernel: one block owns a 64x64 region and refines the flow of its
 // (64 - 2R)^2 interior, R = 2 * sweeps - 1.  It loads the region's linear
@@ -21,9 +24,10 @@
 // floating-point rounding).  It writes U + dU for its interior.
 //
 // var_sor_tma_kernel: the same sweeps in a persistent grid (one block per
-// SM) that walks over the regions, for grids of at least four regions per SM.  One thread loads each region's nine
-// coefficient planes into shared memory with a single TMA tensor copy
-// (cp.async.bulk.tensor, completion on an mbarrier); once every thread has
+// SM) that walks over the regions, for grids of at least four regions per
+// SM.  One thread loads each region's coefficient planes into shared memory
+// with a single TMA tensor copy (cp.async.bulk.tensor, completion on an
+// mbarrier); once every thread has
 // moved its values into registers, the copy of the block's next region is
 // issued and runs during the sweeps.  The box starts at the region's first
 // column rounded down to a multiple of 4 (the 16-byte rule of tensor
@@ -45,7 +49,11 @@ constexpr int kVWarps = kVR / kVS;       // warps per block (stacked strips)
 constexpr int kVThreads = 32 * kVWarps;  // 512
 constexpr size_t kVSmemFloats = 2 * 2 * kVWarps * 2 * 64;  // strip-end exchange
 constexpr size_t kVSmemFloats2 = 2 * 2 * 32 * 2 * 64;       // the same for 32 warps
-enum { kCI11 = 0, kCI22, kCA12, kCB1, kCB2, kCWL, kCWR, kCWU, kCWD, kCPlanes };
+// Coefficient planes of a pixel's system: 1/a11, 1/a22, a12, b1, b2 and the
+// left and upper edge weights.  The right and lower weights of a pixel are
+// the left and upper ones of its neighbours (each the mean of the same two
+// smoothness weights, so equal bit for bit) and are not stored.
+enum { kCI11 = 0, kCI22, kCA12, kCB1, kCB2, kCWL, kCWU, kCPlanes };
 
 constexpr int kTmaBoxW = kVR + 4;  // region columns + the rounding of the box start
 constexpr size_t kTmaCoefFloats = (size_t)kCPlanes * kVR * kTmaBoxW;
@@ -342,9 +350,7 @@ __device__ __forceinline__ void coeff_tile(
     cf[kCB1 * pl] = ps.b1;
     cf[kCB2 * pl] = ps.b2;
     cf[kCWL * pl] = ps.cl;
-    cf[kCWR * pl] = ps.cr;
     cf[kCWU * pl] = ps.cu;
-    cf[kCWD * pl] = ps.cd;
 }
 
 template <typename T>
@@ -482,9 +488,7 @@ __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *_
             c[kCB1 * pl] = ps.b1;
             c[kCB2 * pl] = ps.b2;
             c[kCWL * pl] = ps.cl;
-            c[kCWR * pl] = ps.cr;
             c[kCWU * pl] = ps.cu;
-            c[kCWD * pl] = ps.cd;
         }
         // move the windows down one row
         ixm = ix0; iym = iy0; asm_ = as0;
@@ -546,6 +550,27 @@ __device__ __forceinline__ void store_pair(const float *Uin, float *Uout, size_t
     }
 }
 
+// The right and lower edge weights of a thread's strip from the stored left
+// and upper ones: w_r(x) = w_l(x + 1) (the next lane's first column for the
+// strip's second column; 0 past the region's last column, whose right
+// neighbour holds dU = 0) and w_d(y) = w_u(y + 1) (wub: w_u of the row below
+// the strip).
+template <int VS>
+__device__ __forceinline__ void lower_right_weights(const float (&wl)[VS][2],
+                                                    const float (&wu)[VS][2],
+                                                    const float (&wub)[2], int lane,
+                                                    float (&wr)[VS][2], float (&wd)[VS][2])
+{
+#pragma unroll
+    for (int r = 0; r < VS; ++r) {
+        const float n = __shfl_down_sync(kFull, wl[r][0], 1);
+        wr[r][0] = wl[r][1];
+        wr[r][1] = lane < 31 ? n : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) wd[r][q] = r + 1 < VS ? wu[r + 1][q] : wub[q];
+    }
+}
+
 // A lane's two adjacent values of one plane (c: the first); EVEN: one
 // aligned 8-byte load.
 template <bool EVEN>
@@ -600,9 +625,7 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
             set_pair<EVEN>(b1[r], c + kCB1 * pl);
             set_pair<EVEN>(b2[r], c + kCB2 * pl);
             set_pair<EVEN>(wl[r], c + kCWL * pl);
-            set_pair<EVEN>(wr[r], c + kCWR * pl);
             set_pair<EVEN>(wu[r], c + kCWU * pl);
-            set_pair<EVEN>(wd[r], c + kCWD * pl);
             continue;
         }
         if (!EVEN) {
@@ -619,9 +642,7 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
                 b1[r][q] = in ? c[kCB1 * pl] : 0.0f;
                 b2[r][q] = in ? c[kCB2 * pl] : 0.0f;
                 wl[r][q] = in ? c[kCWL * pl] : 0.0f;
-                wr[r][q] = in ? c[kCWR * pl] : 0.0f;
                 wu[r][q] = in ? c[kCWU * pl] : 0.0f;
-                wd[r][q] = in ? c[kCWD * pl] : 0.0f;
             }
             continue;
         }
@@ -645,11 +666,27 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
             b1[r][q] = in ? (q ? v[kCB1].y : v[kCB1].x) : 0.0f;
             b2[r][q] = in ? (q ? v[kCB2].y : v[kCB2].x) : 0.0f;
             wl[r][q] = in ? (q ? v[kCWL].y : v[kCWL].x) : 0.0f;
-            wr[r][q] = in ? (q ? v[kCWR].y : v[kCWR].x) : 0.0f;
             wu[r][q] = in ? (q ? v[kCWU].y : v[kCWU].x) : 0.0f;
-            wd[r][q] = in ? (q ? v[kCWD].y : v[kCWD].x) : 0.0f;
         }
     }
+
+    // upper weights of the row below the strip (the next strip's first row;
+    // none below the region's last strip, whose lower neighbours hold dU = 0)
+    float wub[2] = {0.0f, 0.0f};
+    if (wp < WARPS - 1) {
+        const int gy = ry0 + (wp + 1) * VS;
+        if (inside) {
+            set_pair<EVEN>(wub, cf + gy * pitch + gx0 + kCWU * pl);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int gx = gx0 + q;
+                if (gx >= 0 && gx < w && gy >= 0 && gy < h)
+                    wub[q] = cf[gy * pitch + gx + kCWU * pl];
+            }
+        }
+    }
+    lower_right_weights<VS>(wl, wu, wub, lane, wr, wd);
 
     // red-black SOR; red = (x + y) even, first.  Given the parity of (x + y)
     // at a strip's first pixel, the column of a given colour in a given row
@@ -780,10 +817,18 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
                 b1[rr][q] = q ? v[kCB1].y : v[kCB1].x;
                 b2[rr][q] = q ? v[kCB2].y : v[kCB2].x;
                 wl[rr][q] = q ? v[kCWL].y : v[kCWL].x;
-                wr[rr][q] = q ? v[kCWR].y : v[kCWR].x;
                 wu[rr][q] = q ? v[kCWU].y : v[kCWU].x;
-                wd[rr][q] = q ? v[kCWD].y : v[kCWD].x;
             }
+        }
+        {
+            float wub[2] = {0.0f, 0.0f};
+            if (wp < kVWarps - 1) {
+                const float2 v = *reinterpret_cast<const float2 *>(
+                    cbuf + kCWU * kVR * kTmaBoxW + (wp + 1) * kVS * kTmaBoxW + ox + 2 * lane);
+                wub[0] = v.x;
+                wub[1] = v.y;
+            }
+            lower_right_weights<kVS>(wl, wu, wub, lane, wr, wd);
         }
         __syncthreads();  // every thread holds its coefficients: the buffer is free
         if (t == 0 && r + (int)gridDim.x < total) {
@@ -879,7 +924,7 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
                                 int frames, const FlowParams &fp, const CUtensorMap *coef_map,
                                 int *err, cudaStream_t st)
 {
-    // the level's planes are packed: frame stride 9 planes of this level
+    // the level's planes are packed: frame stride kCPlanes planes of this level
     const size_t coef_frame_stride = (size_t)kCPlanes * lv.plane;
     int dev = 0;
     cudaGetDevice(&dev);
