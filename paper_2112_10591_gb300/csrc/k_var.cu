@@ -101,7 +101,7 @@ __device__ __forceinline__ void sor_half(float (&du)[VS][2], float (&dv)[VS][2],
             lu = du[r][0];
             lv = dv[r][0];
         }
-        const int col = 2 * lane + q;
+        const int col = q * 32 + lane;  // the exchange rows hold the q = 0 column first
         float uu, uv, dnu, dnv;
         if (r > 0) {
             uu = du[r - 1][q];
@@ -141,15 +141,16 @@ __device__ __forceinline__ void sor_sweeps(float (&du)[VS][2], float (&dv)[VS][2
                                            int pw, int n_half, float omega)
 {
     for (int hs = 0; hs < n_half; ++hs) {
-        // exchange buffer of this half sweep: [top|bottom][warp][du|dv][64]
+        // exchange buffer of this half sweep: [top|bottom][warp][du|dv][q][lane]
+        // (a lane's two columns 32 floats apart: conflict-free accesses)
         float *xb = xch + (hs & 1) * (2 * WARPS * 2 * 64);
         float *xtop = xb, *xbot = xb + WARPS * 2 * 64;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            xtop[(wp * 2 + 0) * 64 + 2 * lane + q] = du[0][q];
-            xtop[(wp * 2 + 1) * 64 + 2 * lane + q] = dv[0][q];
-            xbot[(wp * 2 + 0) * 64 + 2 * lane + q] = du[VS - 1][q];
-            xbot[(wp * 2 + 1) * 64 + 2 * lane + q] = dv[VS - 1][q];
+            xtop[(wp * 2 + 0) * 64 + q * 32 + lane] = du[0][q];
+            xtop[(wp * 2 + 1) * 64 + q * 32 + lane] = dv[0][q];
+            xbot[(wp * 2 + 0) * 64 + q * 32 + lane] = du[VS - 1][q];
+            xbot[(wp * 2 + 1) * 64 + q * 32 + lane] = dv[VS - 1][q];
         }
         __syncthreads();
         if (pw == 0) {
@@ -502,7 +503,7 @@ __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *_
 }
 
 template <int R, typename T>
-__global__ void __launch_bounds__(32 * kCWWarps)
+__global__ void __launch_bounds__(32 * kCWWarps, 8)
 var_coeff_cw_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
                     int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs,
