@@ -233,47 +233,58 @@ edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, in
 }
 
 // ---------------------------------------------------------------- A4
-// Row pass: D(x) = min over columns x' of (x - x')^2 + h(x'), h(x') =
-// g(x', y)^2 -- the lower envelope of the row's parabolas, evaluated at every
-// pixel.  WPR warps serve one row; the row is cut into NB = 32 * WPR bands of
-// B = ceil(W / NB) columns, one band per lane.
-//  1. The row's h is staged in shared memory (-1: column without edge pixels).
-//  2. Each lane builds the lower envelope of its band's parabolas (the stack
-//     construction of the separable exact EDT; breakpoints compared exactly
-//     in 64-bit integers).
-//  3. Each lane walks its band's pixels left to right.  For every band within
-//     NEAR bands it keeps a pointer into that band's envelope and moves it
-//     forward while the next parabola is not higher at x; since the owner of x
-//     within one envelope never moves left as x grows, the walk costs O(1) per
-//     pixel on average.  Farther bands are visited (nearest first, binary
-//     search for the owner) only while their distance^2 is below the best
-//     value so far.
-//  4. Eq. 1 and the 8-bit scale, with coalesced stores.
+// Row pass: D(x) = min over columns s of (x - s)^2 + h(s), h(s) = g(s, y)^2,
+// the lower envelope of the row's parabolas evaluated at every pixel.  With
+// F(s) = s^2 + h(s) it reads D(x) = x^2 + min_s (F(s) - 2 x s): a minimum of
+// lines in x, so the sites that own part of the envelope are exactly the
+// vertices of the lower convex hull of the points (s, F(s)).  One warp serves
+// one row and its 32 lanes own bands of B columns (B odd, so that the lanes'
+// shared-memory accesses fall in distinct banks).
+//  1. The row's F is staged in shared memory (-1: column without edge pixels).
+//  2. Each lane builds the lower hull of its band's points with a stack
+//     (orientation tests exact in 64-bit integers; a point on the segment of
+//     its neighbours is dropped, which never changes a minimum).
+//  3. Five rounds merge the hulls of neighbouring groups of 1, 2, 4, 8 and 16
+//     bands.  The group's first lane finds the lower bridge of the two hulls
+//     by walking from their inner ends (the left hull's last vertex moves left
+//     and the right hull's first vertex moves right while the vertex is not
+//     strictly below the line through the other two); the right hull's
+//     surviving vertices are then moved down behind the left hull's, so a
+//     group's hull always starts at its first column.
+//  4. Each lane walks its band's pixels left to right with a pointer into the
+//     row's hull (binary search for the first pixel): along a strictly convex
+//     hull the owner of x never moves left as x grows.
+//  5. Eq. 1 (or an ablation surface) and the 8-bit scale, coalesced stores.
 // Every step is an exact integer minimum, so D is bit-identical to any exact
-// EDT, whatever WPR and NEAR: single windows use twice the warps per row
-// (half the pixels per lane) to cut latency, batches the narrower layout.
+// EDT.  The work per pixel is a few hull steps whatever the distance to the
+// nearest edge, and the lanes of a warp stay in step.
 
-// With sites a < b < c on an envelope, is b hidden once c arrives?
-// Breakpoint s(p, q) = ((h_q + q^2) - (h_p + p^2)) / (2 (q - p)) for p < q;
-// b is hidden iff s(b, c) <= s(a, b).
-__device__ __forceinline__ bool hidden(int a, int b, int c, const int32_t *h)
+// With hull points a < b < c (columns; F as above): is b on or above the
+// segment from a to c, i.e. not a strict vertex of the lower hull?
+__device__ __forceinline__ bool above_chord(int a, int b, int c, const int32_t *F)
 {
-    const long long fa = (long long)h[a] + (long long)a * a;
-    const long long fb = (long long)h[b] + (long long)b * b;
-    const long long fc = (long long)h[c] + (long long)c * c;
+    const long long fa = F[a], fb = F[b], fc = F[c];
     return (fc - fb) * (long long)(b - a) <= (fb - fa) * (long long)(c - b);
 }
 
-// (x - site)^2 + h(site) < 2^29 for images up to 16384 px a side.
-__device__ __forceinline__ int para(int x, int site, const int32_t *h)
+// (x - s)^2 + h(s) from F(s) = s^2 + h(s); every term is below 2^29 for
+// images up to 16384 px a side.
+__device__ __forceinline__ int para(int x, int s, const int32_t *F)
 {
-    const int d = x - site;
-    return d * d + h[site];
+    const int d = x - s;
+    return d * d + (F[s] - s * s);
 }
 
-__host__ __device__ __forceinline__ size_t rows_smem_words(int W, int wpr)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRowsPerBlock = 4;                  // rows (warps) per block
+constexpr int kRowLoads = 8;                      // column distances in flight per lane
+constexpr size_t kRowsSmemCap = 200 * 1024;       // bytes; 16384-px rows fit one per block
+
+// Shared memory of one row, in bytes: F and D (int32) and the hull's columns
+// (int16: every column is below 2^14), padded to a multiple of 4 bytes.
+__host__ __device__ __forceinline__ size_t rows_smem_bytes(int W)
 {
-    return 3 * (size_t)W + 2 * 32 * (size_t)wpr + 1;
+    return 8 * (size_t)W + 2 * (((size_t)W + 1) & ~(size_t)1);
 }
 
 // Level-0 intensity of the flow block.  FP32 storage keeps I = 255 d_exp.
@@ -304,127 +315,202 @@ __device__ __forceinline__ float ablation_surface(const SurfaceMap &sm, float d)
     return sm.mode == 1 ? d : (sm.mode == 2 ? fminf(d, sm.d_sat) : log1pf(d));
 }
 
-template <int WPR, int NEAR, typename T>
-__global__ void edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs,
-                                        int W, int H, int rows_per_block, SurfaceMap sm,
-                                        int32_t *__restrict__ D_dense,
-                                        float *__restrict__ S_dense, T *__restrict__ I0,
-                                        int ipitch, size_t ifs)
+// Lower bridge of two hulls of one row whose columns are x-separated: the
+// left hull hs[aL, aL + nL), the right one hs[aR, aR + nR), both non-empty.
+// On return the merged hull is hs[aL, aL + i] followed by hs[aR + j, aR + nR).
+// The left end moves left and the right end moves right while the vertex is
+// not strictly below the line through the other two; each move drops a
+// vertex, so the walk ends after at most nL + nR steps.
+__device__ __forceinline__ void bridge(const int16_t *hs, const int32_t *F, int aL, int nL,
+                                       int aR, int nR, int &i, int &j)
+{
+    i = nL - 1;
+    j = 0;
+    int li = hs[aL + i], rj = hs[aR];
+    for (;;) {
+        bool moved = false;
+        while (j + 1 < nR) {
+            const int rn = hs[aR + j + 1];
+            if (!above_chord(li, rj, rn, F)) break;
+            rj = rn;
+            ++j;
+            moved = true;
+        }
+        while (i > 0) {
+            const int lp = hs[aL + i - 1];
+            if (!above_chord(lp, li, rj, F)) break;
+            li = lp;
+            --i;
+            moved = true;
+        }
+        if (!moved) break;
+    }
+}
+
+// WPR warps serve a row (32 WPR bands).  WPR = 1: rows_per_block rows of one
+// warp each, warp-level barriers only.  WPR > 1: one row per block; the merge
+// rounds of groups wider than a warp go through shared memory and block
+// barriers.  D is exact whatever WPR, so the layout never changes a result.
+template <int WPR, typename T>
+__global__ void __launch_bounds__(32 * kRowsPerBlock)
+edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs, int W, int H,
+                        int rows_per_block, SurfaceMap sm, int32_t *__restrict__ D_dense,
+                        float *__restrict__ S_dense, T *__restrict__ I0, int ipitch, size_t ifs)
 {
     constexpr int NB = 32 * WPR;
     extern __shared__ int32_t smem[];
+    __shared__ int s_cnt[NB];         // hull sizes of the group leaders (WPR > 1)
+    __shared__ int s_move[NB / 64 + 1][3];  // src, dst, len of a cross-warp group's move
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rib = warp / WPR, sub = warp % WPR;
+    const int rib = warp / WPR;                 // row within the block
+    const int tr = (warp % WPR) * 32 + lane;    // this lane's band
     const int y = blockIdx.x * rows_per_block + rib;
+    if (y >= H) return;  // WPR = 1: the whole warp; WPR > 1: never (one row per block)
     const int f = blockIdx.y;
-    const bool valid = y < H;
-    int32_t *h = smem + (size_t)rib * rows_smem_words(W, WPR);
-    int32_t *stk = h + W;       // envelope sites, per band
-    int32_t *res = stk + W;     // D per pixel of the row
-    int32_t *cnts = res + W;    // envelope size per band
-    int32_t *minh = cnts + NB;  // smallest h of the band's sites (a lower bound of its parabolas)
-    int32_t *anyf = minh + NB;  // row has an edge pixel
-    const int tr = sub * 32 + lane;  // thread index within the row
+    int32_t *F = smem + (size_t)rib * (rows_smem_bytes(W) / 4);
+    int32_t *res = F + W;  // D of the row's pixels
+    // hull columns; a group's hull starts at its first column
+    int16_t *hs = reinterpret_cast<int16_t *>(res + W);
+    auto row_sync = [] {
+        if (WPR == 1) __syncwarp();
+        else __syncthreads();
+    };
     const int ginf = W + H;
-    if (tr == 0) *anyf = 0;
-    __syncthreads();
-    if (valid) {
-        const int32_t *grow = g + (size_t)f * gfs + (size_t)y * gpitch;
-        int any = 0;
-        for (int x = tr; x < W; x += NB) {
-            const int gv = grow[x];
-            h[x] = gv >= ginf ? -1 : gv * gv;
-            any |= gv < ginf ? 1 : 0;
-        }
-        if (any) *anyf = 1;  // benign race: every writer stores 1
-    }
-    __syncthreads();
-    const bool any = valid && *anyf;
-
-    const int B = (W + NB - 1) / NB;
-    const int bi = tr;  // this lane's band
-    const int a = min(W, bi * B), b = min(W, a + B);
-    int cnt = 0, mh = 0x7fffffff;
-    if (any) {
-        for (int q = a; q < b; ++q) {
-            if (h[q] < 0) continue;
-            mh = min(mh, h[q]);
-            while (cnt >= 2 && hidden(stk[a + cnt - 2], stk[a + cnt - 1], q, h)) --cnt;
-            stk[a + cnt++] = q;
-        }
-    }
-    if (valid) {
-        cnts[bi] = cnt;
-        minh[bi] = mh;
-    }
-    __syncthreads();
-
-    if (any) {
-        int ptr[2 * NEAR + 1];
+    const int32_t *grow = g + (size_t)f * gfs + (size_t)y * gpitch;
+    // loads issued in batches of kRowLoads before their first use
+    for (int x0 = tr; x0 < W; x0 += NB * kRowLoads) {
+        int gv[kRowLoads];
 #pragma unroll
-        for (int k = 0; k <= 2 * NEAR; ++k) ptr[k] = 0;
+        for (int u = 0; u < kRowLoads; ++u) {
+            const int x = x0 + NB * u;
+            gv[u] = x < W ? grow[x] : ginf;
+        }
+#pragma unroll
+        for (int u = 0; u < kRowLoads; ++u) {
+            const int x = x0 + NB * u;
+            if (x < W) F[x] = gv[u] >= ginf ? -1 : gv[u] * gv[u] + x * x;
+        }
+    }
+    row_sync();
+
+    // 2. the lower hull of the lane's band
+    const int B = ((W + NB - 1) / NB) | 1;
+    const int a = min(W, tr * B), b = min(W, a + B);
+    int cnt = 0;
+    for (int q = a; q < b; ++q) {
+        if (F[q] < 0) continue;
+        while (cnt >= 2 && above_chord(hs[a + cnt - 2], hs[a + cnt - 1], q, F)) --cnt;
+        hs[a + cnt++] = (int16_t)q;
+    }
+    __syncwarp();
+
+    // 3. merge rounds within the warp; the first lane of a group holds the
+    // group's hull size
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int gs = 2 << k, half = 1 << k;
+        const int nR = __shfl_down_sync(kFull, cnt, half);  // read by group leaders only
+        const int leader = lane & ~(gs - 1);
+        int src = 0, dst = 0, len = 0;
+        if (lane == leader) {
+            const int AR = min(W, (tr + half) * B);  // the right half's first column
+            int i = cnt - 1, j = 0;
+            if (cnt > 0 && nR > 0) bridge(hs, F, a, cnt, AR, nR, i, j);
+            src = AR + j;
+            dst = a + i + 1;
+            len = nR - j;
+            cnt = i + 1 + len;
+        }
+        src = __shfl_sync(kFull, src, leader);
+        dst = __shfl_sync(kFull, dst, leader);
+        len = __shfl_sync(kFull, len, leader);
+        // move the right hull's survivors down (dst <= src: every read of a
+        // later step lies above every write of an earlier one)
+        const int steps = __reduce_max_sync(kFull, (unsigned)((len + gs - 1) / gs));
+        const int e0 = lane - leader;
+        for (int t = 0; t < steps; ++t) {
+            const int e = t * gs + e0;
+            int v = 0;
+            if (e < len) v = hs[src + e];
+            __syncwarp();
+            if (e < len) hs[dst + e] = (int16_t)v;
+            __syncwarp();
+        }
+    }
+    int n;  // the row's hull: hs[0, n)
+    if (WPR == 1) {
+        n = __shfl_sync(kFull, cnt, 0);
+    } else {
+        // merge rounds across the row's warps
+        if (lane == 0) s_cnt[tr] = cnt;
+        __syncthreads();
+#pragma unroll
+        for (int k = 5; (2 << k) <= NB; ++k) {
+            const int gs = 2 << k, half = 1 << k;
+            const int grp = tr / gs, leader = grp * gs;
+            if (tr == leader) {
+                const int nL = s_cnt[tr], nR = s_cnt[tr + half];
+                const int AR = min(W, (tr + half) * B);
+                int i = nL - 1, j = 0;
+                if (nL > 0 && nR > 0) bridge(hs, F, a, nL, AR, nR, i, j);
+                s_move[grp][0] = AR + j;
+                s_move[grp][1] = a + i + 1;
+                s_move[grp][2] = nR - j;
+                s_cnt[tr] = i + 1 + nR - j;
+            }
+            __syncthreads();
+            const int src = s_move[grp][0], dst = s_move[grp][1], len = s_move[grp][2];
+            int steps = 0;
+#pragma unroll
+            for (int q = 0; q < NB / gs; ++q) steps = max(steps, (s_move[q][2] + gs - 1) / gs);
+            const int e0 = tr - leader;
+            for (int t = 0; t < steps; ++t) {
+                const int e = t * gs + e0;
+                int v = 0;
+                if (e < len) v = hs[src + e];
+                __syncthreads();
+                if (e < len) hs[dst + e] = (int16_t)v;
+                __syncthreads();
+            }
+            __syncthreads();  // s_move is rewritten by the next round
+        }
+        n = s_cnt[0];
+    }
+
+    // 4. D of the lane's pixels
+    if (n > 0 && a < b) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (para(a, hs[mid + 1], F) <= para(a, hs[mid], F)) lo = mid + 1;
+            else hi = mid;
+        }
+        int kk = lo, sk = hs[lo];
         for (int x = a; x < b; ++x) {
-            int best = 0x7fffffff;
-#pragma unroll
-            for (int k = 0; k <= 2 * NEAR; ++k) {
-                const int M = bi + k - NEAR;
-                if (M < 0 || M >= NB) continue;
-                const int ma = min(W, M * B), mb = min(W, ma + B);
-                const int cM = cnts[M];
-                if (cM == 0) continue;
-                const int gap = M < bi ? x - (mb - 1) : (M > bi ? ma - x : 0);
-                // no parabola of band M is below gap^2 + its smallest h
-                if (M != bi && gap * gap + minh[M] >= best) continue;
-                const int32_t *sl = stk + ma;
-                int pk = ptr[k];
-                int cur = para(x, sl[pk], h);
-                while (pk + 1 < cM) {
-                    const int nxt = para(x, sl[pk + 1], h);
-                    if (nxt > cur) break;
-                    cur = nxt;
-                    ++pk;
-                }
-                ptr[k] = pk;
-                best = min(best, cur);
+            int cur = para(x, sk, F);
+            while (kk + 1 < n) {
+                const int sn = hs[kk + 1];
+                const int nx = para(x, sn, F);
+                if (nx > cur) break;
+                cur = nx;
+                sk = sn;
+                ++kk;
             }
-            for (int dist = NEAR + 1; dist < NB; ++dist) {
-                bool progress = false;
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int M = side ? bi + dist : bi - dist;
-                    if (M < 0 || M >= NB) continue;
-                    const int ma = min(W, M * B), mb = min(W, ma + B);
-                    if (ma >= mb) continue;
-                    const int gap = side ? ma - x : x - (mb - 1);  // < 2^14: gap^2 fits
-                    if (gap * gap >= best) continue;
-                    progress = true;
-                    const int cM = cnts[M];
-                    if (cM == 0 || gap * gap + minh[M] >= best) continue;
-                    const int32_t *sl = stk + ma;
-                    int lo = 0, hi = cM - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (para(x, sl[mid + 1], h) <= para(x, sl[mid], h)) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    best = min(best, para(x, sl[lo], h));
-                }
-                if (!progress) break;
-            }
-            res[x] = best;
+            res[x] = cur;
         }
     }
-    __syncthreads();
+    row_sync();
 
-    if (!valid) return;
+    // 5. surface and intensity (n == 0: the image has no edge pixel)
     T *irow = I0 ? I0 + (size_t)f * ifs + (size_t)y * ipitch : nullptr;
     const size_t dbase = (size_t)f * W * H + (size_t)y * W;
+    const float inv_alpha = 1.0f / sm.alpha;
     for (int x = tr; x < W; x += NB) {
-        const int32_t D = any ? res[x] : kInfD;
+        const int32_t D = n > 0 ? res[x] : kInfD;
         float S = 1.0f, C = 0.0f;  // d_exp of Eq. 1 and its complement 1 - d_exp
         if (sm.mode == 0) {
             if (D != kInfD) {
-                C = expf(-sqrtf((float)D) / sm.alpha);
+                C = expf(-sqrtf((float)D) * inv_alpha);
                 S = 1.0f - C;
             }
             if (irow) st_int(&irow[x], S, C);
@@ -513,13 +599,14 @@ void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stri
                                          g_frame_stride, CH);
 }
 
-// Warps per row: one below 640 px, two above; single windows (one or two
-// frames per launch) of rows from 1024 px use four, with a window of four
-// near bands each side (two otherwise).
+// Warps per row: one for batches (fewest instructions per frame) and rows
+// under 512 px; single windows (one or two frames per launch) of wider rows
+// use two, or four from 1024 px, one row per block, to shorten the serial
+// work of a lane.
 int edt_rows_wpr(int W, int frames)
 {
-    const int wpr = W >= 640 ? 2 : 1;
-    return (wpr == 2 && W >= 1024 && frames <= 2) ? 4 : wpr;
+    if (frames > 2 || W < 512) return 1;
+    return W >= 1024 ? 4 : 2;
 }
 
 template <typename T>
@@ -528,20 +615,22 @@ void edt_rows_t(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int
                 size_t i_frame_stride, int frames, cudaStream_t st)
 {
     const int wpr = edt_rows_wpr(W, frames);
-    int rows = wpr == 1 ? 4 : 2;
-    while (rows > 1 && (size_t)rows * rows_smem_words(W, wpr) * 4 > 200 * 1024) --rows;
-    const size_t smem = (size_t)rows * rows_smem_words(W, wpr) * 4;
+    // one warp a row: four rows per block, fewer where a row's shared memory
+    // is large; wider layouts: one row per block
+    int rows = wpr == 1 ? kRowsPerBlock : 1;
+    while (rows > 1 && (size_t)rows * rows_smem_bytes(W) > kRowsSmemCap) --rows;
+    const size_t smem = (size_t)rows * rows_smem_bytes(W);
     dim3 grd((H + rows - 1) / rows, frames);
     if (wpr == 4)
-        edt_rows_surface_kernel<4, 4, T><<<grd, 32 * 4 * rows, smem, st>>>(
-            g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
+        edt_rows_surface_kernel<4, T><<<grd, 128, smem, st>>>(
+            g, g_pitch, g_frame_stride, W, H, 1, sm, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
     else if (wpr == 2)
-        edt_rows_surface_kernel<2, 2, T><<<grd, 32 * 2 * rows, smem, st>>>(
-            g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
+        edt_rows_surface_kernel<2, T><<<grd, 64, smem, st>>>(
+            g, g_pitch, g_frame_stride, W, H, 1, sm, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
     else
-        edt_rows_surface_kernel<1, 2, T><<<grd, 32 * rows, smem, st>>>(
+        edt_rows_surface_kernel<1, T><<<grd, 32 * rows, smem, st>>>(
             g, g_pitch, g_frame_stride, W, H, rows, sm, D_dense, S_dense, I0, i_pitch,
             i_frame_stride);
 }
@@ -571,18 +660,15 @@ void launch_edt_rows_surface(const int32_t *g, int g_pitch, size_t g_frame_strid
 
 void init_front_attributes()
 {
-    cudaFuncSetAttribute(edt_rows_surface_kernel<1, 2, float>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<2, 2, float>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<4, 4, float>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<1, 2, __half>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<2, 2, __half>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(edt_rows_surface_kernel<4, 4, __half>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    auto opt_in = [](const void *fn) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsSmemCap);
+    };
+    opt_in((const void *)edt_rows_surface_kernel<1, float>);
+    opt_in((const void *)edt_rows_surface_kernel<2, float>);
+    opt_in((const void *)edt_rows_surface_kernel<4, float>);
+    opt_in((const void *)edt_rows_surface_kernel<1, __half>);
+    opt_in((const void *)edt_rows_surface_kernel<2, __half>);
+    opt_in((const void *)edt_rows_surface_kernel<4, __half>);
 }
 
 void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pitch, bool half,
