@@ -20,8 +20,27 @@ namespace {
 // ---------------------------------------------------------------- A1 scatter
 // One thread per event.  The window index of an event is
 // floor((t - t_begin) / dt) when it lies in [0, n_windows); duplicates collapse
-// (a byte store of 1 is idempotent).  Counters are aggregated per warp over
-// lanes that share a window, so sorted event streams cost one atomic per warp.
+// (a byte store of 1 is idempotent).  A block walks one contiguous chunk of
+// the events, 32 per warp and step.  Timestamps are sorted, so a warp's 32
+// events nearly always share a window and its counts run in registers until
+// the window changes (then one atomic per counter); a step whose events
+// straddle a window boundary counts per group of lanes that share a window.
+__device__ __forceinline__ void flush_counts(int cur, unsigned long long &c_in,
+                                             unsigned long long &c_oob, unsigned long long &c_time,
+                                             int lane, DevStats *stats,
+                                             unsigned long long *dropped_time)
+{
+    if (lane == 0) {
+        if (cur >= 0) {
+            if (c_in) atomicAdd(&stats[cur].in_window, c_in);
+            if (c_oob) atomicAdd(&stats[cur].dropped_oob, c_oob);
+        } else if (cur == -1 && c_time) {
+            atomicAdd(dropped_time, c_time);
+        }
+    }
+    c_in = c_oob = c_time = 0;
+}
+
 __global__ void scatter_kernel(const uint16_t *__restrict__ x, const uint16_t *__restrict__ y,
                                const int64_t *__restrict__ t, int64_t n, int64_t t_begin,
                                int64_t dt, int n_windows, int W, int H, int pitch,
@@ -30,12 +49,17 @@ __global__ void scatter_kernel(const uint16_t *__restrict__ x, const uint16_t *_
 {
     const int64_t span = dt * (int64_t)n_windows;
     const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t per_block =
+        ((n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+    const int64_t beg = (int64_t)blockIdx.x * per_block;
+    const int64_t end = min(n, beg + per_block);
+    int cur = -3;  // window of the running counts (-1: outside every window, -3: none)
+    unsigned long long c_in = 0, c_oob = 0, c_time = 0;
+    for (int64_t base = beg; base < end; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
         int k = -2;  // -2: no event (tail), -1: outside every window
         bool oob = false;
-        if (i < n) {
+        if (i < end) {
             const int64_t rel = t[i] - t_begin;
             k = -1;
             if (rel >= 0 && rel < span) {
@@ -47,8 +71,26 @@ __global__ void scatter_kernel(const uint16_t *__restrict__ x, const uint16_t *_
                     oob = true;
             }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, k);
+        const unsigned valid = __ballot_sync(0xffffffffu, k != -2);
         const unsigned oob_mask = __ballot_sync(0xffffffffu, oob);
+        if (valid == 0) continue;  // warp-uniform
+        const int kl = __shfl_sync(0xffffffffu, k, __ffs(valid) - 1);
+        if (__all_sync(0xffffffffu, k == -2 || k == kl)) {
+            if (kl != cur) {
+                flush_counts(cur, c_in, c_oob, c_time, lane, stats, dropped_time);
+                cur = kl;
+            }
+            if (kl >= 0) {
+                c_in += __popc(valid);
+                c_oob += __popc(oob_mask);
+            } else {
+                c_time += __popc(valid);
+            }
+            continue;
+        }
+        flush_counts(cur, c_in, c_oob, c_time, lane, stats, dropped_time);
+        cur = -3;
+        const unsigned peers = __match_any_sync(0xffffffffu, k);
         if (lane == __ffs(peers) - 1) {
             if (k >= 0) {
                 atomicAdd(&stats[k].in_window, (unsigned long long)__popc(peers));
@@ -59,6 +101,7 @@ __global__ void scatter_kernel(const uint16_t *__restrict__ x, const uint16_t *_
             }
         }
     }
+    flush_counts(cur, c_in, c_oob, c_time, lane, stats, dropped_time);
 }
 
 // Scatter for a group of streams: frame f takes the events of descriptor f.
@@ -86,14 +129,28 @@ __global__ void scatter_desc_kernel(const ebof_window_desc *__restrict__ desc, i
             }
         }
     }
-    // warp sums, one atomic per warp and counter
+    // block sums, one atomic per block and counter (same-address atomics
+    // serialise in L2)
+    __shared__ unsigned long long s_sum[3][32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         in_w += __shfl_xor_sync(0xffffffffu, in_w, o);
         oob += __shfl_xor_sync(0xffffffffu, oob, o);
         out_t += __shfl_xor_sync(0xffffffffu, out_t, o);
     }
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if (lane == 0) {
+        s_sum[0][warp] = in_w;
+        s_sum[1][warp] = oob;
+        s_sum[2][warp] = out_t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nwarps; ++k) {
+            in_w += s_sum[0][k];
+            oob += s_sum[1][k];
+            out_t += s_sum[2][k];
+        }
         if (in_w) atomicAdd(&stats[f].in_window, in_w);
         if (oob) atomicAdd(&stats[f].dropped_oob, oob);
         if (out_t) atomicAdd(dropped_time, out_t);
@@ -151,8 +208,9 @@ denoise_fill_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Edf, in
         Edf[(size_t)f * fstride + (size_t)y * pitch + x] = v;
         if (export_dense) export_dense[(size_t)f * W * H + (size_t)y * W + x] = v;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, v != 0);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&stats[f].edge_px, (unsigned long long)__popc(m));
+    // one atomic per block: same-address atomics serialise in L2
+    const int nedge = __syncthreads_count(v != 0);
+    if (t == 0 && nedge) atomicAdd(&stats[f].edge_px, (unsigned long long)nedge);
 }
 
 // ---------------------------------------------------------------- A3
@@ -185,10 +243,15 @@ edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, in
     for (int wi = 0; wi < kColMaxWords; ++wi) {
         unsigned m = 0;
         if (wi < nw && colok) {
-            for (int b = 0; b < 32; ++b) {
-                const int y = y0 + wi * 32 + b;
-                if (y < y1 && e[(size_t)y * epitch + x]) m |= 1u << b;
-            }
+            // all 32 loads in flight before the first test (rows past the
+            // chunk read its last row and are masked out)
+            uint8_t ev[32];
+#pragma unroll
+            for (int b = 0; b < 32; ++b)
+                ev[b] = e[(size_t)min(y0 + wi * 32 + b, y1 - 1) * epitch + x];
+#pragma unroll
+            for (int b = 0; b < 32; ++b)
+                if (y0 + wi * 32 + b < y1 && ev[b]) m |= 1u << b;
         }
         mask[wi] = m;
         if (m) {
