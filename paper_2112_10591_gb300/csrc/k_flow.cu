@@ -317,14 +317,36 @@ __device__ __forceinline__ void cover_range(int x, int n, int ps, int stride, in
     last = x >= n - ps;
 }
 
-// MAXC > 0: at most MAXC covering patches per axis, loops unrolled and
-// predicated so that the patches' loads are in flight together; 0: runtime
-// loops.  The patches are summed in the same order either way.
-template <typename T, int MAXC>
-__global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ I1b,
-                               int w, int h, int pitch, size_t pfs, const float *__restrict__ upb,
-                               size_t upfs, int npx, int npy, float *__restrict__ Ub, size_t ufs,
-                               size_t plane, int ps, int stride)
+// Thread per pixel.  NC = ceil(ps / stride) bounds the regular patches that
+// cover a pixel per axis: their loops are unrolled and predicated so that the
+// loads of all of them are in flight together, and the patch flush with the
+// right or lower border (which covers only pixels within ps of it) is a
+// separate branch.  NC = 0: runtime loops.  Every pixel sums its covering
+// patches in ascending (row, column) order, the flush patch last on each
+// axis.  Where the four taps lie inside the level the sample takes its
+// weights from frac(u), frac(v) directly (the clamp cannot act); elsewhere
+// it is the clamped bilinear sample.
+template <typename T>
+__device__ __forceinline__ float dense_sample(const T *__restrict__ I1, int w, int h, int pitch,
+                                              int x, int y, float u, float v)
+{
+    const float fu = floorf(u), fv = floorf(v);
+    const float sxf = (float)x + fu, syf = (float)y + fv;
+    if (sxf >= 0.0f && sxf + 1.0f <= (float)(w - 1) && syf >= 0.0f &&
+        syf + 1.0f <= (float)(h - 1)) {
+        const float ax = u - fu, ay = v - fv;
+        const T *r0 = I1 + (int)syf * pitch + (int)sxf, *r1 = r0 + pitch;
+        const float a = ldp(&r0[0]), b = ldp(&r0[1]), c = ldp(&r1[0]), d = ldp(&r1[1]);
+        return (1.0f - ay) * ((1.0f - ax) * a + ax * b) + ay * ((1.0f - ax) * c + ax * d);
+    }
+    return bilinear_i(I1, w, h, pitch, (float)x + u, (float)y + v);
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256)
+densify_kernel(const T *__restrict__ I0b, const T *__restrict__ I1b, int w, int h, int pitch,
+               size_t pfs, const float *__restrict__ upb, size_t upfs, int npx, int npy,
+               float *__restrict__ Ub, size_t ufs, size_t plane, int ps, int stride)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -332,8 +354,7 @@ __global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ 
     const int f = blockIdx.z;
     const T *I0 = I0b + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
     const float *up = upb + (size_t)f * upfs;
-    const int np = npx * npy;
-    const float *vp = up + np;
+    const float *vp = up + npx * npy;
     int ilo, ihi, jlo, jhi;
     bool ilast, jlast;
     cover_range(x, w, ps, stride, npx, ilo, ihi, ilast);
@@ -342,35 +363,30 @@ __global__ void densify_kernel(const T *__restrict__ I0b, const T *__restrict__ 
     float nu = 0.0f, nv = 0.0f, den = 0.0f;
     auto add = [&](int id) {
         const float u = up[id], v = vp[id];
-        const float r = bilinear_i(I1, w, h, pitch, (float)x + u, (float)y + v) - i0;
+        const float r = dense_sample(I1, w, h, pitch, x, y, u, v) - i0;
         const float lam = 1.0f / fmaxf(1.0f, fabsf(r));
         nu += lam * u; nv += lam * v; den += lam;
     };
-    if (MAXC > 0) {
+    // the patches of row j: regular columns, then the flush one
+    auto row = [&](int j) {
+        const int base = j * npx;
+        if (NC > 0) {
 #pragma unroll
-        for (int dj = 0; dj < (MAXC > 0 ? MAXC : 1); ++dj) {
-            const int jj = jlo + dj;
-            const bool vj = jj <= jhi || (jj == jhi + 1 && jlast);
-            const int j = jj <= jhi ? jj : npy - 1;
-#pragma unroll
-            for (int di = 0; di < (MAXC > 0 ? MAXC : 1); ++di) {
-                const int ii = ilo + di;
-                const bool vi = ii <= ihi || (ii == ihi + 1 && ilast);
-                const int i = ii <= ihi ? ii : npx - 1;
-                if (vj && vi) add(j * npx + i);
-            }
+            for (int di = 0; di < (NC > 0 ? NC : 1); ++di)
+                if (ilo + di <= ihi) add(base + ilo + di);
+        } else {
+            for (int i = ilo; i <= ihi; ++i) add(base + i);
         }
+        if (ilast) add(base + npx - 1);
+    };
+    if (NC > 0) {
+#pragma unroll
+        for (int dj = 0; dj < (NC > 0 ? NC : 1); ++dj)
+            if (jlo + dj <= jhi) row(jlo + dj);
     } else {
-        for (int jj = jlo; jj <= jhi + 1; ++jj) {
-            int j = jj;
-            if (jj == jhi + 1) { if (!jlast) break; j = npy - 1; }
-            for (int ii = ilo; ii <= ihi + 1; ++ii) {
-                int i = ii;
-                if (ii == ihi + 1) { if (!ilast) break; i = npx - 1; }
-                add(j * npx + i);
-            }
-        }
+        for (int j = jlo; j <= jhi; ++j) row(j);
     }
+    if (jlast) row(npy - 1);
     float *U = Ub + (size_t)f * ufs;
     const int p = y * pitch + x;
     U[p] = den > 0.0f ? nu / den : 0.0f;
@@ -649,20 +665,26 @@ void launch_densify(const void *I0, const void *I1, const Level &lv, size_t pyr_
 {
     StageScope sc(kStDensify, 1, st);
     dim3 blk(32, 8);
-    // covering patches per axis: at most ceil(ps / stride) regular ones + the last
-    const bool unrolled = (fp.ps + fp.stride - 1) / fp.stride + 1 <= 4;
     const dim3 grd = grid2d(lv.w, lv.h, frames, blk);
+    // regular patches covering a pixel per axis: at most ceil(ps / stride)
+    const int nc = (fp.ps + fp.stride - 1) / fp.stride;
+#define EBOF_DENSE(T, N)                                                                         \
+    densify_kernel<T, N><<<grd, blk, 0, st>>>((const T *)I0, (const T *)I1, lv.w, lv.h,         \
+                                              lv.pitch, pyr_frame_stride, up, up_frame_stride,   \
+                                              lv.npx, lv.npy, U, u_frame_stride, lv.plane, fp.ps,\
+                                              fp.stride)
     if (fp.half) {
-        auto k = unrolled ? densify_kernel<__half, 4> : densify_kernel<__half, 0>;
-        k<<<grd, blk, 0, st>>>((const __half *)I0, (const __half *)I1, lv.w, lv.h, lv.pitch,
-                               pyr_frame_stride, up, up_frame_stride, lv.npx, lv.npy, U,
-                               u_frame_stride, lv.plane, fp.ps, fp.stride);
+        if (nc == 2) EBOF_DENSE(__half, 2);
+        else if (nc == 3) EBOF_DENSE(__half, 3);
+        else if (nc == 4) EBOF_DENSE(__half, 4);
+        else EBOF_DENSE(__half, 0);
     } else {
-        auto k = unrolled ? densify_kernel<float, 4> : densify_kernel<float, 0>;
-        k<<<grd, blk, 0, st>>>((const float *)I0, (const float *)I1, lv.w, lv.h, lv.pitch,
-                               pyr_frame_stride, up, up_frame_stride, lv.npx, lv.npy, U,
-                               u_frame_stride, lv.plane, fp.ps, fp.stride);
+        if (nc == 2) EBOF_DENSE(float, 2);
+        else if (nc == 3) EBOF_DENSE(float, 3);
+        else if (nc == 4) EBOF_DENSE(float, 4);
+        else EBOF_DENSE(float, 0);
     }
+#undef EBOF_DENSE
 }
 
 template <typename T>
