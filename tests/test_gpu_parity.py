@@ -140,6 +140,51 @@ def test_edt_entry_dense_random(eb):
         assert np.array_equal(D.cpu().numpy(), oracle.edt(E)), (W, H, dens)
 
 
+@pytest.mark.parametrize("W,H", [(600, 40), (1100, 36), (1280, 24)])
+def test_edt_row_layouts_exact(eb, W, H):
+    """The EDT row pass serves a row with one warp in batched calls and with
+    two (from 512 px) or four (from 1024 px) warps, one row per block, for
+    single frames; D must be exact in every layout.  Random pixels plus
+    horizontal runs (long stretches of equal column distance next to them)."""
+    rng = np.random.default_rng(W + H)
+    prm, s = make_stream(eb, W, H, max_batch=3, n_d=0)
+    wins = []
+    for k in range(3):
+        x, y, t, _ = synth.random_edge_events(rng, W, H, int(0.01 * W * H) * (k + 1),
+                                              t_begin=1000 * k, dt=1000)
+        for _ in range(4):
+            r, a0 = int(rng.integers(H)), int(rng.integers(W // 2))
+            run = np.arange(a0, min(W, a0 + int(rng.integers(5, W // 2))))
+            x = np.concatenate([x, run.astype(np.uint16)])
+            y = np.concatenate([y, np.full(run.size, r, np.uint16)])
+            t = np.concatenate([t, np.full(run.size, 1000 * k, np.int64)])
+        wins.append((x, y, t))
+    # shuffled across the windows: warps straddle window boundaries in the
+    # scatter's counts (the edge images do not depend on the order)
+    perm = rng.permutation(sum(w[0].size for w in wins))
+    x, y, t = (np.concatenate([w[i] for w in wins])[perm] for i in range(3))
+    flow = torch.empty((3, 2, H, W), dtype=torch.float32, device="cuda:0")
+    edge = torch.empty((3, H, W), dtype=torch.uint8, device="cuda:0")
+    edt = torch.empty((3, H, W), dtype=torch.int32, device="cuda:0")
+    st = eb.ebof_process_windows(s, 3, dev(x), dev(y), dev(t), None, 0, 1000, flow, edge, edt)
+    assert st == eb.EBOF_NO_PREVIOUS
+    sst, stats = eb.ebof_stream_sync(s, 3)
+    eb.check(sst, "sync")
+    scratch = torch.empty(W * H, dtype=torch.int32, device="cuda:0")
+    D = torch.empty((H, W), dtype=torch.int32, device="cuda:0")
+    for k, (xk, yk, tk) in enumerate(wins):
+        o = oracle_surface(prm, W, H, xk, yk, tk, 1000 * k, 1000 * (k + 1))
+        assert (stats[k].in_window, stats[k].dropped_oob) == (int(o["stats"][1]),
+                                                             int(o["stats"][3])), k
+        assert stats[k].edge_px == int(o["Edf"].sum()), k
+        assert np.array_equal(edge[k].cpu().numpy(), o["Edf"]), k
+        assert np.array_equal(edt[k].cpu().numpy(), o["D"]), ("batched", k)
+        eb.check(eb.ebof_edt(dev(o["Edf"]), W, H, scratch, D, None, 1.08), "ebof_edt")
+        torch.cuda.synchronize()
+        assert np.array_equal(D.cpu().numpy(), o["D"]), ("single", k)
+    s.close()
+
+
 # ---------------------------------------------------------------- whole path
 def test_pipeline_346x260_parity(eb):
     s_ = synth.workload_346x260()
