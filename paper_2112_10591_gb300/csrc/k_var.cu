@@ -5,7 +5,8 @@
 // I1(x + U) for a 32x16 tile plus 2 px in shared memory, builds derivatives
 // of the warped image and the smoothness weights, and writes every pixel's
 // 2x2 linear system (data and gradient-constancy terms normalised, weights
-// lagged at dU = 0): 1/a11, 1/a22, a12, b1, b2 and the left and upper edge
+// lagged at dU = 0): omega/a11, omega/a22 (the SOR relaxation factor folded
+// into the inverted diagonal), a12, b1, b2 and the left and upper edge
 // weights, as seven planes (the right and lower weights are the neighbours'
 // left and upper ones).  Only the staging halo is shared between tiles.  On
 // levels from 1024 px wide the same systems come from var_coeff_cw_kernel,
@@ -49,8 +50,8 @@ constexpr int kVWarps = kVR / kVS;       // warps per block (stacked strips)
 constexpr int kVThreads = 32 * kVWarps;  // 512
 constexpr size_t kVSmemFloats = 2 * 2 * kVWarps * 2 * 64;  // strip-end exchange
 constexpr size_t kVSmemFloats2 = 2 * 2 * 32 * 2 * 64;       // the same for 32 warps
-// Coefficient planes of a pixel's system: 1/a11, 1/a22, a12, b1, b2 and the
-// left and upper edge weights.  The right and lower weights of a pixel are
+// Coefficient planes of a pixel's system: omega/a11, omega/a22, a12, b1, b2
+// and the left and upper edge weights.  The right and lower weights of a pixel are
 // the left and upper ones of its neighbours (each the mean of the same two
 // smoothness weights, so equal bit for bit) and are not stored.
 enum { kCI11 = 0, kCI22, kCA12, kCB1, kCB2, kCWL, kCWU, kCPlanes };
@@ -85,19 +86,18 @@ __device__ __forceinline__ void sor_half(float (&du)[VS][2], float (&dv)[VS][2],
 #pragma unroll
     for (int r = 0; r < VS; ++r) {
         const int q = (C + P + r) & 1;  // compile-time after unrolling
+        // lane 0's left and lane 31's right neighbours lie outside the
+        // region: the shuffles return the lane's own (finite) values there,
+        // and the edge weights wl / wr of those pixels are 0
         float lu, lv, ru, rv;
         if (q == 0) {
-            const float nu = __shfl_up_sync(kFull, du[r][1], 1);
-            const float nv = __shfl_up_sync(kFull, dv[r][1], 1);
-            lu = lane > 0 ? nu : 0.0f;
-            lv = lane > 0 ? nv : 0.0f;
+            lu = __shfl_up_sync(kFull, du[r][1], 1);
+            lv = __shfl_up_sync(kFull, dv[r][1], 1);
             ru = du[r][1];
             rv = dv[r][1];
         } else {
-            const float nu = __shfl_down_sync(kFull, du[r][0], 1);
-            const float nv = __shfl_down_sync(kFull, dv[r][0], 1);
-            ru = lane < 31 ? nu : 0.0f;
-            rv = lane < 31 ? nv : 0.0f;
+            ru = __shfl_down_sync(kFull, du[r][0], 1);
+            rv = __shfl_down_sync(kFull, dv[r][0], 1);
             lu = du[r][0];
             lv = dv[r][0];
         }
@@ -117,12 +117,13 @@ __device__ __forceinline__ void sor_half(float (&du)[VS][2], float (&dv)[VS][2],
             dnu = wp < WARPS - 1 ? xtop[((wp + 1) * 2 + 0) * 64 + col] : 0.0f;
             dnv = wp < WARPS - 1 ? xtop[((wp + 1) * 2 + 1) * 64 + col] : 0.0f;
         }
-        const float nu = om1 * du[r][q] +
-                         omega * (b1[r][q] + wl[r][q] * lu + wr[r][q] * ru + wu[r][q] * uu +
-                                  wd[r][q] * dnu - a12[r][q] * dv[r][q]) * i11[r][q];
-        const float nv = om1 * dv[r][q] +
-                         omega * (b2[r][q] + wl[r][q] * lv + wr[r][q] * rv + wu[r][q] * uv +
-                                  wd[r][q] * dnv - a12[r][q] * nu) * i22[r][q];
+        // i11 = omega / a11, i22 = omega / a22
+        const float nu = om1 * du[r][q] + (b1[r][q] + wl[r][q] * lu + wr[r][q] * ru +
+                                           wu[r][q] * uu + wd[r][q] * dnu - a12[r][q] * dv[r][q]) *
+                                              i11[r][q];
+        const float nv = om1 * dv[r][q] + (b2[r][q] + wl[r][q] * lv + wr[r][q] * rv +
+                                           wu[r][q] * uv + wd[r][q] * dnv - a12[r][q] * nu) *
+                                              i22[r][q];
         du[r][q] = nu;
         dv[r][q] = nv;
     }
@@ -219,12 +220,14 @@ struct PixelSystem {
 // and its four neighbours, used only where that neighbour is in the level
 // (bl, br, bu, bd); u*, v*: the flow at the pixel and its four neighbours (0
 // outside the level); i0, i0x, i0y: the template image and its gradient.
+// The diagonal is stored inverted and scaled by the SOR relaxation factor:
+// i11 = omega / a11, i22 = omega / a22.
 __device__ __forceinline__ PixelSystem pixel_system_vals(
     float ix, float iy, float ixl, float ixr, float ixu, float ixd, float iyu, float iyd,
     float iw, float asp, float asl, float asr, float asu, float asd, float u, float ul, float ur,
     float uu, float ud, float v, float vl, float vr, float vu, float vd, bool bl, bool br,
     bool bu, bool bd, int gx, int gy, int w, int h, float i0, float i0x, float i0y, float delta,
-    float gamma)
+    float gamma, float omega)
 {
     const float Ix = ix, Iy = iy;
     const float Ixx = cdiff(ixr, ixl);
@@ -249,8 +252,8 @@ __device__ __forceinline__ PixelSystem pixel_system_vals(
     const float sw = ps.cl + ps.cr + ps.cu + ps.cd;
     const float su0 = ps.cl * (ul - u) + ps.cr * (ur - u) + ps.cu * (uu - u) + ps.cd * (ud - u);
     const float sv0 = ps.cl * (vl - v) + ps.cr * (vr - v) + ps.cu * (vu - v) + ps.cd * (vd - v);
-    ps.i11 = __fdividef(1.0f, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
-    ps.i22 = __fdividef(1.0f, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
+    ps.i11 = __fdividef(omega, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
+    ps.i22 = __fdividef(omega, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
     ps.a12 = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
     ps.b1 = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
     ps.b2 = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
@@ -267,7 +270,8 @@ __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const floa
                                                     const float *sW, const float *sU,
                                                     const float *sV, int ES, int e, int gx,
                                                     int gy, int w, int h, float i0, float i0x,
-                                                    float i0y, float delta, float gamma)
+                                                    float i0y, float delta, float gamma,
+                                                    float omega)
 {
     const int xp = (IN ? gx + 1 : min(gx + 1, w - 1)) - dx0;
     const int xm = (IN ? gx - 1 : max(gx - 1, 0)) - dx0;
@@ -281,7 +285,7 @@ __device__ __forceinline__ PixelSystem pixel_system(const float *sIx, const floa
         sAs[d + 1], sAs[d - DS], sAs[d + DS], sU[e], sU[e - 1], sU[e + 1], sU[e - ES],
         sU[e + ES], sV[e], sV[e - 1], sV[e + 1], sV[e - ES], sV[e + ES], IN || gx > 0,
         IN || gx + 1 < w, IN || gy > 0, IN || gy + 1 < h, gx, gy, w, h, i0, i0x, i0y, delta,
-        gamma);
+        gamma, omega);
 }
 
 // One coefficient tile.  IN: the tile's staging window (tile + 2 px) lies
@@ -293,7 +297,7 @@ __device__ __forceinline__ void coeff_tile(
     const T *__restrict__ I0b, const T *__restrict__ I0xb, const T *__restrict__ I0yb,
     const T *__restrict__ I1b, int w, int h, int pitch, size_t pfs, const float *__restrict__ Ub,
     size_t ufs, size_t plane, float *__restrict__ coefb, size_t cfs, float delta, float gamma,
-    float alpha_s)
+    float alpha_s, float omega)
 {
     const int f = blockIdx.z;
     const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
@@ -342,7 +346,7 @@ __device__ __forceinline__ void coeff_tile(
     const PixelSystem ps = pixel_system<IN>(
         &sIx[0][0], &sIy[0][0], &sAs[0][0], kADX, dx0, dy0, &sW[0][0], &sU[0][0], &sV[0][0], kAEX,
         (gy - ey0) * kAEX + (gx - ex0), gx, gy, w, h, ldp(&(I0b + po)[p]), ldp(&(I0xb + po)[p]),
-        ldp(&(I0yb + po)[p]), delta, gamma);
+        ldp(&(I0yb + po)[p]), delta, gamma, omega);
     const int pl = (int)plane;
     float *cf = coefb + (size_t)f * cfs + p;
     cf[kCI11 * pl] = ps.i11;
@@ -359,17 +363,18 @@ __global__ void __launch_bounds__(kAX * kAY)
 var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                  const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
                  int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs, size_t plane,
-                 float *__restrict__ coefb, size_t cfs, float delta, float gamma, float alpha_s)
+                 float *__restrict__ coefb, size_t cfs, float delta, float gamma, float alpha_s,
+                 float omega)
 {
     __shared__ float sU[kAEY][kAEX], sV[kAEY][kAEX], sW[kAEY][kAEX];
     __shared__ float sIx[kADY][kADX], sIy[kADY][kADX], sAs[kADY][kADX];
     const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
     if (tx0 >= 2 && ty0 >= 2 && tx0 + kAX + 2 <= w && ty0 + kAY + 2 <= h)
         coeff_tile<true>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
-                         ufs, plane, coefb, cfs, delta, gamma, alpha_s);
+                         ufs, plane, coefb, cfs, delta, gamma, alpha_s, omega);
     else
         coeff_tile<false>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
-                          ufs, plane, coefb, cfs, delta, gamma, alpha_s);
+                          ufs, plane, coefb, cfs, delta, gamma, alpha_s, omega);
 }
 
 // Column-walk form of the same kernel.  A warp owns 28 output columns: lane
@@ -393,7 +398,7 @@ __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *_
                                             int w, int h, int pitch, const float *__restrict__ U,
                                             const float *__restrict__ V, float *__restrict__ cf,
                                             int pl, int x, int y0, bool out_lane, float delta,
-                                            float gamma, float alpha_s)
+                                            float gamma, float alpha_s, float omega)
 {
     const bool xin = IN || (x >= 0 && x < w);
     const bool hx = IN || x + 1 < w;
@@ -480,7 +485,7 @@ __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *_
             __shfl_down_sync(kFull, as0, 1), asm_, asp_, uc, __shfl_up_sync(kFull, uc, 1),
             __shfl_down_sync(kFull, uc, 1), ub, ud, vc, __shfl_up_sync(kFull, vc, 1),
             __shfl_down_sync(kFull, vc, 1), vb, vd, bl, hx, IN || y > 0, IN || y + 1 < h, x, y,
-            w, h, i0, i0x, i0y, delta, gamma);
+            w, h, i0, i0x, i0y, delta, gamma, omega);
         if (out_lane && xin) {
             float *c = cf + p;
             c[kCI11 * pl] = ps.i11;
@@ -508,7 +513,7 @@ var_coeff_cw_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
                     int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs,
                     size_t plane, float *__restrict__ coefb, size_t cfs, float delta,
-                    float gamma, float alpha_s)
+                    float gamma, float alpha_s, float omega)
 {
     const int lane = threadIdx.x;
     const int y0 = (blockIdx.y * kCWWarps + threadIdx.y) * R;
@@ -521,11 +526,11 @@ var_coeff_cw_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     if (cx0 >= 0 && cx0 + 31 < w && y0 >= 2 && y0 + R + 1 < h)
         coeff_strip<R, true>(I0b + po, I0xb + po, I0yb + po, I1b + po, w, h, pitch, U, U + plane,
                              coefb + (size_t)f * cfs, (int)plane, cx0 + lane, y0, out_lane,
-                             delta, gamma, alpha_s);
+                             delta, gamma, alpha_s, omega);
     else
         coeff_strip<R, false>(I0b + po, I0xb + po, I0yb + po, I1b + po, w, h, pitch, U,
                               U + plane, coefb + (size_t)f * cfs, (int)plane, cx0 + lane, y0,
-                              out_lane, delta, gamma, alpha_s);
+                              out_lane, delta, gamma, alpha_s, omega);
 }
 
 // Left and right halo of a region in columns: R rounded up to even, so that
@@ -569,6 +574,20 @@ __device__ __forceinline__ void lower_right_weights(const float (&wl)[VS][2],
         wr[r][1] = lane < 31 ? n : 0.0f;
 #pragma unroll
         for (int q = 0; q < 2; ++q) wd[r][q] = r + 1 < VS ? wu[r + 1][q] : wub[q];
+    }
+}
+
+// The region's first column (lane 0's first) has its left neighbour outside
+// the region, where dU stays 0; a zero edge weight there lets the SOR update
+// take the shuffled value without a select (0 times a finite value adds
+// exactly 0).  Its right neighbour's weight is unaffected: a pixel's right
+// weight is read from the next lane.
+template <int VS>
+__device__ __forceinline__ void zero_region_left_weights(float (&wl)[VS][2], int lane)
+{
+    if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < VS; ++r) wl[r][0] = 0.0f;
     }
 }
 
@@ -688,6 +707,7 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
         }
     }
     lower_right_weights<VS>(wl, wu, wub, lane, wr, wd);
+    zero_region_left_weights<VS>(wl, lane);
 
     // red-black SOR; red = (x + y) even, first.  Given the parity of (x + y)
     // at a strip's first pixel, the column of a given colour in a given row
@@ -830,6 +850,7 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
                 wub[1] = v.y;
             }
             lower_right_weights<kVS>(wl, wu, wub, lane, wr, wd);
+            zero_region_left_weights<kVS>(wl, lane);
         }
         __syncthreads();  // every thread holds its coefficients: the buffer is free
         if (t == 0 && r + (int)gridDim.x < total) {
@@ -953,13 +974,13 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
                     (const __half *)I0, (const __half *)I0x, (const __half *)I0y,
                     (const __half *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
                     u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
-                    fp.alpha_s);
+                    fp.alpha_s, fp.omega);
             else
                 var_coeff_cw_kernel<kCWRows, float><<<wgrd, dim3(32, kCWWarps), 0, st>>>(
                     (const float *)I0, (const float *)I0x, (const float *)I0y,
                     (const float *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
                     u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
-                    fp.alpha_s);
+                    fp.alpha_s, fp.omega);
         } else {
             StageScope sc(kStVarCoeff, 1, st);
             if (fp.half)
@@ -967,13 +988,13 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
                     (const __half *)I0, (const __half *)I0x, (const __half *)I0y,
                     (const __half *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
                     u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
-                    fp.alpha_s);
+                    fp.alpha_s, fp.omega);
             else
                 var_coeff_kernel<float><<<cgrd, dim3(kAX, kAY), 0, st>>>(
                     (const float *)I0, (const float *)I0x, (const float *)I0y,
                     (const float *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
                     u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
-                    fp.alpha_s);
+                    fp.alpha_s, fp.omega);
         }
         {
             StageScope sc(kStVarSor, 1, st);
