@@ -12,7 +12,10 @@ of events per step, larger than the 129 MB L2).
 Prints one JSON line (rank 0).  `value` is the plain path (one
 ebof_process_window call per window); `batched` is the same stream through
 ebof_process_windows; `e2e` goes through ebof_process_window_host with the
-events in pinned host memory and the flow read back every window;
+events in pinned host memory and every window's flow written back into a
+pinned host buffer (page-locked buffers are addressed by the kernels over the
+host link, so the events cross it inside the scatter and the flow inside the
+last kernel; the call returns after synchronising);
 `roofline` covers the dominant stage; `cpu_baseline` is the FP64 oracle on
 a bounded sample of the same stream, on this host's cores.
 

@@ -209,10 +209,14 @@ ebof_status ebof_process_window_list(ebof_stream *s, int32_t n_windows,
 ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *d_flow,
                                  void *cuda_stream);
 
-/* ebof_process_window with HOST buffers: copies the events to the device,
- * runs the window and copies the flow back into h_flow [2][H][W], all on
- * `cuda_stream`, then synchronises it.  Pinned host memory makes the copies
- * asynchronous to the host; pageable memory works but is slower. */
+/* ebof_process_window with HOST buffers: the events go to the device, the
+ * window runs and the flow comes back into h_flow [2][H][W], all on
+ * `cuda_stream`, which is then synchronised.  Pageable buffers are staged
+ * through device memory with copies.  When every buffer is page-locked and
+ * registered with CUDA (addressable by the device at the same address), a
+ * window that has a previous one reads its events and writes its flow in
+ * place over the host link, with no staging copies; the result is the same.
+ * The buffers must not be modified or freed until the call returns. */
 ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const uint16_t *h_y,
                                      const int64_t *h_t, int64_t n_events, int64_t t_begin,
                                      int64_t t_end, float *h_flow, void *cuda_stream);

@@ -757,6 +757,19 @@ ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *
                nullptr, (cudaStream_t)cuda_stream);
 }
 
+// A host buffer the current device can address at the same virtual address:
+// page-locked memory registered with CUDA under unified addressing.
+// Pageable memory is not (the check says no, and the caller stages it).
+static bool device_addressable(const void *h)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == h;
+}
+
 ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const uint16_t *h_y,
                                      const int64_t *h_t, int64_t n_events, int64_t t_begin,
                                      int64_t t_end, float *h_flow, void *cuda_stream)
@@ -769,6 +782,19 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
     if (!dg.ok) return EBOF_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const size_t n = (size_t)n_events;
+    // page-locked buffers of a window with a previous one: the kernels read
+    // the events and write the flow in place over the host link, with no
+    // staging copies (the first window, whose flow is cleared with a memset,
+    // and pageable buffers take the staged path below)
+    if (s->has_prev && s->geo.levels > 0 && device_addressable(h_flow) &&
+        (n == 0 || (device_addressable(h_x) && device_addressable(h_y) &&
+                    device_addressable(h_t)))) {
+        const ebof_status r = run(s, 1, h_x, h_y, h_t, n_events, t_begin, t_end - t_begin,
+                                  nullptr, h_flow, nullptr, nullptr, nullptr, st);
+        if (r < 0) return r;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return EBOF_ERR_CUDA;
+        return r;
+    }
     const size_t bx = ((2 * n + 255) / 256) * 256;
     const size_t need = 2 * bx + 8 * n;
     if (need > s->ev_stage_bytes) {

@@ -326,6 +326,24 @@ def test_reset_interleave_host_and_errors(eb):
                                          np.ascontiguousarray(t), tb, te, hf)
         assert st == (eb.EBOF_NO_PREVIOUS if k == 0 else eb.EBOF_OK)
         assert np.array_equal(hf, ra[k]["flow"])
+    # page-locked host buffers: from the second window on the kernels read the
+    # events and write the flow in place; the same flow
+
+    def pinned(a):
+        buf = torch.empty(max(a.nbytes, 1), dtype=torch.uint8).pin_memory()
+        v = buf.numpy()[:a.nbytes].view(a.dtype)
+        v[:] = a
+        return v, buf
+
+    _, d = make_stream(eb, W, H)
+    hfp, hfp_buf = pinned(np.zeros((2 * H * W,), np.float32))
+    for k in range(3):
+        x, y, t, p, tb, te = s_.window(k)
+        (xp, xb), (yp, yb), (tp, tbuf) = pinned(x), pinned(y), pinned(t)
+        hfp[:] = np.nan
+        st = eb.ebof_process_window_host(d, xp, yp, tp, tb, te, hfp)
+        assert st == (eb.EBOF_NO_PREVIOUS if k == 0 else eb.EBOF_OK)
+        assert np.array_equal(hfp.reshape(2, H, W), ra[k]["flow"]), k
     # argument errors enqueue nothing
     x, y, t, p, tb, te = s_.window(0)
     lib = eb.load()
@@ -340,7 +358,7 @@ def test_reset_interleave_host_and_errors(eb):
     # an empty window is legal: no edge pixel, D = INT32_MAX, S = 1
     g = run_window(eb, a, x[:0], y[:0], t[:0], tb, te)
     assert g["stats"].edge_px == 0 and np.all(g["edt"] == 2147483647) and np.all(g["surf"] == 1.0)
-    for h in (a, b, c):
+    for h in (a, b, c, d):
         h.close()
 
 
