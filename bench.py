@@ -124,6 +124,11 @@ def cpu_workers():
     return max(1, min(n, 16))
 
 
+def workload_name(nwin):
+    return ("1280x720 single stream, %d windows of 10 ms (%d flow frames), 150k-400k "
+            "events/window, 12 affine objects, 3%% noise, seed 1+rank" % (nwin, nwin - 1))
+
+
 def run_reference(args, rank):
     """The reference arm: the FP64 oracle, as it stands, on this host's cores."""
     if rank != 0:
@@ -153,8 +158,12 @@ def run_reference(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "1280x720 stream, frame pairs of 150k-400k-event windows",
-                   "frames_per_step": frames_per_step},
+        "config": {"workload": workload_name(args.windows),
+                   "path": "FP64 oracle: a bounded sample of %d frame pairs of the stream's "
+                           "first windows per step, one per process" % frames_per_step,
+                   "levels": prm["levels"], "patch": prm["patch"], "stride": prm["stride"],
+                   "gn_iters": prm["gn_iters"],
+                   "var": "%dx%d" % (prm["var_outer"], prm["var_sor"])},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                          "sample": "%d frame pairs of the 1280x720 stream per step, one per "
                                    "process" % frames_per_step},
@@ -939,9 +948,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1280x720 single stream, %d windows of 10 ms (%d flow "
-                                   "frames), 150k-400k events/window, 12 affine objects, "
-                                   "3%% noise, seed 1+rank" % (nwin, frames_per_step),
+            "config": {"workload": workload_name(nwin),
                        "path": "plain: one ebof_process_window call per window",
                        "levels": prm.levels, "patch": prm.patch, "stride": prm.stride,
                        "gn_iters": prm.gn_iters, "var": "%dx%d" % (prm.var_outer, prm.var_sor),
