@@ -300,15 +300,17 @@ edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, in
 // the lower envelope of the row's parabolas evaluated at every pixel.  With
 // F(s) = s^2 + h(s) it reads D(x) = x^2 + min_s (F(s) - 2 x s): a minimum of
 // lines in x, so the sites that own part of the envelope are exactly the
-// vertices of the lower convex hull of the points (s, F(s)).  One warp serves
-// one row and its 32 lanes own bands of B columns (B odd, so that the lanes'
-// shared-memory accesses fall in distinct banks).
+// vertices of the lower convex hull of the points (s, F(s)).  One warp (two
+// or four for single frames of wide rows) serves a row, and each lane owns a
+// band of B consecutive columns (B odd, so that the lanes' accesses to F fall
+// in distinct shared-memory banks).
 //  1. The row's F is staged in shared memory (-1: column without edge pixels).
 //  2. Each lane builds the lower hull of its band's points with a stack
 //     (orientation tests exact in 64-bit integers; a point on the segment of
 //     its neighbours is dropped, which never changes a minimum).
-//  3. Five rounds merge the hulls of neighbouring groups of 1, 2, 4, 8 and 16
-//     bands.  The group's first lane finds the lower bridge of the two hulls
+//  3. Rounds merge the hulls of neighbouring groups of 1, 2, 4, ... bands
+//     (five for 32 bands, seven for 128).  The group's first lane finds the
+//     lower bridge of the two hulls
 //     by walking from their inner ends (the left hull's last vertex moves left
 //     and the right hull's first vertex moves right while the vertex is not
 //     strictly below the line through the other two); the right hull's
