@@ -2,7 +2,7 @@
 // fixed-point iteration.
 //
 // var_coeff_kernel, one thread per pixel: stages U and the warped image
-// I1(x + U) for a 32x16 tile plus 2 px in shared memory, builds derivatives
+// I1(x + U) for a 32x12 tile plus 2 px in shared memory, builds derivatives
 // of the warped image and the smoothness weights, and writes every pixel's
 // 2x2 linear system (data and gradient-constancy terms normalised, weights
 // lagged at dU = 0): omega/a11, omega/a22 (the SOR relaxation factor folded
@@ -62,7 +62,9 @@ constexpr size_t kTmaSmemBytes = (kTmaCoefFloats + kVSmemFloats) * sizeof(float)
 constexpr long kTmaSpinLimit = 1L << 22;  // bounded wait on a tensor copy
 constexpr int kMaxDevs = 64;
 int g_num_sms[kMaxDevs];
-constexpr int kAX = 32, kAY = 16;              // coefficient tile
+// coefficient tile: 384 threads at 40 registers, four blocks per SM, so a
+// 640 x 360 level (600 tiles) takes one wave where 32 x 16 tiles took two
+constexpr int kAX = 32, kAY = 12;
 constexpr int kAEX = kAX + 4, kAEY = kAY + 4;  // staging window: tile + 2 px
 constexpr int kADX = kAX + 2, kADY = kAY + 2;  // derivative window: tile + 1 px
 constexpr unsigned kFull = 0xffffffffu;
@@ -307,7 +309,7 @@ __device__ __forceinline__ void coeff_tile(
     const T *I1 = I1b + po;
     const float *U = Ub + (size_t)f * ufs;
     const float *V = U + plane;
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 16 threads, one per tile pixel
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 12 threads, one per tile pixel
 
     const int t = ty * kAX + tx;
     constexpr int kN = kAX * kAY;
