@@ -243,6 +243,27 @@ def test_flow_on_analytic_surfaces(eb, v):
     s.close()
 
 
+def test_many_sor_sweeps_take_the_half_sweep_kernels(eb):
+    """More SOR sweeps than a 64-px region's halo allows (13 sweeps need a
+    25-px halo) run the variational refinement as one launch per half sweep;
+    the same gates against the oracle, with the same number of sweeps."""
+    W, H = 160, 120
+    v = (1.7, 0.9)
+    prm, s = make_stream(eb, W, H, var_sor=13)
+    S0 = _texture(W, H).astype(np.float32)
+    S1 = _texture(W, H, v).astype(np.float32)
+    flow = torch.empty((2, H, W), dtype=torch.float32, device="cuda:0")
+    assert eb.ebof_process_surface(s, dev(S0), flow) == eb.EBOF_NO_PREVIOUS
+    assert eb.ebof_process_surface(s, dev(S1), flow) == eb.EBOF_OK
+    torch.cuda.synchronize()
+    F = flow.cpu().numpy()
+    U = oracle_flow(prm, 255.0 * S0.astype(np.float64), 255.0 * S1.astype(np.float64))
+    assert epe(F, U).mean() <= EPE_TOL
+    inner = (slice(None), slice(16, -16), slice(16, -16))
+    assert epe(F[inner], np.array(v)[:, None, None]).mean() <= 0.05
+    s.close()
+
+
 def test_flat_and_zero_motion_surfaces(eb):
     W, H = 96, 64
     prm, s = make_stream(eb, W, H)
