@@ -237,8 +237,8 @@ class ClockSampler:
 # ---------------------------------------------------------------- roofline
 def algorithmic_bytes_per_launch(stage, level, geo, n_events_per_window, P):
     """Algorithmic bytes of ONE launch of a stage for one window: each
-    kernel's inputs read once and outputs written once (formulas in
-    DESIGN.md, "Kernels and their rooflines").  geo: [(w, h, npx, npy)]."""
+    kernel's inputs read once and outputs written once, by the per-stage
+    formulas below.  geo: [(w, h, npx, npy)] per pyramid level."""
     if level >= 0:
         w, h, npx, npy = geo[level]
         Pl, npl = w * h, npx * npy
