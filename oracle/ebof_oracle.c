@@ -10,8 +10,9 @@
  * "Real-Time Optical Flow for Vehicular Perception with Low- and
  * High-Resolution Event Cameras") that it follows.  Where the paper is
  * silent the reading taken is stated beside the code.  The frame-based flow
- * block (§III-D) leaves the method open ("any state-of-the-art frame-based
- * optical flow method"); the one written here is Dense Inverse Search
+ * block (§III-D) leaves the choice of method open: the surfaces are meant to
+ * be fed to an established frame-based flow method.  The one written here is
+ * Dense Inverse Search
  * (Kroeger et al., ECCV 2016): image pyramid, per-patch inverse-compositional
  * Gauss-Newton, patch densification and variational refinement, with every
  * free constant fixed by the readings below.
@@ -109,9 +110,9 @@ void orc_fill(int W, int H, const uint8_t *Ed, int conn, int n_f, uint8_t *Edf)
 }
 
 /* ---------------------------------------------------------------------------
- * §III-C: Euclidean distance transform.  d_Euc is "the Euclidean distance to
- * the closest edge pixel"; the squared value is an integer and is unique even
- * when several edge pixels are equally close.
+ * §III-C: Euclidean distance transform.  d_Euc is a pixel's Euclidean
+ * distance to its nearest edge pixel; the squared value is an integer and is
+ * unique even when several edge pixels are equally close.
  * ------------------------------------------------------------------------- */
 
 /* The definition itself: minimum over all edge pixels.  O(P * sites). */
