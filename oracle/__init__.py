@@ -80,6 +80,8 @@ def _declare(L):
     L.orc_densify.argtypes = [i32, i32, vp, vp, i32, i32, vp, vp]
     L.orc_variational.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, f64,
                                   f64, f64, f64]
+    L.orc_var_linearise.argtypes = [i32, i32, vp, vp, vp, vp, vp, f64, f64, f64, vp]
+    L.orc_var_sor.argtypes = [i32, i32, vp, vp, i32, f64, vp]
     L.orc_flow.argtypes = [i32, i32, vp, vp, i32, i32, i32, i32, f64, i32, i32, f64,
                            f64, f64, f64, vp]
     L.orc_flow.restype = i32
@@ -271,6 +273,35 @@ def variational(I0, I0x, I0y, I1, U, outer=5, sor=5, delta=5.0, gamma=10.0,
     lib().orc_variational(W, H, _p(a[0]), _p(a[1]), _p(a[2]), _p(a[3]), _p(U),
                           outer, sor, delta, gamma, alpha, omega)
     return U
+
+
+# Planes of the linearised variational system (orc_var_linearise's order).
+VAR_PLANES = ("Ix", "Iy", "Ixx", "Ixy", "Iyy", "Iz", "Ixz", "Iyz", "ad", "ag", "as")
+
+
+def var_linearise(I0, I0x, I0y, I1, U, delta=5.0, gamma=10.0, alpha=20.0):
+    """Reading F6, first half of one outer iteration: the derivative and
+    residual planes of the image warped by U and the frozen robust weights.
+    Returns a dict of the VAR_PLANES, each [H][W]."""
+    H, W = I0.shape
+    a = [np.ascontiguousarray(v, np.float64) for v in (I0, I0x, I0y, I1)]
+    U = np.ascontiguousarray(U, np.float64)
+    Q = np.zeros((len(VAR_PLANES), H, W), np.float64)
+    lib().orc_var_linearise(W, H, _p(a[0]), _p(a[1]), _p(a[2]), _p(a[3]), _p(U),
+                            delta, gamma, alpha, _p(Q))
+    return {k: Q[i] for i, k in enumerate(VAR_PLANES)}
+
+
+def var_sor(planes, U, dU, sweeps, omega=1.6):
+    """Reading F6, second half: `sweeps` red-black SOR sweeps on the
+    linearised system given by ``planes`` (a dict of VAR_PLANES) at flow U,
+    starting from dU; returns the new dU [2][H][W]."""
+    Q = np.ascontiguousarray(np.stack([planes[k] for k in VAR_PLANES]), np.float64)
+    H, W = Q.shape[1:]
+    U = np.ascontiguousarray(U, np.float64)
+    dU = np.array(dU, np.float64, copy=True, order="C")
+    lib().orc_var_sor(W, H, _p(Q), _p(U), int(sweeps), float(omega), _p(dU))
+    return dU
 
 
 def flow(I0, I1, levels=3, patch=8, stride=4, gn_iters=12, gn_damping=0.1, var_outer=5,

@@ -448,96 +448,160 @@ void orc_densify(int W, int H, const double *I0, const double *I1, int ps,
 static double psi_prime(double s2) { return 1.0 / (2.0 * sqrt(s2 + 1e-6)); }
 #define ZETA2 0.01 /* zeta = 0.1 in the constraint normalisation */
 
+/* Planes of the linearised system of one outer iteration of F6, in the
+ * order of orc_var_linearise's output Q [ORC_VQ][H][W]. */
+enum { VQ_IX, VQ_IY, VQ_IXX, VQ_IXY, VQ_IYY, VQ_IZ, VQ_IXZ, VQ_IYZ, VQ_AD, VQ_AG, VQ_AS,
+       ORC_VQ };
+
+/* F6, first half of one outer iteration: warp I1 by U, take the derivatives
+ * of the warped image and the constraint residuals, and the robust weights
+ * frozen at dU = 0.
+ *   I1w = I1(x + U) (bilinear, clamped), Iz = I1w - I0,
+ *   Ix, Iy = central differences of I1w; Ixx, Ixy, Iyy = central
+ *   differences of Ix (x, y) and Iy (y),
+ *   Ixz = Ix - dI0/dx, Iyz = Iy - dI0/dy (I0x, I0y given),
+ *   ad = delta nd Psi'(nd Iz^2),        nd = 1 / (Ix^2 + Iy^2 + zeta^2),
+ *   ag = gamma ng Psi'(ng (Ixz^2 + Iyz^2)),
+ *                        ng = 1 / (Ixx^2 + 2 Ixy^2 + Iyy^2 + zeta^2),
+ *   ad = ag = 0 where x + U lies outside the image,
+ *   as = alpha_s Psi'(|grad u|^2 + |grad v|^2), forward differences (0 at
+ *   the last column / row).
+ * The normalisations nd, ng follow Zimmer, Bruhn and Weickert (IJCV 2011):
+ * the robust weights then measure a displacement rather than an intensity.
+ * Output Q: the ORC_VQ planes in the VQ_* order.
+ * Pins: closed-form derivative planes of a quadratic image warped by an
+ * integer flow, dropped terms where the warp leaves the image, the weight
+ * Psi'(0) of a constant flow. */
+void orc_var_linearise(int W, int H, const double *I0, const double *I0x,
+                       const double *I0y, const double *I1, const double *U,
+                       double delta, double gamma, double alpha_s, double *Q)
+{
+    size_t P = (size_t)W * H;
+    const double *u = U, *v = U + P;
+    double *I1w = (double *)malloc(sizeof(double) * P);
+    double *Ix = Q + VQ_IX * P, *Iy = Q + VQ_IY * P, *Ixx = Q + VQ_IXX * P,
+           *Ixy = Q + VQ_IXY * P, *Iyy = Q + VQ_IYY * P, *Iz = Q + VQ_IZ * P,
+           *Ixz = Q + VQ_IXZ * P, *Iyz = Q + VQ_IYZ * P, *ad = Q + VQ_AD * P,
+           *ag = Q + VQ_AG * P, *as = Q + VQ_AS * P;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            I1w[p] = bilinear(I1, W, H, x + u[p], y + v[p]);
+        }
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            Ix[p] = cdx(I1w, W, x, y); Iy[p] = cdy(I1w, W, H, x, y);
+        }
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            Ixx[p] = cdx(Ix, W, x, y);
+            Ixy[p] = cdy(Ix, W, H, x, y);
+            Iyy[p] = cdy(Iy, W, H, x, y);
+            Iz[p] = I1w[p] - I0[p];
+            Ixz[p] = Ix[p] - I0x[p];
+            Iyz[p] = Iy[p] - I0y[p];
+            /* constraint normalisation (reading F6) */
+            double nd = 1.0 / (Ix[p] * Ix[p] + Iy[p] * Iy[p] + ZETA2);
+            double ng = 1.0 / (Ixx[p] * Ixx[p] + 2.0 * Ixy[p] * Ixy[p] + Iyy[p] * Iyy[p] + ZETA2);
+            ad[p] = delta * nd * psi_prime(nd * Iz[p] * Iz[p]);
+            ag[p] = gamma * ng * psi_prime(ng * (Ixz[p] * Ixz[p] + Iyz[p] * Iyz[p]));
+            double wx = x + u[p], wy = y + v[p];
+            if (wx < 0 || wx > W - 1 || wy < 0 || wy > H - 1) { ad[p] = 0; ag[p] = 0; }
+            double ux = x + 1 < W ? u[p + 1] - u[p] : 0.0;
+            double uy = y + 1 < H ? u[p + W] - u[p] : 0.0;
+            double vx = x + 1 < W ? v[p + 1] - v[p] : 0.0;
+            double vy = y + 1 < H ? v[p + W] - v[p] : 0.0;
+            as[p] = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
+        }
+    free(I1w);
+}
+
+/* F6, second half: `sor` red-black SOR sweeps (relaxation omega) on the
+ * linear system whose solution dU makes the quadratic energy
+ *   sum_x  ad (Ix du + Iy dv + Iz)^2
+ *        + ag ((Ixx du + Ixy dv + Ixz)^2 + (Ixy du + Iyy dv + Iyz)^2)
+ *   + sum over 4-neighbour pairs (x, n) of w_xn (|(u + du)(n) - (u + du)(x)|^2
+ *                                               + |(v + dv)(n) - (v + dv)(x)|^2),
+ *   w_xn = (as(x) + as(n)) / 2,
+ * stationary (its Euler-Lagrange equations): per pixel
+ *   a11 du + a12 dv = r1,  a12 du + a22 dv = r2, with
+ *   a11 = ad Ix^2 + ag (Ixx^2 + Ixy^2) + sum_n w_xn,
+ *   a12 = ad Ix Iy + ag (Ixx Ixy + Ixy Iyy),
+ *   a22 = ad Iy^2 + ag (Ixy^2 + Iyy^2) + sum_n w_xn,
+ *   r1  = sum_n w_xn (u(n) + du(n) - u(x)) - ad Ix Iz - ag (Ixx Ixz + Ixy Iyz),
+ *   r2  = sum_n w_xn (v(n) + dv(n) - v(x)) - ad Iy Iz - ag (Ixy Ixz + Iyy Iyz);
+ * neighbours outside the image are dropped (Neumann border).  A sweep
+ * updates the red pixels ((x + y) even) first, then the black ones, each in
+ * raster order; inside a pixel du first, then dv with the new du.
+ * Q: planes of orc_var_linearise; U: current flow [2][H][W]; dU [2][H][W]:
+ * start values in, result out.
+ * Pins: one sweep on a 2x2 grid worked by hand (tests/golden), and the
+ * converged solution is the minimum of the energy above, differentiated
+ * numerically. */
+void orc_var_sor(int W, int H, const double *Q, const double *U, int sor, double omega,
+                 double *dU)
+{
+    size_t P = (size_t)W * H;
+    const double *u = U, *v = U + P;
+    double *du = dU, *dv = dU + P;
+    const double *Ix = Q + VQ_IX * P, *Iy = Q + VQ_IY * P, *Ixx = Q + VQ_IXX * P,
+                 *Ixy = Q + VQ_IXY * P, *Iyy = Q + VQ_IYY * P, *Iz = Q + VQ_IZ * P,
+                 *Ixz = Q + VQ_IXZ * P, *Iyz = Q + VQ_IYZ * P, *ad = Q + VQ_AD * P,
+                 *ag = Q + VQ_AG * P, *as = Q + VQ_AS * P;
+    for (int s = 0; s < sor; ++s)
+        for (int k = 0; k < 2; ++k) {
+            int colour = (orc_mutation == 13) ? 1 - k : k;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    if (((x + y) & 1) != colour) continue;
+                    size_t p = (size_t)y * W + x;
+                    double sw = 0, su = 0, sv = 0;
+                    const int nx[4] = {x - 1, x + 1, x, x};
+                    const int ny[4] = {y, y, y - 1, y + 1};
+                    for (int e = 0; e < 4; ++e) {
+                        if (nx[e] < 0 || ny[e] < 0 || nx[e] >= W || ny[e] >= H) continue;
+                        size_t q = (size_t)ny[e] * W + nx[e];
+                        double wn = 0.5 * (as[p] + as[q]);
+                        sw += wn;
+                        su += wn * (u[q] + du[q] - u[p]);
+                        sv += wn * (v[q] + dv[q] - v[p]);
+                    }
+                    if (orc_mutation == 9) { su = 0; sv = 0; }
+                    double a11 = ad[p] * Ix[p] * Ix[p] + ag[p] * (Ixx[p] * Ixx[p] + Ixy[p] * Ixy[p]) + sw;
+                    double a12 = ad[p] * Ix[p] * Iy[p];
+                    if (orc_mutation != 12) a12 += ag[p] * (Ixx[p] * Ixy[p] + Ixy[p] * Iyy[p]);
+                    double a22 = ad[p] * Iy[p] * Iy[p] + ag[p] * (Ixy[p] * Ixy[p] + Iyy[p] * Iyy[p]) + sw;
+                    double sd = (orc_mutation == 8) ? -1.0 : 1.0;
+                    double r1 = su - sd * ad[p] * Ix[p] * Iz[p] - ag[p] * (Ixx[p] * Ixz[p] + Ixy[p] * Iyz[p]);
+                    double r2 = sv - sd * ad[p] * Iy[p] * Iz[p] - ag[p] * (Ixy[p] * Ixz[p] + Iyy[p] * Iyz[p]);
+                    if (a11 > 0) du[p] = (1 - omega) * du[p] + omega * (r1 - a12 * dv[p]) / a11;
+                    if (a22 > 0) dv[p] = (1 - omega) * dv[p] + omega * (r2 - a12 * du[p]) / a22;
+                }
+        }
+}
+
 /* F6: variational refinement of the dense flow U (planar [2][H][W], in
- * place).  Per outer iteration: warp I1 by U, build the linearised data
- * (delta), gradient-constancy (gamma) and smoothness (alpha_s) terms with
- * robust weights frozen at dU = 0, solve for dU with `sor` red-black SOR
- * sweeps (red = (x + y) even first; inside a pixel du then dv), U += dU.
- * The data and gradient-constancy constraints are normalised (Zimmer, Bruhn
- * and Weickert, IJCV 2011): the data term is divided by |grad I1w|^2 +
- * zeta^2 and the gradient term by |Hessian I1w|^2 + zeta^2 (zeta = 0.1), so
- * their robust weights measure a displacement rather than an intensity; at
- * a pixel whose warped position x + U leaves the image both terms are
- * dropped.  Smoothness couples the 4 direct neighbours with weight equal to
- * the mean of the two pixels' robust weights; a neighbour outside the image
- * is dropped (Neumann border). */
+ * place): `outer` fixed-point iterations, each one linearising at the
+ * current U (orc_var_linearise), solving for dU from dU = 0 with `sor`
+ * red-black SOR sweeps (orc_var_sor), then U += dU. */
 void orc_variational(int W, int H, const double *I0, const double *I0x,
                      const double *I0y, const double *I1, double *U, int outer,
                      int sor, double delta, double gamma, double alpha_s,
                      double omega)
 {
     size_t P = (size_t)W * H;
-    double *buf = (double *)malloc(sizeof(double) * P * 16);
-    double *I1w = buf, *Ix = buf + P, *Iy = buf + 2 * P, *Ixx = buf + 3 * P,
-           *Ixy = buf + 4 * P, *Iyy = buf + 5 * P, *Iz = buf + 6 * P,
-           *Ixz = buf + 7 * P, *Iyz = buf + 8 * P, *ad = buf + 9 * P,
-           *ag = buf + 10 * P, *as = buf + 11 * P, *du = buf + 12 * P,
-           *dv = buf + 13 * P;
-    double *u = U, *v = U + P;
+    double *Q = (double *)malloc(sizeof(double) * P * ORC_VQ);
+    double *dU = (double *)malloc(sizeof(double) * P * 2);
     for (int k = 0; k < outer; ++k) {
-        for (int y = 0; y < H; ++y)
-            for (int x = 0; x < W; ++x) {
-                size_t p = (size_t)y * W + x;
-                I1w[p] = bilinear(I1, W, H, x + u[p], y + v[p]);
-            }
-        for (int y = 0; y < H; ++y)
-            for (int x = 0; x < W; ++x) {
-                size_t p = (size_t)y * W + x;
-                Ix[p] = cdx(I1w, W, x, y); Iy[p] = cdy(I1w, W, H, x, y);
-            }
-        for (int y = 0; y < H; ++y)
-            for (int x = 0; x < W; ++x) {
-                size_t p = (size_t)y * W + x;
-                Ixx[p] = cdx(Ix, W, x, y);
-                Ixy[p] = cdy(Ix, W, H, x, y);
-                Iyy[p] = cdy(Iy, W, H, x, y);
-                Iz[p] = I1w[p] - I0[p];
-                Ixz[p] = Ix[p] - I0x[p];
-                Iyz[p] = Iy[p] - I0y[p];
-                /* constraint normalisation (reading F6) */
-                double nd = 1.0 / (Ix[p] * Ix[p] + Iy[p] * Iy[p] + ZETA2);
-                double ng = 1.0 / (Ixx[p] * Ixx[p] + 2.0 * Ixy[p] * Ixy[p] + Iyy[p] * Iyy[p] + ZETA2);
-                ad[p] = delta * nd * psi_prime(nd * Iz[p] * Iz[p]);
-                ag[p] = gamma * ng * psi_prime(ng * (Ixz[p] * Ixz[p] + Iyz[p] * Iyz[p]));
-                double wx = x + u[p], wy = y + v[p];
-                if (wx < 0 || wx > W - 1 || wy < 0 || wy > H - 1) { ad[p] = 0; ag[p] = 0; }
-                double ux = x + 1 < W ? u[p + 1] - u[p] : 0.0;
-                double uy = y + 1 < H ? u[p + W] - u[p] : 0.0;
-                double vx = x + 1 < W ? v[p + 1] - v[p] : 0.0;
-                double vy = y + 1 < H ? v[p + W] - v[p] : 0.0;
-                as[p] = alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
-                du[p] = 0.0; dv[p] = 0.0;
-            }
-        for (int s = 0; s < sor; ++s)
-            for (int colour = 0; colour < 2; ++colour)
-                for (int y = 0; y < H; ++y)
-                    for (int x = 0; x < W; ++x) {
-                        if (((x + y) & 1) != colour) continue;
-                        size_t p = (size_t)y * W + x;
-                        double sw = 0, su = 0, sv = 0;
-                        const int nx[4] = {x - 1, x + 1, x, x};
-                        const int ny[4] = {y, y, y - 1, y + 1};
-                        for (int e = 0; e < 4; ++e) {
-                            if (nx[e] < 0 || ny[e] < 0 || nx[e] >= W || ny[e] >= H) continue;
-                            size_t q = (size_t)ny[e] * W + nx[e];
-                            double wn = 0.5 * (as[p] + as[q]);
-                            sw += wn;
-                            su += wn * (u[q] + du[q] - u[p]);
-                            sv += wn * (v[q] + dv[q] - v[p]);
-                        }
-                        if (orc_mutation == 9) { su = 0; sv = 0; }
-                        double a11 = ad[p] * Ix[p] * Ix[p] + ag[p] * (Ixx[p] * Ixx[p] + Ixy[p] * Ixy[p]) + sw;
-                        double a12 = ad[p] * Ix[p] * Iy[p] + ag[p] * (Ixx[p] * Ixy[p] + Ixy[p] * Iyy[p]);
-                        double a22 = ad[p] * Iy[p] * Iy[p] + ag[p] * (Ixy[p] * Ixy[p] + Iyy[p] * Iyy[p]) + sw;
-                        double sd = (orc_mutation == 8) ? -1.0 : 1.0;
-                        double r1 = su - sd * ad[p] * Ix[p] * Iz[p] - ag[p] * (Ixx[p] * Ixz[p] + Ixy[p] * Iyz[p]);
-                        double r2 = sv - sd * ad[p] * Iy[p] * Iz[p] - ag[p] * (Ixy[p] * Ixz[p] + Iyy[p] * Iyz[p]);
-                        if (a11 > 0) du[p] = (1 - omega) * du[p] + omega * (r1 - a12 * dv[p]) / a11;
-                        if (a22 > 0) dv[p] = (1 - omega) * dv[p] + omega * (r2 - a12 * du[p]) / a22;
-                    }
-        for (size_t p = 0; p < P; ++p) { u[p] += du[p]; v[p] += dv[p]; }
+        orc_var_linearise(W, H, I0, I0x, I0y, I1, U, delta, gamma, alpha_s, Q);
+        memset(dU, 0, sizeof(double) * P * 2);
+        orc_var_sor(W, H, Q, U, sor, omega, dU);
+        for (size_t p = 0; p < 2 * P; ++p) U[p] += dU[p];
     }
-    free(buf);
+    free(Q);
+    free(dU);
 }
 
 /* Whole flow block: pyramids of both intensity images, then coarse to fine:

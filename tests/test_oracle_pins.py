@@ -453,6 +453,138 @@ def test_variational_keeps_exact_solution():
     assert np.abs(R - U)[:, :, :30].max() < 1e-8
 
 
+def _var_sor_case(golden_dir):
+    """The hand-worked sweep of tests/golden/var_sor_sweep.txt."""
+    from fractions import Fraction
+    rows = {}
+    with open(os.path.join(golden_dir, "var_sor_sweep.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *vals = line.split()
+            rows[k] = [float(Fraction(v)) for v in vals]
+    W, H = int(rows["grid"][0]), int(rows["grid"][1])
+    pl = {k: np.array(rows[k]).reshape(H, W) for k in oracle.VAR_PLANES}
+    U = np.stack([np.array(rows["u"]), np.array(rows["v"])]).reshape(2, H, W)
+    dU0 = np.stack([np.array(rows["du_start"]), np.array(rows["dv_start"])]).reshape(2, H, W)
+    want = np.stack([np.array(rows["du"]), np.array(rows["dv"])]).reshape(2, H, W)
+    return pl, U, dU0, int(rows["sweeps"][0]), rows["omega"][0], want
+
+
+def test_var_sor_hand_worked_sweep(golden_dir):
+    # one red-black sweep of the Euler-Lagrange system, worked by hand on a
+    # 2x2 grid with a gradient-constancy cross term, unequal smoothness
+    # weights and a relaxation factor that acts on a non-zero start value
+    pl, U, dU0, sweeps, omega, want = _var_sor_case(golden_dir)
+    got = oracle.var_sor(pl, U, dU0, sweeps, omega)
+    assert np.abs(got - want).max() <= 1e-14, (got, want)
+
+
+def _var_energy(pl, U, dU):
+    """The linearised energy whose Euler-Lagrange equations the SOR solves:
+    squared data and gradient-constancy residuals of the increment plus the
+    smoothness of U + dU over 4-neighbour pairs, with the frozen weights."""
+    du, dv = dU
+    e = pl["ad"] * (pl["Ix"] * du + pl["Iy"] * dv + pl["Iz"]) ** 2
+    e = e + pl["ag"] * ((pl["Ixx"] * du + pl["Ixy"] * dv + pl["Ixz"]) ** 2
+                        + (pl["Ixy"] * du + pl["Iyy"] * dv + pl["Iyz"]) ** 2)
+    total = e.sum()
+    a = pl["as"]
+    for c in range(2):
+        f = U[c] + dU[c]
+        wx = 0.5 * (a[:, 1:] + a[:, :-1])
+        wy = 0.5 * (a[1:, :] + a[:-1, :])
+        total += (wx * (f[:, 1:] - f[:, :-1]) ** 2).sum()
+        total += (wy * (f[1:, :] - f[:-1, :]) ** 2).sum()
+    return total
+
+
+def _energy_gradient(pl, U, dU, h=1e-3):
+    # the energy is quadratic in dU, so central differences are exact up to
+    # rounding
+    g = np.zeros_like(dU)
+    for idx in np.ndindex(*dU.shape):
+        d = dU.copy()
+        d[idx] += h
+        ep = _var_energy(pl, U, d)
+        d[idx] -= 2 * h
+        em = _var_energy(pl, U, d)
+        g[idx] = (ep - em) / (2 * h)
+    return g
+
+
+def _warped_pair(W, H):
+    """A textured image and a non-translational copy (a slight rotation and
+    scaling about the centre), so the mixed derivative Ixy is not zero."""
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    cx, cy = (W - 1) / 2, (H - 1) / 2
+    th, sc = 0.08, 1.05
+    xs = cx + sc * (np.cos(th) * (xx - cx) - np.sin(th) * (yy - cy))
+    ys = cy + sc * (np.sin(th) * (xx - cx) + np.cos(th) * (yy - cy))
+
+    def tex(x, y):
+        return (127.5 + 60 * np.sin(2 * np.pi * x / 9.0) * np.cos(2 * np.pi * y / 7.0)
+                + 25 * np.sin(x * y / 11.0))
+    return tex(xx, yy), tex(xs, ys)
+
+
+def test_var_sor_converges_to_the_energy_minimum():
+    # Many sweeps of the SOR solve the linear system; its solution must be the
+    # stationary point of the linearised energy, whose gradient is taken here
+    # by differentiating the energy itself, not from the equations.  A wrong
+    # or missing coefficient (e.g. the gradient-constancy coupling in a12)
+    # moves the solution off the minimum.
+    W, H = 13, 11
+    I0, I1 = _warped_pair(W, H)
+    I0x, I0y = oracle.gradients(I0)
+    rng = np.random.default_rng(5)
+    U = 0.6 * rng.standard_normal((2, H, W))
+    pl = oracle.var_linearise(I0, I0x, I0y, I1, U)
+    assert np.abs(pl["Ixy"]).max() > 1.0 and pl["ag"].max() > 0
+    g0 = _energy_gradient(pl, U, np.zeros((2, H, W)))
+    dU = oracle.var_sor(pl, U, np.zeros((2, H, W)), 6000, 1.6)
+    g = _energy_gradient(pl, U, dU)
+    assert np.abs(g).max() <= 1e-7 * np.abs(g0).max(), (np.abs(g).max(), np.abs(g0).max())
+    # and it is a minimum: any perturbation raises the energy
+    e = _var_energy(pl, U, dU)
+    for _ in range(5):
+        assert _var_energy(pl, U, dU + 1e-2 * rng.standard_normal(dU.shape)) > e
+
+
+def test_var_linearise_planes_closed_forms():
+    # On a quadratic image central differences are exact away from the
+    # border, so the warped image's derivative planes have closed forms; an
+    # integer flow warps exactly.  Where the warp leaves the image the data
+    # and gradient terms are dropped, and a constant flow has the smoothness
+    # weight Psi'(0) alpha = alpha / (2 eps).
+    W, H = 16, 12
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+
+    def quad(x, y):
+        return 100 + 3 * x + 2 * y + 0.5 * x * x + 0.25 * x * y - 0.3 * y * y
+    I1 = quad(xx, yy)
+    I0 = I1 - 7.0
+    I0x = np.zeros_like(I1)
+    I0y = np.full_like(I1, 2.0)
+    U = np.zeros((2, H, W))
+    U[0] = 1.0
+    pl = oracle.var_linearise(I0, I0x, I0y, I1, U, delta=5.0, gamma=10.0, alpha=20.0)
+    i = (slice(2, H - 2), slice(2, W - 3))   # x + 1 stays two pixels inside
+    X, Y = xx[i] + 1.0, yy[i]
+    assert np.allclose(pl["Ix"][i], 3 + X + 0.25 * Y, atol=1e-9)
+    assert np.allclose(pl["Iy"][i], 2 + 0.25 * X - 0.6 * Y, atol=1e-9)
+    assert np.allclose(pl["Ixx"][i], 1.0, atol=1e-9)
+    assert np.allclose(pl["Ixy"][i], 0.25, atol=1e-9)
+    assert np.allclose(pl["Iyy"][i], -0.6, atol=1e-9)
+    assert np.allclose(pl["Iz"][i], quad(X, Y) - I0[i], atol=1e-9)
+    assert np.allclose(pl["Ixz"][i], 3 + X + 0.25 * Y, atol=1e-9)
+    assert np.allclose(pl["Iyz"][i], 0.25 * X - 0.6 * Y, atol=1e-9)
+    assert np.all(pl["ad"][:, :W - 1] > 0) and np.all(pl["ag"][:, :W - 1] > 0)
+    assert np.all(pl["ad"][:, W - 1] == 0) and np.all(pl["ag"][:, W - 1] == 0)
+    assert np.allclose(pl["as"], 20.0 / (2 * 1e-3), rtol=1e-12)
+
+
 def test_event_surface_integer_shift():
     # an edge image shifted by (3, -1) gives exactly shifted D and S, and the
     # flow on the shifted edge pixels recovers (3, -1)
@@ -528,6 +660,9 @@ def _pins_fail():
         me.test_variational_keeps_exact_solution,
         me.test_variational_smooths_without_data,
         me.test_event_surface_integer_shift,
+        lambda: me.test_var_sor_hand_worked_sweep(os.path.join(os.path.dirname(__file__), "golden")),
+        me.test_var_sor_converges_to_the_energy_minimum,
+        me.test_var_linearise_planes_closed_forms,
     ]
     for c in checks:
         try:
@@ -537,7 +672,7 @@ def _pins_fail():
     return False
 
 
-@pytest.mark.parametrize("k", range(1, 12))
+@pytest.mark.parametrize("k", range(1, 14))
 def test_planted_mistakes_are_caught(k):
     try:
         oracle.set_mutation(k)
