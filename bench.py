@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-multistream", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-config0", action="store_true")
+    ap.add_argument("--c0-windows", type=int, default=400,
+                    help="windows of the 346x260 single-window line")
     ap.add_argument("--sv-seconds", type=float, default=0.5,
                     help="arrival span of each timed serving run")
     ap.add_argument("--sv-warmup", type=float, default=0.3)
@@ -66,7 +69,10 @@ def parse():
     ap.add_argument("--sv-max-batch", type=int, default=16,
                     help="windows of one stream the server may batch into one launch")
     ap.add_argument("--sv-scales", type=lambda v: [float(x) for x in v.split(",")],
-                    default=[1.0, 0.35], help="arrival-rate scales of the serving runs")
+                    default=[1.0, 0.8, 0.65, 0.5, 0.42, 0.35],
+                    help="arrival-rate scales of the serving runs")
+    ap.add_argument("--sv-p99-bound-ms", type=float, default=10.0,
+                    help="p99 latency bound of the sustainable-rate search (one window)")
     ap.add_argument("--ms-windows", type=int, default=11,
                     help="windows per stream in the multi-stream run")
     return ap.parse_args()
@@ -119,7 +125,45 @@ def _oracle_noop(_):
     return 0
 
 
+def _oracle_frame_timed(args):
+    """One frame pair in a fresh single-threaded process: (front end of both
+    windows, flow) wall seconds."""
+    import oracle
+    (w0, w1, prm) = args
+    t0 = time.perf_counter()
+    kw = dict(connectivity=prm["connectivity"], n_d=prm["n_d"], n_f=prm["n_f"],
+              alpha=prm["alpha"])
+    s0 = oracle.surface_from_events(W_, H_, *w0, **kw)
+    s1 = oracle.surface_from_events(W_, H_, *w1, **kw)
+    t1 = time.perf_counter()
+    oracle.flow(255.0 * s0["S"], 255.0 * s1["S"], levels=prm["levels"], patch=prm["patch"],
+                stride=prm["stride"], gn_iters=prm["gn_iters"], gn_damping=prm["gn_damping"],
+                var_outer=prm["var_outer"], var_sor=prm["var_sor"], var_delta=prm["var_delta"],
+                var_gamma=prm["var_gamma"], var_alpha=prm["var_alpha"],
+                sor_omega=prm["sor_omega"])
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def oracle_single_thread(stream, prm):
+    """The oracle alone on one core: one frame pair (windows 0 and 1) in one
+    process with nothing else running.  Per window: the front end of one
+    window plus the flow of one pair."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        pool.map(_oracle_noop, [0])
+        front2, flow = pool.map(_oracle_frame_timed,
+                                [(_window_tuple(stream, 0), _window_tuple(stream, 1), prm)])[0]
+    return {"ms_per_window": 1000.0 * (0.5 * front2 + flow),
+            "front_end_ms_per_window": 500.0 * front2, "flow_ms_per_frame": 1000.0 * flow,
+            "threads": 1,
+            "sample": "windows 0 and 1 of the 1280x720 stream: both front ends, one flow"}
+
+
 def cpu_workers():
+    """Processes of the oracle sample: every host core, at most 16."""
     n = os.cpu_count() or 1
     return max(1, min(n, 16))
 
@@ -127,6 +171,16 @@ def cpu_workers():
 def workload_name(nwin):
     return ("1280x720 single stream, %d windows of 10 ms (%d flow frames), 150k-400k "
             "events/window, 12 affine objects, 3%% noise, seed 1+rank" % (nwin, nwin - 1))
+
+
+def bench_config(prm, nwin, world):
+    """The workload and method parameters, identical in both arms."""
+    return {"workload": workload_name(nwin),
+            "levels": prm["levels"], "patch": prm["patch"], "stride": prm["stride"],
+            "gn_iters": prm["gn_iters"], "var": "%dx%d" % (prm["var_outer"], prm["var_sor"]),
+            "l2": "inputs larger than L2: the events of every window of a step (about "
+                  "0.7 GB) resident in HBM",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def run_reference(args, rank):
@@ -153,20 +207,21 @@ def run_reference(args, rank):
             times.append(dt)
     total = sum(times)
     value = frames_per_step * len(times) / total
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    sample = ("each step times %d frame pairs of the workload, one per process on %d host "
+              "cores (of %d): windows 0->1 and 1->2 of a 3-window draw of the same "
+              "1280x720 generator, alternating" % (frames_per_step, workers,
+                                                   os.cpu_count() or 1))
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.windows),
-                   "path": "FP64 oracle: a bounded sample of %d frame pairs of the stream's "
-                           "first windows per step, one per process" % frames_per_step,
-                   "levels": prm["levels"], "patch": prm["patch"], "stride": prm["stride"],
-                   "gn_iters": prm["gn_iters"],
-                   "var": "%dx%d" % (prm["var_outer"], prm["var_sor"])},
+        "config": bench_config(prm, args.windows, world),
+        "path": "FP64 oracle (plain C, one window pair per process), as it stands",
+        "sample": sample,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
-                         "sample": "%d frame pairs of the 1280x720 stream per step, one per "
-                                   "process" % frames_per_step},
+                         "host_cores": os.cpu_count(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -293,6 +348,73 @@ def stage_hbm_fractions(ms_per_frame, P, n_events, n_levels, var_outer, peak):
         out["all stages"] = {"bytes_per_frame": tb, "ms_per_frame": tt,
                              "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
     return out
+
+
+def a8_outer_iteration_roofline(by_level, P0, var_outer, frames, peak, traffic_coeff,
+                                traffic_sor):
+    """Headline roofline of the dominant hot-path step, the variational
+    refinement (A8) at level 0.  Unit: one outer iteration, whose algorithmic
+    bytes are I0, I1, U in and U out, 24 B per pixel (its SOR sweeps run on
+    chip); its time is the level's coefficient and SOR launches of that
+    iteration.  by_level: stage ms per frame at level 0."""
+    t_ms = by_level.get("var_coeff", 0.0) + by_level.get("var_sor", 0.0)
+    if t_ms <= 0.0 or var_outer <= 0:
+        return None
+    per_iter_s = t_ms / 1000.0 / var_outer
+    nbytes = 24.0 * P0
+    achieved = nbytes / per_iter_s / 1e9
+    traffic = None
+    if traffic_coeff is not None and traffic_sor is not None:
+        traffic = traffic_coeff + traffic_sor
+    return {"bound": "hbm", "kernel": "A8 variational refinement at level 0: var_coeff + "
+                                      "var_sor launches of one outer iteration",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "bytes_per_unit": nbytes,
+            "unit_def": "one outer iteration at level 0 (24 B per pixel: I0, I1, U in, U out)",
+            "us_per_unit": per_iter_s * 1e6, "frames_profiled": frames}
+
+
+FP32_LANES_PER_SM = 128   # four sub-partitions of 32 FP32 lanes
+N_SMS = 152
+
+
+def a6_flop_roof(by_level_all, geo, ps, iters, sm_mhz):
+    """A6 (patch inverse search) against the FP32 ALU: 25 flop per patch pixel
+    and Gauss-Newton iteration (bilinear sample, residual, two products and
+    sums), summed over the patches of every level, over the search time.
+    Peak = SMs x FP32 lanes x 2 (FMA) x SM clock."""
+    flops = sum(25.0 * ps * ps * iters * npx * npy for (_, _, npx, npy) in geo)
+    t_ms = sum(v.get("patch_search", 0.0) for k, v in by_level_all.items() if k != "all")
+    if t_ms <= 0.0:
+        return None
+    clock = sm_mhz or 2070.0
+    peak = N_SMS * FP32_LANES_PER_SM * 2.0 * clock * 1e6 / 1e12
+    ach = flops / (t_ms / 1000.0) / 1e12
+    l0 = by_level_all.get("0", {}).get("patch_search", 0.0)
+    f0 = 25.0 * ps * ps * iters * geo[0][2] * geo[0][3]
+    return {"bound": "alu", "flop_per_frame": flops, "ms_per_frame": t_ms,
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "level0": {"flop": f0, "ms": l0,
+                       "achieved": f0 / (l0 / 1000.0) / 1e12 if l0 > 0 else None},
+            "peak_source": "derived: %d SMs x %d FP32 lanes x 2 flop (FMA) x %.0f MHz "
+                           "(median SM clock of the timed region)"
+                           % (N_SMS, FP32_LANES_PER_SM, clock),
+            "l1_smem": profile_figure("patch_search_kernel_1280x720_level0.md",
+                                      "l1tex__throughput")}
+
+
+def profile_figure(name, metric):
+    """A metric's value from a committed ncu summary under profiles/ (the
+    table row whose metric name matches), or None."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        for ln in open(path).read().splitlines():
+            if ("`%s" % metric) in ln and ln.startswith("|"):
+                cells = [c.strip() for c in ln.strip("|").split("|")]
+                return {"metric": metric, "value": cells[-1], "source": "profiles/" + name}
+    except OSError:
+        pass
+    return None
 
 
 def geo_levels(p):
@@ -635,9 +757,74 @@ def run_serving(args, eb, torch, dev, rank):
             "max_latency_ms": float(lat.max()),
             "mean_batch": float(np.mean([c[5] for c in comps])),
             "latency_by_resolution": per_res})
+    bound = args.sv_p99_bound_ms
+    ok_runs = [r for r in out["runs"] if r["p99_latency_ms"] <= bound and not r["errors"]]
+    out["sustainable"] = {
+        "p99_bound_ms": bound,
+        "largest_rate_scale": max((r["rate_scale"] for r in ok_runs), default=None),
+        "offered_mpx_per_s": max((r["offered_mpx_per_s"] for r in ok_runs), default=None),
+        "scales_tried": [r["rate_scale"] for r in out["runs"]],
+        "rule": "largest arrival-rate scale whose p99 latency stays within one 10 ms window"}
     server.close()
     del keep
     return out
+
+
+def run_config0(args, eb, torch, dev, local):
+    """The 346x260 single-window workload (seed 0: 40 segments translating at
+    (3.0, -1.5) px per window, 20 000 events per window, 5 % noise), plain
+    FP32: one ebof_process_window call per window, graph-replayed.  Its two
+    windows are fed alternately, so every call after the first is one flow
+    frame of the workload (0 -> 1, then 1 -> 0: the same work reversed)."""
+    from paper_2112_10591_gb300 import synth
+    ev = synth.workload_346x260(seed=0)
+    W, H = ev.width, ev.height
+    prm = eb.ebof_default_params(W, H)
+    st, s = eb.ebof_stream_create(prm, local)
+    eb.check(st, "ebof_stream_create 346x260")
+    lib = eb.load()
+    cs = torch.cuda.current_stream(dev)
+    wins = []
+    for k in range(2):
+        x, y, t, _, tb, te = ev.window(k)
+        wins.append((torch.from_numpy(np.ascontiguousarray(x)).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(y)).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(t)).to(dev), tb, te))
+    flow = torch.empty((2, H, W), dtype=torch.float32, device=dev)
+    n = max(8, args.c0_windows)
+
+    def call(k):
+        x, y, t, tb, te = wins[k & 1]
+        r = lib.ebof_process_window(s.handle, x.data_ptr(), y.data_ptr(), t.data_ptr(), None,
+                                    x.numel(), tb, te, flow.data_ptr(), None, None, None,
+                                    cs.cuda_stream)
+        if r < 0:
+            raise eb.EbofError(r, "process_window 346x260")
+
+    for k in range(max(3, args.warmup) + 1):
+        call(k)
+    torch.cuda.synchronize(dev)
+    ea = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    eb_ = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(cs)
+    for k in range(n):
+        ea[k].record(cs)
+        call(k)
+        eb_[k].record(cs)
+    t1.record(cs)
+    torch.cuda.synchronize(dev)
+    lat = np.asarray([a.elapsed_time(b) for a, b in zip(ea, eb_)])
+    total = t0.elapsed_time(t1)
+    s.close()
+    return {"value": n / (total / 1000.0), "unit": UNIT, "mpx_per_s": n * W * H / total / 1e3,
+            "p50_latency_ms": float(np.percentile(lat, 50)),
+            "p99_latency_ms": float(np.percentile(lat, 99)), "windows_timed": n,
+            "levels": prm.levels, "patch": prm.patch, "stride": prm.stride,
+            "workload": "346x260, 2 windows of 20 000 events (40 segments at (3.0, -1.5) "
+                        "px/window, 5 % noise, seed 0) fed alternately; plain FP32, one "
+                        "call per window, inputs resident (L2-resident: 0.5 MB of events)"}
 
 
 # ---------------------------------------------------------------- our arm
@@ -676,8 +863,10 @@ def main():
         nfr = args.cpu_frames or workers
         oracle_flows, dt = oracle_sample(stream, _params_dict(prm), nfr, workers)
         cpu = {"value": nfr / dt, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "host_cores": os.cpu_count(),
                "sample": "%d frame pairs (windows 0..%d) of the 1280x720 stream, one per "
-                         "process, FP64, %.1f s wall" % (nfr, nfr, dt)}
+                         "process, FP64, %.1f s wall" % (nfr, nfr, dt),
+               "single_thread": oracle_single_thread(stream, _params_dict(prm))}
 
     eb.load()
     xs = torch.from_numpy(stream.x).to(dev)
@@ -768,18 +957,26 @@ def main():
     per_launch_s = dom_ms / 1000.0 / max(dom_launches, 1)
     achieved = per_launch_bytes / per_launch_s / 1e9
     peak, peak_kind = load_peaks()
-    roofline = {"bound": "hbm", "kernel": dom,
-                "level": level, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": dram_traffic(dom, level),
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "bytes_per_launch": per_launch_bytes, "us_per_launch": per_launch_s * 1e6,
-                "launches_timed": int(dom_launches),
-                "stage_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items()},
-                "stage_ms_per_frame": {k: round(v[0] / (nwin * nprof), 4)
-                                       for k, v in prof.items() if v[1]},
-                "stage_ms_per_frame_by_level": by_level,
-                "stage_timing": "CUDA events around each stage's launches on the "
-                                "caller's stream (eager launches, gaps included)"}
+    kernel_io = {"kernel": dom, "level": level, "achieved": achieved, "unit": "GB/s",
+                 "frac": achieved / peak, "traffic": dram_traffic(dom, level),
+                 "bytes_per_launch": per_launch_bytes, "us_per_launch": per_launch_s * 1e6,
+                 "launches_timed": int(dom_launches),
+                 "bytes_rule": "the kernel's own inputs read once and outputs written once"}
+    ms_frame = {k: v[0] / (nwin * nprof) for k, v in prof.items() if v[1]}
+    roofline = a8_outer_iteration_roofline(by_level.get("0", {}), P, prm.var_outer, nwin * nprof,
+                                           peak, dram_traffic("var_coeff", 0),
+                                           dram_traffic("var_sor", 0)) or {}
+    roofline.update({
+        "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs; burst copy)",
+        "kernel_io": kernel_io,
+        "stage_roofline": stage_hbm_fractions(ms_frame, P, n_ev_win, len(gl), prm.var_outer,
+                                              peak),
+        "stage_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items()},
+        "stage_ms_per_frame": {k: round(v, 4) for k, v in ms_frame.items()},
+        "stage_ms_per_frame_by_level": by_level,
+        "stage_timing": "CUDA events around each stage's launches on the caller's stream "
+                        "(eager launches, gaps included; the graph-replayed path times "
+                        "the whole window only)"})
 
     # batched path: the same stream through ebof_process_windows
     batched = None
@@ -938,6 +1135,10 @@ def main():
                "h2d_bytes_per_step": int(off[-1]) * 12,
                "d2h_bytes_per_step": nwin * 2 * P * 4}
 
+    roofline["a6_patch_search"] = a6_flop_roof(by_level, gl, prm.patch, prm.gn_iters,
+                                               clocks.get("sm_mhz"))
+    config0 = None if args.no_config0 else run_config0(args, eb, torch, dev, local)
+
     multistream = None if args.no_multistream else run_multistream(args, eb, torch, dev, rank)
     serving = None if args.no_serving else run_serving(args, eb, torch, dev, rank)
 
@@ -948,18 +1149,15 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(nwin),
-                       "path": "plain: one ebof_process_window call per window",
-                       "levels": prm.levels, "patch": prm.patch, "stride": prm.stride,
-                       "gn_iters": prm.gn_iters, "var": "%dx%d" % (prm.var_outer, prm.var_sor),
-                       "l2": "inputs larger than L2: %.0f MB of events per step"
-                             % (int(off[-1]) * 13 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": bench_config(_params_dict(prm), nwin, world),
+            "path": "plain: one ebof_process_window call per window (graph replay)",
+            "events_mb_per_step": int(off[-1]) * 13 / 1e6,
             "p50_latency_ms": float(np.percentile(lat, 50)),
             "p99_latency_ms": float(np.percentile(lat, 99)),
             "mpx_per_s": value * P / 1e6,
             "wall_s": wall,
             "batched": batched,
+            "config0_346x260": config0,
             "epe_vs_oracle": epe,
             "flow_quality": quality,
             "fp16_storage": fp16,

@@ -71,3 +71,41 @@ def test_traffic_figures_follow_their_sources(bench, tmp_path, monkeypatch):
     assert bench.dram_traffic("var_sor", 1) is None
     src.write_text("// kernel, changed\n")
     assert bench.dram_traffic("var_sor", 0) is None
+
+
+def test_a8_roofline_reproduces_by_hand(bench):
+    # 24 B per level-0 pixel per outer iteration over that iteration's
+    # coefficient and SOR time; the figures of a level-0 profile of 0.0972 +
+    # 0.1124 ms per frame over 5 iterations give 528 GB/s
+    P = 1280 * 720
+    r = bench.a8_outer_iteration_roofline({"var_coeff": 0.0972, "var_sor": 0.1124}, P, 5, 400,
+                                          6799.3, 22161408, 33199104)
+    assert r["bytes_per_unit"] == 24 * P
+    assert r["us_per_unit"] == pytest.approx((0.0972 + 0.1124) * 1000 / 5)
+    assert r["achieved"] == pytest.approx(24 * P / ((0.0972 + 0.1124) / 5 / 1000) / 1e9)
+    assert r["achieved"] == pytest.approx(528, abs=1)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6799.3)
+    assert r["traffic"] == 22161408 + 33199104
+    assert bench.a8_outer_iteration_roofline({}, P, 5, 1, 6799.3, None, None) is None
+
+
+def test_a6_flop_roof(bench):
+    import paper_2112_10591_gb300 as eb
+    p = eb.ebof_default_params(1280, 720)
+    geo = bench.geo_levels(p)
+    by = {"all": {}, "0": {"patch_search": 0.08}, "1": {"patch_search": 0.02}}
+    r = bench.a6_flop_roof(by, geo, 12, 12, 2070.0)
+    f0 = 25 * 144 * 12 * 318 * 178
+    assert r["level0"]["flop"] == f0 and f0 == pytest.approx(2.445e9, rel=1e-3)
+    assert r["flop_per_frame"] > f0
+    assert r["ms_per_frame"] == pytest.approx(0.1)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_both_arms_report_the_same_config(bench):
+    import paper_2112_10591_gb300 as eb
+    p = eb.ebof_default_params(1280, 720)
+    ours = bench.bench_config(bench._params_dict(p), 201, 1)
+    ref = bench.bench_config(bench._reference_params(), 201, 1)
+    assert ours == ref
