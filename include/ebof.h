@@ -212,10 +212,11 @@ ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *
 /* ebof_process_window with HOST buffers: the events go to the device, the
  * window runs and the flow comes back into h_flow [2][H][W], all on
  * `cuda_stream`, which is then synchronised.  Pageable buffers are staged
- * through device memory with copies.  When every buffer is page-locked and
- * registered with CUDA (addressable by the device at the same address), a
- * window that has a previous one reads its events and writes its flow in
- * place over the host link, with no staging copies; the result is the same.
+ * through device memory with copies.  When every buffer lies, whole, inside
+ * one page-locked range registered with CUDA (addressable by the device at
+ * the same address), a window that has a previous one reads its events and
+ * writes its flow in place over the host link, with no staging copies; the
+ * result is the same.
  * The buffers must not be modified or freed until the call returns. */
 ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const uint16_t *h_y,
                                      const int64_t *h_t, int64_t n_events, int64_t t_begin,
@@ -237,10 +238,9 @@ ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32
 /* ebof_edt without caller scratch, for callers that cannot allocate device
  * memory: code that must not call cudaMalloc once running (a real-time loop
  * where an allocation may synchronise the device and has no latency bound),
- * code inside a host framework that owns all device memory through its own
- * allocator, or code running while a stream is being captured, where
- * cudaMalloc is not allowed.  The paper has no counterpart; this is a
- * deployment variant of the separable EDT entry point above.
+ * or code inside a host framework that owns all device memory through its
+ * own allocator.  The paper has no counterpart; this is a deployment variant
+ * of the separable EDT entry point above.
  * Same inputs, outputs and result as ebof_edt, but the column distances are
  * kept in a static device array of 2^21 int32 (8 MiB) that every device
  * which loads the library holds until the process exits, so width*height
@@ -248,7 +248,9 @@ ebof_status ebof_edt(const uint8_t *d_edge, int32_t width, int32_t height, int32
  * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  * Its first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, and each call
+ * before any stream capture.  The looked-up address is kept for the life of
+ * the process, so after cudaDeviceReset on a device this entry point must
+ * not be called on that device again.  All calls share the one array, and each call
  * overwrites every entry it reads, so nothing carries over from the previous
  * call; calls that overlap on the GPU (on different streams, or from
  * different threads without ordering) race on the array and give wrong
@@ -442,6 +444,29 @@ const char *ebof_stage_name(int32_t stage);
 
 /* Kernels this library has launched in the process so far (all streams). */
 uint64_t ebof_kernel_launches(void);
+
+/* ---- diagnostics: failure injection for tests ------------------------------
+ * Both act on the host side only and change nothing a kernel computes.  The
+ * paper has no counterpart; they let tests drive the error paths above
+ * without faulting a GPU. */
+
+/* Bound, in mbarrier try-wait rounds, of the first wait of the batched SOR
+ * kernel (the copy-ahead form, used when a call's variational grid has at
+ * least four regions per SM) for a region's coefficient copy.  When it runs
+ * out the kernel latches EBOF_ERR_TIMEOUT, reported by ebof_stream_sync, lets
+ * the copy in flight land under a second wait at the default bound, and
+ * leaves the flow of that call undefined.  Applies to launches enqueued
+ * after the call (graphs captured earlier keep their bound); iterations < 0
+ * restores the default, 2^22; 0 makes every such wait run out at once.
+ * EBOF_ERR_BUSY while another thread uses the stream. */
+ebof_status ebof_stream_set_wait_limit(ebof_stream *s, int64_t iterations);
+
+/* The next n device allocations of this library (all threads, all streams)
+ * succeed and the one after fails the way cudaMalloc fails when the device is
+ * out of memory; the hook then disarms itself.  n < 0 disarms it.  The call
+ * that meets the failure returns EBOF_ERR_OOM after freeing what it had
+ * allocated; an existing stream stays usable. */
+void ebof_debug_fail_allocation(int32_t n);
 
 /* Static text for a status code. */
 const char *ebof_status_string(ebof_status st);

@@ -168,6 +168,9 @@ def _declare(L):
     L.ebof_kernel_launches.restype = ctypes.c_uint64
     L.ebof_status_string.argtypes = [ctypes.c_int]
     L.ebof_status_string.restype = ctypes.c_char_p
+    L.ebof_stream_set_wait_limit.argtypes = [vp, i64]
+    L.ebof_debug_fail_allocation.argtypes = [i32]
+    L.ebof_debug_fail_allocation.restype = None
     for name in ("ebof_stream_create", "ebof_stream_destroy", "ebof_stream_reset",
                  "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
                  "ebof_process_window_host", "ebof_stream_sync", "ebof_edt",
@@ -176,7 +179,8 @@ def _declare(L):
                  "ebof_group_reset", "ebof_group_process", "ebof_group_sync",
                  "ebof_process_window_list", "ebof_server_create", "ebof_fwl", "ebof_server_destroy",
                  "ebof_server_open_stream", "ebof_server_close_stream", "ebof_server_submit",
-                 "ebof_server_poll", "ebof_server_drain", "ebof_server_get_info"):
+                 "ebof_server_poll", "ebof_server_drain", "ebof_server_get_info",
+                 "ebof_stream_set_wait_limit"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -459,6 +463,14 @@ def ebof_group_sync(group: Group, n_out: int = None):
 
 
 EBOF_STAGE_COUNT = 12
+
+
+def ebof_stream_set_wait_limit(stream: Stream, iterations: int) -> int:
+    return load().ebof_stream_set_wait_limit(stream.handle, int(iterations))
+
+
+def ebof_debug_fail_allocation(n: int) -> None:
+    load().ebof_debug_fail_allocation(int(n))
 
 
 def ebof_stream_set_profiling(stream: Stream, enable: bool) -> int:

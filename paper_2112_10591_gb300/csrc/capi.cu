@@ -74,6 +74,7 @@ struct ebof_stream {
     cudaStream_t last_stream = nullptr;
     bool have_last = false;
     std::atomic<int> busy{0};
+    long long wait_limit = kWaitLimitDefault;  // ebof_stream_set_wait_limit
     Profiler prof;
     // Per-call window descriptors and flow destinations, read on the device by
     // the descriptor-driven paths: [max_batch] ebof_window_desc followed by
@@ -193,9 +194,21 @@ ebof_status check_params(const ebof_params *p)
     return EBOF_OK;
 }
 
+// Failure injection (ebof_debug_fail_allocation): allocations left before
+// the one that fails; negative = disarmed.
+std::atomic<int> g_alloc_fail_after{-1};
+
+// Every device allocation of the library goes through here.
 template <class T>
 cudaError_t dmalloc(T **ptr, size_t bytes)
 {
+    int c = g_alloc_fail_after.load();
+    while (c >= 0 && !g_alloc_fail_after.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 0) {  // the injected failure; the hook is disarmed now
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     return cudaMalloc((void **)ptr, std::max<size_t>(bytes, 256));
 }
 
@@ -242,6 +255,7 @@ FlowParams flow_params(const ebof_params &p)
     fp.gamma = p.var_gamma;
     fp.alpha_s = p.var_alpha;
     fp.omega = p.sor_omega;
+    fp.wait_limit = kWaitLimitDefault;
     return fp;
 }
 
@@ -294,7 +308,8 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
     const size_t flow_frame = (size_t)2 * W * H;
     if (geo.levels > 0 && nf > 0) {
         const int curf_first = cur_first + ff;
-        const FlowParams fp = flow_params(p);
+        FlowParams fp = flow_params(p);
+        fp.wait_limit = s->wait_limit;
         float *Ucur = nullptr, *Uc = nullptr;
         const Level *lvc = nullptr;
         for (int l = geo.levels - 1; l >= 0; --l) {
@@ -757,17 +772,46 @@ ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *
                nullptr, (cudaStream_t)cuda_stream);
 }
 
-// A host buffer the current device can address at the same virtual address:
-// page-locked memory registered with CUDA under unified addressing.
-// Pageable memory is not (the check says no, and the caller stages it).
-static bool device_addressable(const void *h)
+typedef CUresult (*PointerAttrFn)(void *, CUpointer_attribute, CUdeviceptr);
+
+static PointerAttrFn pointer_attr_fn()
+{
+    static std::atomic<PointerAttrFn> fn{nullptr};
+    static std::atomic<int> tried{0};
+    if (!tried.exchange(1)) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn.store((PointerAttrFn)p);
+        cudaGetLastError();
+    }
+    return fn.load();
+}
+
+// A host buffer of `bytes` bytes that the current device can address at the
+// same virtual address: page-locked memory registered with CUDA under unified
+// addressing, the whole extent inside one registered range (a buffer that
+// starts in a page-locked range and runs past its end is not).  Pageable
+// memory is not addressable either; the caller stages it.
+static bool device_addressable(const void *h, size_t bytes)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeHost && a.devicePointer == h;
+    if (a.type != cudaMemoryTypeHost || a.devicePointer != h) return false;
+    PointerAttrFn fn = pointer_attr_fn();
+    if (!fn) return false;
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (fn(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)h) != CUDA_SUCCESS ||
+        fn(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)h) != CUDA_SUCCESS)
+        return false;
+    const uintptr_t b = (uintptr_t)h, s0 = (uintptr_t)start;
+    return b >= s0 && bytes <= size && b - s0 <= size - bytes;
 }
 
 ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const uint16_t *h_y,
@@ -786,9 +830,10 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
     // the events and write the flow in place over the host link, with no
     // staging copies (the first window, whose flow is cleared with a memset,
     // and pageable buffers take the staged path below)
-    if (s->has_prev && s->geo.levels > 0 && device_addressable(h_flow) &&
-        (n == 0 || (device_addressable(h_x) && device_addressable(h_y) &&
-                    device_addressable(h_t)))) {
+    const size_t flow_bytes = sizeof(float) * 2 * (size_t)s->p.width * s->p.height;
+    if (s->has_prev && s->geo.levels > 0 && device_addressable(h_flow, flow_bytes) &&
+        (n == 0 || (device_addressable(h_x, 2 * n) && device_addressable(h_y, 2 * n) &&
+                    device_addressable(h_t, 8 * n)))) {
         const ebof_status r = run(s, 1, h_x, h_y, h_t, n_events, t_begin, t_end - t_begin,
                                   nullptr, h_flow, nullptr, nullptr, nullptr, st);
         if (r < 0) return r;
@@ -802,7 +847,7 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
         cudaFree(s->ev_stage);
         s->ev_stage = nullptr;
         s->ev_stage_bytes = 0;
-        if (cudaMalloc(&s->ev_stage, std::max<size_t>(need, 1 << 20)) != cudaSuccess) {
+        if (dmalloc(&s->ev_stage, std::max<size_t>(need, 1 << 20)) != cudaSuccess) {
             cudaGetLastError();
             return EBOF_ERR_OOM;
         }
@@ -821,11 +866,21 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
     ebof_status r = run(s, 1, dx, dy, dt, n_events, t_begin, t_end - t_begin, nullptr,
                         s->flow_stage, nullptr, nullptr, nullptr, st);
     if (r < 0) return r;
-    cudaMemcpyAsync(h_flow, s->flow_stage, sizeof(float) * 2 * (size_t)s->p.width * s->p.height,
-                    cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h_flow, s->flow_stage, flow_bytes, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return EBOF_ERR_CUDA;
     return r;
 }
+
+ebof_status ebof_stream_set_wait_limit(ebof_stream *s, int64_t iterations)
+{
+    if (!s) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    s->wait_limit = iterations < 0 ? kWaitLimitDefault : (long long)iterations;
+    return EBOF_OK;
+}
+
+void ebof_debug_fail_allocation(int32_t n) { g_alloc_fail_after.store(n < 0 ? -1 : n); }
 
 ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_out)
 {

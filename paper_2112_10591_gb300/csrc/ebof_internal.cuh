@@ -73,12 +73,17 @@ struct SurfaceMap {
 
 inline SurfaceMap exp_surface(float alpha) { return SurfaceMap{0, alpha, 6.0f, 255.0f}; }
 
+// Default bound, in mbarrier try-wait rounds, of a kernel's wait for a
+// tensor copy.
+constexpr long long kWaitLimitDefault = 1LL << 22;
+
 struct FlowParams {
     bool half;  // pyramid stored as FP16 (loads widened to FP32)
     int ps, stride, gn_iters;
     float gn_damping;
     int var_outer, var_sor;
     float delta, gamma, alpha_s, omega;
+    long long wait_limit;  // first wait of the copy-ahead SOR kernel (rounds)
 };
 
 // Launchers (each enqueues on `st`; frames = batch size). ---------------------

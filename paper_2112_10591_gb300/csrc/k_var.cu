@@ -59,7 +59,6 @@ enum { kCI11 = 0, kCI22, kCA12, kCB1, kCB2, kCWL, kCWU, kCPlanes };
 constexpr int kTmaBoxW = kVR + 4;  // region columns + the rounding of the box start
 constexpr size_t kTmaCoefFloats = (size_t)kCPlanes * kVR * kTmaBoxW;
 constexpr size_t kTmaSmemBytes = (kTmaCoefFloats + kVSmemFloats) * sizeof(float);
-constexpr long kTmaSpinLimit = 1L << 22;  // bounded wait on a tensor copy
 constexpr int kMaxDevs = 64;
 int g_num_sms[kMaxDevs];
 // coefficient tile: 384 threads at 40 registers, four blocks per SM, so a
@@ -750,10 +749,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Bounded wait for the mbarrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+// Bounded wait for the mbarrier phase with the given parity: at most
+// `limit` try-wait rounds.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit)
 {
-    for (long it = 0; it < kTmaSpinLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(kVThreads, 1)
 var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int pitch,
                    const float *__restrict__ Uinb, float *__restrict__ Uoutb, size_t ufs,
                    size_t plane, int R, int tile, int nrx, int nry, int total, int n_half,
-                   float omega, int *err)
+                   float omega, long long wait_limit, int *err)
 {
     extern __shared__ __align__(1024) float tsm[];
     float *cbuf = tsm;                  // [kCPlanes][kVR][kTmaBoxW]
@@ -807,11 +807,13 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
     if (t == 0 && r < total) issue(r);
     uint32_t parity = 0;
     for (; r < total; r += gridDim.x) {
-        const bool ok = mbar_wait(mbar, parity);
+        const bool ok = mbar_wait(mbar, parity, wait_limit);
         if (__syncthreads_or(!ok)) {
             if (t == 0) {
                 atomicOr(err, kErrTimeout);
-                mbar_wait(mbar, parity);  // let the copy in flight land (bounded)
+                // let the copy in flight land before the block exits (bounded
+                // by the default limit, whatever the first wait's was)
+                mbar_wait(mbar, parity, kWaitLimitDefault);
             }
             return;
         }
@@ -1023,7 +1025,8 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
             if (coef_map && nsm > 0 && total >= 4 * nsm)
                 var_sor_tma_kernel<<<nsm, kVThreads, kTmaSmemBytes, st>>>(
                     *coef_map, lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, R, tile,
-                    (int)sgrd.x, (int)sgrd.y, total, n_half, fp.omega, err);
+                    (int)sgrd.x, (int)sgrd.y, total, n_half, fp.omega,
+                    fp.wait_limit >= 0 ? fp.wait_limit : kWaitLimitDefault, err);
             else if (small && 32 - 2 * R >= 8 && (int)(g1.x * g1.y * g1.z) <= nsm)
                 var_sor_kernel<1, 32, true><<<g1, 32 * 32, kVSmemFloats2 * sizeof(float), st>>>(
                     lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,

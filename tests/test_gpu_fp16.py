@@ -11,6 +11,8 @@ from paper_2112_10591_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
+FP16_EPE_TOL = 0.06
+
 torch = pytest.importorskip("torch")
 
 
@@ -62,8 +64,11 @@ def test_fp16_storage_1280x720(eb):
           "(p99 %.4f); FP32 GPU vs oracle %.5f" % (e_gpu.mean(), np.percentile(e_gpu, 99),
                                                   e_orc.mean(), np.percentile(e_orc, 99),
                                                   e32.mean()))
-    assert e_orc.mean() <= 0.15
-    assert e_gpu.mean() <= 0.15
+    # measured 0.049 px mean over 16 frames of this stream (against the
+    # oracle and against the FP32 path); FP16's 11-bit mantissa on the
+    # complement surface adds about as much as the 0.05 px flow gate
+    assert e_orc.mean() <= FP16_EPE_TOL
+    assert e_gpu.mean() <= FP16_EPE_TOL
 
 
 def test_fp16_batched_equals_sequential(eb):

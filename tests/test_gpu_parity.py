@@ -14,6 +14,12 @@ pytestmark = pytest.mark.gpu
 
 SURF_TOL = 1e-5
 EPE_TOL = 0.05
+# p99 of the per-pixel endpoint error on the 1280x720 workload.  DIS is
+# chaotic at a few pixels per frame (a patch whose Gauss-Newton path crosses
+# the reset radius on one side only moves its neighbourhood by up to a
+# pixel), so the tail is wider than the mean; the bar is set from the
+# measured GPU-oracle p99 of these frames with a margin.
+EPE_P99_TOL = 1.0
 
 torch = pytest.importorskip("torch")
 
@@ -216,6 +222,35 @@ def test_pipeline_1280x720_parity(eb):
     e = epe(gs[1]["flow"], U)
     print("1280x720 flow vs oracle: mean EPE %.5f, p99 %.5f" % (e.mean(), np.percentile(e, 99)))
     assert e.mean() <= EPE_TOL
+    assert np.percentile(e, 99) <= EPE_P99_TOL
+    s.close()
+
+
+def test_pipeline_1280x720_graph_path_parity(eb):
+    """The path the benchmark times: one ebof_process_window call per window
+    with the flow as its only output, so every window after the first
+    replays the stream's CUDA graph (one graph per ping-pong slot).  Two flow
+    frames, one from each graph, against the oracle."""
+    s_ = synth.workload_1280x720(n_windows=3)
+    W, H = s_.width, s_.height
+    prm, s = make_stream(eb, W, H)
+    flows = []
+    for k in range(3):
+        x, y, t, _, tb, te = s_.window(k)
+        f = torch.full((2, H, W), float("nan"), dtype=torch.float32, device="cuda:0")
+        st = eb.ebof_process_window(s, dev(x), dev(y), dev(t), None, tb, te, f)
+        assert st == (eb.EBOF_NO_PREVIOUS if k == 0 else eb.EBOF_OK)
+        flows.append(f)
+    eb.check(eb.ebof_stream_sync(s, 1)[0], "sync")
+    Ss = [255.0 * oracle_surface(prm, W, H, *s_.window(k)[:3], *s_.window(k)[4:])["S"]
+          for k in range(3)]
+    for k in (1, 2):
+        U = oracle_flow(prm, Ss[k - 1], Ss[k])
+        e = epe(flows[k].cpu().numpy(), U)
+        print("1280x720 graph path, frame %d: mean EPE %.5f, p99 %.5f"
+              % (k, e.mean(), np.percentile(e, 99)))
+        assert e.mean() <= EPE_TOL
+        assert np.percentile(e, 99) <= EPE_P99_TOL
     s.close()
 
 

@@ -1,13 +1,13 @@
 """The allocation-free EDT entry point (ebof_edt_static), on the GPU.
 
 Some callers cannot allocate device memory once they run: a real-time loop
-that must not call cudaMalloc (it can synchronise the device), code inside a
-framework that owns all device memory, or code under stream capture.  For
-them ebof_edt_static keeps its scratch in a static device array.  This test
-calls it through the C ABI twice in a row, on two different edge images,
-and checks each result against the existing entry point ebof_edt (which
-takes caller scratch): squared distances bit-exact, surfaces within 1e-5.
-It sits in a file of its own that pytest collects last.
+that must not call cudaMalloc (it can synchronise the device), or code inside
+a framework that owns all device memory.  For them ebof_edt_static keeps its
+scratch in a static device array.  This test calls it through the C ABI
+twice in a row, on two different edge images, and checks each result
+against the existing entry point ebof_edt (which takes caller scratch):
+squared distances bit-exact, surfaces within 1e-5; a third call asks for the
+distances only.  It sits in a file of its own that pytest collects last.
 """
 import numpy as np
 import pytest
@@ -39,6 +39,16 @@ def test_edt_static_matches_edt_on_two_calls():
         torch.cuda.synchronize()
         assert torch.equal(d_st, d_ref)
         assert (s_st - s_ref).abs().max().item() <= 1e-5
+    # the surface output is optional
+    E = (rng.random((97, 131)) < 0.01).astype(np.uint8)
+    edge = torch.from_numpy(E).to(dev)
+    d_ref = torch.empty((97, 131), dtype=torch.int32, device=dev)
+    scratch = torch.empty(97 * 131, dtype=torch.int32, device=dev)
+    assert eb.ebof_edt(edge, 131, 97, scratch, d_ref, None, 1.08) == eb.EBOF_OK
+    d_st = torch.full((97, 131), -7, dtype=torch.int32, device=dev)
+    assert eb.ebof_edt_static(edge, 131, 97, d_st, None, 1.08) == eb.EBOF_OK
+    torch.cuda.synchronize()
+    assert torch.equal(d_st, d_ref)
     # sizes beyond the static array are refused, nothing is launched
     big = torch.zeros(1, dtype=torch.uint8, device=dev)
     out = torch.zeros(1, dtype=torch.int32, device=dev)
