@@ -485,9 +485,11 @@ def combine_ranks(ms_local, frames_local, world, dist=None, device=None):
 def run_multistream(args, eb, torch, dev, rank):
     """16 concurrent camera streams in lockstep: 12 at 346x260 and 4 at
     1280x720, lognormal event counts in [5k, 500k] per window, rigid objects
-    with random affine motion, FP16 storage.  One group per resolution (one
-    CUDA-graph replay per group and step, the two groups on two CUDA
-    streams); the patch grid of each resolution is picked by the autotuner."""
+    with random affine motion, FP16 storage.  One group per resolution, both
+    stepped as one CUDA graph per step (ebof_multigroup: each group's step a
+    branch of the graph); for comparison the same groups stepped separately
+    on two CUDA streams.  The patch grid and the variational layouts of each
+    resolution are picked by the autotuner."""
     from paper_2112_10591_gb300 import autotune, synth
     nw = max(3, args.ms_windows)
     specs = [(346, 260, 12, dict(n_objects=4, n_edges=60, radius=(15.0, 60.0),
@@ -518,8 +520,15 @@ def run_multistream(args, eb, torch, dev, rank):
                        "table": table, "cs": torch.cuda.Stream(device=dev),
                        "events": int(sum(int(ev.offsets[-1]) for ev in evs))})
     main = torch.cuda.current_stream(dev)
+    st, mg = eb.ebof_multigroup_create([gr["g"] for gr in groups])
+    eb.check(st, "ebof_multigroup_create")
 
-    def step(k):
+    def step_graph(k):
+        r = eb.ebof_multigroup_process(mg, [[w[0][k] for w in gr["ev"]] for gr in groups])
+        if r < 0:
+            raise eb.EbofError(r, "ebof_multigroup_process")
+
+    def step_streams(k):
         for gr in groups:
             gr["cs"].wait_stream(main)
             with torch.cuda.stream(gr["cs"]):
@@ -529,7 +538,7 @@ def run_multistream(args, eb, torch, dev, rank):
         for gr in groups:
             main.wait_stream(gr["cs"])
 
-    def sweep(times=None):
+    def sweep(step, times=None):
         for gr in groups:
             eb.check(eb.ebof_group_reset(gr["g"]))
         step(0)
@@ -544,14 +553,18 @@ def run_multistream(args, eb, torch, dev, rank):
             else:
                 step(k)
 
-    for _ in range(max(1, min(args.warmup, 2))):
-        sweep()
-    torch.cuda.synchronize(dev)
-    evs = []
-    for _ in range(args.steps):
-        sweep(evs)
-    torch.cuda.synchronize(dev)
-    step_ms = np.asarray([a.elapsed_time(b) for a, b in evs])
+    def timed(step):
+        for _ in range(max(1, min(args.warmup, 2))):
+            sweep(step)
+        torch.cuda.synchronize(dev)
+        evs = []
+        for _ in range(args.steps):
+            sweep(step, evs)
+        torch.cuda.synchronize(dev)
+        return np.asarray([a.elapsed_time(b) for a, b in evs])
+
+    two = timed(step_streams)
+    step_ms = timed(step_graph)
     nstreams = sum(gr["n"] for gr in groups)
     px = sum(gr["n"] * gr["W"] * gr["H"] for gr in groups)
     total_s = step_ms.sum() / 1000.0
@@ -562,13 +575,19 @@ def run_multistream(args, eb, torch, dev, rank):
            "p50_step_ms": float(np.percentile(step_ms, 50)),
            "p99_step_ms": float(np.percentile(step_ms, 99)),
            "steps_timed": int(len(step_ms)),
-           "launch": "one CUDA-graph replay per resolution group and step, groups on two "
-                     "CUDA streams",
-           "autotune": {"%dx%d" % (gr["W"], gr["H"]): {"patch": gr["prm"].patch,
-                                                      "stride": gr["prm"].stride,
-                                                      "levels": gr["prm"].levels,
-                                                      "candidates": gr["table"]}
-                        for gr in groups}}
+           "launch": "one CUDA graph per step (ebof_multigroup): each resolution group's "
+                     "step is one branch of the graph, every stage one launch per "
+                     "resolution, the branches concurrent",
+           "two_streams": {"value": nstreams * len(two) / (two.sum() / 1000.0),
+                           "p99_step_ms": float(np.percentile(two, 99)),
+                           "launch": "one graph replay per group and step, groups on two "
+                                     "CUDA streams"},
+           "autotune": {"%dx%d" % (gr["W"], gr["H"]): {
+               "patch": gr["prm"].patch, "stride": gr["prm"].stride,
+               "levels": gr["prm"].levels,
+               "layouts": {k: getattr(gr["prm"], k) for k in autotune.LAYOUT_CANDIDATES},
+               "table": gr["table"]} for gr in groups}}
+    mg.close()
     for gr in groups:
         gr["g"].close()
     return out

@@ -86,6 +86,19 @@ typedef struct {
     int32_t surface;        /* ebof_surface: Eq. 1, or an ablation surface of §IV-D */
     float d_sat;            /* px: the bound of DS_LB, and the distance whose value
                                maps to intensity 255 for every ablation surface */
+    /* Kernel layouts of the variational refinement: how the work is tiled.
+     * The two SOR settings never change what is computed (every value gives
+     * the same flow bit for bit; the autotuner picks them by time alone).
+     * The two forms of the linear-system kernel evaluate the same expressions
+     * but the compiler fuses their multiply-adds differently, so systems, and
+     * flows, agree to floating-point rounding only. */
+    int32_t coeff_cw_min_width; /* levels at least this wide build their linear systems
+                                   with the column-walk kernel (a warp per 28 columns x 8
+                                   rows), narrower ones with 32x12 tiles; >= 1 (1024) */
+    int32_t sor_tma_min_per_sm; /* SOR grids with at least this many 64x64 regions per
+                                   SM take the persistent copy-ahead kernel; >= 1 (4) */
+    int32_t sor_row_waves;      /* SOR grids that fit this many waves of 64x32 regions
+                                   of one-row strips take that form; 0 = never (1) */
 } ebof_params;
 
 /* Distance surface built from the EDT (§III-C) and handed to the flow block.
@@ -120,7 +133,8 @@ typedef struct ebof_stream ebof_stream;
  * of 12x12 patches from 640 px, stride 4, 12 Gauss-Newton iterations with
  * damping 0.1, 5 x 5
  * variational iterations (delta 5, gamma 10, alpha 20, omega 1.6),
- * max_batch 1, FP32 storage. */
+ * max_batch 1, FP32 storage; layouts: column walk from 1024 px, copy-ahead
+ * SOR from 4 regions per SM, one-row SOR strips for one-wave grids. */
 void ebof_default_params(ebof_params *p, int32_t width, int32_t height);
 
 /* Eq. 2 with eps = 1/255 (Eq. 3): alpha = d_sat / ln(255). */
@@ -313,6 +327,31 @@ const float *ebof_group_flow(const ebof_group *g, int32_t k);
 
 /* As ebof_stream_sync, for the group's streams (out[k] = stream k). */
 ebof_status ebof_group_sync(ebof_group *g, ebof_window_stats *out, int32_t n_out);
+
+/* Groups of different resolutions stepped together as ONE CUDA graph: each
+ * group's step (every stage once for its streams) is one branch of the graph,
+ * the branches forked from and joined into the caller's stream, so the
+ * resolutions run concurrently and a step costs one graph launch.  Each
+ * stage is still one launch per group (per resolution).  The groups stay
+ * owned by the caller and must outlive the multigroup; they must not be
+ * stepped on their own while it is in use.  The first step of a group, and
+ * steps with stage timing on, run eagerly; later steps replay one graph per
+ * pattern of the groups' ping-pong parities, captured on first use.
+ * Results per stream are bit-identical to stepping each group alone. */
+typedef struct ebof_multigroup ebof_multigroup;
+
+/* n_groups (1 .. 64) distinct groups on one device. */
+ebof_status ebof_multigroup_create(ebof_group *const *groups, int32_t n_groups,
+                                   ebof_multigroup **out);
+ebof_status ebof_multigroup_destroy(ebof_multigroup *m);  /* NULL-safe; waits for work */
+
+/* One window per stream of every group: h_descs[i] is a HOST array of
+ * groups[i]'s n_streams descriptors (copied during the call).  Flows stay in
+ * each group's buffer (ebof_group_flow); errors and counts through
+ * ebof_group_sync.  Returns EBOF_NO_PREVIOUS when some group had no previous
+ * window, EBOF_ERR_BUSY if another thread uses one of the groups. */
+ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *const *h_descs,
+                                    void *cuda_stream);
 
 /* ---- serving loop ---------------------------------------------------------
  * A server runs many camera streams on one GPU as their windows arrive.

@@ -47,6 +47,9 @@ class ebof_params(ctypes.Structure):
         ("storage", ctypes.c_int32),
         ("surface", ctypes.c_int32),
         ("d_sat", ctypes.c_float),
+        ("coeff_cw_min_width", ctypes.c_int32),
+        ("sor_tma_min_per_sm", ctypes.c_int32),
+        ("sor_row_waves", ctypes.c_int32),
     ]
 
 
@@ -159,6 +162,9 @@ def _declare(L):
     L.ebof_group_flow.argtypes = [vp, i32]
     L.ebof_group_flow.restype = vp
     L.ebof_group_sync.argtypes = [vp, P(ebof_window_stats), i32]
+    L.ebof_multigroup_create.argtypes = [P(vp), i32, P(vp)]
+    L.ebof_multigroup_destroy.argtypes = [vp]
+    L.ebof_multigroup_process.argtypes = [vp, P(P(ebof_window_desc)), vp]
     L.ebof_stream_set_profiling.argtypes = [vp, i32]
     L.ebof_stream_get_profile.argtypes = [vp, P(ctypes.c_double), P(i64), i32]
     L.ebof_stream_get_profile_level.argtypes = [vp, i32, P(ctypes.c_double), P(i64), i32]
@@ -180,7 +186,8 @@ def _declare(L):
                  "ebof_process_window_list", "ebof_server_create", "ebof_fwl", "ebof_server_destroy",
                  "ebof_server_open_stream", "ebof_server_close_stream", "ebof_server_submit",
                  "ebof_server_poll", "ebof_server_drain", "ebof_server_get_info",
-                 "ebof_stream_set_wait_limit"):
+                 "ebof_stream_set_wait_limit", "ebof_multigroup_create",
+                 "ebof_multigroup_destroy", "ebof_multigroup_process"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -460,6 +467,54 @@ def ebof_group_sync(group: Group, n_out: int = None):
     arr = (ebof_window_stats * max(1, n_out))()
     st = load().ebof_group_sync(group.handle, arr, int(n_out))
     return st, [arr[i] for i in range(n_out)]
+
+
+class MultiGroup:
+    """Owner of an ``ebof_multigroup*`` handle: groups of several resolutions
+    stepped as one CUDA graph.  Keeps its groups referenced."""
+
+    def __init__(self, handle: int, groups):
+        self.handle = handle
+        self.groups = list(groups)
+
+    def close(self):
+        if self.handle:
+            load().ebof_multigroup_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ebof_multigroup_create(groups):
+    """Returns (status, MultiGroup or None)."""
+    arr = (ctypes.c_void_p * len(groups))(*[g.handle for g in groups])
+    h = ctypes.c_void_p()
+    st = load().ebof_multigroup_create(arr, len(groups), ctypes.byref(h))
+    if st < 0:
+        return st, None
+    return st, MultiGroup(h.value, groups)
+
+
+def ebof_multigroup_process(mg: MultiGroup, windows, cuda_stream=None) -> int:
+    """windows[i]: groups[i].n tuples (x, y, t, t_begin, t_end) of CUDA tensors
+    and ints."""
+    if len(windows) != len(mg.groups):
+        raise ValueError("need windows for %d groups, got %d" % (len(mg.groups), len(windows)))
+    arrs = []
+    for g, ws in zip(mg.groups, windows):
+        if len(ws) != g.n:
+            raise ValueError("need %d windows, got %d" % (g.n, len(ws)))
+        a = (ebof_window_desc * g.n)()
+        for k in range(g.n):
+            _window_desc(ws[k], g.device, a[k])
+        arrs.append(a)
+    ptrs = (ctypes.POINTER(ebof_window_desc) * len(arrs))(
+        *[ctypes.cast(a, ctypes.POINTER(ebof_window_desc)) for a in arrs])
+    return load().ebof_multigroup_process(mg.handle, ptrs, _stream_handle(cuda_stream))
 
 
 EBOF_STAGE_COUNT = 12

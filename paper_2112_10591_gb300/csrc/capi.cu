@@ -125,6 +125,16 @@ struct ebof_group {
     CoefMaps cmaps;
 };
 
+struct ebof_multigroup {
+    std::vector<ebof_group *> groups;  // not owned
+    int device = 0;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaEvent_t> fork;  // [0]: fork point, [1 + k]: group k's join
+    // one graph per pattern of the groups' ping-pong parities
+    std::vector<std::pair<unsigned long long, cudaGraphExec_t>> graphs;
+    std::vector<long long> graph_kernels;
+};
+
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -190,6 +200,8 @@ ebof_status check_params(const ebof_params *p)
         return EBOF_ERR_INVALID_ARG;
     if (p->surface < EBOF_SURFACE_EXP || p->surface > EBOF_SURFACE_LOG) return EBOF_ERR_INVALID_ARG;
     if (!(std::isfinite(p->d_sat) && p->d_sat > 0.0f)) return EBOF_ERR_INVALID_ARG;
+    if (p->coeff_cw_min_width < 1 || p->sor_tma_min_per_sm < 1 || p->sor_row_waves < 0)
+        return EBOF_ERR_INVALID_ARG;
     if (p->patch < 4 || p->patch > kMaxPatch) return EBOF_ERR_UNSUPPORTED;
     return EBOF_OK;
 }
@@ -256,6 +268,9 @@ FlowParams flow_params(const ebof_params &p)
     fp.alpha_s = p.var_alpha;
     fp.omega = p.sor_omega;
     fp.wait_limit = kWaitLimitDefault;
+    fp.coeff_cw_min_width = p.coeff_cw_min_width;
+    fp.sor_tma_min_per_sm = p.sor_tma_min_per_sm;
+    fp.sor_row_waves = p.sor_row_waves;
     return fp;
 }
 
@@ -597,6 +612,9 @@ void ebof_default_params(ebof_params *p, int32_t width, int32_t height)
     p->storage = EBOF_STORAGE_FP32;
     p->surface = EBOF_SURFACE_EXP;
     p->d_sat = 6.0f;
+    p->coeff_cw_min_width = 1024;
+    p->sor_tma_min_per_sm = 4;
+    p->sor_row_waves = 1;
 }
 
 float ebof_alpha_from_dsat(float d_sat) { return d_sat / std::log(255.0f); }
@@ -1097,6 +1115,152 @@ ebof_status ebof_group_process(ebof_group *g, const ebof_window_desc *h_desc, fl
     g->have_last = true;
     if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
     return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
+}
+
+ebof_status ebof_multigroup_create(ebof_group *const *groups, int32_t n_groups,
+                                   ebof_multigroup **out)
+{
+    if (!out) return EBOF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!groups || n_groups < 1 || n_groups > 64) return EBOF_ERR_INVALID_ARG;
+    for (int i = 0; i < n_groups; ++i) {
+        if (!groups[i] || groups[i]->device != groups[0]->device) return EBOF_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (groups[j] == groups[i]) return EBOF_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(groups[0]->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    ebof_multigroup *m = new (std::nothrow) ebof_multigroup();
+    if (!m) return EBOF_ERR_OOM;
+    m->groups.assign(groups, groups + n_groups);
+    m->device = groups[0]->device;
+    bool ok = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) == cudaSuccess;
+    m->fork.assign(n_groups + 1, nullptr);
+    for (auto &e : m->fork)
+        ok &= cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        ebof_multigroup_destroy(m);
+        return EBOF_ERR_OOM;
+    }
+    *out = m;
+    return EBOF_OK;
+}
+
+ebof_status ebof_multigroup_destroy(ebof_multigroup *m)
+{
+    if (!m) return EBOF_OK;
+    DeviceGuard dg(m->device);
+    for (ebof_group *g : m->groups)
+        if (g->have_last) cudaEventSynchronize(g->done);
+    for (auto &pg : m->graphs)
+        if (pg.second) cudaGraphExecDestroy(pg.second);
+    for (cudaEvent_t e : m->fork)
+        if (e) cudaEventDestroy(e);
+    if (m->cap) cudaStreamDestroy(m->cap);
+    delete m;
+    return EBOF_OK;
+}
+
+ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *const *h_descs,
+                                    void *cuda_stream)
+{
+    if (!m || !h_descs) return EBOF_ERR_INVALID_ARG;
+    const int ng = (int)m->groups.size();
+    for (int i = 0; i < ng; ++i) {
+        const ebof_group *g = m->groups[i];
+        if (!h_descs[i]) return EBOF_ERR_INVALID_ARG;
+        for (int k = 0; k < g->n; ++k) {
+            const ebof_window_desc &w = h_descs[i][k];
+            if (!events_ok(w.x, w.y, w.t, w.n_events) || w.t_end < w.t_begin)
+                return EBOF_ERR_INVALID_ARG;
+        }
+    }
+    std::vector<BusyGuard *> guards;
+    struct Release {
+        std::vector<BusyGuard *> &v;
+        ~Release()
+        {
+            for (BusyGuard *b : v) delete b;
+        }
+    } release{guards};
+    for (ebof_group *g : m->groups) {
+        guards.push_back(new BusyGuard(g->busy));
+        if (!guards.back()->ok) return EBOF_ERR_BUSY;
+    }
+    DeviceGuard dg(m->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaGetLastError();
+    bool all_prev = true, any_prof = false;
+    unsigned long long key = 0;
+    for (int i = 0; i < ng; ++i) {
+        ebof_group *g = m->groups[i];
+        if (g->have_last && g->last_stream != st) cudaStreamWaitEvent(st, g->done, 0);
+        for (int k = 0; k < g->n; ++k) g->h_events[k] = h_descs[i][k].n_events;
+        cudaMemcpyAsync(g->d_desc, h_descs[i], sizeof(ebof_window_desc) * g->n,
+                        cudaMemcpyHostToDevice, st);
+        all_prev &= g->has_prev;
+        any_prof |= g->prof.on;
+        key |= (unsigned long long)g->parity << i;
+    }
+    if (!all_prev || any_prof) {
+        // first step of some group, or stage timing: each group's step eagerly
+        for (ebof_group *g : m->groups) {
+            ProfScope prof_scope(&g->prof);
+            run_group(g, g->has_prev, st);
+        }
+    } else {
+        size_t slot = m->graphs.size();
+        for (size_t j = 0; j < m->graphs.size(); ++j)
+            if (m->graphs[j].first == key) slot = j;
+        if (slot == m->graphs.size()) {
+            // capture the step once for this parity pattern: every group's
+            // step as one branch of the graph, forked from and joined into
+            // the capture stream, which itself starts after `st`
+            cudaEventRecord(m->fork[0], st);
+            cudaStreamWaitEvent(m->cap, m->fork[0], 0);
+            const unsigned long long before = g_launches.load();
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            if (cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                tl_prof = nullptr;
+                cudaEventRecord(m->fork[0], m->cap);
+                for (int i = 0; i < ng; ++i) {
+                    ebof_group *g = m->groups[i];
+                    cudaStreamWaitEvent(g->cap, m->fork[0], 0);
+                    run_group(g, true, g->cap);
+                    cudaEventRecord(m->fork[1 + i], g->cap);
+                    cudaStreamWaitEvent(m->cap, m->fork[1 + i], 0);
+                }
+                cudaStreamEndCapture(m->cap, &graph);
+            }
+            if (graph && cudaGraphInstantiate(&ge, graph, 0) != cudaSuccess) ge = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+            const long long kernels = (long long)(g_launches.load() - before);
+            g_launches.fetch_sub((unsigned long long)kernels);
+            if (!ge) {
+                cudaGetLastError();
+                return EBOF_ERR_CUDA;
+            }
+            m->graphs.emplace_back(key, ge);
+            m->graph_kernels.push_back(kernels);
+        }
+        if (cudaGraphLaunch(m->graphs[slot].second, st) != cudaSuccess) return EBOF_ERR_CUDA;
+        g_launches.fetch_add((unsigned long long)m->graph_kernels[slot]);
+    }
+    ebof_status ret = EBOF_OK;
+    for (ebof_group *g : m->groups) {
+        if (!g->has_prev) ret = EBOF_NO_PREVIOUS;
+        g->last_had_prev = g->has_prev;
+        g->parity ^= 1;
+        g->has_prev = true;
+        cudaEventRecord(g->done, st);
+        g->last_stream = st;
+        g->have_last = true;
+    }
+    if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
+    return ret;
 }
 
 const float *ebof_group_flow(const ebof_group *g, int32_t k)

@@ -84,6 +84,8 @@ struct FlowParams {
     int var_outer, var_sor;
     float delta, gamma, alpha_s, omega;
     long long wait_limit;  // first wait of the copy-ahead SOR kernel (rounds)
+    // variational layouts (ebof_params): none changes a result
+    int coeff_cw_min_width, sor_tma_min_per_sm, sor_row_waves;
 };
 
 // Launchers (each enqueues on `st`; frames = batch size). ---------------------

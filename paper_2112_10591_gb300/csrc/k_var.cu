@@ -388,7 +388,9 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
 // Each row's U, V loads are issued two iterations and its bilinear taps one
 // iteration before their use.  Values of positions outside the level are 0,
 // as in the staging windows of coeff_tile, and every clamp and border test
-// is the tile form's, so both forms write the same coefficients.
+// is the tile form's, so both forms evaluate the same expressions; the
+// compiler fuses their multiply-adds differently in the two kernels, so the
+// coefficients agree to rounding, not bit for bit.
 constexpr int kCWOut = 28;   // output columns per warp
 constexpr int kCWWarps = 4;  // warps per block, row strips stacked
 constexpr int kCWRows = 8;   // output rows per warp
@@ -960,12 +962,12 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
     const int tile = kVR - 2 * R;                    // interior rows of a 64-row region
     const int tile_x = kVR - 2 * sor_halo_x(R);      // interior columns
     const dim3 cgrd((lv.w + kAX - 1) / kAX, (lv.h + kAY - 1) / kAY, frames);
-    // the coefficient kernel's form depends on the level's geometry and the
-    // storage type only, so single, batched and grouped windows of a level
-    // always run the same one (and give the same coefficients): the column
-    // walk from 1024 px wide (the finest level of 1280 x 720 frames), where
-    // it is the faster; smaller levels keep the tile form
-    const bool column_walk = lv.w >= 1024;
+    // the coefficient kernel's form depends on the level's width and the
+    // stream's parameters only, so single, batched and grouped windows of a
+    // level always run the same one (and give the same coefficients): by
+    // default the column walk from 1024 px wide (the finest level of 1280 x
+    // 720 frames), where it is the faster; smaller levels keep the tile form
+    const bool column_walk = lv.w >= fp.coeff_cw_min_width;
     const dim3 wgrd((lv.w + kCWOut - 1) / kCWOut,
                     ((lv.h + kCWRows - 1) / kCWRows + kCWWarps - 1) / kCWWarps, frames);
     const dim3 sgrd((lv.w + tile_x - 1) / tile_x, (lv.h + tile - 1) / tile, frames);
@@ -1014,7 +1016,8 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
             // iteration, so the choice never changes the result.
             const dim3 g1((lv.w + tile_x - 1) / tile_x,
                           (lv.h + (32 - 2 * R) - 1) / (32 - 2 * R), frames);
-            const bool small = nsm > 0 && total < nsm;
+            const int row_waves = fp.sor_row_waves;
+            const bool small = nsm > 0 && row_waves > 0 && total < row_waves * nsm;
             // even-halo regions (8-byte pairs) unless they take more waves
             // than regions with an R-column halo
             const int todd = kVR - 2 * R;
@@ -1022,12 +1025,12 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
             const int wave = nsm > 0 ? nsm : 1;
             const bool even = (total + wave - 1) / wave <=
                               ((int)(godd.x * godd.y * godd.z) + wave - 1) / wave;
-            if (coef_map && nsm > 0 && total >= 4 * nsm)
+            if (coef_map && nsm > 0 && (long long)total >= (long long)fp.sor_tma_min_per_sm * nsm)
                 var_sor_tma_kernel<<<nsm, kVThreads, kTmaSmemBytes, st>>>(
                     *coef_map, lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, R, tile,
                     (int)sgrd.x, (int)sgrd.y, total, n_half, fp.omega,
                     fp.wait_limit >= 0 ? fp.wait_limit : kWaitLimitDefault, err);
-            else if (small && 32 - 2 * R >= 8 && (int)(g1.x * g1.y * g1.z) <= nsm)
+            else if (small && 32 - 2 * R >= 8 && (int)(g1.x * g1.y * g1.z) <= row_waves * nsm)
                 var_sor_kernel<1, 32, true><<<g1, 32 * 32, kVSmemFloats2 * sizeof(float), st>>>(
                     lv.w, lv.h, lv.pitch, a, b, u_frame_stride, lv.plane, coef,
                     coef_frame_stride, R, n_half, fp.omega);
