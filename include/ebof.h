@@ -96,7 +96,8 @@ typedef struct {
                                    with the column-walk kernel (a warp per 28 columns x 8
                                    rows), narrower ones with 32x12 tiles; >= 1 (1024) */
     int32_t sor_tma_min_per_sm; /* SOR grids with at least this many 64x64 regions per
-                                   SM take the persistent copy-ahead kernel; >= 1 (4) */
+                                   SM take the persistent copy-ahead kernel; >= 1 (4
+                                   below 1024 px wide, 2^20, i.e. never, from 1024 px) */
     int32_t sor_row_waves;      /* SOR grids that fit this many waves of 64x32 regions
                                    of one-row strips take that form; 0 = never (1) */
 } ebof_params;
@@ -134,7 +135,8 @@ typedef struct ebof_stream ebof_stream;
  * damping 0.1, 5 x 5
  * variational iterations (delta 5, gamma 10, alpha 20, omega 1.6),
  * max_batch 1, FP32 storage; layouts: column walk from 1024 px, copy-ahead
- * SOR from 4 regions per SM, one-row SOR strips for one-wave grids. */
+ * SOR from 4 regions per SM below 1024 px wide (never from 1024 px), one-row
+ * SOR strips for one-wave grids. */
 void ebof_default_params(ebof_params *p, int32_t width, int32_t height);
 
 /* Eq. 2 with eps = 1/255 (Eq. 3): alpha = d_sat / ln(255). */

@@ -613,7 +613,9 @@ void ebof_default_params(ebof_params *p, int32_t width, int32_t height)
     p->surface = EBOF_SURFACE_EXP;
     p->d_sat = 6.0f;
     p->coeff_cw_min_width = 1024;
-    p->sor_tma_min_per_sm = 4;
+    // the copy-ahead SOR kernel: 1280 x 720 batches of 40 windows ran 3 %
+    // faster without it (same flow); 346 x 260 groups slightly faster with it
+    p->sor_tma_min_per_sm = width >= 1024 ? (1 << 20) : 4;
     p->sor_row_waves = 1;
 }
 
