@@ -16,8 +16,12 @@ events in pinned host memory and every window's flow written back into a
 pinned host buffer (page-locked buffers are addressed by the kernels over the
 host link, so the events cross it inside the scatter and the flow inside the
 last kernel; the call returns after synchronising);
-`roofline` covers the dominant stage; `cpu_baseline` is the FP64 oracle on
-a bounded sample of the same stream, on this host's cores.
+`roofline` covers the dominant step, the variational refinement at level 0,
+by its algorithmic bytes (24 B per pixel per outer iteration: I0, I1, U in,
+U out) over its kernels' time, with every stage's fraction and the patch
+search against the FP32 ALU beside it; `config0_346x260` is the 346x260
+single-window workload; `cpu_baseline` is the FP64 oracle on a bounded sample
+of the same stream, on this host's cores, and alone on one core.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
