@@ -86,12 +86,10 @@ typedef struct {
     int32_t surface;        /* ebof_surface: Eq. 1, or an ablation surface of §IV-D */
     float d_sat;            /* px: the bound of DS_LB, and the distance whose value
                                maps to intensity 255 for every ablation surface */
-    /* Kernel layouts of the variational refinement: how the work is tiled.
-     * The two SOR settings never change what is computed (every value gives
-     * the same flow bit for bit; the autotuner picks them by time alone).
-     * The two forms of the linear-system kernel evaluate the same expressions
-     * but the compiler fuses their multiply-adds differently, so systems, and
-     * flows, agree to floating-point rounding only. */
+    /* Kernel layouts of the variational refinement: how the work is tiled,
+     * never what is computed.  Every setting gives the same flow bit for bit
+     * (the per-pixel arithmetic has a fixed rounding sequence in every kernel
+     * form), so the autotuner picks them by time alone. */
     int32_t coeff_cw_min_width; /* levels at least this wide build their linear systems
                                    with the column-walk kernel (a warp per 28 columns x 8
                                    rows), narrower ones with 32x12 tiles; >= 1 (1024) */

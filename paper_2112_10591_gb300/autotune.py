@@ -15,8 +15,9 @@ tuner itself only orchestrates and compares.
    path of a candidate configuration matches the FP64 oracle is a property
    of the library, covered by its tests; the tuner runs in the product path,
    which never touches the oracle.
-2. Layout candidates (the SOR kernels' forms: the persistent copy-ahead
-   kernel, regions of one-row strips) never change the flow.  The tuner checks that each one gives the flow of
+2. Layout candidates (the coefficient kernel's form, the SOR kernels' forms:
+   the persistent copy-ahead kernel, regions of one-row strips) never change
+   the flow.  The tuner checks that each one gives the flow of
    the default layout bit for bit and keeps the fastest, one knob at a time
    from the default, then the combination of the winners.
 """
@@ -28,13 +29,12 @@ import numpy as np
 
 from . import binding as eb
 
-# Layout knobs of ebof_params whose every value gives the same flow bit for
-# bit (the SOR forms), and the values tried besides the default.  The
-# coefficient kernel's form (coeff_cw_min_width) agrees to rounding only and
-# is not tuned here.
+# Layout knobs of ebof_params (every value gives the same flow bit for bit)
+# and the values tried besides the default.
 NEVER = 1 << 20
 LAYOUT_CANDIDATES = {
-    "sor_tma_min_per_sm": (2, NEVER),
+    "coeff_cw_min_width": (640, NEVER),
+    "sor_tma_min_per_sm": (2, 4, NEVER),
     "sor_row_waves": (0, 2),
 }
 
@@ -156,6 +156,8 @@ def tune(width, height, calib, storage=eb.EBOF_STORAGE_FP32, candidates=None, ke
     for knob, values in LAYOUT_CANDIDATES.items():
         best_v, best_ms = getattr(out, knob), ref_ms
         for v in values:
+            if v == getattr(out, knob):
+                continue  # the default, timed above
             prm = _copy_params(out)
             setattr(prm, knob, v)
             res, err = _run(prm, calib, width, height, device, repeats, False)

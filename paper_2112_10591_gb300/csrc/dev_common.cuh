@@ -8,6 +8,27 @@ namespace ebof {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+// Arithmetic with a fixed rounding sequence.  The compiler fuses a product
+// and a sum into one multiply-add wherever it sees fit, differently in
+// different kernels; these intrinsics are never fused or split, so an
+// expression written with them rounds the same way in every kernel that
+// evaluates it.  The variational refinement's per-pixel arithmetic and the
+// bilinear sample are written with them, so that every kernel form (tile,
+// column walk, SOR region layouts) gives the same values bit for bit.
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// (1 - fy) ((1 - fx) a + fx b) + fy ((1 - fx) c + fx d), rounded in a fixed order.
+__device__ __forceinline__ float lerp2(float a, float b, float c, float d, float fx, float fy)
+{
+    const float gx = fsub(1.0f, fx);
+    const float top = ffma(fx, b, fmul(gx, a));
+    const float bot = ffma(fx, d, fmul(gx, c));
+    return ffma(fy, bot, fmul(fsub(1.0f, fy), top));
+}
+
 // Pyramid storage: FP32, or FP16 with every load widened to FP32 and every
 // store rounded to nearest.
 __device__ __forceinline__ float ldp(const float *p) { return *p; }
@@ -28,7 +49,7 @@ __device__ __forceinline__ float bilinear(const T *__restrict__ I, int w, int h,
     const float fx = x - xf, fy = y - yf;
     const float a = ldp(&I[(size_t)y0 * pitch + x0]), b = ldp(&I[(size_t)y0 * pitch + x1]);
     const float c = ldp(&I[(size_t)y1 * pitch + x0]), d = ldp(&I[(size_t)y1 * pitch + x1]);
-    return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
+    return lerp2(a, b, c, d, fx, fy);
 }
 
 // The four samples around a clamped position and its fractional offsets.
@@ -61,8 +82,7 @@ __device__ __forceinline__ BilTaps bil_taps_i(const T *__restrict__ I, int w, in
 
 __device__ __forceinline__ float bil_lerp(const BilTaps &t)
 {
-    return (1.0f - t.fy) * ((1.0f - t.fx) * t.a + t.fx * t.b) +
-           t.fy * ((1.0f - t.fx) * t.c + t.fx * t.d);
+    return lerp2(t.a, t.b, t.c, t.d, t.fx, t.fy);
 }
 
 // The bilinear sample with 32-bit offsets (the same arithmetic as
@@ -81,11 +101,14 @@ __device__ __forceinline__ float bilinear_i(const T *__restrict__ I, int w, int 
     const T *r0 = I + y0 * pitch, *r1 = I + y1 * pitch;
     const float a = ldp(&r0[x0]), b = ldp(&r0[x1]);
     const float c = ldp(&r1[x0]), d = ldp(&r1[x1]);
-    return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * c + fx * d);
+    return lerp2(a, b, c, d, fx, fy);
 }
 
 // Robust penaliser derivative Psi'(s^2) = 1 / (2 sqrt(s^2 + eps^2)), eps = 1e-3.
-__device__ __forceinline__ float psi_prime(float s2) { return 0.5f * rsqrtf(s2 + 1e-6f); }
+__device__ __forceinline__ float psi_prime(float s2)
+{
+    return fmul(0.5f, rsqrtf(fadd(s2, 1e-6f)));
+}
 
 constexpr float kZeta2 = 0.01f;  // zeta^2 of the constraint normalisation
 

@@ -118,13 +118,20 @@ __device__ __forceinline__ void sor_half(float (&du)[VS][2], float (&dv)[VS][2],
             dnu = wp < WARPS - 1 ? xtop[((wp + 1) * 2 + 0) * 64 + col] : 0.0f;
             dnv = wp < WARPS - 1 ? xtop[((wp + 1) * 2 + 1) * 64 + col] : 0.0f;
         }
-        // i11 = omega / a11, i22 = omega / a22
-        const float nu = om1 * du[r][q] + (b1[r][q] + wl[r][q] * lu + wr[r][q] * ru +
-                                           wu[r][q] * uu + wd[r][q] * dnu - a12[r][q] * dv[r][q]) *
-                                              i11[r][q];
-        const float nv = om1 * dv[r][q] + (b2[r][q] + wl[r][q] * lv + wr[r][q] * rv +
-                                           wu[r][q] * uv + wd[r][q] * dnv - a12[r][q] * nu) *
-                                              i22[r][q];
+        // i11 = omega / a11, i22 = omega / a22; fixed rounding order (every
+        // SOR layout gives the same values)
+        float tu = ffma(wl[r][q], lu, b1[r][q]);
+        tu = ffma(wr[r][q], ru, tu);
+        tu = ffma(wu[r][q], uu, tu);
+        tu = ffma(wd[r][q], dnu, tu);
+        tu = ffma(-a12[r][q], dv[r][q], tu);
+        const float nu = ffma(tu, i11[r][q], fmul(om1, du[r][q]));
+        float tv = ffma(wl[r][q], lv, b2[r][q]);
+        tv = ffma(wr[r][q], rv, tv);
+        tv = ffma(wu[r][q], uv, tv);
+        tv = ffma(wd[r][q], dnv, tv);
+        tv = ffma(-a12[r][q], nu, tv);
+        const float nv = ffma(tv, i22[r][q], fmul(om1, dv[r][q]));
         du[r][q] = nu;
         dv[r][q] = nv;
     }
@@ -180,14 +187,14 @@ __device__ __forceinline__ void sor_sweeps(float (&du)[VS][2], float (&dv)[VS][2
 __device__ __forceinline__ float smooth_weight(float u, float ur, float ud, float v, float vr,
                                                float vd, bool hx, bool hy, float alpha_s)
 {
-    const float ux = hx ? ur - u : 0.0f;
-    const float uy = hy ? ud - u : 0.0f;
-    const float vx = hx ? vr - v : 0.0f;
-    const float vy = hy ? vd - v : 0.0f;
-    return alpha_s * psi_prime(ux * ux + uy * uy + vx * vx + vy * vy);
+    const float ux = hx ? fsub(ur, u) : 0.0f;
+    const float uy = hy ? fsub(ud, u) : 0.0f;
+    const float vx = hx ? fsub(vr, v) : 0.0f;
+    const float vy = hy ? fsub(vd, v) : 0.0f;
+    return fmul(alpha_s, psi_prime(ffma(vy, vy, ffma(vx, vx, ffma(uy, uy, fmul(ux, ux))))));
 }
 
-__device__ __forceinline__ float cdiff(float hi, float lo) { return 0.5f * (hi - lo); }
+__device__ __forceinline__ float cdiff(float hi, float lo) { return fmul(0.5f, fsub(hi, lo)); }
 
 // Derivatives of the warped image and the smoothness weight at a pixel of a
 // staging window (row stride ES; (e) the pixel, at image position gx, gy).
@@ -230,34 +237,42 @@ __device__ __forceinline__ PixelSystem pixel_system_vals(
     bool bu, bool bd, int gx, int gy, int w, int h, float i0, float i0x, float i0y, float delta,
     float gamma, float omega)
 {
+    // every operation with a fixed rounding (fmul, fadd, fsub, ffma), so that
+    // the two kernel forms that call this function give the same systems
     const float Ix = ix, Iy = iy;
     const float Ixx = cdiff(ixr, ixl);
     const float Ixy = cdiff(ixd, ixu);
     const float Iyy = cdiff(iyd, iyu);
-    const float Iz = iw - i0;
-    const float Ixz = Ix - i0x, Iyz = Iy - i0y;
-    const float nd = __fdividef(1.0f, Ix * Ix + Iy * Iy + kZeta2);
-    const float ng = __fdividef(1.0f, Ixx * Ixx + 2.0f * Ixy * Ixy + Iyy * Iyy + kZeta2);
-    float ad = delta * nd * psi_prime(nd * Iz * Iz);
-    float ag = gamma * ng * psi_prime(ng * (Ixz * Ixz + Iyz * Iyz));
-    const float wx = (float)gx + u, wy = (float)gy + v;
+    const float Iz = fsub(iw, i0);
+    const float Ixz = fsub(Ix, i0x), Iyz = fsub(Iy, i0y);
+    const float nd = __fdividef(1.0f, fadd(ffma(Iy, Iy, fmul(Ix, Ix)), kZeta2));
+    const float ng = __fdividef(
+        1.0f, fadd(ffma(Iyy, Iyy, ffma(fmul(2.0f, Ixy), Ixy, fmul(Ixx, Ixx))), kZeta2));
+    float ad = fmul(fmul(delta, nd), psi_prime(fmul(fmul(nd, Iz), Iz)));
+    float ag = fmul(fmul(gamma, ng), psi_prime(fmul(ng, ffma(Iyz, Iyz, fmul(Ixz, Ixz)))));
+    const float wx = fadd((float)gx, u), wy = fadd((float)gy, v);
     if (wx < 0.0f || wx > (float)(w - 1) || wy < 0.0f || wy > (float)(h - 1)) {
         ad = 0.0f;
         ag = 0.0f;
     }
     PixelSystem ps;
-    ps.cl = bl ? 0.5f * (asp + asl) : 0.0f;
-    ps.cr = br ? 0.5f * (asp + asr) : 0.0f;
-    ps.cu = bu ? 0.5f * (asp + asu) : 0.0f;
-    ps.cd = bd ? 0.5f * (asp + asd) : 0.0f;
-    const float sw = ps.cl + ps.cr + ps.cu + ps.cd;
-    const float su0 = ps.cl * (ul - u) + ps.cr * (ur - u) + ps.cu * (uu - u) + ps.cd * (ud - u);
-    const float sv0 = ps.cl * (vl - v) + ps.cr * (vr - v) + ps.cu * (vu - v) + ps.cd * (vd - v);
-    ps.i11 = __fdividef(omega, ad * Ix * Ix + ag * (Ixx * Ixx + Ixy * Ixy) + sw);
-    ps.i22 = __fdividef(omega, ad * Iy * Iy + ag * (Ixy * Ixy + Iyy * Iyy) + sw);
-    ps.a12 = ad * Ix * Iy + ag * (Ixx * Ixy + Ixy * Iyy);
-    ps.b1 = su0 - ad * Ix * Iz - ag * (Ixx * Ixz + Ixy * Iyz);
-    ps.b2 = sv0 - ad * Iy * Iz - ag * (Ixy * Ixz + Iyy * Iyz);
+    ps.cl = bl ? fmul(0.5f, fadd(asp, asl)) : 0.0f;
+    ps.cr = br ? fmul(0.5f, fadd(asp, asr)) : 0.0f;
+    ps.cu = bu ? fmul(0.5f, fadd(asp, asu)) : 0.0f;
+    ps.cd = bd ? fmul(0.5f, fadd(asp, asd)) : 0.0f;
+    const float sw = fadd(fadd(fadd(ps.cl, ps.cr), ps.cu), ps.cd);
+    const float su0 = ffma(ps.cd, fsub(ud, u),
+                           ffma(ps.cu, fsub(uu, u), ffma(ps.cr, fsub(ur, u),
+                                                         fmul(ps.cl, fsub(ul, u)))));
+    const float sv0 = ffma(ps.cd, fsub(vd, v),
+                           ffma(ps.cu, fsub(vu, v), ffma(ps.cr, fsub(vr, v),
+                                                         fmul(ps.cl, fsub(vl, v)))));
+    const float adx = fmul(ad, Ix), ady = fmul(ad, Iy);
+    ps.i11 = __fdividef(omega, fadd(ffma(ag, ffma(Ixy, Ixy, fmul(Ixx, Ixx)), fmul(adx, Ix)), sw));
+    ps.i22 = __fdividef(omega, fadd(ffma(ag, ffma(Iyy, Iyy, fmul(Ixy, Ixy)), fmul(ady, Iy)), sw));
+    ps.a12 = ffma(ag, ffma(Ixy, Iyy, fmul(Ixx, Ixy)), fmul(adx, Iy));
+    ps.b1 = ffma(-ag, ffma(Ixy, Iyz, fmul(Ixx, Ixz)), ffma(-adx, Iz, su0));
+    ps.b2 = ffma(-ag, ffma(Iyy, Iyz, fmul(Ixy, Ixz)), ffma(-ady, Iz, sv0));
     return ps;
 }
 
@@ -388,9 +403,10 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
 // Each row's U, V loads are issued two iterations and its bilinear taps one
 // iteration before their use.  Values of positions outside the level are 0,
 // as in the staging windows of coeff_tile, and every clamp and border test
-// is the tile form's, so both forms evaluate the same expressions; the
-// compiler fuses their multiply-adds differently in the two kernels, so the
-// coefficients agree to rounding, not bit for bit.
+// is the tile form's; the arithmetic has a fixed rounding sequence (fmul,
+// fadd, ffma), so both forms write the same coefficients bit for bit.  Seven
+// blocks of 72 registers per SM: a 1280 x 720 level's 1058 blocks take one
+// wave (at eight blocks, 64 registers, the kernel spilled).
 constexpr int kCWOut = 28;   // output columns per warp
 constexpr int kCWWarps = 4;  // warps per block, row strips stacked
 constexpr int kCWRows = 8;   // output rows per warp
@@ -511,7 +527,7 @@ __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *_
 }
 
 template <int R, typename T>
-__global__ void __launch_bounds__(32 * kCWWarps, 8)
+__global__ void __launch_bounds__(32 * kCWWarps, 7)
 var_coeff_cw_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                     const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
                     int pitch, size_t pfs, const float *__restrict__ Ub, size_t ufs,

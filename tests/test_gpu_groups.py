@@ -168,12 +168,9 @@ def test_multigroup_one_graph_matches_single_streams(eb):
                                          ("sor_row_waves", (0, 2, 4)),
                                          ("coeff_cw_min_width", (160, 640, 1 << 20))])
 def test_layout_knobs_never_change_the_flow(eb, knob, values):
-    """The variational layouts tile the same computation differently.  The SOR
-    forms give the same flow bit for bit under every setting.  The two forms
-    of the coefficient kernel (32x12 tiles, column walk) evaluate the same
-    expressions, but the compiler contracts their products into fused
-    multiply-adds differently, so their systems agree to rounding only; the
-    flows then stay well within the oracle bar of each other."""
+    """The variational layouts (the coefficient kernel's form, the SOR forms)
+    tile the same computation differently: single and batched calls give
+    the same flow bit for bit under every setting."""
     ev = synth.rigid_objects(n_windows=6, seed=80, events=(60000, 90000), width=1280,
                              height=720)
     W, H, n = 1280, 720, 5
@@ -197,10 +194,4 @@ def test_layout_knobs_never_change_the_flow(eb, knob, values):
         outs.append(flow.cpu().numpy())
         s.close()
     for v, o in zip(values, outs[1:]):
-        if knob == "coeff_cw_min_width":
-            e = np.hypot(o[:, 0] - outs[0][:, 0], o[:, 1] - outs[0][:, 1])
-            print("coefficient form from %d px: mean EPE vs default %.5f, p99 %.4f"
-                  % (v, e.mean(), np.percentile(e, 99)))
-            assert e.mean() <= 0.02
-        else:
-            assert np.array_equal(o, outs[0]), (knob, v)
+        assert np.array_equal(o, outs[0]), (knob, v)
