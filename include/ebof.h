@@ -98,6 +98,11 @@ typedef struct {
                                    below 1024 px wide, 2^20, i.e. never, from 1024 px) */
     int32_t sor_row_waves;      /* SOR grids that fit this many waves of 64x32 regions
                                    of one-row strips take that form; 0 = never (1) */
+    int32_t var_cluster_max;    /* small levels: the whole refinement of a frame in one
+                                   thread-block cluster launch (every outer iteration,
+                                   cluster barriers between the phases) when the level's
+                                   work fits a cluster of at most this many blocks and
+                                   the call's clusters fit one wave; 0 = never (0) */
 } ebof_params;
 
 /* Distance surface built from the EDT (§III-C) and handed to the flow block.
@@ -134,7 +139,7 @@ typedef struct ebof_stream ebof_stream;
  * variational iterations (delta 5, gamma 10, alpha 20, omega 1.6),
  * max_batch 1, FP32 storage; layouts: column walk from 1024 px, copy-ahead
  * SOR from 4 regions per SM below 1024 px wide (never from 1024 px), one-row
- * SOR strips for one-wave grids. */
+ * SOR strips for one-wave grids, no cluster-resident refinement. */
 void ebof_default_params(ebof_params *p, int32_t width, int32_t height);
 
 /* Eq. 2 with eps = 1/255 (Eq. 3): alpha = d_sat / ln(255). */

@@ -16,8 +16,8 @@ tuner itself only orchestrates and compares.
    of the library, covered by its tests; the tuner runs in the product path,
    which never touches the oracle.
 2. Layout candidates (the coefficient kernel's form, the SOR kernels' forms:
-   the persistent copy-ahead kernel, regions of one-row strips) never change
-   the flow.  The tuner checks that each one gives the flow of
+   the persistent copy-ahead kernel, regions of one-row strips; the
+   cluster-resident refinement of small levels) never change the flow.  The tuner checks that each one gives the flow of
    the default layout bit for bit and keeps the fastest, one knob at a time
    from the default, then the combination of the winners.
 """
@@ -36,6 +36,7 @@ LAYOUT_CANDIDATES = {
     "coeff_cw_min_width": (640, NEVER),
     "sor_tma_min_per_sm": (2, 4, NEVER),
     "sor_row_waves": (0, 2),
+    "var_cluster_max": (8, 16),
 }
 
 

@@ -50,6 +50,7 @@ class ebof_params(ctypes.Structure):
         ("coeff_cw_min_width", ctypes.c_int32),
         ("sor_tma_min_per_sm", ctypes.c_int32),
         ("sor_row_waves", ctypes.c_int32),
+        ("var_cluster_max", ctypes.c_int32),
     ]
 
 

@@ -38,6 +38,7 @@
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
 
+#include <cooperative_groups.h>
 #include <mutex>
 
 namespace ebof {
@@ -67,6 +68,27 @@ constexpr int kAX = 32, kAY = 12;
 constexpr int kAEX = kAX + 4, kAEY = kAY + 4;  // staging window: tile + 2 px
 constexpr int kADX = kAX + 2, kADY = kAY + 2;  // derivative window: tile + 1 px
 constexpr unsigned kFull = 0xffffffffu;
+
+// Loads of data that the same launch may have written on another SM earlier
+// (COH: through L2 with ld.global.cg, never from a possibly stale L1 or the
+// read-only path); plain loads otherwise.  The values are the same.
+template <bool COH>
+__device__ __forceinline__ float ldf(const float *p)
+{
+    if constexpr (COH)
+        return __ldcg(p);
+    else
+        return *p;
+}
+template <bool COH>
+__device__ __forceinline__ float2 ldf2(const float *p)
+{
+    if constexpr (COH)
+        return __ldcg(reinterpret_cast<const float2 *>(p));
+    else
+        return *reinterpret_cast<const float2 *>(p);
+}
+
 
 // One red-black half sweep of colour C on a thread's 2-column x VS-row
 // strip; P is the parity of (x + y) at the strip's first pixel.  Pixel
@@ -411,7 +433,7 @@ constexpr int kCWOut = 28;   // output columns per warp
 constexpr int kCWWarps = 4;  // warps per block, row strips stacked
 constexpr int kCWRows = 8;   // output rows per warp
 
-template <int R, bool IN, typename T>
+template <int R, bool IN, typename T, bool COH = false>
 __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *__restrict__ I0x,
                                             const T *__restrict__ I0y, const T *__restrict__ I1,
                                             int w, int h, int pitch, const float *__restrict__ U,
@@ -429,8 +451,8 @@ __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *_
         v = 0.0f;
         if (row_in(r) && xin) {
             const int p = r * pitch + x;
-            u = U[p];
-            v = V[p];
+            u = ldf<COH>(U + p);
+            v = ldf<COH>(V + p);
         }
     };
     auto taps = [&](int r, float u, float v) {
@@ -560,18 +582,19 @@ __host__ __device__ __forceinline__ int sor_halo_x(int R) { return R + (R & 1); 
 // Interior output of a lane's pair (columns gx0, gx0 + 1 of row gy; the
 // pair is interior or not as a whole): U + dU, as pairs where both columns
 // are in the level.
+template <bool COH = false>
 __device__ __forceinline__ void store_pair(const float *Uin, float *Uout, size_t plane, int p,
                                            int gx0, int w, float du0, float du1, float dv0,
                                            float dv1)
 {
     if (gx0 + 1 < w) {
-        const float2 u = *reinterpret_cast<const float2 *>(Uin + p);
-        const float2 v = *reinterpret_cast<const float2 *>(Uin + plane + p);
+        const float2 u = ldf2<COH>(Uin + p);
+        const float2 v = ldf2<COH>(Uin + plane + p);
         *reinterpret_cast<float2 *>(Uout + p) = make_float2(u.x + du0, u.y + du1);
         *reinterpret_cast<float2 *>(Uout + plane + p) = make_float2(v.x + dv0, v.y + dv1);
     } else if (gx0 < w) {
-        Uout[p] = Uin[p] + du0;
-        (Uout + plane)[p] = (Uin + plane)[p] + dv0;
+        Uout[p] = ldf<COH>(Uin + p) + du0;
+        (Uout + plane)[p] = ldf<COH>(Uin + plane + p) + dv0;
     }
 }
 
@@ -612,34 +635,33 @@ __device__ __forceinline__ void zero_region_left_weights(float (&wl)[VS][2], int
 
 // A lane's two adjacent values of one plane (c: the first); EVEN: one
 // aligned 8-byte load.
-template <bool EVEN>
+template <bool EVEN, bool COH = false>
 __device__ __forceinline__ void set_pair(float (&a)[2], const float *c)
 {
     if (EVEN) {
-        const float2 v = *reinterpret_cast<const float2 *>(c);
+        const float2 v = ldf2<COH>(c);
         a[0] = v.x;
         a[1] = v.y;
     } else {
-        a[0] = c[0];
-        a[1] = c[1];
+        a[0] = ldf<COH>(c);
+        a[1] = ldf<COH>(c + 1);
     }
 }
 
 // Region of 64 columns x RH rows, strips of VS rows: RH / VS warps.  EVEN:
 // column halo rounded up to even (pairs loaded and stored as 8 bytes); else
 // a halo of R columns (narrower halo, scalar accesses).
-template <int VS, int RH, bool EVEN>
-__global__ void __launch_bounds__(32 * (RH / VS), 1)
-var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
-               float *__restrict__ Uoutb, size_t ufs, size_t plane,
-               const float *__restrict__ coefb, size_t cfs, int R, int n_half, float omega)
+template <int VS, int RH, bool EVEN, bool COH>
+__device__ __forceinline__ void sor_region(int bx, int by, int f, int w, int h, int pitch,
+                                           const float *__restrict__ Uinb,
+                                           float *__restrict__ Uoutb, size_t ufs, size_t plane,
+                                           const float *__restrict__ coefb, size_t cfs, int R,
+                                           int n_half, float omega, float *xch)
 {
     constexpr int WARPS = RH / VS;
-    extern __shared__ float xch[];  // strip-end exchange, two buffers
-    const int f = blockIdx.z;
     const int hx = EVEN ? sor_halo_x(R) : R;
     const int tile_x = kVR - 2 * hx, tile_y = RH - 2 * R;
-    const int rx0 = blockIdx.x * tile_x - hx, ry0 = blockIdx.y * tile_y - R;
+    const int rx0 = bx * tile_x - hx, ry0 = by * tile_y - R;
     const float *Uin = Uinb + (size_t)f * ufs;
     float *Uout = Uoutb + (size_t)f * ufs;
     const float *cf = coefb + (size_t)f * cfs;
@@ -658,13 +680,13 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
             du[r][0] = du[r][1] = 0.0f;
             dv[r][0] = dv[r][1] = 0.0f;
             const float *c = cf + gy * pitch + gx0;
-            set_pair<EVEN>(i11[r], c + kCI11 * pl);
-            set_pair<EVEN>(i22[r], c + kCI22 * pl);
-            set_pair<EVEN>(a12[r], c + kCA12 * pl);
-            set_pair<EVEN>(b1[r], c + kCB1 * pl);
-            set_pair<EVEN>(b2[r], c + kCB2 * pl);
-            set_pair<EVEN>(wl[r], c + kCWL * pl);
-            set_pair<EVEN>(wu[r], c + kCWU * pl);
+            set_pair<EVEN, COH>(i11[r], c + kCI11 * pl);
+            set_pair<EVEN, COH>(i22[r], c + kCI22 * pl);
+            set_pair<EVEN, COH>(a12[r], c + kCA12 * pl);
+            set_pair<EVEN, COH>(b1[r], c + kCB1 * pl);
+            set_pair<EVEN, COH>(b2[r], c + kCB2 * pl);
+            set_pair<EVEN, COH>(wl[r], c + kCWL * pl);
+            set_pair<EVEN, COH>(wu[r], c + kCWU * pl);
             continue;
         }
         if (!EVEN) {
@@ -675,13 +697,13 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
                 const int gx = gx0 + q;
                 const bool in = gx >= 0 && gx < w && gy >= 0 && gy < h;
                 const float *c = cf + (in ? gy * pitch + gx : 0);
-                i11[r][q] = in ? c[kCI11 * pl] : 0.0f;
-                i22[r][q] = in ? c[kCI22 * pl] : 0.0f;
-                a12[r][q] = in ? c[kCA12 * pl] : 0.0f;
-                b1[r][q] = in ? c[kCB1 * pl] : 0.0f;
-                b2[r][q] = in ? c[kCB2 * pl] : 0.0f;
-                wl[r][q] = in ? c[kCWL * pl] : 0.0f;
-                wu[r][q] = in ? c[kCWU * pl] : 0.0f;
+                i11[r][q] = in ? ldf<COH>(c + kCI11 * pl) : 0.0f;
+                i22[r][q] = in ? ldf<COH>(c + kCI22 * pl) : 0.0f;
+                a12[r][q] = in ? ldf<COH>(c + kCA12 * pl) : 0.0f;
+                b1[r][q] = in ? ldf<COH>(c + kCB1 * pl) : 0.0f;
+                b2[r][q] = in ? ldf<COH>(c + kCB2 * pl) : 0.0f;
+                wl[r][q] = in ? ldf<COH>(c + kCWL * pl) : 0.0f;
+                wu[r][q] = in ? ldf<COH>(c + kCWU * pl) : 0.0f;
             }
             continue;
         }
@@ -693,7 +715,7 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
         float2 v[kCPlanes];
 #pragma unroll
         for (int k = 0; k < kCPlanes; ++k)
-            v[k] = in0 ? *reinterpret_cast<const float2 *>(c + k * pl) : make_float2(0.0f, 0.0f);
+            v[k] = in0 ? ldf2<COH>(c + k * pl) : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const bool in = q ? in1 : in0;
@@ -715,13 +737,13 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
     if (wp < WARPS - 1) {
         const int gy = ry0 + (wp + 1) * VS;
         if (inside) {
-            set_pair<EVEN>(wub, cf + gy * pitch + gx0 + kCWU * pl);
+            set_pair<EVEN, COH>(wub, cf + gy * pitch + gx0 + kCWU * pl);
         } else {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int gx = gx0 + q;
                 if (gx >= 0 && gx < w && gy >= 0 && gy < h)
-                    wub[q] = cf[gy * pitch + gx + kCWU * pl];
+                    wub[q] = ldf<COH>(cf + gy * pitch + gx + kCWU * pl);
             }
         }
     }
@@ -745,8 +767,8 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
                     gy >= h)
                     continue;
                 const int p = gy * pitch + gx;
-                Uout[p] = Uin[p] + du[r][q];
-                (Uout + plane)[p] = (Uin + plane)[p] + dv[r][q];
+                Uout[p] = ldf<COH>(Uin + p) + du[r][q];
+                (Uout + plane)[p] = ldf<COH>(Uin + plane + p) + dv[r][q];
             }
         return;
     }
@@ -756,10 +778,21 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
         for (int r = 0; r < VS; ++r) {
             const int ly = wp * VS + r, gy = ry0 + ly;
             if (ly < R || ly >= R + tile_y || gy >= h) continue;
-            store_pair(Uin, Uout, plane, gy * pitch + gx0, gx0, w, du[r][0], du[r][1], dv[r][0],
-                       dv[r][1]);
+            store_pair<COH>(Uin, Uout, plane, gy * pitch + gx0, gx0, w, du[r][0], du[r][1],
+                            dv[r][0], dv[r][1]);
         }
     }
+}
+
+template <int VS, int RH, bool EVEN>
+__global__ void __launch_bounds__(32 * (RH / VS), 1)
+var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
+               float *__restrict__ Uoutb, size_t ufs, size_t plane,
+               const float *__restrict__ coefb, size_t cfs, int R, int n_half, float omega)
+{
+    extern __shared__ float xch[];  // strip-end exchange, two buffers
+    sor_region<VS, RH, EVEN, false>(blockIdx.x, blockIdx.y, blockIdx.z, w, h, pitch, Uinb, Uoutb,
+                                    ufs, plane, coefb, cfs, R, n_half, omega, xch);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -896,6 +929,71 @@ var_sor_tma_kernel(const __grid_constant__ CUtensorMap cmap, int w, int h, int p
     }
 }
 
+// The whole variational refinement of one small level (every outer
+// iteration) in one launch: one thread-block cluster per frame, C blocks of
+// 512 threads.  Per outer iteration the cluster first builds the level's
+// linear systems, a warp per column-walk strip (28 columns x SR rows, the
+// strips dealt round the cluster's warps; short strips, as the walk down a
+// strip is a chain of dependent loads), into the coefficient planes; a
+// cluster barrier; then runs the SOR sweeps, a block per 64x32 region of
+// 2-row strips (the regions dealt round the blocks), writing U + dU; a
+// cluster barrier.  The
+// device functions are those of var_coeff_cw_kernel and var_sor_kernel and
+// the arithmetic has a fixed rounding sequence, so the flow is the same bit
+// for bit as with the two kernels launched per iteration; it only saves their
+// launches and the blocks' start-up, which dominate on levels this small.
+// Data written earlier in the launch by other blocks (the planes, U) is read
+// through L2 (ld.global.cg) after the barrier, whose release / acquire order
+// makes it visible across the cluster.  Every block of a cluster passes every
+// barrier (the work loops sit between them), so none can wait forever.
+template <int SR, typename T>
+__global__ void __launch_bounds__(kVThreads, 1)
+var_level_cluster_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
+                         const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
+                         int pitch, size_t pfs, float *Ua, float *Ub, size_t ufs, size_t plane,
+                         float *coefb, size_t cfs, int outer, int n_half, int R, int nrx,
+                         int nry, int ncx, int ncy, float delta, float gamma, float alpha_s,
+                         float omega)
+{
+    extern __shared__ float xch[];  // strip-end exchange of the SOR regions
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), C = (int)cluster.num_blocks();
+    const int f = blockIdx.z;  // one cluster per frame
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const size_t po = (size_t)f * pfs;
+    const int nstrips = ncx * ncy, nreg = nrx * nry;
+    const bool out_lane = lane >= 2 && lane < 2 + kCWOut;
+    float *a = Ua, *b = Ub;
+    for (int k = 0; k < outer; ++k) {
+        const float *U = a + (size_t)f * ufs;
+        float *cf = coefb + (size_t)f * cfs;
+        for (int si = rank * kVWarps + wp; si < nstrips; si += C * kVWarps) {
+            const int cx0 = (si % ncx) * kCWOut - 2, y0 = (si / ncx) * SR;
+            if (cx0 >= 0 && cx0 + 31 < w && y0 >= 2 && y0 + SR + 1 < h)
+                coeff_strip<SR, true, T, true>(I0b + po, I0xb + po, I0yb + po, I1b + po, w, h,
+                                               pitch, U, U + plane, cf, (int)plane, cx0 + lane,
+                                               y0, out_lane, delta, gamma, alpha_s, omega);
+            else
+                coeff_strip<SR, false, T, true>(I0b + po, I0xb + po, I0yb + po, I1b + po, w, h,
+                                                pitch, U, U + plane, cf, (int)plane, cx0 + lane,
+                                                y0, out_lane, delta, gamma, alpha_s, omega);
+        }
+        cluster.sync();
+        for (int r = rank; r < nreg; r += C)
+            sor_region<2, 32, true, true>(r % nrx, r / nrx, f, w, h, pitch, a, b, ufs, plane,
+                                          coefb, cfs, R, n_half, omega, xch);
+        cluster.sync();
+        float *t = a;
+        a = b;
+        b = t;
+    }
+}
+
+// Largest cluster of var_level_cluster_kernel that can be resident, per
+// device (0: none); set by init_var_attributes.
+int g_cluster_max[kMaxDevs];
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -959,6 +1057,44 @@ void init_var_attributes()
                          (int)kTmaSmemBytes);
     cudaFuncSetAttribute(var_sor_kernel<1, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(kVSmemFloats2 * sizeof(float)));
+    // clusters of up to 16 blocks for the level-resident refinement: the
+    // largest size whose cluster can be resident with one block per SM
+    cudaFuncSetAttribute(var_level_cluster_kernel<2, float>,
+                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(var_level_cluster_kernel<2, __half>,
+                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(var_level_cluster_kernel<4, float>,
+                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(var_level_cluster_kernel<4, __half>,
+                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int cm = 0;
+    for (int c = 16; c >= 1 && cm == 0; --c) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c, 1, 1);
+        cfg.blockDim = dim3(kVThreads, 1, 1);
+        cfg.dynamicSmemBytes = kVSmemFloats * sizeof(float);
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = c;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        int n32 = 0, n16 = 0;
+        int n32b = 0, n16b = 0;
+        if (cudaOccupancyMaxActiveClusters(&n32, var_level_cluster_kernel<2, float>, &cfg) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&n16, var_level_cluster_kernel<2, __half>, &cfg) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&n32b, var_level_cluster_kernel<4, float>, &cfg) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&n16b, var_level_cluster_kernel<4, __half>, &cfg) ==
+                cudaSuccess &&
+            n32 > 0 && n16 > 0 && n32b > 0 && n16b > 0)
+            cm = c;
+    }
+    cudaGetLastError();
+    if (dev >= 0 && dev < kMaxDevs) g_cluster_max[dev] = cm;
 
 }
 
@@ -987,6 +1123,64 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
     const dim3 wgrd((lv.w + kCWOut - 1) / kCWOut,
                     ((lv.h + kCWRows - 1) / kCWRows + kCWWarps - 1) / kCWWarps, frames);
     const dim3 sgrd((lv.w + tile_x - 1) / tile_x, (lv.h + tile - 1) / tile, frames);
+    // small levels: every outer iteration in one cluster launch per frame
+    // (same flow bit for bit), where one cluster holds the level's work and
+    // all the frames' clusters fit one wave
+    {
+        // strips of 2 rows if the cluster can hold them, else of 4
+        const int cmax = std::min((dev >= 0 && dev < kMaxDevs) ? g_cluster_max[dev] : 0,
+                                  fp.var_cluster_max);
+        // SOR regions of 64 x 32 (2-row strips, 16 warps): the interior is
+        // 32 - 2R rows high
+        const int ty32 = 32 - 2 * R;
+        const int nrx = (lv.w + tile_x - 1) / tile_x;
+        const int nry = ty32 > 0 ? (lv.h + ty32 - 1) / ty32 : 1 << 20;
+        const int ncx = (lv.w + kCWOut - 1) / kCWOut, nreg = nrx * nry;
+        auto need = [&](int sr) {
+            const int ncy_ = (lv.h + sr - 1) / sr;
+            return std::max(nreg, (ncx * ncy_ + kVWarps - 1) / kVWarps);
+        };
+        const int sr = need(2) <= cmax ? 2 : 4;
+        const int ncy = (lv.h + sr - 1) / sr, C = need(sr);
+        if (fp.var_outer > 0 && C <= cmax && nsm > 0 && frames * C <= nsm) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C, 1, frames);
+            cfg.blockDim = dim3(kVThreads, 1, 1);
+            cfg.dynamicSmemBytes = kVSmemFloats * sizeof(float);
+            cfg.stream = st;
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = C;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            cfg.attrs = &at;
+            cfg.numAttrs = 1;
+            cudaError_t e;
+            {
+                StageScope sc(kStVarSor, 1, st);
+                if (fp.half)
+                    e = cudaLaunchKernelEx(&cfg, sr == 2 ? var_level_cluster_kernel<2, __half>
+                                                         : var_level_cluster_kernel<4, __half>,
+                                           (const __half *)I0, (const __half *)I0x,
+                                           (const __half *)I0y, (const __half *)I1, lv.w, lv.h,
+                                           lv.pitch, pyr_frame_stride, U, Utmp, u_frame_stride,
+                                           lv.plane, coef, coef_frame_stride, fp.var_outer,
+                                           n_half, R, nrx, nry, ncx, ncy, fp.delta, fp.gamma,
+                                           fp.alpha_s, fp.omega);
+                else
+                    e = cudaLaunchKernelEx(&cfg, sr == 2 ? var_level_cluster_kernel<2, float>
+                                                         : var_level_cluster_kernel<4, float>,
+                                           (const float *)I0, (const float *)I0x,
+                                           (const float *)I0y, (const float *)I1, lv.w, lv.h,
+                                           lv.pitch, pyr_frame_stride, U, Utmp, u_frame_stride,
+                                           lv.plane, coef, coef_frame_stride, fp.var_outer,
+                                           n_half, R, nrx, nry, ncx, ncy, fp.delta, fp.gamma,
+                                           fp.alpha_s, fp.omega);
+            }
+            if (e == cudaSuccess) return (fp.var_outer & 1) ? Utmp : U;
+            cudaGetLastError();  // not launched: the per-iteration kernels below
+        }
+    }
     float *a = U, *b = Utmp;
     for (int k = 0; k < fp.var_outer; ++k) {
         if (column_walk) {

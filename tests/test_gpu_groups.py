@@ -166,11 +166,13 @@ def test_multigroup_one_graph_matches_single_streams(eb):
 
 @pytest.mark.parametrize("knob,values", [("sor_tma_min_per_sm", (1, 2, 1 << 20)),
                                          ("sor_row_waves", (0, 2, 4)),
-                                         ("coeff_cw_min_width", (160, 640, 1 << 20))])
+                                         ("coeff_cw_min_width", (160, 640, 1 << 20)),
+                                         ("var_cluster_max", (2, 8, 16))])
 def test_layout_knobs_never_change_the_flow(eb, knob, values):
-    """The variational layouts (the coefficient kernel's form, the SOR forms)
-    tile the same computation differently: single and batched calls give
-    the same flow bit for bit under every setting."""
+    """The variational layouts (the coefficient kernel's form, the SOR forms,
+    the cluster-resident refinement of the small levels) tile the same
+    computation differently: single and batched calls give the same flow bit
+    for bit under every setting."""
     ev = synth.rigid_objects(n_windows=6, seed=80, events=(60000, 90000), width=1280,
                              height=720)
     W, H, n = 1280, 720, 5
