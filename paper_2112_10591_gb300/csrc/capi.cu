@@ -10,6 +10,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -1184,16 +1185,11 @@ ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *
                 return EBOF_ERR_INVALID_ARG;
         }
     }
-    std::vector<BusyGuard *> guards;
-    struct Release {
-        std::vector<BusyGuard *> &v;
-        ~Release()
-        {
-            for (BusyGuard *b : v) delete b;
-        }
-    } release{guards};
+    // every group is claimed for the call (released when the guards go)
+    std::vector<std::unique_ptr<BusyGuard>> guards;
     for (ebof_group *g : m->groups) {
-        guards.push_back(new BusyGuard(g->busy));
+        guards.emplace_back(new (std::nothrow) BusyGuard(g->busy));
+        if (!guards.back()) return EBOF_ERR_OOM;
         if (!guards.back()->ok) return EBOF_ERR_BUSY;
     }
     DeviceGuard dg(m->device);
