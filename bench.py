@@ -1051,6 +1051,23 @@ def main():
                 {k: v[0] / frames_per_step for k, v in bprof.items() if v[1]}, P, n_ev_win,
                 len(gl), prm.var_outer, peak)
             sb.close()
+            # the same batches with FP16 storage of surfaces, pyramids and gradients
+            pb.storage = eb.EBOF_STORAGE_FP16
+            st16b, sb = eb.ebof_stream_create(pb, local)
+            if st16b >= 0:
+                for _ in range(args.warmup):
+                    step_batched()
+                barrier()
+                e0.record(cs)
+                for _ in range(args.steps):
+                    step_batched()
+                e1.record(cs)
+                barrier()
+                hms, hval = combine_ranks(e0.elapsed_time(e1), frames_per_step * args.steps,
+                                          world, dist, dev)
+                batched["fp16_storage"] = {"value": hval, "unit": UNIT,
+                                           "ms_per_step": hms / args.steps}
+                sb.close()
         else:
             batched = {"unavailable": eb.ebof_status_string(stb)}
 
