@@ -597,43 +597,70 @@ def run_multistream(args, eb, torch, dev, rank):
     return out
 
 
+def _gt_figures(eb, torch, dev, local, ev):
+    """GPU flow of every window pair of ``ev`` against the generator's ground
+    truth: mean AEE, median error, outlier share (error > 3 px and > 5 % of
+    the motion) and the zero flow's AEE, over the flow frames."""
+    prm = eb.ebof_default_params(ev.width, ev.height)
+    st, s = eb.ebof_stream_create(prm, local)
+    eb.check(st, "ebof_stream_create")
+    W, H = ev.width, ev.height
+    flows = []
+    for k in range(ev.n_windows):
+        x, y, t, _, tb, te = ev.window(k)
+        fl = torch.empty((2, H, W), dtype=torch.float32, device=dev)
+        eb.check(eb.ebof_process_window(s, torch.from_numpy(x).to(dev),
+                                        torch.from_numpy(y).to(dev),
+                                        torch.from_numpy(t).to(dev), None, tb, te, fl))
+        flows.append(fl)
+    torch.cuda.synchronize(dev)
+    errs, med, outl, zero = [], [], [], []
+    for k in range(1, ev.n_windows):
+        U = flows[k].cpu().numpy().astype(np.float64)
+        G, m = ev.true_flow(k)
+        e = np.hypot(U[0] - G[0], U[1] - G[1])[m]
+        mag = np.hypot(G[0], G[1])[m]
+        errs.append(e.mean())
+        med.append(np.median(e))
+        outl.append(((e > 3.0) & (e > 0.05 * mag)).mean())
+        zero.append(mag.mean())
+    s.close()
+    return {"aee_px": float(np.mean(errs)), "median_px": float(np.mean(med)),
+            "outliers_pct": 100 * float(np.mean(outl)),
+            "zero_flow_aee_px": float(np.mean(zero)),
+            "aee_over_zero": float(np.mean(errs) / max(np.mean(zero), 1e-12)),
+            "frames": ev.n_windows - 1}
+
+
 def ground_truth_quality(eb, torch, dev, local):
     """§IV-C's AEE and outlier share (error > 3 px and > 5 % of the motion)
     of the GPU flow against the generator's ground truth at the previous
     window's event pixels: the 346x260 workload pair, and 20 flow frames of
     a 21-window copy of the 1280x720 workload (its own draws: the motion of
-    a stream is drawn for its length).  Sanity figures: the 1280x720 scene
-    moves up to 20 px and 2 degrees per 10 ms window, so its edges smear
-    into bands as wide as the motion."""
+    a stream is drawn for its length).
+
+    ``motion_sweep``: the 1280x720 scene with the largest translation per
+    window set to 2.5, 5, 10 and 20 px (turns scaled alike, 2 degrees at
+    20 px), 3 flow frames each, once with the workload's motion (every
+    object's turn and translation drawn anew for every window) and once with
+    constant velocity (drawn once).  It separates the size of the motion from
+    its change between windows."""
     from paper_2112_10591_gb300 import synth
-    out = {}
-    for name, ev in (("346x260", synth.translating_segments(keep_truth=True)),
-                     ("1280x720", synth.workload_1280x720(n_windows=21, keep_truth=True))):
-        prm = eb.ebof_default_params(ev.width, ev.height)
-        st, s = eb.ebof_stream_create(prm, local)
-        eb.check(st, "ebof_stream_create")
-        W, H = ev.width, ev.height
-        flows = []
-        for k in range(ev.n_windows):
-            x, y, t, _, tb, te = ev.window(k)
-            fl = torch.empty((2, H, W), dtype=torch.float32, device=dev)
-            eb.check(eb.ebof_process_window(s, torch.from_numpy(x).to(dev),
-                                            torch.from_numpy(y).to(dev),
-                                            torch.from_numpy(t).to(dev), None, tb, te, fl))
-            flows.append(fl)
-        torch.cuda.synchronize(dev)
-        errs, outl, zero = [], [], []
-        for k in range(1, ev.n_windows):
-            U = flows[k].cpu().numpy().astype(np.float64)
-            G, m = ev.true_flow(k)
-            e = np.hypot(U[0] - G[0], U[1] - G[1])[m]
-            mag = np.hypot(G[0], G[1])[m]
-            errs.append(e.mean())
-            outl.append(((e > 3.0) & (e > 0.05 * mag)).mean())
-            zero.append(mag.mean())
-        s.close()
-        out[name] = {"aee_px": float(np.mean(errs)), "outliers_pct": 100 * float(np.mean(outl)),
-                     "zero_flow_aee_px": float(np.mean(zero)), "frames": ev.n_windows - 1}
+    out = {"346x260": _gt_figures(eb, torch, dev, local,
+                                  synth.translating_segments(keep_truth=True)),
+           "1280x720": _gt_figures(eb, torch, dev, local,
+                                   synth.workload_1280x720(n_windows=21, keep_truth=True))}
+    sweep = []
+    for const in (False, True):
+        for shift in (2.5, 5.0, 10.0, 20.0):
+            ev = synth.rigid_objects(n_windows=4, max_shift=shift,
+                                     max_rot_deg=2.0 * shift / 20.0, keep_truth=True,
+                                     constant_velocity=const)
+            row = {"motion": "constant velocity" if const else "redrawn every window",
+                   "max_shift_px": shift}
+            row.update(_gt_figures(eb, torch, dev, local, ev))
+            sweep.append(row)
+    out["motion_sweep"] = sweep
     return out
 
 

@@ -227,7 +227,8 @@ def rigid_objects(width=1280, height=720, n_windows=201, n_objects=12,
                   n_edges=300, radius=(40.0, 200.0), extra_length=(10.0, 120.0),
                   max_rot_deg=2.0, max_shift=20.0, events=(150_000, 400_000),
                   noise_frac=0.03, seed=1, dt=WINDOW_US,
-                  lognormal_counts=False, keep_truth=False) -> EventStream:
+                  lognormal_counts=False, keep_truth=False,
+                  constant_velocity=False) -> EventStream:
     """High-resolution stream: rigid objects with their own affine motion.
 
     Default arguments give the 1280x720 stream workload: 201 windows (200
@@ -238,7 +239,10 @@ def rigid_objects(width=1280, height=720, n_windows=201, n_objects=12,
     components U[-20, 20] px (norm capped at 20 px), reflected when the
     centre would leave the image; the background is static and produces
     no events; 3 % uniform noise; seed 1.  With ``lognormal_counts`` the
-    per-window counts are lognormal, clipped to ``events``.
+    per-window counts are lognormal, clipped to ``events``.  With
+    ``constant_velocity`` each object's turn and translation are drawn once
+    and kept for every window (a reflected component stays reflected), so
+    that consecutive windows smear the edges along the same displacement.
     """
     rng = np.random.default_rng(seed)
     centres = rng.random((n_objects, 2)) * [width, height]
@@ -266,11 +270,13 @@ def rigid_objects(width=1280, height=720, n_windows=201, n_objects=12,
     K = n_windows
     theta = np.zeros((K + 1, n_objects))
     shift = np.zeros((K + 1, n_objects, 2))
+    dth = d = None
     for k in range(K):
-        dth = np.deg2rad(rng.uniform(-max_rot_deg, max_rot_deg, n_objects))
-        d = rng.uniform(-max_shift, max_shift, (n_objects, 2))
-        nrm = np.linalg.norm(d, axis=1, keepdims=True)
-        d = np.where(nrm > max_shift, d * (max_shift / np.maximum(nrm, 1e-12)), d)
+        if not constant_velocity or k == 0:
+            dth = np.deg2rad(rng.uniform(-max_rot_deg, max_rot_deg, n_objects))
+            d = rng.uniform(-max_shift, max_shift, (n_objects, 2))
+            nrm = np.linalg.norm(d, axis=1, keepdims=True)
+            d = np.where(nrm > max_shift, d * (max_shift / np.maximum(nrm, 1e-12)), d)
         pos = centres + shift[k] + d
         out_x = (pos[:, 0] < 0) | (pos[:, 0] >= width)
         out_y = (pos[:, 1] < 0) | (pos[:, 1] >= height)
