@@ -567,8 +567,32 @@ def run_multistream(args, eb, torch, dev, rank):
         torch.cuda.synchronize(dev)
         return np.asarray([a.elapsed_time(b) for a, b in evs])
 
+    def kernels_per_step():
+        lib = eb.load()
+        before = lib.ebof_kernel_launches()
+        step_graph(nw - 1)
+        torch.cuda.synchronize(dev)
+        return int(lib.ebof_kernel_launches() - before)
+
     two = timed(step_streams)
     step_ms = timed(step_graph)
+    k_branches = kernels_per_step()
+    # the same steps with every stage one launch for both resolutions
+    fused = None
+    rf = eb.ebof_multigroup_set_fused(mg, True)
+    if rf == eb.EBOF_OK:
+        fused_ms = timed(step_graph)
+        fused = {"value": sum(gr["n"] for gr in groups) * len(fused_ms) / (fused_ms.sum() / 1000.0),
+                 "p50_step_ms": float(np.percentile(fused_ms, 50)),
+                 "p99_step_ms": float(np.percentile(fused_ms, 99)),
+                 "kernels_per_step": kernels_per_step(),
+                 "launch": "one CUDA graph per step, every stage ONE launch for the streams "
+                           "of both resolutions (ebof_multigroup_set_fused): blocks map to "
+                           "(group, frame, tile) through device tables, the scatter walks a "
+                           "device work list of 4096-event chunks"}
+        eb.ebof_multigroup_set_fused(mg, False)
+    else:
+        fused = {"unavailable": eb.ebof_status_string(rf)}
     nstreams = sum(gr["n"] for gr in groups)
     px = sum(gr["n"] * gr["W"] * gr["H"] for gr in groups)
     total_s = step_ms.sum() / 1000.0
@@ -582,6 +606,8 @@ def run_multistream(args, eb, torch, dev, rank):
            "launch": "one CUDA graph per step (ebof_multigroup): each resolution group's "
                      "step is one branch of the graph, every stage one launch per "
                      "resolution, the branches concurrent",
+           "kernels_per_step": k_branches,
+           "fused": fused,
            "two_streams": {"value": nstreams * len(two) / (two.sum() / 1000.0),
                            "p99_step_ms": float(np.percentile(two, 99)),
                            "launch": "one graph replay per group and step, groups on two "

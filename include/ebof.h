@@ -358,6 +358,29 @@ ebof_status ebof_multigroup_destroy(ebof_multigroup *m);  /* NULL-safe; waits fo
 ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *const *h_descs,
                                     void *cuda_stream);
 
+/* Fused steps (§8(f) batched multi-stream; the method per stream is
+ * unchanged, §III-A..§III-D).  fused = 1: from the next captured step on,
+ * every stage of the step is ONE kernel launch for the streams of all
+ * groups, whatever their resolutions and event counts: a block finds its
+ * (group, frame, tile) in a table built on the host once per parity pattern
+ * and passed in the launch's constant bank, and the scatter walks a device
+ * work list of 4096-event chunks over all windows, so uneven windows spread
+ * over every block.  Pyramid levels are aligned at the coarsest level: the
+ * j-th flow level step runs level L - 1 - j of every group with L > j
+ * levels (the small levels of a large resolution share launches with the
+ * larger levels of a small one); a step with one group left runs that
+ * group's own launches.  Groups that differ in storage type, patch size or
+ * search lane layout at a step take one launch per kind there; more than 8
+ * groups take one launch per 8.  Results are
+ * bit-identical to fused = 0 (default: one launch per stage and group, the
+ * groups as concurrent graph branches).  The first step of a group and
+ * steps with stage timing still run each group's own launches.  Returns
+ * EBOF_ERR_UNSUPPORTED if a group has more than 6 pyramid levels or more
+ * SOR sweeps than the register-resident SOR regions hold, EBOF_ERR_BUSY if
+ * another thread uses one of the groups.  Changing the mode waits for the
+ * groups' work and drops the captured graphs. */
+ebof_status ebof_multigroup_set_fused(ebof_multigroup *m, int32_t fused);
+
 /* ---- serving loop ---------------------------------------------------------
  * A server runs many camera streams on one GPU as their windows arrive.
  * §IV (Real-Time Compliance) runs one sensor per pipeline and counts a flow

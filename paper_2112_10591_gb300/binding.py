@@ -166,6 +166,7 @@ def _declare(L):
     L.ebof_multigroup_create.argtypes = [P(vp), i32, P(vp)]
     L.ebof_multigroup_destroy.argtypes = [vp]
     L.ebof_multigroup_process.argtypes = [vp, P(P(ebof_window_desc)), vp]
+    L.ebof_multigroup_set_fused.argtypes = [vp, i32]
     L.ebof_stream_set_profiling.argtypes = [vp, i32]
     L.ebof_stream_get_profile.argtypes = [vp, P(ctypes.c_double), P(i64), i32]
     L.ebof_stream_get_profile_level.argtypes = [vp, i32, P(ctypes.c_double), P(i64), i32]
@@ -188,7 +189,8 @@ def _declare(L):
                  "ebof_server_open_stream", "ebof_server_close_stream", "ebof_server_submit",
                  "ebof_server_poll", "ebof_server_drain", "ebof_server_get_info",
                  "ebof_stream_set_wait_limit", "ebof_multigroup_create",
-                 "ebof_multigroup_destroy", "ebof_multigroup_process"):
+                 "ebof_multigroup_destroy", "ebof_multigroup_process",
+                 "ebof_multigroup_set_fused"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -498,6 +500,11 @@ def ebof_multigroup_create(groups):
     if st < 0:
         return st, None
     return st, MultiGroup(h.value, groups)
+
+
+def ebof_multigroup_set_fused(mg: MultiGroup, fused: bool) -> int:
+    """Every stage one launch for all groups (True) or one per group (False)."""
+    return load().ebof_multigroup_set_fused(mg.handle, 1 if fused else 0)
 
 
 def ebof_multigroup_process(mg: MultiGroup, windows, cuda_stream=None) -> int:

@@ -5,11 +5,13 @@
 #include "ebof.h"
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
+#include "seg.cuh"
 
 #include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <new>
 #include <vector>
@@ -126,6 +128,28 @@ struct ebof_group {
     CoefMaps cmaps;
 };
 
+namespace ebof {
+
+// The fused launches of one step pattern of a multigroup: the enqueue
+// operations in order and the device copy of the scatter work lists they
+// read (an operation reads the list base at run time, so the plan can be
+// built before the lists have a device address).
+struct FusedPlan {
+    std::vector<char> host;  // work lists, each at a 16-byte aligned offset
+    char *dev = nullptr;
+    std::vector<std::function<void(cudaStream_t)>> ops;
+    ~FusedPlan() { cudaFree(dev); }
+    size_t add(const void *p, size_t bytes)
+    {
+        const size_t off = (host.size() + 15) & ~(size_t)15;
+        host.resize(off + bytes);
+        std::memcpy(host.data() + off, p, bytes);
+        return off;
+    }
+};
+
+}  // namespace ebof
+
 struct ebof_multigroup {
     std::vector<ebof_group *> groups;  // not owned
     int device = 0;
@@ -134,6 +158,10 @@ struct ebof_multigroup {
     // one graph per pattern of the groups' ping-pong parities
     std::vector<std::pair<unsigned long long, cudaGraphExec_t>> graphs;
     std::vector<long long> graph_kernels;
+    // fused mode: every stage one launch for all groups (ebof_multigroup_set_fused);
+    // plans[j] holds the tables of graphs[j]
+    bool fused = false;
+    std::vector<std::unique_ptr<FusedPlan>> plans;
 };
 
 namespace {
@@ -576,6 +604,444 @@ void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
         launch_flow_out(Ucur, W, H, g->pitch0, g->u_fs, g->flow, n, st);
     } else {
         cudaMemsetAsync(g->flow, 0, sizeof(float) * flow_frame * n, st);
+    }
+}
+
+// ----------------------------------------------------------------- fused steps
+// Adds one operation per table of `segs` (a segment and its block count
+// each; at most kMaxSeg segments per table) that calls
+// `launch(table, blocks, stream)`; the table travels by value.
+template <class A, class L>
+void emit_seg(FusedPlan &P, const std::vector<std::pair<A, int>> &segs, L launch)
+{
+    for (size_t i = 0; i < segs.size(); i += kMaxSeg) {
+        SegTable<A> t;
+        std::memset(&t, 0, sizeof(t));
+        int blocks = 0;
+        for (size_t j = i; j < std::min(segs.size(), i + kMaxSeg); ++j) {
+            if (segs[j].second <= 0) continue;
+            t.first[t.n] = blocks;
+            t.a[t.n] = segs[j].first;
+            blocks += segs[j].second;
+            ++t.n;
+        }
+        t.first[t.n] = blocks;
+        if (blocks == 0) continue;
+        P.ops.push_back([t, blocks, launch](cudaStream_t st) { launch(t, blocks, st); });
+    }
+}
+
+// Segments sorted by a kernel-instance key: one emit per distinct key.
+template <class A, class L>
+void emit_keyed(FusedPlan &P, const std::vector<std::pair<long long, std::pair<A, int>>> &segs,
+                L launch_for_key)
+{
+    std::vector<long long> keys;
+    for (const auto &s : segs)
+        if (std::find(keys.begin(), keys.end(), s.first) == keys.end()) keys.push_back(s.first);
+    for (long long k : keys) {
+        std::vector<std::pair<A, int>> sub;
+        for (const auto &s : segs)
+            if (s.first == k) sub.push_back(s.second);
+        emit_seg(P, sub, launch_for_key(k));
+    }
+}
+
+// Can the fused launches run group g?  The fused pyramid kernel builds at
+// most seg_max_levels() levels; the fused SOR is the register-strip region
+// kernel, which needs var_fused_supported(var_sor).
+bool fused_supported(const ebof_group *g)
+{
+    return g->geo.levels <= seg_max_levels() && var_fused_supported(g->p.var_sor);
+}
+
+// The plan of one steady-state step of multigroup m (every group has a
+// previous window; parities as the groups hold them now): the stages of
+// run_group in the same order, each stage one launch over all groups (one
+// per kernel instance where groups differ in storage, patch size or lane
+// layout).  Pyramid levels are aligned at the coarsest level (below).
+// Results are those of run_group bit for bit: every kernel body is the
+// group kernel's, and every layout that differs (EDT rows of one warp, the
+// tile form of the coefficients, the even-halo SOR regions) gives the same
+// values.
+void build_fused_plan(ebof_multigroup *m, FusedPlan &P)
+{
+    const int nsm = [] {
+        int d = 0, n = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+        return n > 0 ? n : 152;
+    }();
+    FusedPlan *pp = &P;
+    // per-group banks of this step
+    struct GS {
+        ebof_group *g;
+        char *cur, *prv;
+        float *U;  // result of the last level done (null before the first)
+        const Level *lvc;
+    };
+    std::vector<GS> gs;
+    for (ebof_group *g : m->groups) {
+        const size_t bank = (size_t)g->n * g->pyr_fs * g->es;
+        gs.push_back({g, g->pyr + (size_t)g->parity * bank, g->pyr + (size_t)(g->parity ^ 1) * bank,
+                      nullptr, nullptr});
+    }
+    // counters of this step
+    for (GS &x : gs) {
+        ebof_group *g = x.g;
+        P.ops.push_back([g](cudaStream_t st) {
+            cudaMemsetAsync(g->dstats, 0, sizeof(DevStats) * g->n, st);
+            cudaMemsetAsync(g->d_dropped_time, 0, sizeof(unsigned long long), st);
+            cudaMemsetAsync(g->E, 0, g->e_fs * g->n, st);
+        });
+    }
+    // A1: the work list of all windows
+    {
+        std::vector<ScatterWin> wins;
+        for (GS &x : gs) {
+            ebof_group *g = x.g;
+            for (int k = 0; k < g->n; ++k)
+                wins.push_back({g->d_desc + k, g->E + (size_t)k * g->e_fs, g->dstats + k,
+                                g->d_dropped_time, g->p.width, g->p.height, g->pitch0});
+        }
+        for (size_t i = 0; i < wins.size(); i += kScatterListMax) {
+            const int nw = (int)std::min(wins.size() - i, (size_t)kScatterListMax);
+            const size_t off = P.add(wins.data() + i, sizeof(ScatterWin) * nw);
+            const int blocks = 4 * nsm;
+            P.ops.push_back([pp, off, nw, blocks](cudaStream_t st) {
+                launch_seg_scatter(reinterpret_cast<const ScatterWin *>(pp->dev + off), nw,
+                                   blocks, st);
+            });
+        }
+    }
+    // A2
+    {
+        std::vector<std::pair<SegDenoise, int>> segs;
+        for (GS &x : gs) {
+            ebof_group *g = x.g;
+            const ebof_params &p = g->p;
+            SegDenoise a = {};
+            a.E = g->E;
+            a.Edf = g->Edf;
+            a.stats = g->dstats;
+            a.fs = g->e_fs;
+            a.W = p.width;
+            a.H = p.height;
+            a.pitch = g->pitch0;
+            a.conn = p.connectivity;
+            a.n_d = p.n_d;
+            a.n_f = p.n_f;
+            a.gx = (p.width + 31) / 32;
+            a.gy = (p.height + 7) / 8;
+            segs.push_back({a, a.gx * a.gy * g->n});
+        }
+        emit_seg(P, segs, launch_seg_denoise_fill);
+    }
+    // A3
+    {
+        std::vector<std::pair<SegEdtCols, int>> segs;
+        int nch_max = 1;
+        for (GS &x : gs) {
+            ebof_group *g = x.g;
+            SegEdtCols a = {};
+            a.E = g->Edf;
+            a.g = g->g;
+            a.efs = g->e_fs;
+            a.gfs = g->g_fs;
+            a.epitch = a.gpitch = g->pitch0;
+            a.W = g->p.width;
+            a.H = g->p.height;
+            edt_cols_chunks(a.H, a.CH, a.nch);
+            a.gx = (a.W + 31) / 32;
+            nch_max = std::max(nch_max, a.nch);
+            segs.push_back({a, a.gx * g->n});
+        }
+        emit_seg(P, segs, [nch_max](const SegTable<SegEdtCols> &t, int b, cudaStream_t st) {
+            launch_seg_edt_cols(t, b, nch_max, st);
+        });
+    }
+    // A4 (keyed by storage): rows of one warp
+    {
+        std::vector<std::pair<long long, std::pair<SegEdtRows, int>>> segs;
+        int rows_max = 1;
+        size_t smem = 0;
+        for (GS &x : gs) {
+            ebof_group *g = x.g;
+            SegEdtRows a = {};
+            a.g = g->g;
+            a.I0 = x.cur;
+            a.gfs = g->g_fs;
+            a.ifs = g->pyr_fs;
+            a.sm = surface_map(g->p);
+            a.gpitch = a.ipitch = g->pitch0;
+            a.W = g->p.width;
+            a.H = g->p.height;
+            a.rows = edt_rows_block_rows(a.W);
+            a.gx = (a.H + a.rows - 1) / a.rows;
+            rows_max = std::max(rows_max, a.rows);
+            smem = std::max(smem, edt_rows_smem(a.W, a.rows));
+            segs.push_back({g->p.storage == EBOF_STORAGE_FP16, {a, a.gx * g->n}});
+        }
+        emit_keyed(P, segs, [rows_max, smem](long long half) {
+            return [rows_max, smem, half](const SegTable<SegEdtRows> &t, int b, cudaStream_t st) {
+                launch_seg_edt_rows(t, b, rows_max, smem, half != 0, st);
+            };
+        });
+    }
+    // A5 (keyed by storage): box means, then gradients
+    {
+        std::vector<std::pair<long long, std::pair<SegPyr, int>>> means, grads;
+        for (GS &x : gs) {
+            ebof_group *g = x.g;
+            SegPyr a = {};
+            a.slots = x.cur;
+            a.fs = g->pyr_fs;
+            a.d = make_pyr_desc(g->geo);
+            const long long half = g->p.storage == EBOF_STORAGE_FP16;
+            if (a.d.levels > 1) {
+                a.gx = (a.d.w[1] + 31) / 32;
+                a.gy = (a.d.h[1] + 31) / 32;
+                means.push_back({half, {a, a.gx * a.gy * g->n}});
+            }
+            a.gx = a.d.blk0[a.d.levels];
+            a.gy = 1;
+            grads.push_back({half, {a, a.gx * g->n}});
+        }
+        emit_keyed(P, means, [](long long half) {
+            return [half](const SegTable<SegPyr> &t, int b, cudaStream_t st) {
+                launch_seg_pyr_means(t, b, half != 0, st);
+            };
+        });
+        emit_keyed(P, grads, [](long long half) {
+            return [half](const SegTable<SegPyr> &t, int b, cudaStream_t st) {
+                launch_seg_pyr_grads(t, b, half != 0, st);
+            };
+        });
+    }
+    // A6-A8 per level.  The levels are aligned at the coarsest one: step j
+    // runs level L - 1 - j of every group with L > j levels, so the small
+    // levels of a large resolution, which leave most SMs idle, share their
+    // launches with the larger levels of a small one.  A step with one group
+    // left runs that group's own launches (with its own layouts).
+    int Lmax = 0;
+    for (GS &x : gs) Lmax = std::max(Lmax, x.g->geo.levels);
+    int cax = 32, cay = 12;
+    coeff_tile_shape(cax, cay);
+    for (int j = 0; j < Lmax; ++j) {
+        int active = 0;
+        for (GS &x : gs) active += j < x.g->geo.levels;
+        if (active == 1) {
+            for (GS &x : gs) {
+                ebof_group *g = x.g;
+                if (j >= g->geo.levels) continue;
+                const int l = g->geo.levels - 1 - j;
+                const Level *lv = &g->geo.lv[l];
+                const size_t es = g->es;
+                const char *I0 = x.prv + g->geo.pyr_off[l] * es;
+                const char *I1 = x.cur + g->geo.pyr_off[l] * es;
+                const char *I0x = I0 + lv->plane * es, *I0y = I0 + 2 * lv->plane * es;
+                float *Ucur = (x.U == g->Ua) ? g->Ub : g->Ua;
+                float *Utmp = (Ucur == g->Ua) ? g->Ub : g->Ua;
+                const FlowParams fp = flow_params(g->p);
+                const float *Uc = x.U;
+                const Level *lvc = x.lvc;
+                const CUtensorMap *cmap = g->cmaps.ok[l] ? &g->cmaps.map[l] : nullptr;
+                P.ops.push_back([=](cudaStream_t st) {
+                    tl_level = l;
+                    launch_patch_search(I0, I0x, I0y, I1, *lv, g->pyr_fs, Uc, lvc, g->u_fs, g->up,
+                                        g->up_fs, g->n, fp, g->d_err, st);
+                    launch_densify(I0, I1, *lv, g->pyr_fs, g->up, g->up_fs, Ucur, g->u_fs, g->n,
+                                   fp, st);
+                    launch_variational(I0, I0x, I0y, I1, *lv, g->pyr_fs, Ucur, Utmp, g->u_fs,
+                                       g->work, g->work_fs, g->n, fp, cmap, g->d_err, st);
+                    tl_level = -1;
+                });
+                // where launch_variational leaves the result
+                x.U = (fp.var_outer > 0 && (fp.var_outer & 1)) ? Utmp : Ucur;
+                x.lvc = lv;
+            }
+            continue;
+        }
+        std::vector<std::pair<long long, std::pair<SegSearch, int>>> search;
+        std::vector<std::pair<long long, std::pair<SegDensify, int>>> dense;
+        struct VarSeg {
+            GS *x;
+            const Level *lv;
+            const char *I0, *I0x, *I0y, *I1;
+            float *a, *b;
+        };
+        std::vector<VarSeg> var;
+        for (GS &x : gs) {
+            ebof_group *g = x.g;
+            if (j >= g->geo.levels) continue;
+            const int l = g->geo.levels - 1 - j;
+            const ebof_params &p = g->p;
+            const Level &lv = g->geo.lv[l];
+            const size_t es = g->es;
+            const char *I0 = x.prv + g->geo.pyr_off[l] * es;
+            const char *I1 = x.cur + g->geo.pyr_off[l] * es;
+            const char *I0x = I0 + lv.plane * es, *I0y = I0 + 2 * lv.plane * es;
+            float *Ucur = (x.U == g->Ua) ? g->Ub : g->Ua;
+            const long long half = p.storage == EBOF_STORAGE_FP16;
+            const int np = lv.npx * lv.npy;
+            if (np > 0) {
+                const bool wide = search_wide(np);
+                SegSearch a = {};
+                a.I0 = I0;
+                a.I0x = I0x;
+                a.I0y = I0y;
+                a.I1 = I1;
+                a.Uc = x.U;
+                a.up = g->up;
+                a.err = g->d_err;
+                a.pfs = g->pyr_fs;
+                a.plane_c = x.lvc ? x.lvc->plane : 0;
+                a.ucfs = g->u_fs;
+                a.upfs = g->up_fs;
+                a.w = lv.w;
+                a.h = lv.h;
+                a.pitch = lv.pitch;
+                a.npx = lv.npx;
+                a.npy = lv.npy;
+                a.wc = x.lvc ? x.lvc->w : 0;
+                a.hc = x.lvc ? x.lvc->h : 0;
+                a.pitch_c = x.lvc ? x.lvc->pitch : 0;
+                a.stride = p.stride;
+                a.iters = p.gn_iters;
+                a.kappa = p.gn_damping;
+                const int ppb = search_patches_per_block(p.patch, wide);
+                a.gx = (np + ppb - 1) / ppb;
+                search.push_back({(half << 40) | ((long long)p.patch << 8) | (wide ? 1 : 0),
+                                  {a, a.gx * g->n}});
+            }
+            {
+                SegDensify a = {};
+                a.I0 = I0;
+                a.I1 = I1;
+                a.up = g->up;
+                a.U = Ucur;
+                a.pfs = g->pyr_fs;
+                a.upfs = g->up_fs;
+                a.ufs = g->u_fs;
+                a.plane = lv.plane;
+                a.w = lv.w;
+                a.h = lv.h;
+                a.pitch = lv.pitch;
+                a.npx = lv.npx;
+                a.npy = lv.npy;
+                a.ps = p.patch;
+                a.stride = p.stride;
+                a.gx = (lv.w + 31) / 32;
+                a.gy = (lv.h + 7) / 8;
+                const int nc = (p.patch + p.stride - 1) / p.stride;
+                const long long nck = (nc >= 2 && nc <= 4) ? nc : 0;
+                dense.push_back({(half << 40) | nck, {a, a.gx * a.gy * g->n}});
+            }
+            float *Utmp = (Ucur == g->Ua) ? g->Ub : g->Ua;
+            var.push_back({&x, &lv, I0, I0x, I0y, I1, Ucur, Utmp});
+            x.U = Ucur;  // the densified flow; the variational steps move it
+            x.lvc = &lv;
+        }
+        emit_keyed(P, search, [](long long k) {
+            const bool half = (k >> 40) != 0, wide = (k & 1) != 0;
+            const int ps = (int)((k >> 8) & 0xff);
+            return [half, wide, ps](const SegTable<SegSearch> &t, int b, cudaStream_t st) {
+                launch_seg_search(t, b, ps, wide, half, st);
+            };
+        });
+        emit_keyed(P, dense, [](long long k) {
+            const bool half = (k >> 40) != 0;
+            const int nc = (int)(k & 0xff);
+            return [half, nc](const SegTable<SegDensify> &t, int b, cudaStream_t st) {
+                launch_seg_densify(t, b, nc, half, st);
+            };
+        });
+        // A8: outer iteration k of every group that has it: coefficients,
+        // then SOR, a and b swapping as in launch_variational
+        int outer_max = 0;
+        for (const VarSeg &v : var) outer_max = std::max(outer_max, v.x->g->p.var_outer);
+        for (int k = 0; k < outer_max; ++k) {
+            std::vector<std::pair<long long, std::pair<SegCoeff, int>>> coeff;
+            std::vector<std::pair<SegSor, int>> sor;
+            for (VarSeg &v : var) {
+                const ebof_params &p = v.x->g->p;
+                if (k >= p.var_outer) continue;
+                const FlowParams fp = flow_params(p);
+                const Level &lv = *v.lv;
+                const size_t cfs = (size_t)coeff_planes() * lv.plane;
+                SegCoeff c = {};
+                c.I0 = v.I0;
+                c.I0x = v.I0x;
+                c.I0y = v.I0y;
+                c.I1 = v.I1;
+                c.U = v.a;
+                c.coef = v.x->g->work;
+                c.pfs = v.x->g->pyr_fs;
+                c.ufs = v.x->g->u_fs;
+                c.plane = lv.plane;
+                c.cfs = cfs;
+                c.w = lv.w;
+                c.h = lv.h;
+                c.pitch = lv.pitch;
+                c.gx = (lv.w + cax - 1) / cax;
+                c.gy = (lv.h + cay - 1) / cay;
+                c.delta = fp.delta;
+                c.gamma = fp.gamma;
+                c.alpha_s = fp.alpha_s;
+                c.omega = fp.omega;
+                coeff.push_back({fp.half ? 1 : 0, {c, c.gx * c.gy * v.x->g->n}});
+                const int n_half = 2 * fp.var_sor;
+                SegSor r = {};
+                r.Uin = v.a;
+                r.Uout = v.b;
+                r.coef = v.x->g->work;
+                r.ufs = v.x->g->u_fs;
+                r.plane = lv.plane;
+                r.cfs = cfs;
+                r.w = lv.w;
+                r.h = lv.h;
+                r.pitch = lv.pitch;
+                r.R = n_half > 0 ? n_half - 1 : 0;
+                r.n_half = n_half;
+                r.omega = fp.omega;
+                r.gx = (lv.w + sor_tile_x(r.R) - 1) / sor_tile_x(r.R);
+                r.gy = (lv.h + sor_tile_y(r.R) - 1) / sor_tile_y(r.R);
+                sor.push_back({r, r.gx * r.gy * v.x->g->n});
+                std::swap(v.a, v.b);
+                v.x->U = v.a;
+            }
+            emit_keyed(P, coeff, [](long long half) {
+                return [half](const SegTable<SegCoeff> &t, int b, cudaStream_t st) {
+                    launch_seg_coeff(t, b, half != 0, st);
+                };
+            });
+            emit_seg(P, sor, launch_seg_sor);
+        }
+    }
+    // A9: each group's level-0 flow into its flow buffer
+    {
+        std::vector<std::pair<SegFlowOut, int>> segs;
+        for (GS &x : gs) {
+            ebof_group *g = x.g;
+            const int W = g->p.width, H = g->p.height;
+            if (g->geo.levels == 0) {
+                P.ops.push_back([g, W, H](cudaStream_t st) {
+                    cudaMemsetAsync(g->flow, 0, sizeof(float) * 2 * (size_t)W * H * g->n, st);
+                });
+                continue;
+            }
+            SegFlowOut a = {};
+            a.U = x.U;
+            a.flow = g->flow;
+            a.ufs = g->u_fs;
+            a.plane = (size_t)g->pitch0 * H;
+            a.W = W;
+            a.H = H;
+            a.pitch = g->pitch0;
+            a.gx = (W + 255) / 256;
+            segs.push_back({a, a.gx * H * g->n});
+        }
+        emit_seg(P, segs, launch_seg_flow_out);
     }
 }
 
@@ -1171,6 +1637,33 @@ ebof_status ebof_multigroup_destroy(ebof_multigroup *m)
     return EBOF_OK;
 }
 
+ebof_status ebof_multigroup_set_fused(ebof_multigroup *m, int32_t fused)
+{
+    if (!m || (fused != 0 && fused != 1)) return EBOF_ERR_INVALID_ARG;
+    if (fused)
+        for (const ebof_group *g : m->groups)
+            if (!fused_supported(g)) return EBOF_ERR_UNSUPPORTED;
+    if (m->fused == (fused != 0)) return EBOF_OK;
+    std::vector<std::unique_ptr<BusyGuard>> guards;
+    for (ebof_group *g : m->groups) {
+        guards.emplace_back(new (std::nothrow) BusyGuard(g->busy));
+        if (!guards.back()) return EBOF_ERR_OOM;
+        if (!guards.back()->ok) return EBOF_ERR_BUSY;
+    }
+    DeviceGuard dg(m->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    // graphs in flight may still read their tables
+    for (ebof_group *g : m->groups)
+        if (g->have_last) cudaEventSynchronize(g->done);
+    for (auto &pg : m->graphs)
+        if (pg.second) cudaGraphExecDestroy(pg.second);
+    m->graphs.clear();
+    m->graph_kernels.clear();
+    m->plans.clear();
+    m->fused = fused != 0;
+    return EBOF_OK;
+}
+
 ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *const *h_descs,
                                     void *cuda_stream)
 {
@@ -1227,15 +1720,36 @@ ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *
             const unsigned long long before = g_launches.load();
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t ge = nullptr;
+            std::unique_ptr<FusedPlan> plan;
+            if (m->fused) {
+                // the fused launches' tables, copied to the device once
+                plan.reset(new (std::nothrow) FusedPlan());
+                if (!plan) return EBOF_ERR_OOM;
+                build_fused_plan(m, *plan);
+                if (dmalloc(&plan->dev, plan->host.size()) != cudaSuccess) {
+                    cudaGetLastError();
+                    return EBOF_ERR_OOM;
+                }
+                if (cudaMemcpyAsync(plan->dev, plan->host.data(), plan->host.size(),
+                                    cudaMemcpyHostToDevice, m->cap) != cudaSuccess ||
+                    cudaStreamSynchronize(m->cap) != cudaSuccess) {
+                    cudaGetLastError();
+                    return EBOF_ERR_CUDA;
+                }
+            }
             if (cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 tl_prof = nullptr;
-                cudaEventRecord(m->fork[0], m->cap);
-                for (int i = 0; i < ng; ++i) {
-                    ebof_group *g = m->groups[i];
-                    cudaStreamWaitEvent(g->cap, m->fork[0], 0);
-                    run_group(g, true, g->cap);
-                    cudaEventRecord(m->fork[1 + i], g->cap);
-                    cudaStreamWaitEvent(m->cap, m->fork[1 + i], 0);
+                if (plan) {
+                    for (auto &op : plan->ops) op(m->cap);
+                } else {
+                    cudaEventRecord(m->fork[0], m->cap);
+                    for (int i = 0; i < ng; ++i) {
+                        ebof_group *g = m->groups[i];
+                        cudaStreamWaitEvent(g->cap, m->fork[0], 0);
+                        run_group(g, true, g->cap);
+                        cudaEventRecord(m->fork[1 + i], g->cap);
+                        cudaStreamWaitEvent(m->cap, m->fork[1 + i], 0);
+                    }
                 }
                 cudaStreamEndCapture(m->cap, &graph);
             }
@@ -1249,6 +1763,7 @@ ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *
             }
             m->graphs.emplace_back(key, ge);
             m->graph_kernels.push_back(kernels);
+            m->plans.push_back(std::move(plan));
         }
         if (cudaGraphLaunch(m->graphs[slot].second, st) != cudaSuccess) return EBOF_ERR_CUDA;
         g_launches.fetch_add((unsigned long long)m->graph_kernels[slot]);

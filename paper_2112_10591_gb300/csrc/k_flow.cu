@@ -14,6 +14,7 @@
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
 #include "dev_common.cuh"
+#include "seg.cuh"
 
 namespace ebof {
 
@@ -47,15 +48,17 @@ __device__ __forceinline__ float as_stored(float v, const __half *)
 constexpr int kPyrTile = 32;
 constexpr int kPyrFused = 6;
 
+// (bx, by): the level-1 tile, f: the frame.
 template <typename T>
-__global__ void __launch_bounds__(256)
-pyramid_means_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
+__device__ __forceinline__ void pyramid_means_body(T *__restrict__ slots, size_t fs,
+                                                   const PyrDesc &d, unsigned bx, unsigned by,
+                                                   unsigned f)
 {
     __shared__ float ta[kPyrTile][kPyrTile + 1];
     __shared__ float tb[kPyrTile / 2][kPyrTile / 2 + 1];
-    T *slot = slots + (size_t)blockIdx.z * fs;
+    T *slot = slots + (size_t)f * fs;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    const int x1b = blockIdx.x * kPyrTile, y1b = blockIdx.y * kPyrTile;
+    const int x1b = bx * kPyrTile, y1b = by * kPyrTile;
     {
         const T *I0 = slot + d.off[0];
         T *I1 = slot + d.off[1];
@@ -98,26 +101,60 @@ pyramid_means_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
     }
 }
 
-// Central differences of every level of a slot in one launch: the blocks of
-// level l are blk0[l] .. blk0[l + 1] - 1 (32 x 8 pixels each).
 template <typename T>
 __global__ void __launch_bounds__(256)
-pyramid_gradients_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
+pyramid_means_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
+{
+    pyramid_means_body(slots, fs, d, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Central differences of every level of a slot in one launch: the blocks of
+// level l are blk0[l] .. blk0[l + 1] - 1 (32 x 8 pixels each).  bb: the
+// block, f: the frame.
+template <typename T>
+__device__ __forceinline__ void pyramid_gradients_body(T *__restrict__ slots, size_t fs,
+                                                       const PyrDesc &d, unsigned bb, unsigned f)
 {
     int l = 0;
-    while (l + 1 < d.levels && (int)blockIdx.x >= d.blk0[l + 1]) ++l;
-    const int b = blockIdx.x - d.blk0[l];
+    while (l + 1 < d.levels && (int)bb >= d.blk0[l + 1]) ++l;
+    const int b = bb - d.blk0[l];
     const int w = d.w[l], h = d.h[l], pitch = d.pitch[l];
     const int nbx = (w + 31) / 32;
     const int x = (b % nbx) * 32 + threadIdx.x, y = (b / nbx) * 8 + threadIdx.y;
     if (x >= w || y >= h) return;
-    T *im = slots + (size_t)blockIdx.z * fs + d.off[l];
+    T *im = slots + (size_t)f * fs + d.off[l];
     T *Ix = im + d.plane[l], *Iy = im + 2 * d.plane[l];
     const int xp = min(x + 1, w - 1), xm = max(x - 1, 0);
     const int yp = min(y + 1, h - 1), ym = max(y - 1, 0);
     const size_t p = (size_t)y * pitch + x;
     stp(&Ix[p], 0.5f * (ldp(&im[(size_t)y * pitch + xp]) - ldp(&im[(size_t)y * pitch + xm])));
     stp(&Iy[p], 0.5f * (ldp(&im[(size_t)yp * pitch + x]) - ldp(&im[(size_t)ym * pitch + x])));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+pyramid_gradients_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
+{
+    pyramid_gradients_body(slots, fs, d, blockIdx.x, blockIdx.z);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+seg_pyramid_means_kernel(const __grid_constant__ SegTable<SegPyr> tab)
+{
+    int b;
+    const SegPyr &a = seg_of(tab, b);
+    const int r = b / a.gx;
+    pyramid_means_body((T *)a.slots, a.fs, a.d, b % a.gx, r % a.gy, r / a.gy);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+seg_pyramid_gradients_kernel(const __grid_constant__ SegTable<SegPyr> tab)
+{
+    int b;
+    const SegPyr &a = seg_of(tab, b);
+    pyramid_gradients_body((T *)a.slots, a.fs, a.d, b % a.gx, b / a.gx);
 }
 
 // ---------------------------------------------------------------- A6
@@ -151,21 +188,21 @@ struct SearchShape {
 };
 constexpr int kWideSearchPatches = 8192;
 
+// bx: the block of patches, f: the frame.
 template <int PS, int CG, int RG, typename T>
-__global__ void __launch_bounds__(128)
-patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
-                    const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
-                    int pitch, size_t pfs, int npx, int npy, const float *__restrict__ Ucb, int wc,
-                    int hc, int pitch_c, size_t plane_c, size_t ucfs, float *__restrict__ upb,
-                    size_t upfs, int stride, int iters, float kappa, int *err)
+__device__ __forceinline__ void patch_search_body(
+    const T *__restrict__ I0b, const T *__restrict__ I0xb, const T *__restrict__ I0yb,
+    const T *__restrict__ I1b, int w, int h, int pitch, size_t pfs, int npx, int npy,
+    const float *__restrict__ Ucb, int wc, int hc, int pitch_c, size_t plane_c, size_t ucfs,
+    float *__restrict__ upb, size_t upfs, int stride, int iters, float kappa, int *err,
+    unsigned bx, unsigned f)
 {
     constexpr int G = CG * RG;
     constexpr int CPL = (PS + CG - 1) / CG;
     constexpr int RPL = (PS + RG - 1) / RG;
-    const int f = blockIdx.y;
     const int c = threadIdx.x % G;
     const int np = npx * npy;
-    const int pid_raw = blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+    const int pid_raw = bx * (128 / G) + threadIdx.x / G;
     const bool real = pid_raw < np;
     const int pid = real ? pid_raw : np - 1;
     const int i = pid % npx, j = pid / npx;
@@ -305,6 +342,31 @@ patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
     }
 }
 
+template <int PS, int CG, int RG, typename T>
+__global__ void __launch_bounds__(128)
+patch_search_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
+                    const T *__restrict__ I0yb, const T *__restrict__ I1b, int w, int h,
+                    int pitch, size_t pfs, int npx, int npy, const float *__restrict__ Ucb, int wc,
+                    int hc, int pitch_c, size_t plane_c, size_t ucfs, float *__restrict__ upb,
+                    size_t upfs, int stride, int iters, float kappa, int *err)
+{
+    patch_search_body<PS, CG, RG, T>(I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, npx, npy, Ucb, wc, hc,
+                                     pitch_c, plane_c, ucfs, upb, upfs, stride, iters, kappa, err,
+                                     blockIdx.x, blockIdx.y);
+}
+
+template <int PS, int CG, int RG, typename T>
+__global__ void __launch_bounds__(128)
+seg_patch_search_kernel(const __grid_constant__ SegTable<SegSearch> tab)
+{
+    int b;
+    const SegSearch &a = seg_of(tab, b);
+    patch_search_body<PS, CG, RG, T>(
+        (const T *)a.I0, (const T *)a.I0x, (const T *)a.I0y, (const T *)a.I1, a.w, a.h, a.pitch,
+        a.pfs, a.npx, a.npy, a.Uc, a.wc, a.hc, a.pitch_c, a.plane_c, a.ucfs, a.up, a.upfs,
+        a.stride, a.iters, a.kappa, a.err, b % a.gx, b / a.gx);
+}
+
 // ---------------------------------------------------------------- A7
 __device__ __forceinline__ void cover_range(int x, int n, int ps, int stride, int cnt, int &lo,
                                             int &hi, bool &last)
@@ -342,16 +404,18 @@ __device__ __forceinline__ float dense_sample(const T *__restrict__ I1, int w, i
     return bilinear_i(I1, w, h, pitch, (float)x + u, (float)y + v);
 }
 
+// (bx, by): the 32 x 8 tile, f: the frame.
 template <typename T, int NC>
-__global__ void __launch_bounds__(256)
-densify_kernel(const T *__restrict__ I0b, const T *__restrict__ I1b, int w, int h, int pitch,
-               size_t pfs, const float *__restrict__ upb, size_t upfs, int npx, int npy,
-               float *__restrict__ Ub, size_t ufs, size_t plane, int ps, int stride)
+__device__ __forceinline__ void densify_body(const T *__restrict__ I0b, const T *__restrict__ I1b,
+                                             int w, int h, int pitch, size_t pfs,
+                                             const float *__restrict__ upb, size_t upfs, int npx,
+                                             int npy, float *__restrict__ Ub, size_t ufs,
+                                             size_t plane, int ps, int stride, unsigned bx,
+                                             unsigned by, unsigned f)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = bx * 32 + threadIdx.x;
+    const int y = by * 8 + threadIdx.y;
     if (x >= w || y >= h) return;
-    const int f = blockIdx.z;
     const T *I0 = I0b + (size_t)f * pfs, *I1 = I1b + (size_t)f * pfs;
     const float *up = upb + (size_t)f * upfs;
     const float *vp = up + npx * npy;
@@ -391,6 +455,28 @@ densify_kernel(const T *__restrict__ I0b, const T *__restrict__ I1b, int w, int 
     const int p = y * pitch + x;
     U[p] = den > 0.0f ? nu / den : 0.0f;
     (U + plane)[p] = den > 0.0f ? nv / den : 0.0f;
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256)
+densify_kernel(const T *__restrict__ I0b, const T *__restrict__ I1b, int w, int h, int pitch,
+               size_t pfs, const float *__restrict__ upb, size_t upfs, int npx, int npy,
+               float *__restrict__ Ub, size_t ufs, size_t plane, int ps, int stride)
+{
+    densify_body<T, NC>(I0b, I1b, w, h, pitch, pfs, upb, upfs, npx, npy, Ub, ufs, plane, ps,
+                        stride, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256)
+seg_densify_kernel(const __grid_constant__ SegTable<SegDensify> tab)
+{
+    int b;
+    const SegDensify &a = seg_of(tab, b);
+    const int r = b / a.gx;
+    densify_body<T, NC>((const T *)a.I0, (const T *)a.I1, a.w, a.h, a.pitch, a.pfs, a.up, a.upfs,
+                        a.npx, a.npy, a.U, a.ufs, a.plane, a.ps, a.stride, b % a.gx, r % a.gy,
+                        r / a.gy);
 }
 
 // ---------------------------------------------------------------- A8
@@ -516,17 +602,33 @@ __global__ void add_kernel(int w, int h, int pitch, float *__restrict__ Ub, size
     U[plane + p] += wk[kDV * plane + p];
 }
 
-__global__ void flow_out_kernel(const float *__restrict__ Ub, int W, int H, int pitch,
-                                size_t ufs, size_t plane, float *__restrict__ flow)
+// bx: the block of 256 pixels of row y, f: the frame.
+__device__ __forceinline__ void flow_out_body(const float *__restrict__ Ub, int W, int H,
+                                              int pitch, size_t ufs, size_t plane,
+                                              float *__restrict__ flow, unsigned bx, unsigned y,
+                                              unsigned f)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int x = bx * 256 + threadIdx.x;
     if (x >= W) return;
-    const int f = blockIdx.z;
     const float *U = Ub + (size_t)f * ufs;
     const size_t o = (size_t)f * 2 * W * H + (size_t)y * W + x;
     flow[o] = U[(size_t)y * pitch + x];
     flow[o + (size_t)W * H] = U[plane + (size_t)y * pitch + x];
+}
+
+__global__ void flow_out_kernel(const float *__restrict__ Ub, int W, int H, int pitch,
+                                size_t ufs, size_t plane, float *__restrict__ flow)
+{
+    flow_out_body(Ub, W, H, pitch, ufs, plane, flow, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__global__ void __launch_bounds__(256)
+seg_flow_out_kernel(const __grid_constant__ SegTable<SegFlowOut> tab)
+{
+    int b;
+    const SegFlowOut &a = seg_of(tab, b);
+    const int r = b / a.gx;
+    flow_out_body(a.U, a.W, a.H, a.pitch, a.ufs, a.plane, a.flow, b % a.gx, r % a.H, r / a.H);
 }
 
 // Same as flow_out_kernel, with frame f's destination read from dst[f] in
@@ -552,7 +654,7 @@ void search_ps(const T *I0, const T *I0x, const T *I0y, const T *I1,
 {
     using SS = SearchShape<PS>;
     const int np = lv.npx * lv.npy;
-    const bool wide = np >= kWideSearchPatches;
+    const bool wide = search_wide(np);
     const int G = wide ? SS::kWideCG : SS::kNarrowCG * SS::kNarrowRG;
     const int per_block = 128 / G;
     dim3 grd((np + per_block - 1) / per_block, frames);
@@ -573,10 +675,9 @@ dim3 grid2d(int w, int h, int frames, dim3 blk)
 
 void init_flow_attributes() { init_var_attributes(); }
 
-void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int frames, bool half,
-                    cudaStream_t st)
+PyrDesc make_pyr_desc(const Geometry &geo)
 {
-    PyrDesc d;
+    PyrDesc d = {};
     d.levels = std::max(geo.levels, 1);
     int nb = 0;
     for (int l = 0; l < d.levels; ++l) {
@@ -590,6 +691,14 @@ void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int f
         nb += ((lv.w + 31) / 32) * ((lv.h + 7) / 8);
     }
     d.blk0[d.levels] = nb;
+    return d;
+}
+
+void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int frames, bool half,
+                    cudaStream_t st)
+{
+    const PyrDesc d = make_pyr_desc(geo);
+    const int nb = d.blk0[d.levels];
     const int extra = std::max(0, d.levels - kPyrFused);
     StageScope sc(kStPyramid, 1 + (d.levels > 1 ? 1 : 0) + extra, st);
     const dim3 blk(32, 8);
@@ -745,6 +854,91 @@ float *launch_variational(const void *I0, const void *I0x, const void *I0y, cons
                           (const float *)I1, lv, pyr_frame_stride, U, u_frame_stride, work,
                           work_frame_stride, frames, fp, st);
     return U;
+}
+
+bool search_wide(int n_patches) { return n_patches >= kWideSearchPatches; }
+
+int search_patches_per_block(int ps, bool wide)
+{
+    int G = 0;
+#define EBOF_G(N)                                                                                \
+    case N:                                                                                      \
+        G = wide ? SearchShape<N>::kWideCG : SearchShape<N>::kNarrowCG * SearchShape<N>::kNarrowRG; \
+        break;
+    switch (ps) {
+        EBOF_G(4) EBOF_G(5) EBOF_G(6) EBOF_G(7) EBOF_G(8) EBOF_G(9) EBOF_G(10) EBOF_G(11)
+        EBOF_G(12) EBOF_G(13) EBOF_G(14) EBOF_G(15) EBOF_G(16)
+        default: break;
+    }
+#undef EBOF_G
+    return G > 0 ? 128 / G : 0;
+}
+
+void launch_seg_pyr_means(const SegTable<SegPyr> &t, int blocks, bool half, cudaStream_t st)
+{
+    StageScope sc(kStPyramid, 1, st);
+    if (half) seg_pyramid_means_kernel<__half><<<blocks, dim3(32, 8), 0, st>>>(t);
+    else seg_pyramid_means_kernel<float><<<blocks, dim3(32, 8), 0, st>>>(t);
+}
+
+void launch_seg_pyr_grads(const SegTable<SegPyr> &t, int blocks, bool half, cudaStream_t st)
+{
+    StageScope sc(kStPyramid, 1, st);
+    if (half) seg_pyramid_gradients_kernel<__half><<<blocks, dim3(32, 8), 0, st>>>(t);
+    else seg_pyramid_gradients_kernel<float><<<blocks, dim3(32, 8), 0, st>>>(t);
+}
+
+int seg_max_levels() { return kPyrFused; }
+
+void launch_seg_search(const SegTable<SegSearch> &t, int blocks, int ps, bool wide, bool half,
+                       cudaStream_t st)
+{
+    StageScope sc(kStSearch, 1, st);
+#define EBOF_SPS(N)                                                                              \
+    case N: {                                                                                    \
+        using SS = SearchShape<N>;                                                               \
+        if (half)                                                                                \
+            (wide ? seg_patch_search_kernel<N, SS::kWideCG, 1, __half>                           \
+                  : seg_patch_search_kernel<N, SS::kNarrowCG, SS::kNarrowRG, __half>)            \
+                <<<blocks, 128, 0, st>>>(t);                                                     \
+        else                                                                                     \
+            (wide ? seg_patch_search_kernel<N, SS::kWideCG, 1, float>                            \
+                  : seg_patch_search_kernel<N, SS::kNarrowCG, SS::kNarrowRG, float>)             \
+                <<<blocks, 128, 0, st>>>(t);                                                     \
+        break;                                                                                   \
+    }
+    switch (ps) {
+        EBOF_SPS(4) EBOF_SPS(5) EBOF_SPS(6) EBOF_SPS(7) EBOF_SPS(8) EBOF_SPS(9) EBOF_SPS(10)
+        EBOF_SPS(11) EBOF_SPS(12) EBOF_SPS(13) EBOF_SPS(14) EBOF_SPS(15) EBOF_SPS(16)
+        default: break;
+    }
+#undef EBOF_SPS
+}
+
+void launch_seg_densify(const SegTable<SegDensify> &t, int blocks, int nc, bool half,
+                        cudaStream_t st)
+{
+    StageScope sc(kStDensify, 1, st);
+    const dim3 blk(32, 8);
+#define EBOF_SDENSE(T, N) seg_densify_kernel<T, N><<<blocks, blk, 0, st>>>(t)
+    if (half) {
+        if (nc == 2) EBOF_SDENSE(__half, 2);
+        else if (nc == 3) EBOF_SDENSE(__half, 3);
+        else if (nc == 4) EBOF_SDENSE(__half, 4);
+        else EBOF_SDENSE(__half, 0);
+    } else {
+        if (nc == 2) EBOF_SDENSE(float, 2);
+        else if (nc == 3) EBOF_SDENSE(float, 3);
+        else if (nc == 4) EBOF_SDENSE(float, 4);
+        else EBOF_SDENSE(float, 0);
+    }
+#undef EBOF_SDENSE
+}
+
+void launch_seg_flow_out(const SegTable<SegFlowOut> &t, int blocks, cudaStream_t st)
+{
+    StageScope sc(kStFlowOut, 1, st);
+    seg_flow_out_kernel<<<blocks, 256, 0, st>>>(t);
 }
 
 void launch_flow_out_ptr(const float *U, int W, int H, int pitch, size_t u_frame_stride,

@@ -8,6 +8,7 @@
 #include "ebof.h"
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
+#include "seg.cuh"
 
 #include <cuda_fp16.h>
 
@@ -157,6 +158,91 @@ __global__ void scatter_desc_kernel(const ebof_window_desc *__restrict__ desc, i
     }
 }
 
+// Scatter of a fused launch over several groups: a work list of event
+// chunks (kScatterChunk events of one window) over all the windows.  Every
+// block turns the windows' event counts, read from their device
+// descriptors, into chunk offsets in shared memory, then walks the chunks
+// blockIdx.x, blockIdx.x + gridDim.x, ...: windows of very different sizes
+// spread evenly over the blocks.  The counts of a chunk go out as one atomic
+// per counter and block, as in scatter_desc_kernel.
+__global__ void __launch_bounds__(256)
+scatter_list_kernel(const ScatterWin *__restrict__ wins, int n_wins)
+{
+    __shared__ int s_off[kScatterListMax + 1];
+    __shared__ unsigned long long s_sum[3][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        int run = 0;
+        for (int base = 0; base < n_wins; base += 32) {
+            const int i = base + lane;
+            int c = 0;
+            if (i < n_wins) {
+                const int64_t ne = wins[i].desc->n_events;
+                c = (int)((ne + kScatterChunk - 1) / kScatterChunk);
+            }
+            int v = c;  // inclusive scan over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (i < n_wins) s_off[i] = run + v - c;
+            run += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) s_off[n_wins] = run;
+    }
+    __syncthreads();
+    const int total = s_off[n_wins];
+    for (int c = blockIdx.x; c < total; c += gridDim.x) {
+        // the window of chunk c: the last one whose chunks start at or before c
+        int lo = 0, hi = n_wins - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const ScatterWin &w = wins[lo];
+        const ebof_window_desc d = *w.desc;
+        const int64_t i0 = (int64_t)(c - s_off[lo]) * kScatterChunk;
+        const int64_t i1 = min(d.n_events, i0 + (int64_t)kScatterChunk);
+        unsigned long long in_w = 0, oob = 0, out_t = 0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int64_t tt = d.t[i];
+            if (tt >= d.t_begin && tt < d.t_end) {
+                ++in_w;
+                const int xi = d.x[i], yi = d.y[i];
+                if (xi < w.W && yi < w.H) w.E[(size_t)yi * w.pitch + xi] = 1;
+                else ++oob;
+            } else {
+                ++out_t;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            in_w += __shfl_xor_sync(0xffffffffu, in_w, o);
+            oob += __shfl_xor_sync(0xffffffffu, oob, o);
+            out_t += __shfl_xor_sync(0xffffffffu, out_t, o);
+        }
+        if (lane == 0) {
+            s_sum[0][warp] = in_w;
+            s_sum[1][warp] = oob;
+            s_sum[2][warp] = out_t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+                in_w += s_sum[0][k];
+                oob += s_sum[1][k];
+                out_t += s_sum[2][k];
+            }
+            if (in_w) atomicAdd(&w.stats->in_window, in_w);
+            if (oob) atomicAdd(&w.stats->dropped_oob, oob);
+            if (out_t) atomicAdd(w.dropped_time, out_t);
+        }
+        __syncthreads();  // s_sum is rewritten by the next chunk
+    }
+}
+
 // ---------------------------------------------------------------- A2
 // Alg. 1 then Alg. 2 in one pass: a block stages E for its 32 x 8 tile plus
 // a 2-pixel halo in shared memory, denoises the tile plus 1 pixel there
@@ -172,16 +258,17 @@ __device__ __forceinline__ int count_tile(const uint8_t (*t)[kDfX + 4], int lx, 
     return c;
 }
 
-__global__ void __launch_bounds__(kDfX * kDfY)
-denoise_fill_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Edf, int W, int H,
-                    int pitch, size_t fstride, int conn, int n_d, int n_f,
-                    uint8_t *__restrict__ export_dense, DevStats *stats)
+// (bx, by): the tile, f: the frame.
+__device__ __forceinline__ void denoise_fill_body(const uint8_t *__restrict__ E,
+                                                  uint8_t *__restrict__ Edf, int W, int H,
+                                                  int pitch, size_t fstride, int conn, int n_d,
+                                                  int n_f, uint8_t *__restrict__ export_dense,
+                                                  DevStats *stats, int bx, int by, int f)
 {
     __shared__ uint8_t sE[kDfY + 4][kDfX + 4];
     __shared__ uint8_t sD[kDfY + 4][kDfX + 4];  // denoised, 1-pixel ring inside a 2-pixel frame
-    const int f = blockIdx.z;
     const uint8_t *e = E + (size_t)f * fstride;
-    const int x0 = blockIdx.x * kDfX - 2, y0 = blockIdx.y * kDfY - 2;
+    const int x0 = bx * kDfX - 2, y0 = by * kDfY - 2;
     const int t = threadIdx.y * kDfX + threadIdx.x;
     for (int i = t; i < (kDfX + 4) * (kDfY + 4); i += kDfX * kDfY) {
         const int lx = i % (kDfX + 4), ly = i / (kDfX + 4);
@@ -199,7 +286,7 @@ denoise_fill_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Edf, in
         sD[ly][lx] = v;
     }
     __syncthreads();
-    const int x = blockIdx.x * kDfX + threadIdx.x, y = blockIdx.y * kDfY + threadIdx.y;
+    const int x = bx * kDfX + threadIdx.x, y = by * kDfY + threadIdx.y;
     uint8_t v = 0;
     if (x < W && y < H) {
         const int lx = threadIdx.x + 2, ly = threadIdx.y + 2;
@@ -211,6 +298,25 @@ denoise_fill_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Edf, in
     // one atomic per block: same-address atomics serialise in L2
     const int nedge = __syncthreads_count(v != 0);
     if (t == 0 && nedge) atomicAdd(&stats[f].edge_px, (unsigned long long)nedge);
+}
+
+__global__ void __launch_bounds__(kDfX * kDfY)
+denoise_fill_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Edf, int W, int H,
+                    int pitch, size_t fstride, int conn, int n_d, int n_f,
+                    uint8_t *__restrict__ export_dense, DevStats *stats)
+{
+    denoise_fill_body(E, Edf, W, H, pitch, fstride, conn, n_d, n_f, export_dense, stats,
+                      blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__global__ void __launch_bounds__(kDfX * kDfY)
+seg_denoise_fill_kernel(const __grid_constant__ SegTable<SegDenoise> tab)
+{
+    int b;
+    const SegDenoise &a = seg_of(tab, b);
+    const int bx = b % a.gx, r = b / a.gx;
+    denoise_fill_body(a.E, a.Edf, a.W, a.H, a.pitch, a.fs, a.conn, a.n_d, a.n_f, nullptr,
+                      a.stats, bx, r % a.gy, r / a.gy);
 }
 
 // ---------------------------------------------------------------- A3
@@ -226,15 +332,18 @@ denoise_fill_kernel(const uint8_t *__restrict__ E, uint8_t *__restrict__ Edf, in
 constexpr int kColMaxWords = 16;   // CH <= 512 rows
 constexpr int kColMaxChunks = 32;  // chunks per column
 
-__global__ void __launch_bounds__(1024)
-edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, int H,
-                int32_t *__restrict__ g, int gpitch, size_t gfs, int CH)
+// bx: the block of 32 columns, f: the frame; nch chunks (at most blockDim.y:
+// threads of chunks past the last one only take part in the barrier).
+__device__ __forceinline__ void edt_cols_body(const uint8_t *__restrict__ E, int epitch,
+                                              size_t efs, int W, int H,
+                                              int32_t *__restrict__ g, int gpitch, size_t gfs,
+                                              int CH, int nch, unsigned bx, unsigned f)
 {
     __shared__ int s_first[kColMaxChunks][32], s_last[kColMaxChunks][32];
-    const int c = threadIdx.x, k = threadIdx.y, nch = blockDim.y;
-    const int x = blockIdx.x * 32 + c;
-    const bool colok = x < W;
-    const uint8_t *e = E + (size_t)blockIdx.y * efs;
+    const int c = threadIdx.x, k = threadIdx.y;
+    const int x = bx * 32 + c;
+    const bool colok = x < W;  // chunks k >= nch start at or below row H: nothing to do
+    const uint8_t *e = E + (size_t)f * efs;
     const int y0 = k * CH, y1 = min(H, y0 + CH);
     const int nw = (CH + 31) / 32;
     unsigned mask[kColMaxWords];
@@ -269,7 +378,7 @@ edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, in
     for (int j = k + 1; j < nch; ++j)
         if (s_first[j][c] >= 0) { below = s_first[j][c]; break; }
     const int ginf = W + H;
-    int32_t *gc = g + (size_t)blockIdx.y * gfs + x;
+    int32_t *gc = g + (size_t)f * gfs + x;
     int run_above = above;  // nearest edge row before word wi
 #pragma unroll
     for (int wi = 0; wi < kColMaxWords; ++wi) {
@@ -293,6 +402,22 @@ edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, in
         }
         if (m) run_above = y0 + wi * 32 + 31 - __clz(m);
     }
+}
+
+__global__ void __launch_bounds__(1024)
+edt_cols_kernel(const uint8_t *__restrict__ E, int epitch, size_t efs, int W, int H,
+                int32_t *__restrict__ g, int gpitch, size_t gfs, int CH)
+{
+    edt_cols_body(E, epitch, efs, W, H, g, gpitch, gfs, CH, blockDim.y, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(1024)
+seg_edt_cols_kernel(const __grid_constant__ SegTable<SegEdtCols> tab)
+{
+    int b;
+    const SegEdtCols &a = seg_of(tab, b);
+    edt_cols_body(a.E, a.epitch, a.efs, a.W, a.H, a.g, a.gpitch, a.gfs, a.CH, a.nch, b % a.gx,
+                  b / a.gx);
 }
 
 // ---------------------------------------------------------------- A4
@@ -416,11 +541,14 @@ __device__ __forceinline__ void bridge(const int16_t *hs, const int32_t *F, int 
 // warp each, warp-level barriers only.  WPR > 1: one row per block; the merge
 // rounds of groups wider than a warp go through shared memory and block
 // barriers.  D is exact whatever WPR, so the layout never changes a result.
+// bx: the block of rows, f: the frame.  A warp past the block's
+// rows_per_block rows (a fused launch sized for another segment's) exits
+// (WPR = 1 has warp-level barriers only).
 template <int WPR, typename T>
-__global__ void __launch_bounds__(32 * kRowsPerBlock)
-edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs, int W, int H,
-                        int rows_per_block, SurfaceMap sm, int32_t *__restrict__ D_dense,
-                        float *__restrict__ S_dense, T *__restrict__ I0, int ipitch, size_t ifs)
+__device__ __forceinline__ void edt_rows_surface_body(
+    const int32_t *__restrict__ g, int gpitch, size_t gfs, int W, int H, int rows_per_block,
+    const SurfaceMap &sm, int32_t *__restrict__ D_dense, float *__restrict__ S_dense,
+    T *__restrict__ I0, int ipitch, size_t ifs, int bx, int f)
 {
     constexpr int NB = 32 * WPR;
     extern __shared__ int32_t smem[];
@@ -429,9 +557,9 @@ edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs, i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rib = warp / WPR;                 // row within the block
     const int tr = (warp % WPR) * 32 + lane;    // this lane's band
-    const int y = blockIdx.x * rows_per_block + rib;
-    if (y >= H) return;  // WPR = 1: the whole warp; WPR > 1: never (one row per block)
-    const int f = blockIdx.y;
+    const int y = bx * rows_per_block + rib;
+    // WPR = 1: the whole warp; WPR > 1: never (one row per block)
+    if (rib >= rows_per_block || y >= H) return;
     int32_t *F = smem + (size_t)rib * (rows_smem_bytes(W) / 4);
     int32_t *res = F + W;  // D of the row's pixels
     // hull columns; a group's hull starts at its first column
@@ -589,6 +717,26 @@ edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs, i
     }
 }
 
+template <int WPR, typename T>
+__global__ void __launch_bounds__(32 * kRowsPerBlock)
+edt_rows_surface_kernel(const int32_t *__restrict__ g, int gpitch, size_t gfs, int W, int H,
+                        int rows_per_block, SurfaceMap sm, int32_t *__restrict__ D_dense,
+                        float *__restrict__ S_dense, T *__restrict__ I0, int ipitch, size_t ifs)
+{
+    edt_rows_surface_body<WPR, T>(g, gpitch, gfs, W, H, rows_per_block, sm, D_dense, S_dense, I0,
+                                  ipitch, ifs, blockIdx.x, blockIdx.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kRowsPerBlock)
+seg_edt_rows_kernel(const __grid_constant__ SegTable<SegEdtRows> tab)
+{
+    int b;
+    const SegEdtRows &a = seg_of(tab, b);
+    edt_rows_surface_body<1, T>(a.g, a.gpitch, a.gfs, a.W, a.H, a.rows, a.sm, nullptr, nullptr,
+                                (T *)a.I0, a.ipitch, a.ifs, b % a.gx, b / a.gx);
+}
+
 // Caller-given surface (dense, d_exp in [0, 1]) to the level-0 intensity.
 template <typename T>
 __global__ void surface_to_intensity_kernel(const float *__restrict__ S, int W, int H,
@@ -649,20 +797,35 @@ void launch_denoise_fill(const uint8_t *E, uint8_t *Ed, uint8_t *Edf, int W, int
                                              export_dense, stats);
 }
 
+void edt_cols_chunks(int H, int &CH, int &nch)
+{
+    // chunks of CH rows, CH a multiple of 32: at most 32 chunks of at most 512 rows
+    nch = (H + 31) / 32;
+    if (nch > kColMaxChunks) nch = kColMaxChunks;
+    CH = ((H + nch - 1) / nch + 31) / 32 * 32;
+    nch = (H + CH - 1) / CH;
+}
+
 void launch_edt_columns(const uint8_t *E, int edge_pitch, size_t edge_frame_stride, int W,
                         int H, int32_t *g, int g_pitch, size_t g_frame_stride, int frames,
                         cudaStream_t st)
 {
     StageScope sc(kStEdtCols, 1, st);
-    // chunks of CH rows, CH a multiple of 32: at most 32 chunks of at most 512 rows
-    int nch = (H + 31) / 32;
-    if (nch > kColMaxChunks) nch = kColMaxChunks;
-    int CH = ((H + nch - 1) / nch + 31) / 32 * 32;
-    nch = (H + CH - 1) / CH;
+    int CH, nch;
+    edt_cols_chunks(H, CH, nch);
     dim3 blk(32, nch), grd((W + 31) / 32, frames);
     edt_cols_kernel<<<grd, blk, 0, st>>>(E, edge_pitch, edge_frame_stride, W, H, g, g_pitch,
                                          g_frame_stride, CH);
 }
+
+int edt_rows_block_rows(int W)
+{
+    int rows = kRowsPerBlock;
+    while (rows > 1 && (size_t)rows * rows_smem_bytes(W) > kRowsSmemCap) --rows;
+    return rows;
+}
+
+size_t edt_rows_smem(int W, int rows) { return (size_t)rows * rows_smem_bytes(W); }
 
 // Warps per row: one for batches (fewest instructions per frame) and rows
 // under 512 px; single windows (one or two frames per launch) of wider rows
@@ -682,9 +845,8 @@ void edt_rows_t(const int32_t *g, int g_pitch, size_t g_frame_stride, int W, int
     const int wpr = edt_rows_wpr(W, frames);
     // one warp a row: four rows per block, fewer where a row's shared memory
     // is large; wider layouts: one row per block
-    int rows = wpr == 1 ? kRowsPerBlock : 1;
-    while (rows > 1 && (size_t)rows * rows_smem_bytes(W) > kRowsSmemCap) --rows;
-    const size_t smem = (size_t)rows * rows_smem_bytes(W);
+    const int rows = wpr == 1 ? edt_rows_block_rows(W) : 1;
+    const size_t smem = edt_rows_smem(W, rows);
     dim3 grd((H + rows - 1) / rows, frames);
     if (wpr == 4)
         edt_rows_surface_kernel<4, T><<<grd, 128, smem, st>>>(
@@ -734,6 +896,37 @@ void init_front_attributes()
     opt_in((const void *)edt_rows_surface_kernel<1, __half>);
     opt_in((const void *)edt_rows_surface_kernel<2, __half>);
     opt_in((const void *)edt_rows_surface_kernel<4, __half>);
+    opt_in((const void *)seg_edt_rows_kernel<float>);
+    opt_in((const void *)seg_edt_rows_kernel<__half>);
+}
+
+void launch_seg_scatter(const ScatterWin *wins, int n_wins, int blocks, cudaStream_t st)
+{
+    StageScope sc(kStScatter, 1, st);
+    scatter_list_kernel<<<blocks, 256, 0, st>>>(wins, n_wins);
+}
+
+void launch_seg_denoise_fill(const SegTable<SegDenoise> &t, int blocks, cudaStream_t st)
+{
+    StageScope sc(kStDenoiseFill, 1, st);
+    seg_denoise_fill_kernel<<<blocks, dim3(kDfX, kDfY), 0, st>>>(t);
+}
+
+void launch_seg_edt_cols(const SegTable<SegEdtCols> &t, int blocks, int nch_max,
+                         cudaStream_t st)
+{
+    StageScope sc(kStEdtCols, 1, st);
+    seg_edt_cols_kernel<<<blocks, dim3(32, nch_max), 0, st>>>(t);
+}
+
+void launch_seg_edt_rows(const SegTable<SegEdtRows> &t, int blocks, int rows_max, size_t smem,
+                         bool half, cudaStream_t st)
+{
+    StageScope sc(kStEdtRows, 1, st);
+    if (half)
+        seg_edt_rows_kernel<__half><<<blocks, 32 * rows_max, smem, st>>>(t);
+    else
+        seg_edt_rows_kernel<float><<<blocks, 32 * rows_max, smem, st>>>(t);
 }
 
 void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pitch, bool half,

@@ -37,6 +37,7 @@
 #include "dev_common.cuh"
 #include "ebof_internal.cuh"
 #include "profiler.cuh"
+#include "seg.cuh"
 
 #include <cooperative_groups.h>
 #include <mutex>
@@ -335,10 +336,9 @@ __device__ __forceinline__ void coeff_tile(
     const T *__restrict__ I0b, const T *__restrict__ I0xb, const T *__restrict__ I0yb,
     const T *__restrict__ I1b, int w, int h, int pitch, size_t pfs, const float *__restrict__ Ub,
     size_t ufs, size_t plane, float *__restrict__ coefb, size_t cfs, float delta, float gamma,
-    float alpha_s, float omega)
+    float alpha_s, float omega, unsigned bx, unsigned by, unsigned f)
 {
-    const int f = blockIdx.z;
-    const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
+    const int tx0 = bx * kAX, ty0 = by * kAY;
     const int ex0 = tx0 - 2, ey0 = ty0 - 2, dx0 = tx0 - 1, dy0 = ty0 - 1;
     // frame base pointers once; offsets within a frame fit in 32 bits
     const size_t po = (size_t)f * pfs;
@@ -396,6 +396,25 @@ __device__ __forceinline__ void coeff_tile(
     cf[kCWU * pl] = ps.cu;
 }
 
+// (bx, by): the tile, f: the frame.
+template <typename T>
+__device__ __forceinline__ void var_coeff_body(
+    const T *__restrict__ I0b, const T *__restrict__ I0xb, const T *__restrict__ I0yb,
+    const T *__restrict__ I1b, int w, int h, int pitch, size_t pfs, const float *__restrict__ Ub,
+    size_t ufs, size_t plane, float *__restrict__ coefb, size_t cfs, float delta, float gamma,
+    float alpha_s, float omega, unsigned bx, unsigned by, unsigned f)
+{
+    __shared__ float sU[kAEY][kAEX], sV[kAEY][kAEX], sW[kAEY][kAEX];
+    __shared__ float sIx[kADY][kADX], sIy[kADY][kADX], sAs[kADY][kADX];
+    const int tx0 = bx * kAX, ty0 = by * kAY;
+    if (tx0 >= 2 && ty0 >= 2 && tx0 + kAX + 2 <= w && ty0 + kAY + 2 <= h)
+        coeff_tile<true>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
+                         ufs, plane, coefb, cfs, delta, gamma, alpha_s, omega, bx, by, f);
+    else
+        coeff_tile<false>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
+                          ufs, plane, coefb, cfs, delta, gamma, alpha_s, omega, bx, by, f);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kAX * kAY)
 var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
@@ -404,15 +423,20 @@ var_coeff_kernel(const T *__restrict__ I0b, const T *__restrict__ I0xb,
                  float *__restrict__ coefb, size_t cfs, float delta, float gamma, float alpha_s,
                  float omega)
 {
-    __shared__ float sU[kAEY][kAEX], sV[kAEY][kAEX], sW[kAEY][kAEX];
-    __shared__ float sIx[kADY][kADX], sIy[kADY][kADX], sAs[kADY][kADX];
-    const int tx0 = blockIdx.x * kAX, ty0 = blockIdx.y * kAY;
-    if (tx0 >= 2 && ty0 >= 2 && tx0 + kAX + 2 <= w && ty0 + kAY + 2 <= h)
-        coeff_tile<true>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
-                         ufs, plane, coefb, cfs, delta, gamma, alpha_s, omega);
-    else
-        coeff_tile<false>(sU, sV, sW, sIx, sIy, sAs, I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub,
-                          ufs, plane, coefb, cfs, delta, gamma, alpha_s, omega);
+    var_coeff_body(I0b, I0xb, I0yb, I1b, w, h, pitch, pfs, Ub, ufs, plane, coefb, cfs, delta,
+                   gamma, alpha_s, omega, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAX * kAY)
+seg_var_coeff_kernel(const __grid_constant__ SegTable<SegCoeff> tab)
+{
+    int b;
+    const SegCoeff &a = seg_of(tab, b);
+    const int r = b / a.gx;
+    var_coeff_body((const T *)a.I0, (const T *)a.I0x, (const T *)a.I0y, (const T *)a.I1, a.w, a.h,
+                   a.pitch, a.pfs, a.U, a.ufs, a.plane, a.coef, a.cfs, a.delta, a.gamma,
+                   a.alpha_s, a.omega, b % a.gx, r % a.gy, r / a.gy);
 }
 
 // Column-walk form of the same kernel.  A warp owns 28 output columns: lane
@@ -795,6 +819,19 @@ var_sor_kernel(int w, int h, int pitch, const float *__restrict__ Uinb,
                                     ufs, plane, coefb, cfs, R, n_half, omega, xch);
 }
 
+// The even-halo 64 x 64 regions of several groups' levels in one launch.
+__global__ void __launch_bounds__(kVThreads, 1)
+seg_var_sor_kernel(const __grid_constant__ SegTable<SegSor> tab)
+{
+    extern __shared__ float xch[];
+    int b;
+    const SegSor &a = seg_of(tab, b);
+    const int r = b / a.gx;
+    sor_region<kVS, kVR, true, false>(b % a.gx, r % a.gy, r / a.gy, a.w, a.h, a.pitch, a.Uin,
+                                      a.Uout, a.ufs, a.plane, a.coef, a.cfs, a.R, a.n_half,
+                                      a.omega, xch);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -1096,6 +1133,28 @@ void init_var_attributes()
     cudaGetLastError();
     if (dev >= 0 && dev < kMaxDevs) g_cluster_max[dev] = cm;
 
+}
+
+int sor_tile_x(int R) { return kVR - 2 * sor_halo_x(R); }
+int sor_tile_y(int R) { return kVR - 2 * R; }
+void coeff_tile_shape(int &x, int &y)
+{
+    x = kAX;
+    y = kAY;
+}
+int coeff_planes() { return kCPlanes; }
+
+void launch_seg_coeff(const SegTable<SegCoeff> &t, int blocks, bool half, cudaStream_t st)
+{
+    StageScope sc(kStVarCoeff, 1, st);
+    if (half) seg_var_coeff_kernel<__half><<<blocks, dim3(kAX, kAY), 0, st>>>(t);
+    else seg_var_coeff_kernel<float><<<blocks, dim3(kAX, kAY), 0, st>>>(t);
+}
+
+void launch_seg_sor(const SegTable<SegSor> &t, int blocks, cudaStream_t st)
+{
+    StageScope sc(kStVarSor, 1, st);
+    seg_var_sor_kernel<<<blocks, kVThreads, kVSmemFloats * sizeof(float), st>>>(t);
 }
 
 float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y,
