@@ -579,20 +579,25 @@ def run_multistream(args, eb, torch, dev, rank):
     k_branches = kernels_per_step()
     # the same steps with every stage one launch for both resolutions
     fused = None
-    rf = eb.ebof_multigroup_set_fused(mg, True)
-    if rf == eb.EBOF_OK:
-        fused_ms = timed(step_graph)
-        fused = {"value": sum(gr["n"] for gr in groups) * len(fused_ms) / (fused_ms.sum() / 1000.0),
-                 "p50_step_ms": float(np.percentile(fused_ms, 50)),
-                 "p99_step_ms": float(np.percentile(fused_ms, 99)),
-                 "kernels_per_step": kernels_per_step(),
-                 "launch": "one CUDA graph per step, every stage ONE launch for the streams "
-                           "of both resolutions (ebof_multigroup_set_fused): blocks map to "
-                           "(group, frame, tile) through device tables, the scatter walks a "
-                           "device work list of 4096-event chunks"}
-        eb.ebof_multigroup_set_fused(mg, False)
-    else:
-        fused = {"unavailable": eb.ebof_status_string(rf)}
+    def fused_mode(mode, launch):
+        rf = eb.ebof_multigroup_set_fused(mg, mode)
+        if rf != eb.EBOF_OK:
+            return {"unavailable": eb.ebof_status_string(rf)}
+        ms = timed(step_graph)
+        res = {"value": sum(gr["n"] for gr in groups) * len(ms) / (ms.sum() / 1000.0),
+               "p50_step_ms": float(np.percentile(ms, 50)),
+               "p99_step_ms": float(np.percentile(ms, 99)),
+               "kernels_per_step": kernels_per_step(), "launch": launch}
+        eb.ebof_multigroup_set_fused(mg, 0)
+        return res
+
+    fused = fused_mode(1, "one CUDA graph per step, every stage ONE launch for the streams "
+                          "of both resolutions (ebof_multigroup_set_fused 1): blocks map to "
+                          "(group, frame, tile) through tables, the scatter walks a device "
+                          "work list of 4096-event chunks")
+    front_fused = fused_mode(2, "one CUDA graph per step, the front-end stages one launch for "
+                                "both resolutions, the flow levels of each resolution a "
+                                "concurrent branch (ebof_multigroup_set_fused 2)")
     nstreams = sum(gr["n"] for gr in groups)
     px = sum(gr["n"] * gr["W"] * gr["H"] for gr in groups)
     total_s = step_ms.sum() / 1000.0
@@ -608,6 +613,7 @@ def run_multistream(args, eb, torch, dev, rank):
                      "resolution, the branches concurrent",
            "kernels_per_step": k_branches,
            "fused": fused,
+           "front_end_fused": front_fused,
            "two_streams": {"value": nstreams * len(two) / (two.sum() / 1000.0),
                            "p99_step_ms": float(np.percentile(two, 99)),
                            "launch": "one graph replay per group and step, groups on two "

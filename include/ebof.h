@@ -371,12 +371,14 @@ ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *
  * larger levels of a small one); a step with one group left runs that
  * group's own launches.  Groups that differ in storage type, patch size or
  * search lane layout at a step take one launch per kind there; more than 8
- * groups take one launch per 8.  Results are
- * bit-identical to fused = 0 (default: one launch per stage and group, the
- * groups as concurrent graph branches).  The first step of a group and
+ * groups take one launch per 8.  fused = 2: the front-end stages (§III-A
+ * to the pyramid) so, the flow levels of each group as a concurrent branch
+ * of the step's graph.  Results are bit-identical to fused = 0 (default:
+ * one launch per stage and group, the groups as concurrent graph branches).  The first step of a group and
  * steps with stage timing still run each group's own launches.  Returns
- * EBOF_ERR_UNSUPPORTED if a group has more than 6 pyramid levels or more
- * SOR sweeps than the register-resident SOR regions hold, EBOF_ERR_BUSY if
+ * EBOF_ERR_UNSUPPORTED if a group has more than 6 pyramid levels or (mode
+ * 1) more SOR sweeps than the register-resident SOR regions hold,
+ * EBOF_ERR_INVALID_ARG for another mode, EBOF_ERR_BUSY if
  * another thread uses one of the groups.  Changing the mode waits for the
  * groups' work and drops the captured graphs. */
 ebof_status ebof_multigroup_set_fused(ebof_multigroup *m, int32_t fused);

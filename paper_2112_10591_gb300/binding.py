@@ -502,9 +502,11 @@ def ebof_multigroup_create(groups):
     return st, MultiGroup(h.value, groups)
 
 
-def ebof_multigroup_set_fused(mg: MultiGroup, fused: bool) -> int:
-    """Every stage one launch for all groups (True) or one per group (False)."""
-    return load().ebof_multigroup_set_fused(mg.handle, 1 if fused else 0)
+def ebof_multigroup_set_fused(mg: MultiGroup, fused) -> int:
+    """0 / False: one launch per stage and group; 1 / True: every stage one
+    launch for all groups; 2: the front-end stages fused, the flow levels as
+    per-group branches."""
+    return load().ebof_multigroup_set_fused(mg.handle, int(fused))
 
 
 def ebof_multigroup_process(mg: MultiGroup, windows, cuda_stream=None) -> int:

@@ -158,9 +158,10 @@ struct ebof_multigroup {
     // one graph per pattern of the groups' ping-pong parities
     std::vector<std::pair<unsigned long long, cudaGraphExec_t>> graphs;
     std::vector<long long> graph_kernels;
-    // fused mode: every stage one launch for all groups (ebof_multigroup_set_fused);
-    // plans[j] holds the tables of graphs[j]
-    bool fused = false;
+    // fused mode (ebof_multigroup_set_fused): 0 none, 1 every stage one launch
+    // for all groups, 2 the front-end stages so and the flow levels as
+    // per-group branches; plans[j] holds the work lists of graphs[j]
+    int fused = 0;
     std::vector<std::unique_ptr<FusedPlan>> plans;
 };
 
@@ -556,6 +557,8 @@ void free_group(ebof_group *g)
 // current windows go to bank `parity`, the previous ones are in the other
 // bank.  Enqueued on `st`; nothing here depends on host values that change
 // between steps of the same parity, so the sequence can be captured.
+void run_group_flow(ebof_group *g, bool with_flow, cudaStream_t st);
+
 void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
 {
     const ebof_params &p = g->p;
@@ -578,6 +581,18 @@ void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
                             g->pitch0, g->pyr_fs, n, half, st);
     tl_level = 0;
     launch_pyramid(cur, geo, g->pyr_fs, n, half, st);
+    run_group_flow(g, with_flow, st);
+}
+
+// The flow part of a group step (A6-A9), after its pyramid.
+void run_group_flow(ebof_group *g, bool with_flow, cudaStream_t st)
+{
+    const ebof_params &p = g->p;
+    const Geometry &geo = g->geo;
+    const int W = p.width, H = p.height, n = g->n;
+    const size_t es = g->es;
+    char *cur = g->pyr + (size_t)g->parity * n * g->pyr_fs * es;
+    char *prv = g->pyr + (size_t)(g->parity ^ 1) * n * g->pyr_fs * es;
     const size_t flow_frame = (size_t)2 * W * H;
     if (with_flow && geo.levels > 0) {
         const FlowParams fp = flow_params(p);
@@ -650,9 +665,10 @@ void emit_keyed(FusedPlan &P, const std::vector<std::pair<long long, std::pair<A
 // Can the fused launches run group g?  The fused pyramid kernel builds at
 // most seg_max_levels() levels; the fused SOR is the register-strip region
 // kernel, which needs var_fused_supported(var_sor).
-bool fused_supported(const ebof_group *g)
+bool fused_supported(const ebof_group *g, int mode)
 {
-    return g->geo.levels <= seg_max_levels() && var_fused_supported(g->p.var_sor);
+    return g->geo.levels <= seg_max_levels() &&
+           (mode == 2 || var_fused_supported(g->p.var_sor));
 }
 
 // The plan of one steady-state step of multigroup m (every group has a
@@ -664,7 +680,7 @@ bool fused_supported(const ebof_group *g)
 // group kernel's, and every layout that differs (EDT rows of one warp, the
 // tile form of the coefficients, the even-halo SOR regions) gives the same
 // values.
-void build_fused_plan(ebof_multigroup *m, FusedPlan &P)
+void build_fused_plan(ebof_multigroup *m, FusedPlan &P, int mode)
 {
     const int nsm = [] {
         int d = 0, n = 0;
@@ -817,6 +833,21 @@ void build_fused_plan(ebof_multigroup *m, FusedPlan &P)
                 launch_seg_pyr_grads(t, b, half != 0, st);
             };
         });
+    }
+    if (mode == 2) {
+        // the flow of each group as one branch, forked from and joined into
+        // the step's stream: the latency-bound levels of the groups overlap
+        P.ops.push_back([m](cudaStream_t st) {
+            cudaEventRecord(m->fork[0], st);
+            for (size_t i = 0; i < m->groups.size(); ++i) {
+                ebof_group *g = m->groups[i];
+                cudaStreamWaitEvent(g->cap, m->fork[0], 0);
+                run_group_flow(g, true, g->cap);
+                cudaEventRecord(m->fork[1 + i], g->cap);
+                cudaStreamWaitEvent(st, m->fork[1 + i], 0);
+            }
+        });
+        return;
     }
     // A6-A8 per level.  The levels are aligned at the coarsest one: step j
     // runs level L - 1 - j of every group with L > j levels, so the small
@@ -1639,11 +1670,11 @@ ebof_status ebof_multigroup_destroy(ebof_multigroup *m)
 
 ebof_status ebof_multigroup_set_fused(ebof_multigroup *m, int32_t fused)
 {
-    if (!m || (fused != 0 && fused != 1)) return EBOF_ERR_INVALID_ARG;
+    if (!m || fused < 0 || fused > 2) return EBOF_ERR_INVALID_ARG;
     if (fused)
         for (const ebof_group *g : m->groups)
-            if (!fused_supported(g)) return EBOF_ERR_UNSUPPORTED;
-    if (m->fused == (fused != 0)) return EBOF_OK;
+            if (!fused_supported(g, fused)) return EBOF_ERR_UNSUPPORTED;
+    if (m->fused == fused) return EBOF_OK;
     std::vector<std::unique_ptr<BusyGuard>> guards;
     for (ebof_group *g : m->groups) {
         guards.emplace_back(new (std::nothrow) BusyGuard(g->busy));
@@ -1660,7 +1691,7 @@ ebof_status ebof_multigroup_set_fused(ebof_multigroup *m, int32_t fused)
     m->graphs.clear();
     m->graph_kernels.clear();
     m->plans.clear();
-    m->fused = fused != 0;
+    m->fused = fused;
     return EBOF_OK;
 }
 
@@ -1725,7 +1756,7 @@ ebof_status ebof_multigroup_process(ebof_multigroup *m, const ebof_window_desc *
                 // the fused launches' tables, copied to the device once
                 plan.reset(new (std::nothrow) FusedPlan());
                 if (!plan) return EBOF_ERR_OOM;
-                build_fused_plan(m, *plan);
+                build_fused_plan(m, *plan, m->fused);
                 if (dmalloc(&plan->dev, plan->host.size()) != cudaSuccess) {
                     cudaGetLastError();
                     return EBOF_ERR_OOM;

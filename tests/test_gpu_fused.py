@@ -1,6 +1,7 @@
 """Fused multigroup steps (ebof_multigroup_set_fused): every stage one launch
 for the streams of all groups, whatever their resolutions, storage, patch
-sizes and event counts.
+sizes and event counts (mode 1), or only the front-end stages fused and
+the flow levels as per-group graph branches (mode 2).
 
 The gate is bit identity: each stream's flow, edge counts and dropped-event
 counts equal those of the same groups stepped with one launch per stage and
@@ -71,7 +72,7 @@ def _run(eb, specs, nwin, fused):
     st, mg = eb.ebof_multigroup_create(groups)
     eb.check(st)
     if fused:
-        eb.check(eb.ebof_multigroup_set_fused(mg, True))
+        eb.check(eb.ebof_multigroup_set_fused(mg, fused))
     out, launches = [], []
     for k in range(nwin):
         wins = []
@@ -128,11 +129,14 @@ def test_fused_step_equals_per_group_launches(eb):
     prm = eb.ebof_default_params(300, 200)
     prm.var_outer, prm.var_sor, prm.gn_iters, prm.connectivity = 3, 3, 8, 4
     specs.append((prm, [_noisy_windows(300, 200, nwin, 9000, 99)]))
-    ref, l_ref = _run(eb, specs, nwin, False)
-    got, l_got = _run(eb, specs, nwin, True)
+    ref, l_ref = _run(eb, specs, nwin, 0)
+    got, l_got = _run(eb, specs, nwin, 1)
     _compare(ref, got)
-    print("kernels per steady step: per group %s, fused %s" % (l_ref[2:], l_got[2:]))
-    assert max(l_got[2:]) < min(l_ref[2:])
+    front, l_front = _run(eb, specs, nwin, 2)
+    _compare(ref, front)
+    print("kernels per steady step: per group %s, fused %s, front end fused %s"
+          % (l_ref[2:], l_got[2:], l_front[2:]))
+    assert max(l_got[2:]) < min(l_front[2:]) < min(l_ref[2:])
 
 
 def test_fused_step_with_more_groups_than_a_table_holds(eb):
@@ -145,9 +149,10 @@ def test_fused_step_with_more_groups_than_a_table_holds(eb):
     for i, (W, H) in enumerate(sizes):
         prm = eb.ebof_default_params(W, H)
         specs.append((prm, [_noisy_windows(W, H, nwin, max(50, W * H // 8), 200 + i)]))
-    ref, _ = _run(eb, specs, nwin, False)
-    got, _ = _run(eb, specs, nwin, True)
-    _compare(ref, got)
+    ref, _ = _run(eb, specs, nwin, 0)
+    for mode in (1, 2):
+        got, _ = _run(eb, specs, nwin, mode)
+        _compare(ref, got)
 
 
 def test_fused_mode_refuses_groups_it_cannot_run(eb):
@@ -157,8 +162,10 @@ def test_fused_mode_refuses_groups_it_cannot_run(eb):
     eb.check(st)
     st, mg = eb.ebof_multigroup_create([g])
     eb.check(st)
-    assert eb.ebof_multigroup_set_fused(mg, True) == eb.EBOF_ERR_UNSUPPORTED
-    assert eb.ebof_multigroup_set_fused(mg, False) == eb.EBOF_OK
+    assert eb.ebof_multigroup_set_fused(mg, 1) == eb.EBOF_ERR_UNSUPPORTED
+    assert eb.ebof_multigroup_set_fused(mg, 2) == eb.EBOF_OK  # the flow stays per group
+    assert eb.ebof_multigroup_set_fused(mg, 0) == eb.EBOF_OK
+    assert eb.ebof_multigroup_set_fused(mg, 3) == eb.EBOF_ERR_INVALID_ARG
     mg.close()
     g.close()
     prm = eb.ebof_default_params(1280, 720)
