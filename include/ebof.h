@@ -103,6 +103,8 @@ typedef struct {
                                    cluster barriers between the phases) when the level's
                                    work fits a cluster of at most this many blocks and
                                    the call's clusters fit one wave; 0 = never (0) */
+    int32_t coeff_cw_rows;      /* rows a warp of the column-walk kernel walks down (the
+                                   strip's height): 4, 8 or 16 (8) */
 } ebof_params;
 
 /* Distance surface built from the EDT (§III-C) and handed to the flow block.

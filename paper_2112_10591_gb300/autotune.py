@@ -15,9 +15,10 @@ tuner itself only orchestrates and compares.
    path of a candidate configuration matches the FP64 oracle is a property
    of the library, covered by its tests; the tuner runs in the product path,
    which never touches the oracle.
-2. Layout candidates (the coefficient kernel's form, the SOR kernels' forms:
-   the persistent copy-ahead kernel, regions of one-row strips; the
-   cluster-resident refinement of small levels) never change the flow.  The tuner checks that each one gives the flow of
+2. Layout candidates (the coefficient kernel's form and the height of its
+   column-walk strips, the SOR kernels' forms: the persistent copy-ahead
+   kernel, regions of one-row strips; the cluster-resident refinement of
+   small levels) never change the flow.  The tuner checks that each one gives the flow of
    the default layout bit for bit and keeps the fastest, one knob at a time
    from the default, then the combination of the winners.
 """
@@ -37,6 +38,7 @@ LAYOUT_CANDIDATES = {
     "sor_tma_min_per_sm": (2, 4, NEVER),
     "sor_row_waves": (0, 2),
     "var_cluster_max": (8, 16),
+    "coeff_cw_rows": (4, 16),
 }
 
 

@@ -51,6 +51,7 @@ class ebof_params(ctypes.Structure):
         ("sor_tma_min_per_sm", ctypes.c_int32),
         ("sor_row_waves", ctypes.c_int32),
         ("var_cluster_max", ctypes.c_int32),
+        ("coeff_cw_rows", ctypes.c_int32),
     ]
 
 

@@ -231,7 +231,8 @@ ebof_status check_params(const ebof_params *p)
     if (p->surface < EBOF_SURFACE_EXP || p->surface > EBOF_SURFACE_LOG) return EBOF_ERR_INVALID_ARG;
     if (!(std::isfinite(p->d_sat) && p->d_sat > 0.0f)) return EBOF_ERR_INVALID_ARG;
     if (p->coeff_cw_min_width < 1 || p->sor_tma_min_per_sm < 1 || p->sor_row_waves < 0 ||
-        p->var_cluster_max < 0)
+        p->var_cluster_max < 0 ||
+        (p->coeff_cw_rows != 4 && p->coeff_cw_rows != 8 && p->coeff_cw_rows != 16))
         return EBOF_ERR_INVALID_ARG;
     if (p->patch < 4 || p->patch > kMaxPatch) return EBOF_ERR_UNSUPPORTED;
     return EBOF_OK;
@@ -303,6 +304,7 @@ FlowParams flow_params(const ebof_params &p)
     fp.sor_tma_min_per_sm = p.sor_tma_min_per_sm;
     fp.sor_row_waves = p.sor_row_waves;
     fp.var_cluster_max = p.var_cluster_max;
+    fp.coeff_cw_rows = p.coeff_cw_rows;
     return fp;
 }
 
@@ -1121,6 +1123,7 @@ void ebof_default_params(ebof_params *p, int32_t width, int32_t height)
     // measured no faster inside a graph (1544 vs 1573 frames/s at 1280 x 720):
     // off unless chosen (the autotuner tries it for groups)
     p->var_cluster_max = 0;
+    p->coeff_cw_rows = 8;
 }
 
 float ebof_alpha_from_dsat(float d_sat) { return d_sat / std::log(255.0f); }

@@ -85,7 +85,7 @@ struct FlowParams {
     float delta, gamma, alpha_s, omega;
     long long wait_limit;  // first wait of the copy-ahead SOR kernel (rounds)
     // variational layouts (ebof_params): none changes a result
-    int coeff_cw_min_width, sor_tma_min_per_sm, sor_row_waves, var_cluster_max;
+    int coeff_cw_min_width, sor_tma_min_per_sm, sor_row_waves, var_cluster_max, coeff_cw_rows;
 };
 
 // Launchers (each enqueues on `st`; frames = batch size). ---------------------

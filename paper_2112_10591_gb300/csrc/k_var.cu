@@ -455,7 +455,7 @@ seg_var_coeff_kernel(const __grid_constant__ SegTable<SegCoeff> tab)
 // wave (at eight blocks, 64 registers, the kernel spilled).
 constexpr int kCWOut = 28;   // output columns per warp
 constexpr int kCWWarps = 4;  // warps per block, row strips stacked
-constexpr int kCWRows = 8;   // output rows per warp
+constexpr int kCWRows = 8;   // output rows per warp (default; ebof_params.coeff_cw_rows)
 
 template <int R, bool IN, typename T, bool COH = false>
 __device__ __forceinline__ void coeff_strip(const T *__restrict__ I0, const T *__restrict__ I0x,
@@ -1179,8 +1179,10 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
     // default the column walk from 1024 px wide (the finest level of 1280 x
     // 720 frames), where it is the faster; smaller levels keep the tile form
     const bool column_walk = lv.w >= fp.coeff_cw_min_width;
+    const int cw_rows = fp.coeff_cw_rows == 4 || fp.coeff_cw_rows == 16 ? fp.coeff_cw_rows
+                                                                       : kCWRows;
     const dim3 wgrd((lv.w + kCWOut - 1) / kCWOut,
-                    ((lv.h + kCWRows - 1) / kCWRows + kCWWarps - 1) / kCWWarps, frames);
+                    ((lv.h + cw_rows - 1) / cw_rows + kCWWarps - 1) / kCWWarps, frames);
     const dim3 sgrd((lv.w + tile_x - 1) / tile_x, (lv.h + tile - 1) / tile, frames);
     // small levels: every outer iteration in one cluster launch per frame
     // (same flow bit for bit), where one cluster holds the level's work and
@@ -1244,18 +1246,21 @@ float *launch_variational_fused(const void *I0, const void *I0x, const void *I0y
     for (int k = 0; k < fp.var_outer; ++k) {
         if (column_walk) {
             StageScope sc(kStVarCoeff, 1, st);
-            if (fp.half)
-                var_coeff_cw_kernel<kCWRows, __half><<<wgrd, dim3(32, kCWWarps), 0, st>>>(
-                    (const __half *)I0, (const __half *)I0x, (const __half *)I0y,
-                    (const __half *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
-                    u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
-                    fp.alpha_s, fp.omega);
-            else
-                var_coeff_cw_kernel<kCWRows, float><<<wgrd, dim3(32, kCWWarps), 0, st>>>(
-                    (const float *)I0, (const float *)I0x, (const float *)I0y,
-                    (const float *)I1, lv.w, lv.h, lv.pitch, pyr_frame_stride, a,
-                    u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta, fp.gamma,
-                    fp.alpha_s, fp.omega);
+#define EBOF_CW(R, T)                                                                          \
+    var_coeff_cw_kernel<R, T><<<wgrd, dim3(32, kCWWarps), 0, st>>>(                             \
+        (const T *)I0, (const T *)I0x, (const T *)I0y, (const T *)I1, lv.w, lv.h, lv.pitch,     \
+        pyr_frame_stride, a, u_frame_stride, lv.plane, coef, coef_frame_stride, fp.delta,       \
+        fp.gamma, fp.alpha_s, fp.omega)
+            if (fp.half) {
+                if (cw_rows == 4) EBOF_CW(4, __half);
+                else if (cw_rows == 16) EBOF_CW(16, __half);
+                else EBOF_CW(kCWRows, __half);
+            } else {
+                if (cw_rows == 4) EBOF_CW(4, float);
+                else if (cw_rows == 16) EBOF_CW(16, float);
+                else EBOF_CW(kCWRows, float);
+            }
+#undef EBOF_CW
         } else {
             StageScope sc(kStVarCoeff, 1, st);
             if (fp.half)

@@ -167,7 +167,8 @@ def test_multigroup_one_graph_matches_single_streams(eb):
 @pytest.mark.parametrize("knob,values", [("sor_tma_min_per_sm", (1, 2, 1 << 20)),
                                          ("sor_row_waves", (0, 2, 4)),
                                          ("coeff_cw_min_width", (160, 640, 1 << 20)),
-                                         ("var_cluster_max", (2, 8, 16))])
+                                         ("var_cluster_max", (2, 8, 16)),
+                                         ("coeff_cw_rows", (4, 16))])
 def test_layout_knobs_never_change_the_flow(eb, knob, values):
     """The variational layouts (the coefficient kernel's form, the SOR forms,
     the cluster-resident refinement of the small levels) tile the same
