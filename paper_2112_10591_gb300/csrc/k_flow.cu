@@ -183,6 +183,7 @@ __device__ __forceinline__ float group_sum(float v)
 template <int PS>
 struct SearchShape {
     static constexpr int kWideCG = PS <= 8 ? 8 : (PS <= 12 ? 4 : 8);
+    static constexpr int kWideRG = 1;
     static constexpr int kNarrowCG = PS <= 8 ? 8 : 16;
     static constexpr int kNarrowRG = PS <= 8 ? 1 : 2;
 };
@@ -655,10 +656,10 @@ void search_ps(const T *I0, const T *I0x, const T *I0y, const T *I1,
     using SS = SearchShape<PS>;
     const int np = lv.npx * lv.npy;
     const bool wide = search_wide(np);
-    const int G = wide ? SS::kWideCG : SS::kNarrowCG * SS::kNarrowRG;
+    const int G = wide ? SS::kWideCG * SS::kWideRG : SS::kNarrowCG * SS::kNarrowRG;
     const int per_block = 128 / G;
     dim3 grd((np + per_block - 1) / per_block, frames);
-    auto kern = wide ? patch_search_kernel<PS, SS::kWideCG, 1, T>
+    auto kern = wide ? patch_search_kernel<PS, SS::kWideCG, SS::kWideRG, T>
                      : patch_search_kernel<PS, SS::kNarrowCG, SS::kNarrowRG, T>;
     kern<<<grd, 128, 0, st>>>(
         I0, I0x, I0y, I1, lv.w, lv.h, lv.pitch, pfs, lv.npx, lv.npy, Uc, lvc ? lvc->w : 0,
@@ -863,7 +864,8 @@ int search_patches_per_block(int ps, bool wide)
     int G = 0;
 #define EBOF_G(N)                                                                                \
     case N:                                                                                      \
-        G = wide ? SearchShape<N>::kWideCG : SearchShape<N>::kNarrowCG * SearchShape<N>::kNarrowRG; \
+        G = wide ? SearchShape<N>::kWideCG * SearchShape<N>::kWideRG                             \
+                 : SearchShape<N>::kNarrowCG * SearchShape<N>::kNarrowRG;                          \
         break;
     switch (ps) {
         EBOF_G(4) EBOF_G(5) EBOF_G(6) EBOF_G(7) EBOF_G(8) EBOF_G(9) EBOF_G(10) EBOF_G(11)
@@ -898,11 +900,11 @@ void launch_seg_search(const SegTable<SegSearch> &t, int blocks, int ps, bool wi
     case N: {                                                                                    \
         using SS = SearchShape<N>;                                                               \
         if (half)                                                                                \
-            (wide ? seg_patch_search_kernel<N, SS::kWideCG, 1, __half>                           \
+            (wide ? seg_patch_search_kernel<N, SS::kWideCG, SS::kWideRG, __half>                 \
                   : seg_patch_search_kernel<N, SS::kNarrowCG, SS::kNarrowRG, __half>)            \
                 <<<blocks, 128, 0, st>>>(t);                                                     \
         else                                                                                     \
-            (wide ? seg_patch_search_kernel<N, SS::kWideCG, 1, float>                            \
+            (wide ? seg_patch_search_kernel<N, SS::kWideCG, SS::kWideRG, float>                  \
                   : seg_patch_search_kernel<N, SS::kNarrowCG, SS::kNarrowRG, float>)             \
                 <<<blocks, 128, 0, st>>>(t);                                                     \
         break;                                                                                   \
