@@ -11,11 +11,13 @@ of events per step, larger than the 129 MB L2).
 
 Prints one JSON line (rank 0).  `value` is the plain path (one
 ebof_process_window call per window); `batched` is the same stream through
-ebof_process_windows; `e2e` goes through ebof_process_window_host with the
-events in pinned host memory and every window's flow written back into a
-pinned host buffer (page-locked buffers are addressed by the kernels over the
-host link, so the events cross it inside the scatter and the flow inside the
-last kernel; the call returns after synchronising);
+ebof_process_windows; `e2e` streams the windows through
+ebof_process_window_host_async with the events in pinned host memory and
+every window's flow written back into a pinned host buffer (page-locked
+buffers are addressed by the kernels over the host link, so the events cross
+it inside the scatter and the flow inside the last kernel), one
+ebof_stream_sync per step; `e2e.synchronous_per_window` is the same through
+ebof_process_window_host, which synchronises after every window;
 `roofline` covers the dominant step, the variational refinement at level 0,
 by its algorithmic bytes (24 B per pixel per outer iteration: I0, I1, U in,
 U out) over its kernels' time, with every stage's fraction and the patch
@@ -1221,18 +1223,46 @@ def main():
                 if r < 0:
                     raise eb.EbofError(r, "process_window_host")
 
-        for _ in range(min(args.warmup, 1)):
-            step_host()
-        barrier()
-        h0 = time.perf_counter()
-        for _ in range(args.steps):
-            step_host()
-        barrier()
-        hms, hval = combine_ranks(1000.0 * (time.perf_counter() - h0),
-                                  frames_per_step * args.steps, world, dist, dev)
+        # streaming: every window enqueued without waiting (its kernels read
+        # the pinned events and write the flow into a ring of 8 pinned host
+        # buffers in place), one synchronisation per step
+        hring = [torch.empty((2, H, W), dtype=torch.float32).pin_memory().numpy()
+                 for _ in range(8)]
+
+        def step_host_async():
+            eb.check(lib.ebof_stream_reset(s.handle), "reset")
+            for k in range(nwin):
+                a, b = off[k], off[k + 1]
+                r = lib.ebof_process_window_host_async(
+                    s.handle, hx.ctypes.data + 2 * a, hy.ctypes.data + 2 * a,
+                    ht.ctypes.data + 8 * a, b - a, tb[k], tb[k] + stream.dt,
+                    hring[k % 8].ctypes.data, handle)
+                if r < 0:
+                    raise eb.EbofError(r, "process_window_host_async")
+            eb.check(lib.ebof_stream_sync(s.handle, None, 0), "sync")
+
+        def timed_host(step):
+            for _ in range(min(args.warmup, 1)):
+                step()
+            barrier()
+            h0 = time.perf_counter()
+            for _ in range(args.steps):
+                step()
+            barrier()
+            return combine_ranks(1000.0 * (time.perf_counter() - h0),
+                                 frames_per_step * args.steps, world, dist, dev)
+
+        _, hval_sync = timed_host(step_host)
+        hms, hval = timed_host(step_host_async)
         e2e = {"value": hval, "unit": UNIT,
                "h2d_bytes_per_step": int(off[-1]) * 12,
-               "d2h_bytes_per_step": nwin * 2 * P * 4}
+               "d2h_bytes_per_step": nwin * 2 * P * 4,
+               "call": "ebof_process_window_host_async per window (pinned events read and "
+                       "flows written in place by the kernels), one ebof_stream_sync per step",
+               "synchronous_per_window": {
+                   "value": hval_sync, "unit": UNIT,
+                   "call": "ebof_process_window_host per window (returns after its "
+                           "stream synchronises)"}}
 
     roofline["a6_patch_search"] = a6_flop_roof(by_level, gl, prm.patch, prm.gn_iters,
                                                clocks.get("sm_mhz"))

@@ -243,6 +243,23 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
                                      const int64_t *h_t, int64_t n_events, int64_t t_begin,
                                      int64_t t_end, float *h_flow, void *cuda_stream);
 
+/* ebof_process_window_host without the synchronisation, for callers that
+ * stream windows and collect the flows later.  When every buffer lies,
+ * whole, inside one page-locked range registered with CUDA, the call only
+ * enqueues and returns: the events are copied in on an internal copy stream,
+ * the window runs on `cuda_stream` (after them), and the flow is copied out
+ * into h_flow on a second internal copy stream, through two device staging
+ * slots used by alternate calls, so that one window's copies overlap its
+ * neighbours' kernels.  h_flow holds the flow once ebof_stream_sync(s)
+ * returns (a synchronisation of `cuda_stream` alone does not cover the copy
+ * out); the buffers must stay valid and unmodified until then.  Otherwise
+ * (pageable buffers) it is ebof_process_window_host itself, synchronous.
+ * Same return values; EBOF_ERR_OOM if the staging slots cannot be made. */
+ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
+                                           const uint16_t *h_y, const int64_t *h_t,
+                                           int64_t n_events, int64_t t_begin, int64_t t_end,
+                                           float *h_flow, void *cuda_stream);
+
 /* Waits for the stream's work, then reports the first device-side error
  * (if any) and copies the counts of the last call's windows into out[0..
  * n_out-1] (n_out may be 0 and out NULL).  The latched error is cleared. */

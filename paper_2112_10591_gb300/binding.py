@@ -154,6 +154,7 @@ def _declare(L):
     L.ebof_server_drain.argtypes = [vp, i32]
     L.ebof_server_get_info.argtypes = [vp, P(ebof_server_info)]
     L.ebof_process_window_host.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, vp]
+    L.ebof_process_window_host_async.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, vp]
     L.ebof_stream_sync.argtypes = [vp, P(ebof_window_stats), i32]
     L.ebof_edt.argtypes = [vp, i32, i32, vp, vp, vp, f32, vp]
     L.ebof_edt_static.argtypes = [vp, i32, i32, vp, vp, f32, vp]
@@ -182,7 +183,8 @@ def _declare(L):
     L.ebof_debug_fail_allocation.restype = None
     for name in ("ebof_stream_create", "ebof_stream_destroy", "ebof_stream_reset",
                  "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
-                 "ebof_process_window_host", "ebof_stream_sync", "ebof_edt",
+                 "ebof_process_window_host", "ebof_process_window_host_async",
+                 "ebof_stream_sync", "ebof_edt",
                  "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static",
                  "ebof_stream_get_profile_level", "ebof_group_create", "ebof_group_destroy",
                  "ebof_group_reset", "ebof_group_process", "ebof_group_sync",
@@ -376,6 +378,20 @@ def ebof_process_window_host(stream: Stream, x, y, t, t_begin: int, t_end: int, 
     W, H = stream.params.width, stream.params.height
     n = len(x)
     return load().ebof_process_window_host(
+        stream.handle, _hptr(x, np.uint16, n, "x"), _hptr(y, np.uint16, n, "y"),
+        _hptr(t, np.int64, n, "t"), n, int(t_begin), int(t_end),
+        _hptr(flow, np.float32, 2 * W * H, "flow"), _stream_handle(cuda_stream))
+
+
+def ebof_process_window_host_async(stream: Stream, x, y, t, t_begin: int, t_end: int, flow,
+                                   cuda_stream=None) -> int:
+    """As ebof_process_window_host, returning before the work completes when
+    every buffer is page-locked (the buffers must then stay alive until
+    ebof_stream_sync)."""
+    import numpy as np
+    W, H = stream.params.width, stream.params.height
+    n = len(x)
+    return load().ebof_process_window_host_async(
         stream.handle, _hptr(x, np.uint16, n, "x"), _hptr(y, np.uint16, n, "y"),
         _hptr(t, np.int64, n, "t"), n, int(t_begin), int(t_end),
         _hptr(flow, np.float32, 2 * W * H, "flow"), _stream_handle(cuda_stream))

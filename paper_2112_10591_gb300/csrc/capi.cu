@@ -96,6 +96,20 @@ struct ebof_stream {
     bool last_list = false;
     cudaStream_t cap = nullptr;
     CoefMaps cmaps;  // tensor maps of the variational coefficient planes per level
+    // asynchronous host-buffer calls (ebof_process_window_host_async): the
+    // events go in on stream h2d, the flow comes back on stream d2h, both
+    // through two device staging slots used alternately, so that the copies
+    // of one window overlap the kernels of its neighbours
+    struct HostPipe {
+        cudaStream_t h2d = nullptr, d2h = nullptr;
+        cudaEvent_t in_done[2] = {}, run_done[2] = {}, out_done[2] = {};
+        bool used[2] = {false, false};
+        void *ev[2] = {nullptr, nullptr};
+        size_t ev_bytes[2] = {0, 0};
+        float *flow[2] = {nullptr, nullptr};
+        int slot = 0;
+        bool ready = false;
+    } pipe;
 };
 
 struct ebof_group {
@@ -268,6 +282,17 @@ void free_all(ebof_stream *s)
         if (ge) cudaGraphExecDestroy(ge);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->done) cudaEventDestroy(s->done);
+    auto &q = s->pipe;
+    for (int j = 0; j < 2; ++j) {
+        if (q.used[j]) cudaEventSynchronize(q.out_done[j]);
+        cudaFree(q.ev[j]);
+        cudaFree(q.flow[j]);
+        if (q.in_done[j]) cudaEventDestroy(q.in_done[j]);
+        if (q.run_done[j]) cudaEventDestroy(q.run_done[j]);
+        if (q.out_done[j]) cudaEventDestroy(q.out_done[j]);
+    }
+    if (q.h2d) cudaStreamDestroy(q.h2d);
+    if (q.d2h) cudaStreamDestroy(q.d2h);
 }
 
 SurfaceMap surface_map(const ebof_params &p)
@@ -1398,6 +1423,108 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
     return r;
 }
 
+ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
+                                           const uint16_t *h_y, const int64_t *h_t,
+                                           int64_t n_events, int64_t t_begin, int64_t t_end,
+                                           float *h_flow, void *cuda_stream)
+{
+    if (!s || !h_flow || !events_ok(h_x, h_y, h_t, n_events) || t_end < t_begin)
+        return EBOF_ERR_INVALID_ARG;
+    const size_t n = (size_t)n_events;
+    const size_t flow_bytes = sizeof(float) * 2 * (size_t)s->p.width * s->p.height;
+    bool pinned;
+    {
+        DeviceGuard dg(s->device);
+        if (!dg.ok) return EBOF_ERR_CUDA;
+        pinned = device_addressable(h_flow, flow_bytes) &&
+                 (n == 0 || (device_addressable(h_x, 2 * n) && device_addressable(h_y, 2 * n) &&
+                             device_addressable(h_t, 8 * n)));
+    }
+    // pageable buffers: the synchronous staged call
+    if (!pinned)
+        return ebof_process_window_host(s, h_x, h_y, h_t, n_events, t_begin, t_end, h_flow,
+                                        cuda_stream);
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    auto &q = s->pipe;
+    if (!q.ready) {
+        bool ok = cudaStreamCreateWithFlags(&q.h2d, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&q.d2h, cudaStreamNonBlocking) == cudaSuccess;
+        for (int j = 0; j < 2 && ok; ++j) {
+            ok &= cudaEventCreateWithFlags(&q.in_done[j], cudaEventDisableTiming) == cudaSuccess;
+            ok &= cudaEventCreateWithFlags(&q.run_done[j], cudaEventDisableTiming) == cudaSuccess;
+            ok &= cudaEventCreateWithFlags(&q.out_done[j], cudaEventDisableTiming) == cudaSuccess;
+            ok &= dmalloc(&q.flow[j], flow_bytes) == cudaSuccess;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            // undo, so that a later call starts again from nothing
+            for (int k = 0; k < 2; ++k) {
+                cudaFree(q.flow[k]);
+                q.flow[k] = nullptr;
+                for (cudaEvent_t *e : {&q.in_done[k], &q.run_done[k], &q.out_done[k]})
+                    if (*e) {
+                        cudaEventDestroy(*e);
+                        *e = nullptr;
+                    }
+            }
+            for (cudaStream_t *x : {&q.h2d, &q.d2h})
+                if (*x) {
+                    cudaStreamDestroy(*x);
+                    *x = nullptr;
+                }
+            return EBOF_ERR_OOM;
+        }
+        q.ready = true;
+    }
+    const int j = q.slot;
+    // the slot's events buffer: the window two calls back must have read it
+    const size_t bx = ((2 * n + 255) / 256) * 256;
+    const size_t need = 2 * bx + 8 * n;
+    if (need > q.ev_bytes[j]) {
+        if (q.used[j]) cudaEventSynchronize(q.run_done[j]);
+        cudaFree(q.ev[j]);
+        q.ev[j] = nullptr;
+        q.ev_bytes[j] = 0;
+        const size_t bytes = std::max<size_t>(need, 1 << 20);
+        if (dmalloc(&q.ev[j], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return EBOF_ERR_OOM;
+        }
+        q.ev_bytes[j] = bytes;
+    }
+    char *base = (char *)q.ev[j];
+    uint16_t *dx = (uint16_t *)base;
+    uint16_t *dy = (uint16_t *)(base + bx);
+    int64_t *dt = (int64_t *)(base + 2 * bx);
+    // events in: after the window two calls back has run (it read this slot)
+    if (q.used[j]) cudaStreamWaitEvent(q.h2d, q.run_done[j], 0);
+    if (n) {
+        cudaMemcpyAsync(dx, h_x, 2 * n, cudaMemcpyHostToDevice, q.h2d);
+        cudaMemcpyAsync(dy, h_y, 2 * n, cudaMemcpyHostToDevice, q.h2d);
+        cudaMemcpyAsync(dt, h_t, 8 * n, cudaMemcpyHostToDevice, q.h2d);
+    }
+    cudaEventRecord(q.in_done[j], q.h2d);
+    // the window: after its events are in and the slot's previous flow is out
+    cudaStreamWaitEvent(st, q.in_done[j], 0);
+    if (q.used[j]) cudaStreamWaitEvent(st, q.out_done[j], 0);
+    const ebof_status r = run(s, 1, dx, dy, dt, n_events, t_begin, t_end - t_begin, nullptr,
+                              q.flow[j], nullptr, nullptr, nullptr, st);
+    if (r < 0) return r;
+    // flow out, overlapping the next window's kernels
+    cudaEventRecord(q.run_done[j], st);
+    cudaStreamWaitEvent(q.d2h, q.run_done[j], 0);
+    cudaMemcpyAsync(h_flow, q.flow[j], flow_bytes, cudaMemcpyDeviceToHost, q.d2h);
+    cudaEventRecord(q.out_done[j], q.d2h);
+    q.used[j] = true;
+    q.slot = j ^ 1;
+    if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
+    return r;
+}
+
 ebof_status ebof_stream_set_wait_limit(ebof_stream *s, int64_t iterations)
 {
     if (!s) return EBOF_ERR_INVALID_ARG;
@@ -1417,6 +1544,9 @@ ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_o
     DeviceGuard dg(s->device);
     if (!dg.ok) return EBOF_ERR_CUDA;
     if (s->have_last && cudaEventSynchronize(s->done) != cudaSuccess) return EBOF_ERR_CUDA;
+    for (int j = 0; j < 2; ++j)
+        if (s->pipe.used[j] && cudaEventSynchronize(s->pipe.out_done[j]) != cudaSuccess)
+            return EBOF_ERR_CUDA;
     int err = 0;
     if (cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return EBOF_ERR_CUDA;

@@ -400,6 +400,29 @@ def test_reset_interleave_host_and_errors(eb):
         st = eb.ebof_process_window_host(d, xp, yp, tp, tb, te, hfp)
         assert st == (eb.EBOF_NO_PREVIOUS if k == 0 else eb.EBOF_OK)
         assert np.array_equal(hfp.reshape(2, H, W), ra[k]["flow"]), k
+    # the asynchronous variant: every window enqueued before one sync, each
+    # into its own page-locked flow buffer (events in and flows out on the
+    # stream's copy streams, through alternating staging slots); the same flows
+    _, e = make_stream(eb, W, H)
+    keep, outs = [], []
+    for k in range(3):
+        x, y, t, p, tb, te = s_.window(k)
+        (xp, xb), (yp, yb), (tp, tbuf) = pinned(x), pinned(y), pinned(t)
+        hf_k, hf_buf = pinned(np.full((2 * H * W,), np.nan, np.float32))
+        keep.append((xb, yb, tbuf, hf_buf))
+        st = eb.ebof_process_window_host_async(e, xp, yp, tp, tb, te, hf_k)
+        assert st == (eb.EBOF_NO_PREVIOUS if k == 0 else eb.EBOF_OK)
+        outs.append(hf_k)
+    assert eb.ebof_stream_sync(e, 1)[0] == eb.EBOF_OK
+    for k in range(3):
+        assert np.array_equal(outs[k].reshape(2, H, W), ra[k]["flow"]), k
+    # pageable buffers take the synchronous staged call
+    x, y, t, p, tb, te = s_.window(1)
+    hf = np.empty((2, H, W), np.float32)
+    assert eb.ebof_process_window_host_async(e, np.ascontiguousarray(x), np.ascontiguousarray(y),
+                                             np.ascontiguousarray(t), tb, te, hf) == eb.EBOF_OK
+    assert np.isfinite(hf).all()
+    e.close()
     # argument errors enqueue nothing
     x, y, t, p, tb, te = s_.window(0)
     lib = eb.load()
