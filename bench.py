@@ -9,8 +9,12 @@ search, densification, variational refinement) over every window of the
 stream, with all events resident in HBM before the timed region (715 MB
 of events per step, larger than the 129 MB L2).
 
-Prints one JSON line (rank 0).  `value` is the plain path (one
-ebof_process_window call per window); `batched` is the same stream through
+Prints one JSON line (rank 0).  `value` is one window per call through the
+pipelined ebof_process_window_async (a window's front end overlaps the
+previous window's flow levels; CUDA events on the caller's stream, the step
+closed by ebof_stream_join); `in_order` the same windows through
+ebof_process_window (every stage of a window in order on the caller's
+stream), which also gives the per-window latencies; `batched` is the same stream through
 ebof_process_windows; `e2e` streams the windows through
 ebof_process_window_host_async with the events in pinned host memory and
 every window's flow written back into a pinned host buffer (page-locked
@@ -1010,10 +1014,45 @@ def main():
     barrier()
     wall = time.perf_counter() - w0
     lat += [evs_a[k].elapsed_time(evs_b[k]) for k in range(1, nwin)]
+    launches_in_order = eb.ebof_kernel_launches() - launches0
+    ms_in_order, value_in_order = combine_ranks(t_start.elapsed_time(t_end),
+                                                frames_per_step * args.steps, world, dist, dev)
+
+    # the same windows through the pipelined call: each window's front end
+    # overlaps the previous window's flow levels; the timed region on the
+    # caller's stream is closed by ebof_stream_join
+    def step_pipelined():
+        eb.check(lib.ebof_stream_reset(s.handle), "reset")
+        for k in range(nwin):
+            a, b = off[k], off[k + 1]
+            r = lib.ebof_process_window_async(
+                s.handle, xs.data_ptr() + 2 * a, ys.data_ptr() + 2 * a, ts.data_ptr() + 8 * a,
+                ps.data_ptr() + a, b - a, tb[k], tb[k] + stream.dt, flows[k].data_ptr(), handle)
+            if r < 0:
+                raise eb.EbofError(r, "process_window_async")
+        eb.check(lib.ebof_stream_join(s.handle, handle), "join")
+
+    for _ in range(args.warmup):
+        step_pipelined()
+    barrier()
+    p_start = torch.cuda.Event(enable_timing=True)
+    p_end = torch.cuda.Event(enable_timing=True)
+    launches0 = eb.ebof_kernel_launches()
+    p_start.record(cs)
+    for _ in range(args.steps):
+        step_pipelined()
+    p_end.record(cs)
+    barrier()
     launches = eb.ebof_kernel_launches() - launches0
     clocks = clk.stop()
-    ms, value = combine_ranks(t_start.elapsed_time(t_end), frames_per_step * args.steps, world,
-                              dist, dev)
+    # `value`: the pipelined calls; `in_order`: each window's stages in order
+    # on the caller's stream (the latencies above)
+    ms, value = combine_ranks(p_start.elapsed_time(p_end), frames_per_step * args.steps,
+                              world, dist, dev)
+    in_order = {"value": value_in_order, "unit": UNIT, "ms_per_step": ms_in_order / args.steps,
+                "gpu_launches": int(launches_in_order),
+                "call": "ebof_process_window per window: every stage of a window in order on "
+                        "the caller's stream, one CUDA graph replay per window"}
 
     # stage profile over the same steps (events bracket each stage's launches)
     eb.check(eb.ebof_stream_set_profiling(s, True))
@@ -1279,12 +1318,16 @@ def main():
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": bench_config(_params_dict(prm), nwin, world),
-            "path": "plain: one ebof_process_window call per window (graph replay)",
+            "path": "one window per call, pipelined (ebof_process_window_async: a window's "
+                    "front end on one internal stream overlaps the previous window's flow "
+                    "on another, graph replays, ebof_stream_join closes the step); "
+                    "latencies from in-order ebof_process_window calls",
             "events_mb_per_step": int(off[-1]) * 13 / 1e6,
             "p50_latency_ms": float(np.percentile(lat, 50)),
             "p99_latency_ms": float(np.percentile(lat, 99)),
             "mpx_per_s": value * P / 1e6,
             "wall_s": wall,
+            "in_order": in_order,
             "batched": batched,
             "config0_346x260": config0,
             "epe_vs_oracle": epe,

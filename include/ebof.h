@@ -243,22 +243,44 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
                                      const int64_t *h_t, int64_t n_events, int64_t t_begin,
                                      int64_t t_end, float *h_flow, void *cuda_stream);
 
-/* ebof_process_window_host without the synchronisation, for callers that
- * stream windows and collect the flows later.  When every buffer lies,
+/* Pipelined windows (§III-A..§III-D per window, as ebof_process_window):
+ * for callers that stream windows and collect the flows later.  The call
+ * enqueues and returns; the window's front end (events to the pyramid) runs
+ * on an internal stream after the caller's work on `cuda_stream` so far, and
+ * its flow on a second internal stream after its front end, with three
+ * pyramid slots of the stream's own, so that each window's front end
+ * overlaps the previous window's flow levels.  Nothing is enqueued on
+ * `cuda_stream`: d_flow holds the flow, and the event buffers may be reused,
+ * once ebof_stream_sync(s) returns.  Results are bit-identical to
+ * ebof_process_window; the two kinds of call may be mixed on one stream
+ * (the newest window's pyramid is handed over with one device copy).
+ * Same return values; EBOF_ERR_OOM if the pipeline's slots (three pyramid
+ * slots) cannot be allocated. */
+ebof_status ebof_process_window_async(ebof_stream *s, const uint16_t *d_x, const uint16_t *d_y,
+                                      const int64_t *d_t, const int8_t *d_p, int64_t n_events,
+                                      int64_t t_begin, int64_t t_end, float *d_flow,
+                                      void *cuda_stream);
+
+/* ebof_process_window_async with HOST buffers.  When every buffer lies,
  * whole, inside one page-locked range registered with CUDA, the call only
  * enqueues and returns: the events are copied in on an internal copy stream,
- * the window runs on `cuda_stream` (after them), and the flow is copied out
- * into h_flow on a second internal copy stream, through two device staging
- * slots used by alternate calls, so that one window's copies overlap its
- * neighbours' kernels.  h_flow holds the flow once ebof_stream_sync(s)
- * returns (a synchronisation of `cuda_stream` alone does not cover the copy
- * out); the buffers must stay valid and unmodified until then.  Otherwise
- * (pageable buffers) it is ebof_process_window_host itself, synchronous.
- * Same return values; EBOF_ERR_OOM if the staging slots cannot be made. */
+ * the window runs pipelined as in ebof_process_window_async, and the flow is
+ * copied out into h_flow on a second internal copy stream, through two
+ * device staging slots used by alternate calls, so that a window's copies
+ * overlap its neighbours' kernels.  `cuda_stream` is not used.  h_flow holds
+ * the flow once ebof_stream_sync(s) returns; the buffers must stay valid and
+ * unmodified until then.  Otherwise (pageable buffers) it is
+ * ebof_process_window_host itself, synchronous.  Same return values;
+ * EBOF_ERR_OOM if the staging slots cannot be made. */
 ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
                                            const uint16_t *h_y, const int64_t *h_t,
                                            int64_t n_events, int64_t t_begin, int64_t t_end,
                                            float *h_flow, void *cuda_stream);
+
+/* Makes the work enqueued on `cuda_stream` after this call wait for
+ * everything the stream `s` has enqueued so far, including the pipelined
+ * windows and their copies out (without blocking the host). */
+ebof_status ebof_stream_join(ebof_stream *s, void *cuda_stream);
 
 /* Waits for the stream's work, then reports the first device-side error
  * (if any) and copies the counts of the last call's windows into out[0..

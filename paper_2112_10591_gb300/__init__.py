@@ -9,7 +9,7 @@ from .binding import (  # noqa: F401
     EBOF_ERR_OOM, EBOF_ERR_TIMEOUT, EBOF_ERR_UNSUPPORTED, EBOF_NO_PREVIOUS, EBOF_OK,
     EbofError, Stream, check, ebof_alpha_from_dsat, ebof_default_params, ebof_edt,
     ebof_params, ebof_process_surface, ebof_process_window, ebof_process_window_host,
-    ebof_process_window_host_async,
+    ebof_process_window_host_async, ebof_process_window_async, ebof_stream_join,
     ebof_process_windows, ebof_status_string, ebof_stream_create, ebof_stream_destroy,
     ebof_stream_reset, ebof_stream_sync, ebof_window_stats, library_path, load,
     EBOF_STAGE_COUNT, ebof_kernel_launches, ebof_stage_name, ebof_stream_get_profile,

@@ -155,6 +155,8 @@ def _declare(L):
     L.ebof_server_get_info.argtypes = [vp, P(ebof_server_info)]
     L.ebof_process_window_host.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, vp]
     L.ebof_process_window_host_async.argtypes = [vp, vp, vp, vp, i64, i64, i64, vp, vp]
+    L.ebof_process_window_async.argtypes = [vp, vp, vp, vp, vp, i64, i64, i64, vp, vp]
+    L.ebof_stream_join.argtypes = [vp, vp]
     L.ebof_stream_sync.argtypes = [vp, P(ebof_window_stats), i32]
     L.ebof_edt.argtypes = [vp, i32, i32, vp, vp, vp, f32, vp]
     L.ebof_edt_static.argtypes = [vp, i32, i32, vp, vp, f32, vp]
@@ -184,6 +186,7 @@ def _declare(L):
     for name in ("ebof_stream_create", "ebof_stream_destroy", "ebof_stream_reset",
                  "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
                  "ebof_process_window_host", "ebof_process_window_host_async",
+                 "ebof_process_window_async", "ebof_stream_join",
                  "ebof_stream_sync", "ebof_edt",
                  "ebof_stream_set_profiling", "ebof_stream_get_profile", "ebof_edt_static",
                  "ebof_stream_get_profile_level", "ebof_group_create", "ebof_group_destroy",
@@ -317,6 +320,20 @@ def ebof_process_window(stream: Stream, x, y, t, p, t_begin: int, t_end: int, fl
         _ptr(surface, torch.float32, W * H, "surface", dev), _stream_handle(cuda_stream))
 
 
+def ebof_process_window_async(stream: Stream, x, y, t, p, t_begin: int, t_end: int, flow,
+                              cuda_stream=None) -> int:
+    """Pipelined window: returns after enqueueing; the flow is in `flow` (and
+    the event tensors may be reused) once ebof_stream_sync returns."""
+    import torch
+    W, H, dev = stream.params.width, stream.params.height, stream.device
+    n = 0 if x is None else x.numel()
+    return load().ebof_process_window_async(
+        stream.handle, _ptr(x, torch.uint16, n, "x", dev), _ptr(y, torch.uint16, n, "y", dev),
+        _ptr(t, torch.int64, n, "t", dev), _ptr(p, torch.int8, n, "p", dev), n, int(t_begin),
+        int(t_end), _ptr(flow, torch.float32, 2 * W * H, "flow", dev),
+        _stream_handle(cuda_stream))
+
+
 def ebof_process_windows(stream: Stream, n_windows: int, x, y, t, p, t_begin: int, dt: int,
                          flow, edge=None, edt=None, surface=None, cuda_stream=None) -> int:
     import torch
@@ -385,9 +402,9 @@ def ebof_process_window_host(stream: Stream, x, y, t, t_begin: int, t_end: int, 
 
 def ebof_process_window_host_async(stream: Stream, x, y, t, t_begin: int, t_end: int, flow,
                                    cuda_stream=None) -> int:
-    """As ebof_process_window_host, returning before the work completes when
-    every buffer is page-locked (the buffers must then stay alive until
-    ebof_stream_sync)."""
+    """As ebof_process_window_async with host buffers: returns before the
+    work completes when every buffer is page-locked (the buffers must then
+    stay alive until ebof_stream_sync)."""
     import numpy as np
     W, H = stream.params.width, stream.params.height
     n = len(x)
@@ -395,6 +412,11 @@ def ebof_process_window_host_async(stream: Stream, x, y, t, t_begin: int, t_end:
         stream.handle, _hptr(x, np.uint16, n, "x"), _hptr(y, np.uint16, n, "y"),
         _hptr(t, np.int64, n, "t"), n, int(t_begin), int(t_end),
         _hptr(flow, np.float32, 2 * W * H, "flow"), _stream_handle(cuda_stream))
+
+
+def ebof_stream_join(stream: Stream, cuda_stream=None) -> int:
+    """Makes later work on cuda_stream wait for all of the stream's work."""
+    return load().ebof_stream_join(stream.handle, _stream_handle(cuda_stream))
 
 
 def ebof_stream_sync(stream: Stream, n_out: int = 1):

@@ -110,6 +110,25 @@ struct ebof_stream {
         int slot = 0;
         bool ready = false;
     } pipe;
+    // pipelined calls (ebof_process_window_async, ebof_process_window_host_async):
+    // a window's front end (A1-A5) runs on stream `front`, its flow (A6-A9) on
+    // stream `flow`, with three pyramid slots of their own, so that a
+    // window's front end overlaps the previous window's flow levels
+    struct Pipeline {
+        bool ready = false;
+        cudaStream_t front = nullptr, flow = nullptr;
+        char *pyr = nullptr;   // three slots
+        char *call = nullptr;  // per slot: the window's descriptor and flow destination
+        std::vector<char> h_call;
+        int head = 0;            // slot of the newest window
+        bool has_prev = false;   // the newest window is in these slots
+        bool latest = false;     // these slots, not the ordinary ones, hold the newest window
+        cudaEvent_t inputs = nullptr;
+        cudaEvent_t front_done[3] = {}, flow_done[3] = {};
+        bool flow_used[3] = {false, false, false};
+        cudaGraphExec_t front_graph[3] = {}, flow_graph[3] = {};
+        long long front_k[3] = {}, flow_k[3] = {};
+    } pl;
 };
 
 struct ebof_group {
@@ -293,6 +312,20 @@ void free_all(ebof_stream *s)
     }
     if (q.h2d) cudaStreamDestroy(q.h2d);
     if (q.d2h) cudaStreamDestroy(q.d2h);
+    auto &L = s->pl;
+    if (L.front) cudaStreamSynchronize(L.front);
+    if (L.flow) cudaStreamSynchronize(L.flow);
+    for (int j = 0; j < 3; ++j) {
+        if (L.front_graph[j]) cudaGraphExecDestroy(L.front_graph[j]);
+        if (L.flow_graph[j]) cudaGraphExecDestroy(L.flow_graph[j]);
+        if (L.front_done[j]) cudaEventDestroy(L.front_done[j]);
+        if (L.flow_done[j]) cudaEventDestroy(L.flow_done[j]);
+    }
+    if (L.inputs) cudaEventDestroy(L.inputs);
+    cudaFree(L.pyr);
+    cudaFree(L.call);
+    if (L.front) cudaStreamDestroy(L.front);
+    if (L.flow) cudaStreamDestroy(L.flow);
 }
 
 SurfaceMap surface_map(const ebof_params &p)
@@ -339,42 +372,54 @@ FlowParams flow_params(const ebof_params &p)
 // (so the same sequence can be captured into a graph).  With `via_args`, the
 // events and flow destination of window k are read from s->d_wins[k] and
 // s->d_flows[k].
+// Parts of the sequence (enqueue's `parts`): A1-A5 of the current windows,
+// A6-A9 of the windows that have a previous one.
+constexpr int kPartFront = 1, kPartFlow = 2, kPartAll = 3;
+
 void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const int64_t *t,
              int64_t nev, int64_t t_begin, int64_t dt, const float *surface_in, float *d_flow,
              uint8_t *d_edge, int32_t *d_edt, float *d_surface, bool via_args, int cur_first,
-             int prev_first, bool had_prev, cudaStream_t st)
+             int prev_first, bool had_prev, cudaStream_t st, int parts = kPartAll,
+             char *pyr = nullptr, const ebof_window_desc *d_wins = nullptr,
+             float *const *d_flows = nullptr)
 {
     const ebof_params &p = s->p;
     const Geometry &geo = s->geo;
     const int W = p.width, H = p.height;
+    if (!pyr) pyr = s->pyr;
+    if (!d_wins) d_wins = s->d_wins;
+    if (!d_flows) d_flows = s->d_flows;
     tl_level = -1;
-    cudaMemsetAsync(s->dstats, 0, sizeof(DevStats) * n, st);
-    cudaMemsetAsync(s->d_dropped_time, 0, sizeof(unsigned long long), st);
     const bool half = p.storage == EBOF_STORAGE_FP16;
     const size_t es = s->es;
-    char *I0cur = s->pyr + (size_t)cur_first * s->pyr_fs * es;
+    char *I0cur = pyr + (size_t)cur_first * s->pyr_fs * es;
+    if (parts & kPartFront) {
+        cudaMemsetAsync(s->dstats, 0, sizeof(DevStats) * n, st);
+        cudaMemsetAsync(s->d_dropped_time, 0, sizeof(unsigned long long), st);
 
-    if (surface_in) {
-        launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, half,
-                                    surface_map(p), st);
-    } else {
-        cudaMemsetAsync(s->E, 0, s->e_fs * n, st);
-        if (via_args)
-            launch_scatter_desc(s->d_wins, n, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
-                                s->d_dropped_time, st);
-        else
-            launch_scatter(x, y, t, nev, t_begin, dt, n, W, H, s->pitch0, s->E, s->e_fs,
-                           s->dstats, s->d_dropped_time, st);
-        launch_denoise_fill(s->E, s->Ed, s->Edf, W, H, s->pitch0, s->e_fs, n, p.connectivity,
-                            p.n_d, p.n_f, d_edge, s->dstats, st);
-        launch_edt_columns(s->Edf, s->pitch0, s->e_fs, W, H, s->g, s->pitch0, s->g_fs, n, st);
-        launch_edt_rows_surface(s->g, s->pitch0, s->g_fs, W, H, surface_map(p), d_edt, d_surface,
-                                I0cur, s->pitch0, s->pyr_fs, n, half, st);
+        if (surface_in) {
+            launch_surface_to_intensity(surface_in, W, H, I0cur, s->pitch0, half,
+                                        surface_map(p), st);
+        } else {
+            cudaMemsetAsync(s->E, 0, s->e_fs * n, st);
+            if (via_args)
+                launch_scatter_desc(d_wins, n, W, H, s->pitch0, s->E, s->e_fs, s->dstats,
+                                    s->d_dropped_time, st);
+            else
+                launch_scatter(x, y, t, nev, t_begin, dt, n, W, H, s->pitch0, s->E, s->e_fs,
+                               s->dstats, s->d_dropped_time, st);
+            launch_denoise_fill(s->E, s->Ed, s->Edf, W, H, s->pitch0, s->e_fs, n, p.connectivity,
+                                p.n_d, p.n_f, d_edge, s->dstats, st);
+            launch_edt_columns(s->Edf, s->pitch0, s->e_fs, W, H, s->g, s->pitch0, s->g_fs, n, st);
+            launch_edt_rows_surface(s->g, s->pitch0, s->g_fs, W, H, surface_map(p), d_edt,
+                                    d_surface, I0cur, s->pitch0, s->pyr_fs, n, half, st);
+        }
+
+        // A5: pyramid and gradients of the current window(s)
+        tl_level = 0;
+        launch_pyramid(I0cur, geo, s->pyr_fs, n, half, st);
     }
-
-    // A5: pyramid and gradients of the current window(s)
-    tl_level = 0;
-    launch_pyramid(I0cur, geo, s->pyr_fs, n, half, st);
+    if (!(parts & kPartFlow)) return;
 
     // A6-A9: flow for every window that has a previous one
     const int ff = had_prev ? 0 : 1;
@@ -389,8 +434,8 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
         for (int l = geo.levels - 1; l >= 0; --l) {
             tl_level = l;
             const Level &lv = geo.lv[l];
-            const char *I0 = s->pyr + ((size_t)prev_first * s->pyr_fs + geo.pyr_off[l]) * es;
-            const char *I1 = s->pyr + ((size_t)curf_first * s->pyr_fs + geo.pyr_off[l]) * es;
+            const char *I0 = pyr + ((size_t)prev_first * s->pyr_fs + geo.pyr_off[l]) * es;
+            const char *I1 = pyr + ((size_t)curf_first * s->pyr_fs + geo.pyr_off[l]) * es;
             const char *I0x = I0 + lv.plane * es, *I0y = I0 + 2 * lv.plane * es;
             Ucur = (Uc == s->Ua) ? s->Ub : s->Ua;
             launch_patch_search(I0, I0x, I0y, I1, lv, s->pyr_fs, Uc, lvc, s->u_fs, s->up,
@@ -406,7 +451,7 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
         }
         tl_level = -1;
         if (via_args)
-            launch_flow_out_ptr(Ucur, W, H, s->pitch0, s->u_fs, s->d_flows + ff, nf, st);
+            launch_flow_out_ptr(Ucur, W, H, s->pitch0, s->u_fs, d_flows + ff, nf, st);
         else
             launch_flow_out(Ucur, W, H, s->pitch0, s->u_fs, d_flow + (size_t)ff * flow_frame,
                             nf, st);
@@ -438,7 +483,8 @@ void stage_call(ebof_stream *s, int n, const ebof_window_desc *wins, float *cons
 // already queued on st.  Returns nullptr on failure; *kernels gets the number
 // of kernels in the graph.
 cudaGraphExec_t capture(ebof_stream *s, int n, int cur_first, int prev_first, cudaStream_t st,
-                        long long *kernels)
+                        long long *kernels, int parts = kPartAll, char *pyr = nullptr,
+                        const ebof_window_desc *d_wins = nullptr, float *const *d_flows = nullptr)
 {
     cudaEvent_t ready;
     cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
@@ -452,7 +498,7 @@ cudaGraphExec_t capture(ebof_stream *s, int n, int cur_first, int prev_first, cu
         Profiler *keep = tl_prof;
         tl_prof = nullptr;
         enqueue(s, n, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, nullptr,
-                nullptr, true, cur_first, prev_first, true, s->cap);
+                nullptr, true, cur_first, prev_first, true, s->cap, parts, pyr, d_wins, d_flows);
         tl_prof = keep;
         cudaStreamEndCapture(s->cap, &gr);
     }
@@ -468,11 +514,14 @@ cudaGraphExec_t capture(ebof_stream *s, int n, int cur_first, int prev_first, cu
 // window's pyramid is moved to slot 0 (if it is not there) and the current
 // windows go to slots 1..n, so the enqueued sequence depends on n alone and is
 // replayed from list_graph[n].
+void pipeline_leave(ebof_stream *s, cudaStream_t st);
+
 ebof_status run_list(ebof_stream *s, int n, const ebof_window_desc *wins, float *const *flows,
                      cudaStream_t st)
 {
     ProfScope prof_scope(&s->prof);
     cudaGetLastError();
+    pipeline_leave(s, st);
     if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
     const bool had_prev = s->has_prev;
     if (had_prev && s->head != 0)
@@ -521,6 +570,7 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
 {
     ProfScope prof_scope(&s->prof);
     cudaGetLastError();  // start from a clean error state
+    pipeline_leave(s, st);
     if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
 
     if (n > 1 && s->head + n >= s->nslots) {
@@ -568,6 +618,163 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
     return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
 }
 
+// ----------------------------------------------------------------- pipelined calls
+constexpr size_t kPipeCallBytes = 128;  // per slot: one ebof_window_desc, one float *
+
+ebof_window_desc *pipe_wins(ebof_stream *s, int j)
+{
+    return (ebof_window_desc *)(s->pl.call + (size_t)j * kPipeCallBytes);
+}
+
+float **pipe_flows(ebof_stream *s, int j)
+{
+    return (float **)(s->pl.call + (size_t)j * kPipeCallBytes + 64);
+}
+
+// Streams, events, slots and descriptor blocks of the pipelined calls, made
+// on first use.  On failure everything made here is released again.
+ebof_status pipeline_ready(ebof_stream *s)
+{
+    auto &L = s->pl;
+    if (L.ready) return EBOF_OK;
+    static_assert(sizeof(ebof_window_desc) <= 64, "descriptor block");
+    bool ok = cudaStreamCreateWithFlags(&L.front, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&L.flow, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&L.inputs, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; j < 3 && ok; ++j)
+        ok = cudaEventCreateWithFlags(&L.front_done[j], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&L.flow_done[j], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && dmalloc(&L.pyr, s->es * s->pyr_fs * 3) == cudaSuccess &&
+         dmalloc(&L.call, 3 * kPipeCallBytes) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (int j = 0; j < 3; ++j) {
+            if (L.front_done[j]) cudaEventDestroy(L.front_done[j]);
+            if (L.flow_done[j]) cudaEventDestroy(L.flow_done[j]);
+            L.front_done[j] = L.flow_done[j] = nullptr;
+        }
+        if (L.inputs) cudaEventDestroy(L.inputs);
+        if (L.front) cudaStreamDestroy(L.front);
+        if (L.flow) cudaStreamDestroy(L.flow);
+        cudaFree(L.pyr);
+        cudaFree(L.call);
+        L.inputs = nullptr;
+        L.front = L.flow = nullptr;
+        L.pyr = L.call = nullptr;
+        return EBOF_ERR_OOM;
+    }
+    L.h_call.assign(3 * kPipeCallBytes, 0);
+    L.ready = true;
+    return EBOF_OK;
+}
+
+// The ordinary calls and the pipelined ones keep their own pyramid slots;
+// the newest window's pyramid moves over, with one copy, when the kind of
+// call changes (after the work that wrote it).
+void pipeline_enter(ebof_stream *s)
+{
+    auto &L = s->pl;
+    if (L.latest) return;
+    L.has_prev = s->has_prev;
+    if (s->has_prev) {
+        if (s->have_last) cudaStreamWaitEvent(L.front, s->done, 0);
+        const size_t slot = s->pyr_fs * s->es;
+        cudaMemcpyAsync(L.pyr + (size_t)L.head * slot, s->pyr + (size_t)s->head * slot, slot,
+                        cudaMemcpyDeviceToDevice, L.front);
+    }
+    L.latest = true;
+}
+
+void pipeline_leave(ebof_stream *s, cudaStream_t st)
+{
+    auto &L = s->pl;
+    if (!L.latest) return;
+    if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
+    s->has_prev = L.has_prev;
+    if (L.has_prev) {
+        const size_t slot = s->pyr_fs * s->es;
+        cudaMemcpyAsync(s->pyr + (size_t)s->head * slot, L.pyr + (size_t)L.head * slot, slot,
+                        cudaMemcpyDeviceToDevice, st);
+    }
+    L.latest = false;
+}
+
+// One pipelined window.  The caller has made L.front wait for the window's
+// inputs (and L.flow for d_flow to be free, if it reuses it).  The front end
+// goes to L.front after the flow that last read its slot; the flow to L.flow
+// after the front end; the descriptors travel in the slot's own block.
+ebof_status run_pipelined(ebof_stream *s, const uint16_t *x, const uint16_t *y, const int64_t *t,
+                          int64_t nev, int64_t t_begin, int64_t dt, float *d_flow)
+{
+    auto &L = s->pl;
+    ProfScope prof_scope(&s->prof);
+    pipeline_enter(s);
+    const int j = (L.head + 1) % 3, prev = L.head;
+    const bool had_prev = L.has_prev;
+    // slot j was the previous slot of the flow two calls back, whose
+    // current slot is j + 1 (the flow three calls back, slot j's own, ran
+    // before it on L.flow)
+    const int k2 = (j + 1) % 3;
+    if (L.flow_used[k2]) cudaStreamWaitEvent(L.front, L.flow_done[k2], 0);
+    ebof_window_desc w;
+    w.x = x;
+    w.y = y;
+    w.t = t;
+    w.n_events = nev;
+    w.t_begin = t_begin;
+    w.t_end = t_begin + dt;
+    std::memcpy(L.h_call.data() + (size_t)j * kPipeCallBytes, &w, sizeof(w));
+    std::memcpy(L.h_call.data() + (size_t)j * kPipeCallBytes + 64, &d_flow, sizeof(d_flow));
+    cudaMemcpyAsync(L.call + (size_t)j * kPipeCallBytes, L.h_call.data() + (size_t)j * kPipeCallBytes,
+                    kPipeCallBytes, cudaMemcpyHostToDevice, L.front);
+    const bool graphs = !s->prof.on;
+    if (graphs) {
+        if (!L.front_graph[j]) {
+            L.front_graph[j] = capture(s, 1, j, prev, L.front, &L.front_k[j], kPartFront, L.pyr,
+                                       pipe_wins(s, j), pipe_flows(s, j));
+            if (!L.front_graph[j]) return EBOF_ERR_CUDA;
+        }
+        if (cudaGraphLaunch(L.front_graph[j], L.front) != cudaSuccess) return EBOF_ERR_CUDA;
+        g_launches.fetch_add((unsigned long long)L.front_k[j]);
+    } else {
+        enqueue(s, 1, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, nullptr,
+                nullptr, true, j, prev, had_prev, L.front, kPartFront, L.pyr, pipe_wins(s, j),
+                pipe_flows(s, j));
+    }
+    cudaEventRecord(L.front_done[j], L.front);
+    cudaStreamWaitEvent(L.flow, L.front_done[j], 0);
+    if (had_prev && s->geo.levels > 0) {
+        if (graphs) {
+            if (!L.flow_graph[j]) {
+                L.flow_graph[j] = capture(s, 1, j, prev, L.flow, &L.flow_k[j], kPartFlow, L.pyr,
+                                          pipe_wins(s, j), pipe_flows(s, j));
+                if (!L.flow_graph[j]) return EBOF_ERR_CUDA;
+            }
+            if (cudaGraphLaunch(L.flow_graph[j], L.flow) != cudaSuccess) return EBOF_ERR_CUDA;
+            g_launches.fetch_add((unsigned long long)L.flow_k[j]);
+        } else {
+            enqueue(s, 1, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, true, j, prev, true, L.flow, kPartFlow, L.pyr, pipe_wins(s, j),
+                    pipe_flows(s, j));
+        }
+    } else {
+        cudaMemsetAsync(d_flow, 0, sizeof(float) * 2 * (size_t)s->p.width * s->p.height, L.flow);
+    }
+    cudaEventRecord(L.flow_done[j], L.flow);
+    L.flow_used[j] = true;
+    L.head = j;
+    L.has_prev = true;
+    s->last_list = false;
+    s->last_n = 1;
+    s->last_events = nev;
+    s->last_had_prev = had_prev;
+    cudaEventRecord(s->done, L.flow);
+    s->last_stream = L.flow;
+    s->have_last = true;
+    if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
+    return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
+}
+
 void free_group(ebof_group *g)
 {
     for (int b = 0; b < 2; ++b)
@@ -594,7 +801,6 @@ void run_group(ebof_group *g, bool with_flow, cudaStream_t st)
     const bool half = p.storage == EBOF_STORAGE_FP16;
     const size_t es = g->es;
     char *cur = g->pyr + (size_t)g->parity * n * g->pyr_fs * es;
-    char *prv = g->pyr + (size_t)(g->parity ^ 1) * n * g->pyr_fs * es;
     tl_level = -1;
     cudaMemsetAsync(g->dstats, 0, sizeof(DevStats) * n, st);
     cudaMemsetAsync(g->d_dropped_time, 0, sizeof(unsigned long long), st);
@@ -1258,6 +1464,8 @@ ebof_status ebof_stream_reset(ebof_stream *s)
     if (s->have_last && cudaEventSynchronize(s->done) != cudaSuccess) return EBOF_ERR_CUDA;
     s->has_prev = false;
     s->head = 0;
+    s->pl.has_prev = false;
+    s->pl.latest = false;
     return EBOF_OK;
 }
 
@@ -1423,11 +1631,36 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
     return r;
 }
 
+ebof_status ebof_process_window_async(ebof_stream *s, const uint16_t *d_x, const uint16_t *d_y,
+                                      const int64_t *d_t, const int8_t *d_p, int64_t n_events,
+                                      int64_t t_begin, int64_t t_end, float *d_flow,
+                                      void *cuda_stream)
+{
+    (void)d_p;  // polarity is not used (§III-A)
+    if (!s || !d_flow || !events_ok(d_x, d_y, d_t, n_events) || t_end < t_begin)
+        return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    cudaGetLastError();
+    const ebof_status rp = pipeline_ready(s);
+    if (rp < 0) return rp;
+    auto &L = s->pl;
+    // the window's inputs: the caller's work on its stream so far
+    cudaEventRecord(L.inputs, (cudaStream_t)cuda_stream);
+    cudaStreamWaitEvent(L.front, L.inputs, 0);
+    // d_flow: the caller's stream may read what an earlier call wrote there
+    cudaStreamWaitEvent(L.flow, L.inputs, 0);
+    return run_pipelined(s, d_x, d_y, d_t, n_events, t_begin, t_end - t_begin, d_flow);
+}
+
 ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
                                            const uint16_t *h_y, const int64_t *h_t,
                                            int64_t n_events, int64_t t_begin, int64_t t_end,
                                            float *h_flow, void *cuda_stream)
 {
+    (void)cuda_stream;  // every step runs on the stream's own streams
     if (!s || !h_flow || !events_ok(h_x, h_y, h_t, n_events) || t_end < t_begin)
         return EBOF_ERR_INVALID_ARG;
     const size_t n = (size_t)n_events;
@@ -1448,7 +1681,10 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
     if (!bg.ok) return EBOF_ERR_BUSY;
     DeviceGuard dg(s->device);
     if (!dg.ok) return EBOF_ERR_CUDA;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaGetLastError();
+    ebof_status rp = pipeline_ready(s);
+    if (rp < 0) return rp;
+    auto &L = s->pl;
     auto &q = s->pipe;
     if (!q.ready) {
         bool ok = cudaStreamCreateWithFlags(&q.h2d, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1481,7 +1717,7 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
         q.ready = true;
     }
     const int j = q.slot;
-    // the slot's events buffer: the window two calls back must have read it
+    // the slot's events buffer: the front end two calls back must have read it
     const size_t bx = ((2 * n + 255) / 256) * 256;
     const size_t need = 2 * bx + 8 * n;
     if (need > q.ev_bytes[j]) {
@@ -1500,7 +1736,7 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
     uint16_t *dx = (uint16_t *)base;
     uint16_t *dy = (uint16_t *)(base + bx);
     int64_t *dt = (int64_t *)(base + 2 * bx);
-    // events in: after the window two calls back has run (it read this slot)
+    // events in, after the front end that last read this slot
     if (q.used[j]) cudaStreamWaitEvent(q.h2d, q.run_done[j], 0);
     if (n) {
         cudaMemcpyAsync(dx, h_x, 2 * n, cudaMemcpyHostToDevice, q.h2d);
@@ -1508,21 +1744,35 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
         cudaMemcpyAsync(dt, h_t, 8 * n, cudaMemcpyHostToDevice, q.h2d);
     }
     cudaEventRecord(q.in_done[j], q.h2d);
-    // the window: after its events are in and the slot's previous flow is out
-    cudaStreamWaitEvent(st, q.in_done[j], 0);
-    if (q.used[j]) cudaStreamWaitEvent(st, q.out_done[j], 0);
-    const ebof_status r = run(s, 1, dx, dy, dt, n_events, t_begin, t_end - t_begin, nullptr,
-                              q.flow[j], nullptr, nullptr, nullptr, st);
+    cudaStreamWaitEvent(L.front, q.in_done[j], 0);
+    // the flow staging slot: after the copy out two calls back
+    if (q.used[j]) cudaStreamWaitEvent(L.flow, q.out_done[j], 0);
+    const ebof_status r = run_pipelined(s, dx, dy, dt, n_events, t_begin, t_end - t_begin,
+                                        q.flow[j]);
     if (r < 0) return r;
-    // flow out, overlapping the next window's kernels
-    cudaEventRecord(q.run_done[j], st);
-    cudaStreamWaitEvent(q.d2h, q.run_done[j], 0);
+    cudaEventRecord(q.run_done[j], L.front);  // the front end has read the events
+    // flow out, overlapping the next windows' kernels
+    cudaStreamWaitEvent(q.d2h, s->done, 0);
     cudaMemcpyAsync(h_flow, q.flow[j], flow_bytes, cudaMemcpyDeviceToHost, q.d2h);
     cudaEventRecord(q.out_done[j], q.d2h);
     q.used[j] = true;
     q.slot = j ^ 1;
     if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
     return r;
+}
+
+ebof_status ebof_stream_join(ebof_stream *s, void *cuda_stream)
+{
+    if (!s) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (s->have_last) cudaStreamWaitEvent(st, s->done, 0);
+    for (int j = 0; j < 2; ++j)
+        if (s->pipe.used[j]) cudaStreamWaitEvent(st, s->pipe.out_done[j], 0);
+    return cudaGetLastError() == cudaSuccess ? EBOF_OK : EBOF_ERR_CUDA;
 }
 
 ebof_status ebof_stream_set_wait_limit(ebof_stream *s, int64_t iterations)
