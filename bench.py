@@ -1319,9 +1319,10 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": bench_config(_params_dict(prm), nwin, world),
             "path": "one window per call, pipelined (ebof_process_window_async: a window's "
-                    "front end on one internal stream overlaps the previous window's flow "
-                    "on another, graph replays, ebof_stream_join closes the step); "
-                    "latencies from in-order ebof_process_window calls",
+                    "front end on one internal stream, its flow on one of four flow "
+                    "streams in turn, so that front ends and the flows of four "
+                    "consecutive windows overlap; graph replays; ebof_stream_join closes "
+                    "the step); latencies from in-order ebof_process_window calls",
             "events_mb_per_step": int(off[-1]) * 13 / 1e6,
             "p50_latency_ms": float(np.percentile(lat, 50)),
             "p99_latency_ms": float(np.percentile(lat, 99)),

@@ -155,7 +155,8 @@ ebof_status ebof_stream_create(const ebof_params *p, int device, ebof_stream **o
 
 /* Device bytes ebof_stream_create would allocate for these parameters (for
  * admission control against a memory budget), or -1 if they are invalid.
- * Allocates nothing. */
+ * Allocates nothing.  The pipelined and streaming host calls allocate their
+ * own buffers on first use, on top of this. */
 int64_t ebof_stream_device_bytes(const ebof_params *p);
 
 /* Frees the stream after waiting for its work.  NULL is accepted. */
@@ -247,15 +248,19 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
  * for callers that stream windows and collect the flows later.  The call
  * enqueues and returns; the window's front end (events to the pyramid) runs
  * on an internal stream after the caller's work on `cuda_stream` so far, and
- * its flow on a second internal stream after its front end, with three
- * pyramid slots of the stream's own, so that each window's front end
- * overlaps the previous window's flow levels.  Nothing is enqueued on
+ * its flow after its front end on one of four internal flow streams, in
+ * turn, each with its own scratch buffers, over eight pyramid slots of the
+ * stream's own: a window's front end and the flows of four consecutive
+ * windows (each pair's flow depends only on their pyramids, §III-D) overlap
+ * one another, the latency-bound coarse levels of one window filling the
+ * SMs that another window's levels leave idle.  Nothing is enqueued on
  * `cuda_stream`: d_flow holds the flow, and the event buffers may be reused,
  * once ebof_stream_sync(s) returns.  Results are bit-identical to
  * ebof_process_window; the two kinds of call may be mixed on one stream
  * (the newest window's pyramid is handed over with one device copy).
- * Same return values; EBOF_ERR_OOM if the pipeline's slots (three pyramid
- * slots) cannot be allocated. */
+ * Same return values; EBOF_ERR_OOM if the pipeline's buffers (eight pyramid
+ * slots and three scratch sets: about 260 MB at 1280x720 FP32) cannot be
+ * allocated. */
 ebof_status ebof_process_window_async(ebof_stream *s, const uint16_t *d_x, const uint16_t *d_y,
                                       const int64_t *d_t, const int8_t *d_p, int64_t n_events,
                                       int64_t t_begin, int64_t t_end, float *d_flow,
@@ -265,8 +270,8 @@ ebof_status ebof_process_window_async(ebof_stream *s, const uint16_t *d_x, const
  * whole, inside one page-locked range registered with CUDA, the call only
  * enqueues and returns: the events are copied in on an internal copy stream,
  * the window runs pipelined as in ebof_process_window_async, and the flow is
- * copied out into h_flow on a second internal copy stream, through two
- * device staging slots used by alternate calls, so that a window's copies
+ * copied out into h_flow on a second internal copy stream, through five
+ * device staging slots used in turn, so that a window's copies
  * overlap its neighbours' kernels.  `cuda_stream` is not used.  h_flow holds
  * the flow once ebof_stream_sync(s) returns; the buffers must stay valid and
  * unmodified until then.  Otherwise (pageable buffers) it is

@@ -98,36 +98,41 @@ struct ebof_stream {
     CoefMaps cmaps;  // tensor maps of the variational coefficient planes per level
     // asynchronous host-buffer calls (ebof_process_window_host_async): the
     // events go in on stream h2d, the flow comes back on stream d2h, both
-    // through two device staging slots used alternately, so that the copies
-    // of one window overlap the kernels of its neighbours
+    // through device staging slots used in turn, so that the copies of one
+    // window overlap the kernels of its neighbours
     struct HostPipe {
+        static constexpr int kSlots = 5;  // more than the flows in flight
         cudaStream_t h2d = nullptr, d2h = nullptr;
-        cudaEvent_t in_done[2] = {}, run_done[2] = {}, out_done[2] = {};
-        bool used[2] = {false, false};
-        void *ev[2] = {nullptr, nullptr};
-        size_t ev_bytes[2] = {0, 0};
-        float *flow[2] = {nullptr, nullptr};
+        cudaEvent_t in_done[kSlots] = {}, run_done[kSlots] = {}, out_done[kSlots] = {};
+        bool used[kSlots] = {};
+        void *ev[kSlots] = {};
+        size_t ev_bytes[kSlots] = {};
+        float *flow[kSlots] = {};
         int slot = 0;
         bool ready = false;
     } pipe;
     // pipelined calls (ebof_process_window_async, ebof_process_window_host_async):
-    // a window's front end (A1-A5) runs on stream `front`, its flow (A6-A9) on
-    // stream `flow`, with three pyramid slots of their own, so that a
-    // window's front end overlaps the previous window's flow levels
+    // a window's front end (A1-A5) runs on stream `front`, its flow (A6-A9)
+    // on flow[k % kFlows] with scratch set k % kFlows, and the pipeline keeps
+    // 2 kFlows pyramid slots of its own, so that a window's front end and the
+    // flows of kFlows consecutive windows overlap one another
     struct Pipeline {
+        static constexpr int kFlows = 4, kSlots = 2 * kFlows;
         bool ready = false;
-        cudaStream_t front = nullptr, flow = nullptr;
-        char *pyr = nullptr;   // three slots
+        cudaStream_t front = nullptr, flow[kFlows] = {};
+        char *pyr = nullptr;   // kSlots slots
         char *call = nullptr;  // per slot: the window's descriptor and flow destination
         std::vector<char> h_call;
+        // scratch sets 1 .. kFlows - 1 (set 0: the stream's own buffers)
+        float *up[kFlows] = {}, *Ua[kFlows] = {}, *Ub[kFlows] = {}, *work[kFlows] = {};
         int head = 0;            // slot of the newest window
         bool has_prev = false;   // the newest window is in these slots
         bool latest = false;     // these slots, not the ordinary ones, hold the newest window
         cudaEvent_t inputs = nullptr;
-        cudaEvent_t front_done[3] = {}, flow_done[3] = {};
-        bool flow_used[3] = {false, false, false};
-        cudaGraphExec_t front_graph[3] = {}, flow_graph[3] = {};
-        long long front_k[3] = {}, flow_k[3] = {};
+        cudaEvent_t front_done[kSlots] = {}, flow_done[kSlots] = {};
+        bool flow_used[kSlots] = {};
+        cudaGraphExec_t front_graph[kSlots] = {}, flow_graph[kSlots] = {};
+        long long front_k[kSlots] = {}, flow_k[kSlots] = {};
     } pl;
 };
 
@@ -302,7 +307,7 @@ void free_all(ebof_stream *s)
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->done) cudaEventDestroy(s->done);
     auto &q = s->pipe;
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < ebof_stream::HostPipe::kSlots; ++j) {
         if (q.used[j]) cudaEventSynchronize(q.out_done[j]);
         cudaFree(q.ev[j]);
         cudaFree(q.flow[j]);
@@ -314,8 +319,9 @@ void free_all(ebof_stream *s)
     if (q.d2h) cudaStreamDestroy(q.d2h);
     auto &L = s->pl;
     if (L.front) cudaStreamSynchronize(L.front);
-    if (L.flow) cudaStreamSynchronize(L.flow);
-    for (int j = 0; j < 3; ++j) {
+    for (cudaStream_t f : L.flow)
+        if (f) cudaStreamSynchronize(f);
+    for (int j = 0; j < ebof_stream::Pipeline::kSlots; ++j) {
         if (L.front_graph[j]) cudaGraphExecDestroy(L.front_graph[j]);
         if (L.flow_graph[j]) cudaGraphExecDestroy(L.flow_graph[j]);
         if (L.front_done[j]) cudaEventDestroy(L.front_done[j]);
@@ -324,8 +330,15 @@ void free_all(ebof_stream *s)
     if (L.inputs) cudaEventDestroy(L.inputs);
     cudaFree(L.pyr);
     cudaFree(L.call);
+    for (int f = 0; f < ebof_stream::Pipeline::kFlows; ++f) {
+        cudaFree(L.up[f]);
+        cudaFree(L.Ua[f]);
+        cudaFree(L.Ub[f]);
+        cudaFree(L.work[f]);
+    }
     if (L.front) cudaStreamDestroy(L.front);
-    if (L.flow) cudaStreamDestroy(L.flow);
+    for (cudaStream_t f : L.flow)
+        if (f) cudaStreamDestroy(f);
 }
 
 SurfaceMap surface_map(const ebof_params &p)
@@ -376,12 +389,18 @@ FlowParams flow_params(const ebof_params &p)
 // A6-A9 of the windows that have a previous one.
 constexpr int kPartFront = 1, kPartFlow = 2, kPartAll = 3;
 
+// The buffers the flow part works in (the stream's own unless given).
+struct FlowScratch {
+    float *up, *Ua, *Ub, *work;
+    const CoefMaps *cmaps;  // tensor maps of `work`, or null (direct loads, same result)
+};
+
 void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const int64_t *t,
              int64_t nev, int64_t t_begin, int64_t dt, const float *surface_in, float *d_flow,
              uint8_t *d_edge, int32_t *d_edt, float *d_surface, bool via_args, int cur_first,
              int prev_first, bool had_prev, cudaStream_t st, int parts = kPartAll,
              char *pyr = nullptr, const ebof_window_desc *d_wins = nullptr,
-             float *const *d_flows = nullptr)
+             float *const *d_flows = nullptr, const FlowScratch *scratch = nullptr)
 {
     const ebof_params &p = s->p;
     const Geometry &geo = s->geo;
@@ -429,6 +448,8 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
         const int curf_first = cur_first + ff;
         FlowParams fp = flow_params(p);
         fp.wait_limit = s->wait_limit;
+        const FlowScratch own = {s->up, s->Ua, s->Ub, s->work, &s->cmaps};
+        const FlowScratch &sc = scratch ? *scratch : own;
         float *Ucur = nullptr, *Uc = nullptr;
         const Level *lvc = nullptr;
         for (int l = geo.levels - 1; l >= 0; --l) {
@@ -437,15 +458,16 @@ void enqueue(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, const 
             const char *I0 = pyr + ((size_t)prev_first * s->pyr_fs + geo.pyr_off[l]) * es;
             const char *I1 = pyr + ((size_t)curf_first * s->pyr_fs + geo.pyr_off[l]) * es;
             const char *I0x = I0 + lv.plane * es, *I0y = I0 + 2 * lv.plane * es;
-            Ucur = (Uc == s->Ua) ? s->Ub : s->Ua;
-            launch_patch_search(I0, I0x, I0y, I1, lv, s->pyr_fs, Uc, lvc, s->u_fs, s->up,
+            Ucur = (Uc == sc.Ua) ? sc.Ub : sc.Ua;
+            launch_patch_search(I0, I0x, I0y, I1, lv, s->pyr_fs, Uc, lvc, s->u_fs, sc.up,
                                 s->up_fs, nf, fp, s->d_err, st);
-            launch_densify(I0, I1, lv, s->pyr_fs, s->up, s->up_fs, Ucur, s->u_fs, nf, fp, st);
+            launch_densify(I0, I1, lv, s->pyr_fs, sc.up, s->up_fs, Ucur, s->u_fs, nf, fp, st);
             // the coarser flow is consumed by the search: its buffer is free
-            float *Utmp = (Ucur == s->Ua) ? s->Ub : s->Ua;
+            float *Utmp = (Ucur == sc.Ua) ? sc.Ub : sc.Ua;
+            const CUtensorMap *cmap =
+                sc.cmaps && sc.cmaps->ok[l] ? &sc.cmaps->map[l] : nullptr;
             Ucur = launch_variational(I0, I0x, I0y, I1, lv, s->pyr_fs, Ucur, Utmp, s->u_fs,
-                                      s->work, s->work_fs, nf, fp,
-                                      s->cmaps.ok[l] ? &s->cmaps.map[l] : nullptr, s->d_err, st);
+                                      sc.work, s->work_fs, nf, fp, cmap, s->d_err, st);
             Uc = Ucur;
             lvc = &lv;
         }
@@ -484,7 +506,8 @@ void stage_call(ebof_stream *s, int n, const ebof_window_desc *wins, float *cons
 // of kernels in the graph.
 cudaGraphExec_t capture(ebof_stream *s, int n, int cur_first, int prev_first, cudaStream_t st,
                         long long *kernels, int parts = kPartAll, char *pyr = nullptr,
-                        const ebof_window_desc *d_wins = nullptr, float *const *d_flows = nullptr)
+                        const ebof_window_desc *d_wins = nullptr, float *const *d_flows = nullptr,
+                        const FlowScratch *scratch = nullptr)
 {
     cudaEvent_t ready;
     cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
@@ -498,7 +521,8 @@ cudaGraphExec_t capture(ebof_stream *s, int n, int cur_first, int prev_first, cu
         Profiler *keep = tl_prof;
         tl_prof = nullptr;
         enqueue(s, n, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, nullptr,
-                nullptr, true, cur_first, prev_first, true, s->cap, parts, pyr, d_wins, d_flows);
+                nullptr, true, cur_first, prev_first, true, s->cap, parts, pyr, d_wins, d_flows,
+                scratch);
         tl_prof = keep;
         cudaStreamEndCapture(s->cap, &gr);
     }
@@ -619,6 +643,8 @@ ebof_status run(ebof_stream *s, int n, const uint16_t *x, const uint16_t *y, con
 }
 
 // ----------------------------------------------------------------- pipelined calls
+constexpr int kPipeSlots = ebof_stream::Pipeline::kSlots;
+constexpr int kPipeFlows = ebof_stream::Pipeline::kFlows;
 constexpr size_t kPipeCallBytes = 128;  // per slot: one ebof_window_desc, one float *
 
 ebof_window_desc *pipe_wins(ebof_stream *s, int j)
@@ -631,39 +657,61 @@ float **pipe_flows(ebof_stream *s, int j)
     return (float **)(s->pl.call + (size_t)j * kPipeCallBytes + 64);
 }
 
-// Streams, events, slots and descriptor blocks of the pipelined calls, made
-// on first use.  On failure everything made here is released again.
+// Releases what pipeline_ready made (after a failure there).
+void pipeline_release(ebof_stream *s)
+{
+    auto &L = s->pl;
+    for (int j = 0; j < kPipeSlots; ++j) {
+        if (L.front_done[j]) cudaEventDestroy(L.front_done[j]);
+        if (L.flow_done[j]) cudaEventDestroy(L.flow_done[j]);
+        L.front_done[j] = L.flow_done[j] = nullptr;
+    }
+    if (L.inputs) cudaEventDestroy(L.inputs);
+    L.inputs = nullptr;
+    if (L.front) cudaStreamDestroy(L.front);
+    L.front = nullptr;
+    for (cudaStream_t &f : L.flow) {
+        if (f) cudaStreamDestroy(f);
+        f = nullptr;
+    }
+    for (char **b : {&L.pyr, &L.call}) {
+        cudaFree(*b);
+        *b = nullptr;
+    }
+    for (int f = 0; f < kPipeFlows; ++f)
+        for (float **b : {&L.up[f], &L.Ua[f], &L.Ub[f], &L.work[f]}) {
+            cudaFree(*b);
+            *b = nullptr;
+        }
+}
+
+// Streams, events, slots, descriptor blocks and the extra scratch sets of
+// the pipelined calls, made on first use.
 ebof_status pipeline_ready(ebof_stream *s)
 {
     auto &L = s->pl;
     if (L.ready) return EBOF_OK;
     static_assert(sizeof(ebof_window_desc) <= 64, "descriptor block");
     bool ok = cudaStreamCreateWithFlags(&L.front, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&L.flow, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&L.inputs, cudaEventDisableTiming) == cudaSuccess;
-    for (int j = 0; j < 3 && ok; ++j)
+    for (int f = 0; f < kPipeFlows && ok; ++f)
+        ok = cudaStreamCreateWithFlags(&L.flow[f], cudaStreamNonBlocking) == cudaSuccess;
+    for (int j = 0; j < kPipeSlots && ok; ++j)
         ok = cudaEventCreateWithFlags(&L.front_done[j], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&L.flow_done[j], cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && dmalloc(&L.pyr, s->es * s->pyr_fs * 3) == cudaSuccess &&
-         dmalloc(&L.call, 3 * kPipeCallBytes) == cudaSuccess;
+    ok = ok && dmalloc(&L.pyr, s->es * s->pyr_fs * kPipeSlots) == cudaSuccess &&
+         dmalloc(&L.call, kPipeSlots * kPipeCallBytes) == cudaSuccess;
+    for (int f = 1; f < kPipeFlows && ok; ++f)
+        ok = dmalloc(&L.up[f], sizeof(float) * s->up_fs) == cudaSuccess &&
+             dmalloc(&L.Ua[f], sizeof(float) * s->u_fs) == cudaSuccess &&
+             dmalloc(&L.Ub[f], sizeof(float) * s->u_fs) == cudaSuccess &&
+             dmalloc(&L.work[f], sizeof(float) * s->work_fs) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        for (int j = 0; j < 3; ++j) {
-            if (L.front_done[j]) cudaEventDestroy(L.front_done[j]);
-            if (L.flow_done[j]) cudaEventDestroy(L.flow_done[j]);
-            L.front_done[j] = L.flow_done[j] = nullptr;
-        }
-        if (L.inputs) cudaEventDestroy(L.inputs);
-        if (L.front) cudaStreamDestroy(L.front);
-        if (L.flow) cudaStreamDestroy(L.flow);
-        cudaFree(L.pyr);
-        cudaFree(L.call);
-        L.inputs = nullptr;
-        L.front = L.flow = nullptr;
-        L.pyr = L.call = nullptr;
+        pipeline_release(s);
         return EBOF_ERR_OOM;
     }
-    L.h_call.assign(3 * kPipeCallBytes, 0);
+    L.h_call.assign(kPipeSlots * kPipeCallBytes, 0);
     L.ready = true;
     return EBOF_OK;
 }
@@ -699,23 +747,23 @@ void pipeline_leave(ebof_stream *s, cudaStream_t st)
     L.latest = false;
 }
 
-// One pipelined window.  The caller has made L.front wait for the window's
-// inputs (and L.flow for d_flow to be free, if it reuses it).  The front end
-// goes to L.front after the flow that last read its slot; the flow to L.flow
-// after the front end; the descriptors travel in the slot's own block.
+// One pipelined window in slot j = head + 1 (mod kSlots).  The caller has
+// made L.front wait for the window's inputs (and every flow stream for
+// d_flow to be free, if it reuses it).  The front end goes to L.front after
+// the flows that last read slot j and its descriptor block (kSlots - 1 and
+// kSlots calls back: their current slots are j + 1 and j); the flow goes to
+// flow[j % kFlows], whose scratch set it uses, after the front end.  s->done
+// then follows every flow stream.
 ebof_status run_pipelined(ebof_stream *s, const uint16_t *x, const uint16_t *y, const int64_t *t,
                           int64_t nev, int64_t t_begin, int64_t dt, float *d_flow)
 {
     auto &L = s->pl;
     ProfScope prof_scope(&s->prof);
     pipeline_enter(s);
-    const int j = (L.head + 1) % 3, prev = L.head;
+    const int j = (L.head + 1) % kPipeSlots, prev = L.head;
     const bool had_prev = L.has_prev;
-    // slot j was the previous slot of the flow two calls back, whose
-    // current slot is j + 1 (the flow three calls back, slot j's own, ran
-    // before it on L.flow)
-    const int k2 = (j + 1) % 3;
-    if (L.flow_used[k2]) cudaStreamWaitEvent(L.front, L.flow_done[k2], 0);
+    for (int c : {(j + 1) % kPipeSlots, j})
+        if (L.flow_used[c]) cudaStreamWaitEvent(L.front, L.flow_done[c], 0);
     ebof_window_desc w;
     w.x = x;
     w.y = y;
@@ -723,11 +771,18 @@ ebof_status run_pipelined(ebof_stream *s, const uint16_t *x, const uint16_t *y, 
     w.n_events = nev;
     w.t_begin = t_begin;
     w.t_end = t_begin + dt;
-    std::memcpy(L.h_call.data() + (size_t)j * kPipeCallBytes, &w, sizeof(w));
-    std::memcpy(L.h_call.data() + (size_t)j * kPipeCallBytes + 64, &d_flow, sizeof(d_flow));
-    cudaMemcpyAsync(L.call + (size_t)j * kPipeCallBytes, L.h_call.data() + (size_t)j * kPipeCallBytes,
-                    kPipeCallBytes, cudaMemcpyHostToDevice, L.front);
+    char *hc = L.h_call.data() + (size_t)j * kPipeCallBytes;
+    std::memcpy(hc, &w, sizeof(w));
+    std::memcpy(hc + 64, &d_flow, sizeof(d_flow));
+    cudaMemcpyAsync(L.call + (size_t)j * kPipeCallBytes, hc, kPipeCallBytes,
+                    cudaMemcpyHostToDevice, L.front);
     const bool graphs = !s->prof.on;
+    // slot j's flow stream and scratch set (kSlots is a multiple of kFlows,
+    // so consecutive windows take consecutive sets)
+    const int f = j % kPipeFlows;
+    const FlowScratch setf = {L.up[f], L.Ua[f], L.Ub[f], L.work[f], nullptr};
+    const FlowScratch *sc = f ? &setf : nullptr;  // set 0: the stream's own buffers
+    cudaStream_t fl = L.flow[f];
     if (graphs) {
         if (!L.front_graph[j]) {
             L.front_graph[j] = capture(s, 1, j, prev, L.front, &L.front_k[j], kPartFront, L.pyr,
@@ -742,34 +797,39 @@ ebof_status run_pipelined(ebof_stream *s, const uint16_t *x, const uint16_t *y, 
                 pipe_flows(s, j));
     }
     cudaEventRecord(L.front_done[j], L.front);
-    cudaStreamWaitEvent(L.flow, L.front_done[j], 0);
+    cudaStreamWaitEvent(fl, L.front_done[j], 0);
     if (had_prev && s->geo.levels > 0) {
         if (graphs) {
             if (!L.flow_graph[j]) {
-                L.flow_graph[j] = capture(s, 1, j, prev, L.flow, &L.flow_k[j], kPartFlow, L.pyr,
-                                          pipe_wins(s, j), pipe_flows(s, j));
+                L.flow_graph[j] = capture(s, 1, j, prev, fl, &L.flow_k[j], kPartFlow, L.pyr,
+                                          pipe_wins(s, j), pipe_flows(s, j), sc);
                 if (!L.flow_graph[j]) return EBOF_ERR_CUDA;
             }
-            if (cudaGraphLaunch(L.flow_graph[j], L.flow) != cudaSuccess) return EBOF_ERR_CUDA;
+            if (cudaGraphLaunch(L.flow_graph[j], fl) != cudaSuccess) return EBOF_ERR_CUDA;
             g_launches.fetch_add((unsigned long long)L.flow_k[j]);
         } else {
             enqueue(s, 1, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, nullptr,
-                    nullptr, true, j, prev, true, L.flow, kPartFlow, L.pyr, pipe_wins(s, j),
-                    pipe_flows(s, j));
+                    nullptr, true, j, prev, true, fl, kPartFlow, L.pyr, pipe_wins(s, j),
+                    pipe_flows(s, j), sc);
         }
     } else {
-        cudaMemsetAsync(d_flow, 0, sizeof(float) * 2 * (size_t)s->p.width * s->p.height, L.flow);
+        cudaMemsetAsync(d_flow, 0, sizeof(float) * 2 * (size_t)s->p.width * s->p.height, fl);
     }
-    cudaEventRecord(L.flow_done[j], L.flow);
+    cudaEventRecord(L.flow_done[j], fl);
     L.flow_used[j] = true;
+    // s->done: after this flow and the previous windows' (on the other streams)
+    for (int b = 1; b < kPipeFlows; ++b) {
+        const int c = (j + kPipeSlots - b) % kPipeSlots;
+        if (L.flow_used[c]) cudaStreamWaitEvent(fl, L.flow_done[c], 0);
+    }
+    cudaEventRecord(s->done, fl);
     L.head = j;
     L.has_prev = true;
     s->last_list = false;
     s->last_n = 1;
     s->last_events = nev;
     s->last_had_prev = had_prev;
-    cudaEventRecord(s->done, L.flow);
-    s->last_stream = L.flow;
+    s->last_stream = fl;
     s->have_last = true;
     if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
     return had_prev ? EBOF_OK : EBOF_NO_PREVIOUS;
@@ -1651,7 +1711,7 @@ ebof_status ebof_process_window_async(ebof_stream *s, const uint16_t *d_x, const
     cudaEventRecord(L.inputs, (cudaStream_t)cuda_stream);
     cudaStreamWaitEvent(L.front, L.inputs, 0);
     // d_flow: the caller's stream may read what an earlier call wrote there
-    cudaStreamWaitEvent(L.flow, L.inputs, 0);
+    for (cudaStream_t f : L.flow) cudaStreamWaitEvent(f, L.inputs, 0);
     return run_pipelined(s, d_x, d_y, d_t, n_events, t_begin, t_end - t_begin, d_flow);
 }
 
@@ -1689,7 +1749,7 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
     if (!q.ready) {
         bool ok = cudaStreamCreateWithFlags(&q.h2d, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&q.d2h, cudaStreamNonBlocking) == cudaSuccess;
-        for (int j = 0; j < 2 && ok; ++j) {
+        for (int j = 0; j < ebof_stream::HostPipe::kSlots && ok; ++j) {
             ok &= cudaEventCreateWithFlags(&q.in_done[j], cudaEventDisableTiming) == cudaSuccess;
             ok &= cudaEventCreateWithFlags(&q.run_done[j], cudaEventDisableTiming) == cudaSuccess;
             ok &= cudaEventCreateWithFlags(&q.out_done[j], cudaEventDisableTiming) == cudaSuccess;
@@ -1698,7 +1758,7 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
         if (!ok) {
             cudaGetLastError();
             // undo, so that a later call starts again from nothing
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < ebof_stream::HostPipe::kSlots; ++k) {
                 cudaFree(q.flow[k]);
                 q.flow[k] = nullptr;
                 for (cudaEvent_t *e : {&q.in_done[k], &q.run_done[k], &q.out_done[k]})
@@ -1717,7 +1777,7 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
         q.ready = true;
     }
     const int j = q.slot;
-    // the slot's events buffer: the front end two calls back must have read it
+    // the slot's events buffer: the front end kSlots calls back must have read it
     const size_t bx = ((2 * n + 255) / 256) * 256;
     const size_t need = 2 * bx + 8 * n;
     if (need > q.ev_bytes[j]) {
@@ -1745,8 +1805,9 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
     }
     cudaEventRecord(q.in_done[j], q.h2d);
     cudaStreamWaitEvent(L.front, q.in_done[j], 0);
-    // the flow staging slot: after the copy out two calls back
-    if (q.used[j]) cudaStreamWaitEvent(L.flow, q.out_done[j], 0);
+    // the flow staging slot: after the copy out kSlots calls back
+    if (q.used[j])
+        for (cudaStream_t f : L.flow) cudaStreamWaitEvent(f, q.out_done[j], 0);
     const ebof_status r = run_pipelined(s, dx, dy, dt, n_events, t_begin, t_end - t_begin,
                                         q.flow[j]);
     if (r < 0) return r;
@@ -1756,7 +1817,7 @@ ebof_status ebof_process_window_host_async(ebof_stream *s, const uint16_t *h_x,
     cudaMemcpyAsync(h_flow, q.flow[j], flow_bytes, cudaMemcpyDeviceToHost, q.d2h);
     cudaEventRecord(q.out_done[j], q.d2h);
     q.used[j] = true;
-    q.slot = j ^ 1;
+    q.slot = (j + 1) % ebof_stream::HostPipe::kSlots;
     if (cudaGetLastError() != cudaSuccess) return EBOF_ERR_CUDA;
     return r;
 }
@@ -1770,7 +1831,7 @@ ebof_status ebof_stream_join(ebof_stream *s, void *cuda_stream)
     if (!dg.ok) return EBOF_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (s->have_last) cudaStreamWaitEvent(st, s->done, 0);
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < ebof_stream::HostPipe::kSlots; ++j)
         if (s->pipe.used[j]) cudaStreamWaitEvent(st, s->pipe.out_done[j], 0);
     return cudaGetLastError() == cudaSuccess ? EBOF_OK : EBOF_ERR_CUDA;
 }
@@ -1794,7 +1855,7 @@ ebof_status ebof_stream_sync(ebof_stream *s, ebof_window_stats *out, int32_t n_o
     DeviceGuard dg(s->device);
     if (!dg.ok) return EBOF_ERR_CUDA;
     if (s->have_last && cudaEventSynchronize(s->done) != cudaSuccess) return EBOF_ERR_CUDA;
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < ebof_stream::HostPipe::kSlots; ++j)
         if (s->pipe.used[j] && cudaEventSynchronize(s->pipe.out_done[j]) != cudaSuccess)
             return EBOF_ERR_CUDA;
     int err = 0;

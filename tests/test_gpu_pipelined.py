@@ -1,9 +1,10 @@
 """Pipelined windows (ebof_process_window_async): a window's front end runs
-on one internal stream, its flow on another, with three pyramid slots of
-the stream's own, so that each front end overlaps the previous window's flow
-levels.  The gate is bit identity with ebof_process_window on the same
-windows (whose parity with the oracle the other tests establish): every
-flow, through graph replays of all three slots, with FP16 storage, with
+on one internal stream, its flow on one of four flow streams in turn (each
+with its own scratch buffers), over eight pyramid slots of the stream's own,
+so that front ends and the flows of consecutive windows overlap.  The gate
+is bit identity with ebof_process_window on the same windows (whose parity
+with the oracle the other tests establish): every flow, through graph
+replays of all eight slots, with FP16 storage, with
 stage timing on (the eager path), mixed with ordinary calls on one stream
 (the pyramid handed over both ways) and across a reset.
 """
@@ -68,7 +69,7 @@ def _steps(eb, s, prm, wins, kinds):
 
 @pytest.mark.parametrize("W,H,storage", [(1280, 720, 0), (346, 260, 1)])
 def test_pipelined_equals_ordinary_calls(eb, W, H, storage):
-    n = 8
+    n = 18  # every slot and every flow stream more than once
     if W == 1280:
         ev = synth.rigid_objects(n_windows=n, seed=41, events=(60000, 150000))
     else:
