@@ -9,7 +9,8 @@
 * A device allocation that fails (ebof_debug_fail_allocation, an injected
   cudaMalloc failure): stream creation reports EBOF_ERR_OOM and frees what
   it had allocated; an existing stream whose host-buffer call meets the
-  failure reports EBOF_ERR_OOM and stays usable.
+  failure reports EBOF_ERR_OOM and stays usable; so does a first pipelined
+  call whose buffers cannot all be allocated.
 * Two host threads on one stream: the second call is refused with
   EBOF_ERR_BUSY and enqueues nothing.
 """
@@ -201,3 +202,52 @@ def test_second_thread_on_a_busy_stream_is_refused(eb):
     assert eb.EBOF_ERR_BUSY in seen, seen
     assert eb.ebof_stream_sync(s, 1)[0] == eb.EBOF_OK
     s.close()
+
+
+def test_pipeline_allocation_failure_reports_oom_and_recovers(eb):
+    """The pipelined call allocates its buffers (eight pyramid slots, three
+    scratch sets) on first use.  A failure among them is reported as
+    EBOF_ERR_OOM with nothing enqueued and everything made so far released;
+    a later call allocates again and gives the flows of ordinary calls."""
+    ev = synth.translating_segments(n_windows=4, seed=13)
+    W, H = ev.width, ev.height
+    p = eb.ebof_default_params(W, H)
+    st, s = eb.ebof_stream_create(p, 0)
+    eb.check(st)
+    st, ref = eb.ebof_stream_create(p, 0)
+    eb.check(st)
+    wins = []
+    for k in range(4):
+        x, y, t, _, tb, te = ev.window(k)
+        wins.append((_dev(x), _dev(y), _dev(t), tb, te))
+    f = torch.empty((2, H, W), dtype=torch.float32, device="cuda:0")
+    free = []
+    # the buffers are 14 allocations (slots, descriptor blocks, three sets
+    # of four); fail the first, the fourth and the ninth
+    for n in (0, 0, 3, 8):
+        eb.ebof_debug_fail_allocation(n)
+        try:
+            x, y, t, tb, te = wins[0]
+            assert eb.ebof_process_window_async(s, x, y, t, None, tb, te, f) == eb.EBOF_ERR_OOM
+        finally:
+            eb.ebof_debug_fail_allocation(-1)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+    # nothing is kept from one failed attempt to the next (the first attempt
+    # may leave the driver's own stream and event bookkeeping behind; the
+    # slots alone are 12 MB here)
+    assert max(free[1:]) - min(free[1:]) < (1 << 20), free
+    got, want = [], []
+    for x, y, t, tb, te in wins:
+        a = torch.empty((2, H, W), dtype=torch.float32, device="cuda:0")
+        b = torch.empty((2, H, W), dtype=torch.float32, device="cuda:0")
+        eb.check(eb.ebof_process_window_async(s, x, y, t, None, tb, te, a))
+        eb.check(eb.ebof_process_window(ref, x, y, t, None, tb, te, b))
+        got.append(a)
+        want.append(b)
+    assert eb.ebof_stream_sync(s, 1)[0] == eb.EBOF_OK
+    torch.cuda.synchronize()
+    for a, b in zip(got, want):
+        assert torch.equal(a, b)
+    s.close()
+    ref.close()
