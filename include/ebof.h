@@ -255,7 +255,9 @@ ebof_status ebof_process_window_host(ebof_stream *s, const uint16_t *h_x, const 
  * one another, the latency-bound coarse levels of one window filling the
  * SMs that another window's levels leave idle.  Nothing is enqueued on
  * `cuda_stream`: d_flow holds the flow, and the event buffers may be reused,
- * once ebof_stream_sync(s) returns.  Results are bit-identical to
+ * once ebof_stream_sync(s) returns.  Calls may share d_flow: its writes then
+ * follow the call order (the later window waits for the earlier one), so
+ * it ends with the newest flow.  Results are bit-identical to
  * ebof_process_window; the two kinds of call may be mixed on one stream
  * (the newest window's pyramid is handed over with one device copy).
  * Same return values; EBOF_ERR_OOM if the pipeline's buffers (eight pyramid

@@ -131,6 +131,7 @@ struct ebof_stream {
         cudaEvent_t inputs = nullptr;
         cudaEvent_t front_done[kSlots] = {}, flow_done[kSlots] = {};
         bool flow_used[kSlots] = {};
+        float *dflow[kSlots] = {};  // the flow destination of each slot's window
         cudaGraphExec_t front_graph[kSlots] = {}, flow_graph[kSlots] = {};
         long long front_k[kSlots] = {}, flow_k[kSlots] = {};
     } pl;
@@ -798,6 +799,12 @@ ebof_status run_pipelined(ebof_stream *s, const uint16_t *x, const uint16_t *y, 
     }
     cudaEventRecord(L.front_done[j], L.front);
     cudaStreamWaitEvent(fl, L.front_done[j], 0);
+    // windows in flight that write the same flow destination write it in
+    // call order
+    for (int c = 0; c < kPipeSlots; ++c)
+        if (c != j && L.flow_used[c] && L.dflow[c] == d_flow)
+            cudaStreamWaitEvent(fl, L.flow_done[c], 0);
+    L.dflow[j] = d_flow;
     if (had_prev && s->geo.levels > 0) {
         if (graphs) {
             if (!L.flow_graph[j]) {

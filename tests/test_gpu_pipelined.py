@@ -134,3 +134,23 @@ def test_pipelined_with_stage_timing(eb):
                   "flow_out"):
         assert prof[stage][1] > 0, stage
     s.close()
+
+
+def test_pipelined_calls_sharing_one_flow_buffer(eb):
+    """Every window into the same flow buffer: the writes follow the call
+    order, so the buffer ends with the newest window's flow."""
+    n = 7
+    ev = synth.rigid_objects(n_windows=n, seed=45, events=(60000, 150000))
+    prm = eb.ebof_default_params(1280, 720)
+    wins = _windows(ev, n)
+    ref = _ordinary(eb, prm, wins)
+    st, s = eb.ebof_stream_create(prm, 0)
+    eb.check(st)
+    f = torch.full((2, 720, 1280), float("nan"), dtype=torch.float32, device="cuda")
+    for x, y, t, tb, te in wins:
+        eb.check(eb.ebof_process_window_async(s, x, y, t, None, tb, te, f))
+    assert eb.ebof_stream_sync(s, 1)[0] == eb.EBOF_OK
+    torch.cuda.synchronize()
+    assert np.array_equal(f.cpu().numpy(), ref[-1])
+    s.close()
+
