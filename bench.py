@@ -1124,6 +1124,14 @@ def main():
         "stage_timing": "CUDA events around each stage's launches on the caller's stream "
                         "(eager launches, gaps included; the graph-replayed path times "
                         "the whole window only)"})
+    # the whole path at the pipelined rate: every stage's algorithmic bytes
+    # per frame times the frames per second of `value`
+    allb = roofline["stage_roofline"].get("all stages", {}).get("bytes_per_frame")
+    if allb:
+        roofline["pipelined_all_stages"] = {
+            "bytes_per_frame": allb, "frames_per_s": value,
+            "achieved_gbs": round(allb * value / 1e9, 1),
+            "frac": round(allb * value / 1e9 / peak, 4)}
 
     # batched path: the same stream through ebof_process_windows
     batched = None
