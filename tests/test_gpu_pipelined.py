@@ -154,3 +154,32 @@ def test_pipelined_calls_sharing_one_flow_buffer(eb):
     assert np.array_equal(f.cpu().numpy(), ref[-1])
     s.close()
 
+
+
+@pytest.mark.parametrize("W,H", [(160, 120), (6, 6)])
+def test_pipelined_empty_windows_and_images_without_levels(eb, W, H):
+    """A window without events between windows with events, and an image
+    smaller than the patch (no pyramid level: the flow is zero): the same
+    flows as ordinary calls, with a non-default max_batch (more ordinary
+    slots) in the mix."""
+    n = 6
+    rng = np.random.default_rng(W)
+    wins = []
+    for k in range(n):
+        tb = k * synth.WINDOW_US
+        m = 0 if k == 2 else max(20, W * H // 6)
+        x, y, t, _ = synth.random_edge_events(rng, W, H, m, t_begin=tb)
+        order = np.argsort(t, kind="stable")
+        wins.append(tuple(torch.from_numpy(np.ascontiguousarray(a[order])).cuda()
+                          for a in (x, y, t)) + (tb, tb + synth.WINDOW_US))
+    prm = eb.ebof_default_params(W, H)
+    ref = _ordinary(eb, prm, wins)
+    prm.max_batch = 3
+    st, s = eb.ebof_stream_create(prm, 0)
+    eb.check(st)
+    sts, got = _steps(eb, s, prm, wins, "oaaaoa")
+    for k in range(n):
+        assert np.array_equal(got[k], ref[k]), k
+    if W == 6:
+        assert all(np.all(g == 0.0) for g in got)
+    s.close()
