@@ -1115,11 +1115,11 @@ void build_fused_plan(ebof_multigroup *m, FusedPlan &P, int mode)
             a.d = make_pyr_desc(g->geo);
             const long long half = g->p.storage == EBOF_STORAGE_FP16;
             if (a.d.levels > 1) {
-                a.gx = (a.d.w[1] + 31) / 32;
-                a.gy = (a.d.h[1] + 31) / 32;
+                a.gx = (a.d.w[0] + 63) / 64;  // 64 x 64 regions of level 0
+                a.gy = (a.d.h[0] + 63) / 64;
                 means.push_back({half, {a, a.gx * a.gy * g->n}});
             }
-            a.gx = a.d.blk0[a.d.levels];
+            a.gx = a.d.blk0[a.d.levels] - a.d.gb0;
             a.gy = 1;
             grads.push_back({half, {a, a.gx * g->n}});
         }

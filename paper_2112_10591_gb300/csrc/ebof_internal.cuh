@@ -49,6 +49,8 @@ struct PyrDesc {
     size_t off[kMaxLevels];    // element offset of level l's I in a slot
     size_t plane[kMaxLevels];  // Ix and Iy follow I at one and two planes
     int blk0[kMaxLevels + 1];  // first block of level l in the gradient launch
+    int gb0;                   // first block launched (blk0[1] when the box means
+                               // kernel writes level 0's gradients, else 0)
 };
 
 // Per-window event counters kept on the device (one per batch slot).

@@ -41,12 +41,104 @@ __device__ __forceinline__ float as_stored(float v, const __half *)
     return __half2float(__float2half_rn(v));
 }
 
-// Box-mean levels 1 .. min(levels, kPyrFused) - 1 of a slot in one launch:
-// a block owns a 32 x 32 tile of level 1 (a 64 x 64 region of level 0) and
-// halves it in shared memory down to 2 x 2 at level 5.  Same sums in the same
-// order as downsample_kernel, so the levels are identical.
+// Box-mean levels 1 .. min(levels, kPyrFused) - 1 of a slot in one launch,
+// and the central differences of level 0: a block stages a 64 x 64 region of
+// level 0 with a one-pixel ring (replicated at the image border, as the
+// clamps of the gradient stencil read it) in shared memory, writes the
+// region's level-0 gradients, then halves its 32 x 32 tile of level 1 in
+// shared memory down to 2 x 2 at level 5.  Same sums in the same order as
+// downsample_kernel and pyramid_gradients_body, so the levels and gradients
+// are identical; the gradient launch then covers levels 1 and up only.
 constexpr int kPyrTile = 32;
 constexpr int kPyrFused = 6;
+constexpr int kPyrStage = 2 * kPyrTile + 2;  // staged level-0 rows and columns
+
+// Four consecutive elements of a row as one 16-byte (FP32) or 8-byte (FP16)
+// load.
+template <typename T> struct Quad;
+template <> struct Quad<float> {
+    using V = float4;
+    static __device__ __forceinline__ void unpack(const V &v, float (&o)[4])
+    {
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+};
+template <> struct Quad<__half> {
+    using V = uint2;
+    static __device__ __forceinline__ void unpack(const V &v, float (&o)[4])
+    {
+        const __half2 a = *reinterpret_cast<const __half2 *>(&v.x);
+        const __half2 b = *reinterpret_cast<const __half2 *>(&v.y);
+        o[0] = __low2float(a); o[1] = __high2float(a);
+        o[2] = __low2float(b); o[3] = __high2float(b);
+    }
+};
+
+// Level 0 at the clamped positions (x0b - 1 + c, y0b - 1 + r), r, c < 66,
+// into s0; every load of a thread is issued before the first shared-memory
+// store.  Regions whose 64 columns lie inside the level read them as quads
+// (x0b is a multiple of 64 and rows start on 128-byte boundaries, so the
+// quads are aligned) and the two ring columns as single elements.
+template <typename T>
+__device__ __forceinline__ void stage_level0(float (&s0)[kPyrStage][kPyrStage + 1],
+                                             const T *__restrict__ I0, int w0, int h0, int p0,
+                                             int x0b, int y0b, int t)
+{
+    constexpr int E = kPyrStage;
+    if (x0b + 2 * kPyrTile <= w0) {
+        using V = typename Quad<T>::V;
+        constexpr int NQ = E * (2 * kPyrTile / 4);  // quads of the 64 columns
+        constexpr int KQ = (NQ + 255) / 256;
+        V v[KQ];
+#pragma unroll
+        for (int k = 0; k < KQ; ++k) {
+            const int i = t + 256 * k;
+            if (i < NQ) {
+                const int r = i / (2 * kPyrTile / 4), c = i % (2 * kPyrTile / 4);
+                const int gy = min(max(y0b - 1 + r, 0), h0 - 1);
+                v[k] = *reinterpret_cast<const V *>(I0 + gy * p0 + x0b + 4 * c);
+            }
+        }
+        float hv = 0.0f;  // ring columns x0b - 1 and x0b + 64
+        const int hr = t >> 1, hc = (t & 1) ? E - 1 : 0;
+        if (t < 2 * E) {
+            const int gy = min(max(y0b - 1 + hr, 0), h0 - 1);
+            const int gx = min(max(x0b - 1 + hc, 0), w0 - 1);
+            hv = ldp(&I0[gy * p0 + gx]);
+        }
+#pragma unroll
+        for (int k = 0; k < KQ; ++k) {
+            const int i = t + 256 * k;
+            if (i < NQ) {
+                const int r = i / (2 * kPyrTile / 4), c = i % (2 * kPyrTile / 4);
+                float o[4];
+                Quad<T>::unpack(v[k], o);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s0[r][1 + 4 * c + q] = o[q];
+            }
+        }
+        if (t < 2 * E) s0[hr][hc] = hv;
+    } else {
+        constexpr int KS = (E * E + 255) / 256;
+        float v[KS];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int i = t + 256 * k;
+            v[k] = 0.0f;
+            if (i < E * E) {
+                const int r = i / E, c = i % E;
+                const int gy = min(max(y0b - 1 + r, 0), h0 - 1);
+                const int gx = min(max(x0b - 1 + c, 0), w0 - 1);
+                v[k] = ldp(&I0[gy * p0 + gx]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int i = t + 256 * k;
+            if (i < E * E) s0[i / E][i % E] = v[k];
+        }
+    }
+}
 
 // (bx, by): the level-1 tile, f: the frame.
 template <typename T>
@@ -54,22 +146,43 @@ __device__ __forceinline__ void pyramid_means_body(T *__restrict__ slots, size_t
                                                    const PyrDesc &d, unsigned bx, unsigned by,
                                                    unsigned f)
 {
+    __shared__ float s0[kPyrStage][kPyrStage + 1];
     __shared__ float ta[kPyrTile][kPyrTile + 1];
     __shared__ float tb[kPyrTile / 2][kPyrTile / 2 + 1];
     T *slot = slots + (size_t)f * fs;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int t = ty * 32 + tx;
     const int x1b = bx * kPyrTile, y1b = by * kPyrTile;
+    const int x0b = 2 * x1b, y0b = 2 * y1b;
+    const int w0 = d.w[0], h0 = d.h[0], p0 = d.pitch[0];
+    stage_level0<T>(s0, slot + d.off[0], w0, h0, p0, x0b, y0b, t);
+    __syncthreads();
     {
-        const T *I0 = slot + d.off[0];
+        // level-0 gradients of the region: s0[r][c] holds level 0 at the
+        // clamped position (x0b - 1 + c, y0b - 1 + r)
+        T *Ix = slot + d.off[0] + d.plane[0], *Iy = slot + d.off[0] + 2 * d.plane[0];
+#pragma unroll
+        for (int i = 0; i < 2 * kPyrTile / 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int lx = tx + 32 * j, ly = ty + 8 * i;
+                const int x = x0b + lx, y = y0b + ly;
+                if (x < w0 && y < h0) {
+                    const int p = y * p0 + x;
+                    stp(&Ix[p], 0.5f * (s0[ly + 1][lx + 2] - s0[ly + 1][lx]));
+                    stp(&Iy[p], 0.5f * (s0[ly + 2][lx + 1] - s0[ly][lx + 1]));
+                }
+            }
+    }
+    {
         T *I1 = slot + d.off[1];
-        const int p0 = d.pitch[0];
 #pragma unroll
         for (int i = 0; i < kPyrTile / 8; ++i) {
             const int ly = ty + 8 * i, x = x1b + tx, y = y1b + ly;
             float v = 0.0f;
             if (x < d.w[1] && y < d.h[1]) {
-                const size_t r0 = (size_t)(2 * y) * p0 + 2 * x, r1 = r0 + p0;
-                v = 0.25f * (ldp(&I0[r0]) + ldp(&I0[r0 + 1]) + ldp(&I0[r1]) + ldp(&I0[r1 + 1]));
+                const int sx = 2 * tx + 1, sy = 2 * ly + 1;
+                v = 0.25f * (s0[sy][sx] + s0[sy][sx + 1] + s0[sy + 1][sx] + s0[sy + 1][sx + 1]);
                 stp(&I1[(size_t)y * d.pitch[1] + x], v);
                 v = as_stored(v, I1);
             }
@@ -77,7 +190,6 @@ __device__ __forceinline__ void pyramid_means_body(T *__restrict__ slots, size_t
         }
     }
     __syncthreads();
-    const int t = ty * 32 + tx;
     int side = kPyrTile / 2;
     for (int l = 2; l < d.levels && l < kPyrFused; ++l, side >>= 1) {
         // level l - 1 is in ta for even l, in tb for odd l
@@ -108,13 +220,15 @@ pyramid_means_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
     pyramid_means_body(slots, fs, d, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// Central differences of every level of a slot in one launch: the blocks of
-// level l are blk0[l] .. blk0[l + 1] - 1 (32 x 8 pixels each).  bb: the
-// block, f: the frame.
+// Central differences of the levels of a slot in one launch: the blocks of
+// level l are blk0[l] .. blk0[l + 1] - 1 (32 x 8 pixels each), launched from
+// block gb0 on (level 1 when the box-mean kernel wrote level 0's).  bb: the
+// block of the launch, f: the frame.
 template <typename T>
 __device__ __forceinline__ void pyramid_gradients_body(T *__restrict__ slots, size_t fs,
                                                        const PyrDesc &d, unsigned bb, unsigned f)
 {
+    bb += d.gb0;
     int l = 0;
     while (l + 1 < d.levels && (int)bb >= d.blk0[l + 1]) ++l;
     const int b = bb - d.blk0[l];
@@ -692,6 +806,7 @@ PyrDesc make_pyr_desc(const Geometry &geo)
         nb += ((lv.w + 31) / 32) * ((lv.h + 7) / 8);
     }
     d.blk0[d.levels] = nb;
+    d.gb0 = d.levels > 1 ? d.blk0[1] : 0;  // level 0's gradients come with the box means
     return d;
 }
 
@@ -699,14 +814,16 @@ void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int f
                     cudaStream_t st)
 {
     const PyrDesc d = make_pyr_desc(geo);
-    const int nb = d.blk0[d.levels];
+    const int nb = d.blk0[d.levels] - d.gb0;
     const int extra = std::max(0, d.levels - kPyrFused);
     StageScope sc(kStPyramid, 1 + (d.levels > 1 ? 1 : 0) + extra, st);
     const dim3 blk(32, 8);
     const size_t es = half ? 2 : 4;
     if (d.levels > 1) {
-        const dim3 grd((d.w[1] + kPyrTile - 1) / kPyrTile, (d.h[1] + kPyrTile - 1) / kPyrTile,
-                       frames);
+        // tiles over the whole of level 0 (an odd last column or row of level 0
+        // lies past level 1's tiles when the width or height is 64k + 1)
+        const dim3 grd((d.w[0] + 2 * kPyrTile - 1) / (2 * kPyrTile),
+                       (d.h[0] + 2 * kPyrTile - 1) / (2 * kPyrTile), frames);
         if (half)
             pyramid_means_kernel<__half><<<grd, blk, 0, st>>>((__half *)slots, frame_stride, d);
         else

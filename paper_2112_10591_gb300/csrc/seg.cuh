@@ -83,8 +83,8 @@ struct SegEdtRows {
     int gpitch, ipitch, W, H, rows, gx;
 };
 
-// A5: the pyramid of one slot per frame; means: gx x gy level-1 tiles,
-// gradients: gx blocks over all levels.
+// A5: the pyramid of one slot per frame; means: gx x gy level-1 tiles (and
+// level 0's gradients), gradients: gx blocks over the other levels.
 struct SegPyr {
     void *slots;
     size_t fs;

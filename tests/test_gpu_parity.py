@@ -278,6 +278,36 @@ def test_flow_on_analytic_surfaces(eb, v):
     s.close()
 
 
+@pytest.mark.parametrize("W,H", [(193, 129), (129, 97)])
+def test_flow_with_odd_level0_edges(eb, W, H):
+    """Widths and heights of 64k + 1 pixels: level 0's last column (row) lies
+    past the 64-pixel regions that level 1's tiles cover, and its gradients
+    are still written (the box-mean launch covers all of level 0).  The flow
+    matches the oracle over the whole image and over the bands along the
+    right and lower borders, where the patches flush with the border read
+    the last column's and row's gradients."""
+    v = (1.7, 0.9)
+    prm, s = make_stream(eb, W, H)
+    S0 = _texture(W, H).astype(np.float32)
+    S1 = _texture(W, H, v).astype(np.float32)
+    flow = torch.full((2, H, W), float("nan"), dtype=torch.float32, device="cuda:0")
+    assert eb.ebof_process_surface(s, dev(S0), flow) == eb.EBOF_NO_PREVIOUS
+    assert eb.ebof_process_surface(s, dev(S1), flow) == eb.EBOF_OK
+    torch.cuda.synchronize()
+    F = flow.cpu().numpy()
+    assert np.isfinite(F).all()
+    U = oracle_flow(prm, 255.0 * S0.astype(np.float64), 255.0 * S1.astype(np.float64))
+    e = epe(F, U)
+    print("%dx%d: mean EPE %.5f, right band %.5f, lower band %.5f"
+          % (W, H, e.mean(), e[:, -prm.patch:].mean(), e[-prm.patch:, :].mean()))
+    assert e.mean() <= EPE_TOL
+    assert e[:, -prm.patch:].mean() <= EPE_TOL
+    assert e[-prm.patch:, :].mean() <= EPE_TOL
+    inner = (slice(None), slice(16, -16), slice(16, -16))
+    assert epe(F[inner], np.array(v)[:, None, None]).mean() <= 0.05  # not a trivial flow
+    s.close()
+
+
 def test_many_sor_sweeps_take_the_half_sweep_kernels(eb):
     """More SOR sweeps than a 64-px region's halo allows (13 sweeps need a
     25-px halo) run the variational refinement as one launch per half sweep;
