@@ -16,6 +16,8 @@
 #include "dev_common.cuh"
 #include "seg.cuh"
 
+#include <type_traits>
+
 namespace ebof {
 
 namespace {
@@ -392,38 +394,50 @@ __device__ __forceinline__ void patch_search_body(
         // gradients sum to zero, so both means drop out: b = sum g w - sum g T
         // (exactly zero when the warped patch equals the template)
         float b1 = 0.0f, b2 = 0.0f;
-        // The displacement is the same for the whole patch: when every
-        // sample of the patch and its right/lower neighbour lies inside the
-        // image, the clamped bilinear sample reduces to fixed weights on a
-        // fixed (PS+1) x (PS+1) window, and each row's horizontal lerps serve
-        // two output rows.
+        // The displacement is the same for the whole patch, so the bilinear
+        // sample has fixed weights (ax, ay) on a fixed (PS+1) x (PS+1) window
+        // of texels from (sx0, sy0), and each row's horizontal lerps serve
+        // two output rows.  Clamping the sample position to the level, the
+        // reading of the oracle, gives the same value as clamping the
+        // window's row and column indices (outside the level both taps of a
+        // lerp are the same edge texel, and a + t (a - a) = a exactly).  The
+        // window's rows and columns are clamped only where some lane's
+        // window leaves the level; inside it the clamps do nothing, so the
+        // form a warp takes never changes a value.
         const float uc = fminf(fmaxf(u, -lim), lim), vc = fminf(fmaxf(v, -lim), lim);
         const float fu = floorf(uc), fv = floorf(vc);
         const int sx0 = x0 + (int)fu, sy0 = y0 + (int)fv;
         const float ax = uc - fu, ay = vc - fv;
-        const bool fast = sx0 >= 0 && sy0 >= 0 && sx0 + PS <= w - 1 && sy0 + PS <= h - 1 &&
-                          uc == u && vc == v;
-        if (fast) {
-            // columns c0 .. c0 + CPL and rows r0 .. r0 + RPL of the window
-            // (the last of each only as the right / lower neighbour); no
-            // column or row beyond PS is read
-            const T *pp = I1 + (sy0 + r0) * pitch + sx0 + c0;
+        const bool inside = sx0 >= 0 && sy0 >= 0 && sx0 + PS <= w - 1 && sy0 + PS <= h - 1;
+        // columns c0 .. c0 + CPL and rows r0 .. r0 + RPL of the window (the
+        // last of each only as the right / lower neighbour); no column or row
+        // beyond PS is read
+        auto window = [&](auto clamped) {
+            constexpr bool C = decltype(clamped)::value;
+            int cx[CPL + 1];
+#pragma unroll
+            for (int k = 0; k <= CPL; ++k)
+                cx[k] = C ? clampi(sx0 + c0 + k, 0, w - 1) : sx0 + c0 + k;
+            auto row = [&](int rr) {
+                return I1 + (C ? clampi(sy0 + rr, 0, h - 1) : sy0 + rr) * pitch;
+            };
             float hp[CPL];
             {
+                const T *q = row(r0);
                 float s[CPL + 1];
 #pragma unroll
                 for (int k = 0; k <= CPL; ++k)
-                    s[k] = c0 + k <= PS && r0 <= PS ? ldp(&pp[k]) : 0.0f;
+                    s[k] = c0 + k <= PS && r0 <= PS ? ldp(&q[cx[k]]) : 0.0f;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) hp[k] = s[k] + ax * (s[k + 1] - s[k]);
             }
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
-                const T *q = pp + (r + 1) * pitch;
+                const T *q = row(r0 + r + 1);
                 const bool rin = r0 + r + 1 <= PS;
                 float s[CPL + 1];
 #pragma unroll
-                for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS && rin ? ldp(&q[k]) : 0.0f;
+                for (int k = 0; k <= CPL; ++k) s[k] = c0 + k <= PS && rin ? ldp(&q[cx[k]]) : 0.0f;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     const float hn = s[k] + ax * (s[k + 1] - s[k]);
@@ -433,18 +447,11 @@ __device__ __forceinline__ void patch_search_body(
                     b2 += GY[r][k] * wv;
                 }
             }
-        } else {
-#pragma unroll
-            for (int r = 0; r < RPL; ++r)
-#pragma unroll
-                for (int k = 0; k < CPL; ++k) {
-                    if (c0 + k >= PS || r0 + r >= PS) continue;
-                    const float wv = bilinear_i(I1, w, h, pitch, (float)(x0 + c0 + k) + u,
-                                                (float)(y0 + r0 + r) + v);
-                    b1 += GX[r][k] * wv;
-                    b2 += GY[r][k] * wv;
-                }
-        }
+        };
+        if (__all_sync(0xffffffffu, inside))
+            window(std::integral_constant<bool, false>());
+        else
+            window(std::integral_constant<bool, true>());
         b1 = group_sum<G>(b1 - tb1); b2 = group_sum<G>(b2 - tb2);
         u -= (a22 * b1 - h12 * b2) * inv_det;
         v -= (a11 * b2 - h12 * b1) * inv_det;
