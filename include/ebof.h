@@ -231,6 +231,19 @@ ebof_status ebof_process_window_list(ebof_stream *s, int32_t n_windows,
 ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *d_flow,
                                  void *cuda_stream);
 
+/* Level `level` (0 = finest) of the pyramid of the stream's newest window, as
+ * the flow block (§III-D) uses it: the 2x2 box-mean intensity image I_l and
+ * its central differences (replicated border) Ix_l, Iy_l, each copied into a
+ * dense caller-owned device array of [H_l][W_l] floats, H_l = H >> level,
+ * W_l = W >> level (FP16 storage is widened exactly).  Any of d_I, d_Ix, d_Iy
+ * may be NULL.  The copies are enqueued on `cuda_stream` after the stream's
+ * work so far (pipelined calls included); later calls on the stream write
+ * that pyramid only after them.  Returns EBOF_NO_PREVIOUS (nothing copied)
+ * before the first window, EBOF_ERR_INVALID_ARG for a level outside
+ * 0 .. levels_used - 1. */
+ebof_status ebof_stream_get_pyramid(ebof_stream *s, int32_t level, float *d_I, float *d_Ix,
+                                    float *d_Iy, void *cuda_stream);
+
 /* ebof_process_window with HOST buffers: the events go to the device, the
  * window runs and the flow comes back into h_flow [2][H][W], all on
  * `cuda_stream`, which is then synchronised.  Pageable buffers are staged

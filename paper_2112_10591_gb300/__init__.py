@@ -23,5 +23,5 @@ from .binding import (  # noqa: F401
     ebof_server_submit, EBOF_SURFACE_EXP, EBOF_SURFACE_LINEAR, EBOF_SURFACE_BOUNDED,
     EBOF_SURFACE_LOG, ebof_fwl, ebof_fwl_scratch_bytes, ebof_stream_set_wait_limit,
     ebof_debug_fail_allocation, MultiGroup, ebof_multigroup_create, ebof_multigroup_process,
-    ebof_multigroup_set_fused,
+    ebof_multigroup_set_fused, ebof_stream_get_pyramid,
 )

@@ -137,6 +137,7 @@ def _declare(L):
     L.ebof_process_window.argtypes = [vp, vp, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
     L.ebof_process_windows.argtypes = [vp, i32, vp, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
     L.ebof_process_surface.argtypes = [vp, vp, vp, vp]
+    L.ebof_stream_get_pyramid.argtypes = [vp, i32, vp, vp, vp, vp]
     L.ebof_process_window_list.argtypes = [vp, i32, P(ebof_window_desc), P(vp), vp]
     L.ebof_fwl_scratch_bytes.argtypes = [i32, i32]
     L.ebof_fwl_scratch_bytes.restype = ctypes.c_size_t
@@ -185,6 +186,7 @@ def _declare(L):
     L.ebof_debug_fail_allocation.restype = None
     for name in ("ebof_stream_create", "ebof_stream_destroy", "ebof_stream_reset",
                  "ebof_process_window", "ebof_process_windows", "ebof_process_surface",
+                 "ebof_stream_get_pyramid",
                  "ebof_process_window_host", "ebof_process_window_host_async",
                  "ebof_process_window_async", "ebof_stream_join",
                  "ebof_stream_sync", "ebof_edt",
@@ -387,6 +389,19 @@ def ebof_process_surface(stream: Stream, surface, flow, cuda_stream=None) -> int
     return load().ebof_process_surface(
         stream.handle, _ptr(surface, torch.float32, W * H, "surface", dev),
         _ptr(flow, torch.float32, 2 * W * H, "flow", dev), _stream_handle(cuda_stream))
+
+
+def ebof_stream_get_pyramid(stream: Stream, level: int, I=None, Ix=None, Iy=None,
+                            cuda_stream=None) -> int:
+    """Level `level` of the newest window's pyramid into dense float32 CUDA
+    tensors of (H >> level) x (W >> level) elements (any may be None)."""
+    import torch
+    lv = max(int(level), 0)  # the library refuses a level outside the pyramid
+    W, H, dev = stream.params.width >> lv, stream.params.height >> lv, stream.device
+    return load().ebof_stream_get_pyramid(
+        stream.handle, int(level), _ptr(I, torch.float32, W * H, "I", dev),
+        _ptr(Ix, torch.float32, W * H, "Ix", dev), _ptr(Iy, torch.float32, W * H, "Iy", dev),
+        _stream_handle(cuda_stream))
 
 
 def ebof_process_window_host(stream: Stream, x, y, t, t_begin: int, t_end: int, flow,

@@ -1599,6 +1599,36 @@ ebof_status ebof_process_surface(ebof_stream *s, const float *d_surface, float *
                nullptr, (cudaStream_t)cuda_stream);
 }
 
+ebof_status ebof_stream_get_pyramid(ebof_stream *s, int32_t level, float *d_I, float *d_Ix,
+                                    float *d_Iy, void *cuda_stream)
+{
+    if (!s || level < 0 || level >= s->geo.levels) return EBOF_ERR_INVALID_ARG;
+    BusyGuard bg(s->busy);
+    if (!bg.ok) return EBOF_ERR_BUSY;
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return EBOF_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaGetLastError();
+    // the newest window's pyramid into the ordinary slots (after the work
+    // that wrote it), as before an ordinary call
+    pipeline_leave(s, st);
+    if (!s->has_prev) return EBOF_NO_PREVIOUS;
+    if (s->have_last && s->last_stream != st) cudaStreamWaitEvent(st, s->done, 0);
+    const Level &lv = s->geo.lv[level];
+    const char *I = s->pyr + ((size_t)s->head * s->pyr_fs + s->geo.pyr_off[level]) * s->es;
+    const bool half = s->es == 2;
+    float *dst[3] = {d_I, d_Ix, d_Iy};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k])
+            launch_pyramid_export(I + (size_t)k * lv.plane * s->es, half, lv.w, lv.h, lv.pitch,
+                                  dst[k], st);
+    // later calls write this slot only after the copies
+    cudaEventRecord(s->done, st);
+    s->last_stream = st;
+    s->have_last = true;
+    return cudaGetLastError() == cudaSuccess ? EBOF_OK : EBOF_ERR_CUDA;
+}
+
 typedef CUresult (*PointerAttrFn)(void *, CUpointer_attribute, CUdeviceptr);
 
 static PointerAttrFn pointer_attr_fn()

@@ -137,6 +137,9 @@ void launch_surface_to_intensity(const float *S, int W, int H, void *I0, int pit
 // starting at `slots` (level 0 must be in place), in two launches.
 void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int frames, bool half,
                     cudaStream_t st);
+// One plane of a level (row pitch `pitch`) into a dense w x h FP32 array.
+void launch_pyramid_export(const void *plane, bool half, int w, int h, int pitch, float *dst,
+                           cudaStream_t st);
 
 // A6: patch inverse search at one level.
 void launch_patch_search(const void *I0, const void *I0x, const void *I0y, const void *I1,

@@ -247,6 +247,16 @@ __device__ __forceinline__ void pyramid_gradients_body(T *__restrict__ slots, si
     stp(&Iy[p], 0.5f * (ldp(&im[(size_t)yp * pitch + x]) - ldp(&im[(size_t)ym * pitch + x])));
 }
 
+// One plane of a pyramid level (row pitch `pitch`) into a dense w x h FP32
+// array (FP16 storage widened exactly).
+template <typename T>
+__global__ void __launch_bounds__(256)
+pyramid_export_kernel(const T *__restrict__ src, int w, int h, int pitch, float *__restrict__ dst)
+{
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x < w && y < h) dst[(size_t)y * w + x] = ldp(&src[(size_t)y * pitch + x]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 pyramid_gradients_kernel(T *__restrict__ slots, size_t fs, PyrDesc d)
@@ -853,6 +863,16 @@ void launch_pyramid(void *slots, const Geometry &geo, size_t frame_stride, int f
         pyramid_gradients_kernel<__half><<<ggrd, blk, 0, st>>>((__half *)slots, frame_stride, d);
     else
         pyramid_gradients_kernel<float><<<ggrd, blk, 0, st>>>((float *)slots, frame_stride, d);
+}
+
+void launch_pyramid_export(const void *plane, bool half, int w, int h, int pitch, float *dst,
+                           cudaStream_t st)
+{
+    const dim3 blk(32, 8), grd((w + 31) / 32, (h + 7) / 8);
+    if (half)
+        pyramid_export_kernel<__half><<<grd, blk, 0, st>>>((const __half *)plane, w, h, pitch, dst);
+    else
+        pyramid_export_kernel<float><<<grd, blk, 0, st>>>((const float *)plane, w, h, pitch, dst);
 }
 
 template <typename T>
